@@ -1,0 +1,167 @@
+"""Seeded synthetic workloads for the repeated-range-query join.
+
+This module only draws inputs: object positions, per-tick moves and query
+rectangles.  It holds none of the join's arithmetic, so both the CUDA path and
+the CPU oracle (which never import each other) can be fed from it.
+
+The paper's own generator (a Brinkhoff-derived moving-object generator inside
+a third-party benchmarking framework, Sec. 6) and its road-network dataset are
+not available; these generators keep the structure of its workloads (Table 1):
+uniform or Gaussian-hotspot object distributions, square queries centred on
+the objects that issue them, bounded random-walk motion between ticks.  The
+paper's region is a 22500u square with query sides of 200-800u; here the
+region is the unit square and sides are given as fractions of it.
+
+All draws use ``numpy.random.default_rng`` seeded through ``SeedSequence``;
+values are produced in float64, clamped, then cast to float32.  Query corners
+are computed in float32 as ``c - s/2`` and ``c + s/2`` (round to nearest), so a
+query always contains the object that issued it (self-inclusion, Def. 1).
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field
+
+import numpy as np
+
+TOP = np.float32(1.0) - np.float32(2.0 ** -24)   # largest float32 below 1
+
+
+def _rngs(seed: int, k: int):
+    return [np.random.default_rng(s) for s in np.random.SeedSequence(seed).spawn(k)]
+
+
+def squares_around(centres: np.ndarray, sides) -> np.ndarray:
+    """Closed squares (xa, ya, xb, yb) of the given sides centred on ``centres``."""
+    c = np.asarray(centres, np.float32).reshape(-1, 2)
+    h = (np.asarray(sides, np.float64) / 2.0).astype(np.float32)
+    h = np.broadcast_to(h, (c.shape[0],))
+    out = np.empty((c.shape[0], 4), np.float32)
+    out[:, 0] = c[:, 0] - h
+    out[:, 1] = c[:, 1] - h
+    out[:, 2] = c[:, 0] + h
+    out[:, 3] = c[:, 1] + h
+    return out
+
+
+def uniform_points(n: int, rng) -> np.ndarray:
+    return np.clip(rng.random((n, 2)), 0.0, TOP).astype(np.float32)
+
+
+@dataclass
+class Tick:
+    """One tick: the updates of the tick (ids, xy) and its queries."""
+    ids: np.ndarray          # u32[n]
+    xy: np.ndarray           # f32[n, 2]
+    rects: np.ndarray        # f32[Q, 4]  (xa, ya, xb, yb)
+    issuers: np.ndarray      # u32[Q]     object that issued each query
+
+
+# ----------------------------------------------------------------------------
+# 16K uniform objects, 1,024 side-0.01 queries, one tick.
+# ----------------------------------------------------------------------------
+def uniform_small(seed: int = 0, n: int = 16384, q: int = 1024, side: float = 0.01) -> Tick:
+    r_init, r_q = _rngs(seed, 2)
+    xy = uniform_points(n, r_init)
+    iss = r_q.integers(0, n, size=q).astype(np.uint32)       # with replacement
+    rects = squares_around(xy[iss], side)
+    return Tick(np.arange(n, dtype=np.uint32), xy, rects, iss)
+
+
+# ----------------------------------------------------------------------------
+# Random-walk world: uniform start, Gaussian steps clamped to the unit square,
+# a fixed fraction of objects issuing fixed-side queries each tick.
+# ----------------------------------------------------------------------------
+@dataclass
+class UniformWalk:
+    n: int = 1_000_000
+    q: int = 100_000
+    side: float = 0.002
+    step: float = 0.0005
+    seed: int = 0
+    _xy: np.ndarray = field(init=False, repr=False)
+
+    def __post_init__(self):
+        self._r_init, self._r_move, self._r_q = _rngs(self.seed, 3)
+        self._xy = uniform_points(self.n, self._r_init).astype(np.float64)
+        self._t = 0
+
+    def next_tick(self) -> Tick:
+        if self._t > 0:
+            self._xy = np.clip(self._xy + self._r_move.normal(0.0, self.step, (self.n, 2)), 0.0, float(TOP))
+        self._t += 1
+        xy = self._xy.astype(np.float32)
+        iss = np.sort(self._r_q.choice(self.n, size=self.q, replace=False)).astype(np.uint32)
+        rects = squares_around(xy[iss], self.side)
+        return Tick(np.arange(self.n, dtype=np.uint32), xy, rects, iss)
+
+
+# ----------------------------------------------------------------------------
+# Skewed world: a mixture of Gaussian hotspots (centres uniform, sigma
+# log-uniform) plus a uniform background; objects random-walk and hotspot
+# members also follow their hotspot's drift (fixed heading per hotspot,
+# reflected at the borders); queries of log-uniform side centred on objects
+# sampled without replacement.
+# ----------------------------------------------------------------------------
+@dataclass
+class HotspotWalk:
+    n: int = 4_000_000
+    q: int = 400_000
+    hotspots: int = 64
+    frac_hot: float = 0.9
+    sigma_lo: float = 0.002
+    sigma_hi: float = 0.02
+    side_lo: float = 0.0005
+    side_hi: float = 0.005
+    step: float = 0.0005
+    drift: float = 0.001
+    seed: int = 0
+
+    def __post_init__(self):
+        r_init, self._r_move, self._r_q, r_hot = _rngs(self.seed, 4)
+        H = self.hotspots
+        self.centres = r_hot.random((H, 2))
+        self.sigmas = np.exp(r_hot.uniform(np.log(self.sigma_lo), np.log(self.sigma_hi), H))
+        ang = r_hot.uniform(0.0, 2.0 * np.pi, H)
+        self.heading = np.stack([np.cos(ang), np.sin(ang)], 1)
+        n_hot = int(round(self.n * self.frac_hot))
+        member = np.full(self.n, -1, np.int64)
+        member[:n_hot] = r_init.integers(0, H, size=n_hot)
+        r_init.shuffle(member)
+        self.member = member
+        hot = member >= 0
+        xy = np.empty((self.n, 2))
+        xy[hot] = self.centres[member[hot]] + r_init.normal(0.0, 1.0, (int(hot.sum()), 2)) * self.sigmas[member[hot], None]
+        xy[~hot] = r_init.random((int((~hot).sum()), 2))
+        self._xy = np.clip(xy, 0.0, float(TOP))
+        self._t = 0
+
+    def _advance_hotspots(self):
+        c = self.centres + self.heading * self.drift
+        for d in range(2):
+            lo = c[:, d] < 0.0
+            hi = c[:, d] > 1.0
+            c[lo, d] = -c[lo, d]
+            c[hi, d] = 2.0 - c[hi, d]
+            self.heading[lo | hi, d] *= -1.0
+        delta = c - self.centres
+        self.centres = c
+        return delta
+
+    def next_tick(self) -> Tick:
+        if self._t > 0:
+            delta = self._advance_hotspots()
+            hot = self.member >= 0
+            move = self._r_move.normal(0.0, self.step, (self.n, 2))
+            move[hot] += delta[self.member[hot]]
+            self._xy = np.clip(self._xy + move, 0.0, float(TOP))
+        self._t += 1
+        xy = self._xy.astype(np.float32)
+        iss = np.sort(self._r_q.choice(self.n, size=self.q, replace=False)).astype(np.uint32)
+        sides = np.exp(self._r_q.uniform(np.log(self.side_lo), np.log(self.side_hi), self.q))
+        rects = squares_around(xy[iss], sides)
+        return Tick(np.arange(self.n, dtype=np.uint32), xy, rects, iss)
+
+
+def hotspot_small(seed: int = 0, n: int = 200_000, q: int = 20_000) -> HotspotWalk:
+    """A reduced hotspot world with the same recipe (for parity tests)."""
+    return HotspotWalk(n=n, q=q, seed=seed)

@@ -1,0 +1,437 @@
+"""Pins of the CPU oracle against what the paper and the mathematics fix.
+
+Every oracle routine is checked against something other than itself: values
+worked by hand from the paper's definitions (golden fixtures), independent
+numpy brute force on small inputs, closed forms, invariants the paper states,
+and a statistical check against the paper's subquery-count estimate.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1411_3212_gb300 import workloads
+from tests.conftest import read_golden
+
+
+def _f32(s):
+    return np.float32(float(s))
+
+
+# ----------------------------------------------------------------------------
+# helpers written independently of the oracle
+# ----------------------------------------------------------------------------
+def np_brute(pos, present, rects):
+    """Def. 1 with numpy broadcasting: list of ascending id arrays per query."""
+    ids = np.nonzero(present)[0]
+    x = pos[ids, 0][None, :]
+    y = pos[ids, 1][None, :]
+    r = rects.astype(np.float32)
+    m = (r[:, 0:1] <= x) & (x <= r[:, 2:3]) & (r[:, 1:2] <= y) & (y <= r[:, 3:4])
+    return [ids[np.nonzero(row)[0]].astype(np.uint32) for row in m]
+
+
+def py_interleave(i, j, bits=15):
+    z = 0
+    for b in range(bits):
+        z |= ((i >> b) & 1) << (2 * b)
+        z |= ((j >> b) & 1) << (2 * b + 1)
+    return z
+
+
+def py_deinterleave(z, bits=15):
+    i = j = 0
+    for b in range(bits):
+        i |= ((z >> (2 * b)) & 1) << b
+        j |= ((z >> (2 * b + 1)) & 1) << b
+    return i, j
+
+
+def assert_csr_equal(off, ids, lists):
+    assert len(off) == len(lists) + 1
+    for q, want in enumerate(lists):
+        got = ids[int(off[q]):int(off[q + 1])]
+        np.testing.assert_array_equal(got, want, err_msg="query %d" % q)
+
+
+# ----------------------------------------------------------------------------
+# Def. 1 -- golden, hand-worked closed-rectangle cases
+# ----------------------------------------------------------------------------
+def _def1_fixture():
+    recs = read_golden("def1_closed_rectangles.txt")
+    objs = [(int(r[1]), _f32(r[2]), _f32(r[3])) for r in recs if r[0] == "object"]
+    qs = [(int(r[1]), [_f32(v) for v in r[2:6]]) for r in recs if r[0] == "query"]
+    exp = {int(r[1]): [int(v) for v in r[2:]] for r in recs if r[0] == "expect"}
+    n = max(o[0] for o in objs) + 1
+    st = oracle.State(n)
+    st.apply_updates([o[0] for o in objs], [[o[1], o[2]] for o in objs])
+    rects = np.array([q[1] for q in sorted(qs)], np.float32)
+    return st, rects, [np.array(exp[q], np.uint32) for q in range(len(qs))]
+
+
+@pytest.mark.parametrize("cell", [1e-3, 0.05, 0.3, 2.0])
+def test_def1_golden_grid(cell):
+    st, rects, want = _def1_fixture()
+    off, ids = oracle.join_grid(st, rects, cell_side=cell)
+    assert_csr_equal(off, ids, want)
+
+
+def test_def1_golden_brute():
+    st, rects, want = _def1_fixture()
+    off, ids = oracle.join_brute(st, rects)
+    assert_csr_equal(off, ids, want)
+
+
+# ----------------------------------------------------------------------------
+# Def. 1 -- oracle grid join vs independent numpy brute force
+# ----------------------------------------------------------------------------
+def _random_case(seed, n, q, adversarial):
+    rng = np.random.default_rng(seed)
+    pos = rng.random((n, 2)).astype(np.float32)
+    if adversarial:
+        # snap many coordinates to a coarse lattice so that query edges land
+        # exactly on object coordinates; add duplicates, out-of-bounds points,
+        # NaN / inf coordinates and -0.0.
+        lat = (np.round(rng.random((n, 2)) * 16) / 16).astype(np.float32)
+        snap = rng.random(n) < 0.5
+        pos[snap] = lat[snap]
+        k = max(1, n // 16)
+        pos[rng.integers(0, n, k)] = pos[rng.integers(0, n, k)]
+        pos[rng.integers(0, n, k)] = rng.uniform(-0.5, 1.5, (k, 2)).astype(np.float32)
+        specials = np.array([np.nan, np.inf, -np.inf, -0.0, 0.0, 1.0], np.float32)
+        for _ in range(k):
+            pos[rng.integers(0, n), rng.integers(0, 2)] = specials[rng.integers(0, len(specials))]
+    present = (rng.random(n) < 0.9).astype(np.uint8)
+    c = pos[rng.integers(0, n, q)]
+    sides = rng.choice([0.0, 1 / 16, 0.05, 0.2, 0.7], q)
+    rects = workloads.squares_around(np.nan_to_num(c, nan=0.5, posinf=1.0, neginf=0.0), sides)
+    if adversarial:
+        lat = (np.round(rng.random((q, 4)) * 16) / 16).astype(np.float32)
+        pick = rng.random(q) < 0.5
+        rects[pick] = np.sort(lat[pick].reshape(-1, 2, 2), axis=1).reshape(-1, 4)[:, [0, 2, 1, 3]]
+        flip = rng.random(q) < 0.05
+        rects[flip] = rects[flip][:, [2, 3, 0, 1]]           # inverted
+        rects[rng.integers(0, q, max(1, q // 32)), rng.integers(0, 4)] = np.nan
+        rects[rng.integers(0, q, max(1, q // 32))] = [-np.inf, -np.inf, np.inf, np.inf]
+    st = oracle.State(n)
+    ids = np.nonzero(present)[0].astype(np.uint32)
+    st.apply_updates(ids, pos[ids])
+    return st, pos, present, rects
+
+
+@pytest.mark.parametrize("seed", range(6))
+@pytest.mark.parametrize("adv", [False, True])
+def test_grid_join_matches_numpy_brute(seed, adv):
+    n, q = 700 + 113 * seed, 150
+    st, pos, present, rects = _random_case(seed, n, q, adv)
+    want = np_brute(st.pos, st.present, rects)
+    for cell in (1.0 / 4096, 0.013, 0.1, 3.0):
+        off, ids = oracle.join_grid(st, rects, cell_side=cell)
+        assert_csr_equal(off, ids, want)
+    off, ids = oracle.join_brute(st, rects)
+    assert_csr_equal(off, ids, want)
+    cnt = oracle.count_grid(st, rects, cell_side=0.05)
+    np.testing.assert_array_equal(cnt, [len(w) for w in want])
+
+
+def test_grid_join_nonunit_bounds():
+    rng = np.random.default_rng(7)
+    n = 900
+    pos = (rng.random((n, 2)) * [300.0, 40.0] + [-100.0, 5.0]).astype(np.float32)
+    st = oracle.State(n)
+    st.apply_updates(np.arange(n), pos)
+    rects = workloads.squares_around(pos[rng.integers(0, n, 120)], rng.uniform(0, 30, 120))
+    want = np_brute(st.pos, st.present, rects)
+    off, ids = oracle.join_grid(st, rects, bounds=(-100, 5, 200, 45), cell_side=7.0)
+    assert_csr_equal(off, ids, want)
+
+
+def test_empty_inputs():
+    st = oracle.State(0)
+    off, ids = oracle.join_grid(st, np.zeros((3, 4), np.float32))
+    assert list(off) == [0, 0, 0, 0] and len(ids) == 0
+    st = oracle.State(5)
+    off, ids = oracle.join_grid(st, np.zeros((0, 4), np.float32))
+    assert list(off) == [0] and len(ids) == 0
+
+
+def test_self_inclusion():
+    """Def. 1 remark: a query centred on its issuer contains the issuer."""
+    t = workloads.uniform_small(seed=3, n=3000, q=400)
+    st = oracle.State(3000)
+    st.apply_updates(t.ids, t.xy)
+    off, ids = oracle.join_grid(st, t.rects, cell_side=0.01)
+    for qi, issuer in enumerate(t.issuers):
+        assert issuer in ids[int(off[qi]):int(off[qi + 1])]
+
+
+# ----------------------------------------------------------------------------
+# Sec. 2.2 -- last update of a tick wins
+# ----------------------------------------------------------------------------
+def test_apply_updates_last_wins():
+    rng = np.random.default_rng(11)
+    nmax = 50
+    st = oracle.State(nmax)
+    ref = {}
+    for _ in range(5):
+        k = 80
+        ids = rng.integers(0, nmax - 5, k).astype(np.uint32)       # duplicates; last 5 never set
+        xy = rng.random((k, 2)).astype(np.float32)
+        st.apply_updates(ids, xy)
+        for i, id_ in enumerate(ids):
+            ref[int(id_)] = xy[i]
+    for id_ in range(nmax):
+        if id_ in ref:
+            assert st.present[id_] == 1
+            np.testing.assert_array_equal(st.pos[id_], ref[id_])
+        else:
+            assert st.present[id_] == 0
+    with pytest.raises(ValueError):
+        st.apply_updates([nmax], [[0.0, 0.0]])
+
+
+# ----------------------------------------------------------------------------
+# Morton codes and the FP32 cell function (Alg. 1, l_max = 15)
+# ----------------------------------------------------------------------------
+def test_morton_closed_forms():
+    assert oracle.morton(0, 0) == 0
+    assert oracle.morton(1, 0) == 1
+    assert oracle.morton(0, 1) == 2
+    assert oracle.morton(1, 1) == 3
+    assert oracle.morton(2, 0) == 4
+    assert oracle.morton(32767, 0) == (4 ** 15 - 1) // 3            # bits 0,2,..,28
+    assert oracle.morton(0, 32767) == 2 * ((4 ** 15 - 1) // 3)      # bits 1,3,..,29
+    assert oracle.morton(32767, 32767) == 2 ** 30 - 1
+    rng = np.random.default_rng(0)
+    for i, j in rng.integers(0, 32768, (300, 2)):
+        z = oracle.morton(int(i), int(j))
+        assert py_deinterleave(z) == (i, j)
+        # quadrant structure: the level-l prefix is the Morton code of the
+        # level-l cell (i >> (15-l), j >> (15-l))
+        for l in (1, 5, 9, 14):
+            assert z >> (2 * (15 - l)) == py_interleave(int(i) >> (15 - l), int(j) >> (15 - l), l)
+
+
+def test_cell_function_closed_form_unit_bounds():
+    sc = oracle.scale(0.0, 1.0)
+    assert sc == 32768.0
+    rng = np.random.default_rng(1)
+    xs = np.concatenate([rng.random(2000).astype(np.float32),
+                         np.array([0.0, -0.0, 2 ** -24, 0.5, 1 - 2 ** -24, 1.0], np.float32)])
+    for x in xs:
+        want = min(int(math.floor(float(x) * 32768.0)), 32767)      # exact: power-of-two scale
+        assert oracle.cell(float(x), 0.0, sc) == want
+    assert oracle.cell(float("nan"), 0.0, sc) == 0
+    assert oracle.cell(float("-inf"), 0.0, sc) == 0
+    assert oracle.cell(float("inf"), 0.0, sc) == 32767
+    assert oracle.cell(-3.0, 0.0, sc) == 0
+    assert oracle.cell(7.0, 0.0, sc) == 32767
+
+
+def test_cell_function_monotone_general_bounds():
+    rng = np.random.default_rng(2)
+    for lo, hi in [(-100.0, 200.0), (0.1, 0.7), (3.0, 3.001)]:
+        sc = oracle.scale(lo, hi)
+        xs = np.sort(rng.uniform(lo - 0.1 * (hi - lo), hi + 0.1 * (hi - lo), 3000).astype(np.float32))
+        cells = [oracle.cell(float(x), lo, sc) for x in xs]
+        assert all(a <= b for a, b in zip(cells, cells[1:]))
+        assert oracle.cell(lo, lo, sc) == 0 and oracle.cell(hi, lo, sc) == 32767
+
+
+def test_keys_absent_and_values():
+    st = oracle.State(4)
+    st.apply_updates([0, 2, 3], [[0.0, 0.0], [1.0, 1.0], [0.5, 0.25]])
+    k = oracle.keys(st)
+    assert k[1] == 0xFFFFFFFF
+    assert k[0] == 0 and k[2] == 2 ** 30 - 1
+    assert k[3] == py_interleave(16384, 8192)
+
+
+# ----------------------------------------------------------------------------
+# Alg. 1 -- PR-quadtree construction
+# ----------------------------------------------------------------------------
+def test_quadtree_fig5_golden():
+    recs = read_golden("alg1_fig5_quadtree.txt")
+    keys = [int(v) for r in recs if r[0] == "keys" for v in r[1:]]
+    th = int(next(r[1] for r in recs if r[0] == "th_quad"))
+    lmax = int(next(r[1] for r in recs if r[0] == "l_max"))
+    want = [(int(r[1]), int(r[2])) for r in recs if r[0] == "leaf"]
+    lv = oracle.quadtree(np.sort(np.array(keys, np.uint32)), th, lmax)
+    assert [(int(a), int(b)) for a, b in zip(lv["level"], lv["z"])] == want
+    assert len(lv) == 10 and int((lv["level"] == 2).sum()) == 8
+
+
+def geometric_quadtree(cells, cap, lmax):
+    """PR-quadtree by its geometric definition: count the points of each
+    quadrant directly from their cell coordinates; split iff count > cap and
+    level < lmax.  Returns [(level, z, count)] in Morton order."""
+    out = []
+
+    def rec(l, bi, bj):
+        side = 1 << (lmax - l)
+        m = (cells[:, 0] >= bi) & (cells[:, 0] < bi + side) & (cells[:, 1] >= bj) & (cells[:, 1] < bj + side)
+        cnt = int(m.sum())
+        if cnt > cap and l < lmax:
+            h = side // 2
+            for c in range(4):                       # Morton digit: bit0 -> i, bit1 -> j
+                rec(l + 1, bi + (c & 1) * h, bj + (c >> 1) * h)
+        else:
+            out.append((l, py_interleave(bi >> (lmax - l), bj >> (lmax - l), l), cnt))
+
+    rec(0, 0, 0)
+    return out
+
+
+@pytest.mark.parametrize("seed", range(4))
+@pytest.mark.parametrize("cap", [1, 2, 3, 8, 40])
+@pytest.mark.parametrize("lmax", [3, 6])
+def test_quadtree_matches_geometric_definition(seed, cap, lmax):
+    rng = np.random.default_rng(seed * 100 + cap)
+    n = int(rng.integers(0, 120))
+    side = 1 << lmax
+    if seed % 2:
+        cells = np.clip(rng.normal(side * 0.3, side * 0.05, (n, 2)), 0, side - 1).astype(np.int64)
+    else:
+        cells = rng.integers(0, side, (n, 2))
+    keys = np.sort(np.array([py_interleave(int(i), int(j), lmax) for i, j in cells], np.uint32))
+    lv = oracle.quadtree(keys, cap, lmax)
+    want = geometric_quadtree(cells, cap, lmax)
+    got = [(int(l), int(z), int(e - b)) for l, z, b, e in zip(lv["level"], lv["z"], lv["begin"], lv["end"])]
+    assert got == want
+
+
+@pytest.mark.parametrize("cap", [1, 4, 64, 128, 5000, 2 ** 31])
+def test_quadtree_invariants_lmax15(cap):
+    """Leaves partition [0, 4^15) in Morton order, own contiguous runs of the
+    sorted objects (Sec. 5.3), hold <= th_quad objects unless at l_max, and
+    every parent of a leaf holds > th_quad objects."""
+    w = workloads.HotspotWalk(n=6000, q=10, hotspots=4, seed=cap % 97)
+    t = w.next_tick()
+    st = oracle.State(w.n)
+    st.apply_updates(t.ids, t.xy)
+    keys = np.sort(oracle.keys(st))
+    keys[:20] = keys[0]                                   # a pile of identical points
+    keys = np.sort(keys)
+    lv = oracle.quadtree(keys, min(cap, 2 ** 32 - 1), 15)
+    nxt = 0
+    for l, z, b, e in lv:
+        s = 2 * (15 - int(l))
+        assert int(z) << s == nxt
+        nxt = (int(z) + 1) << s
+        assert np.all((keys[b:e] >> s) == z)
+        assert e - b <= cap or l == 15
+        if l > 0:
+            pz = int(z) >> 2
+            ps = s + 2
+            assert int(((keys >> ps) == pz).sum()) > cap
+    assert nxt == 4 ** 15
+    assert lv["begin"][0] == 0 and lv["end"][-1] == len(keys)
+    assert np.all(lv["begin"][1:] == lv["end"][:-1])
+
+
+# ----------------------------------------------------------------------------
+# Def. "Mapping functions" -- query splitting into subqueries
+# ----------------------------------------------------------------------------
+def _leaf_table(pairs):
+    dt = np.dtype([("level", np.uint32), ("z", np.uint32), ("begin", np.uint32), ("end", np.uint32)])
+    a = np.zeros(len(pairs), dt)
+    for k, (l, z) in enumerate(pairs):
+        a[k] = (l, z, k, k + 1)          # every leaf non-empty
+    return a
+
+
+def test_subqueries_fig3_golden():
+    recs = read_golden("fig3_query_splitting.txt")
+    leaves = _leaf_table([(int(r[1]), int(r[2])) for r in recs if r[0] == "leaf"])
+    rect = [float(v) for r in recs if r[0] == "query" for v in r[1:5]]
+    want = [(int(r[1]), int(r[2]), int(r[3])) for r in recs if r[0] == "sub"]
+    li, cov = oracle.subqueries(leaves, rect)
+    got = [(int(leaves["level"][k]), int(leaves["z"][k]), int(c)) for k, c in zip(li, cov)]
+    assert got == want
+    assert len(got) == 7 and sum(c for _, _, c in got) == 1
+
+
+def test_subqueries_match_box_geometry_and_are_exact():
+    """Every (q, leaf) with overlapping cell boxes is a subquery, exactly once;
+    covering leaves hold only objects that pass the FP32 test; and every
+    result of Def. 1 lies in a subquery's leaf."""
+    rng = np.random.default_rng(5)
+    w = workloads.HotspotWalk(n=3000, q=60, hotspots=3, side_lo=0.002, side_hi=0.3, seed=5)
+    t = w.next_tick()
+    st = oracle.State(w.n)
+    st.apply_updates(t.ids, t.xy)
+    keys_slot = oracle.keys(st)
+    order = np.argsort(keys_slot, kind="stable")
+    keys = keys_slot[order]
+    lv = oracle.quadtree(keys, 16, 15)
+    sc = oracle.scale(0.0, 1.0)
+    want_sets = np_brute(st.pos, st.present, t.rects)
+    for qi, r in enumerate(t.rects):
+        li, cov = oracle.subqueries(lv, r)
+        i0, i1 = oracle.cell(float(r[0]), 0.0, sc), oracle.cell(float(r[2]), 0.0, sc)
+        j0, j1 = oracle.cell(float(r[1]), 0.0, sc), oracle.cell(float(r[3]), 0.0, sc)
+        exp = []
+        for k, (l, z, b, e) in enumerate(lv):
+            if b == e:
+                continue
+            s = 15 - int(l)
+            bi, bj = py_deinterleave(int(z) << (2 * s))
+            if bi + (1 << s) - 1 < i0 or bi > i1 or bj + (1 << s) - 1 < j0 or bj > j1:
+                continue
+            exp.append((k, int(bi > i0 and bi + (1 << s) - 1 < i1 and bj > j0 and bj + (1 << s) - 1 < j1)))
+        assert list(zip(li.tolist(), cov.tolist())) == exp
+        members = []
+        for k, c in zip(li, cov):
+            objs = order[lv["begin"][k]:lv["end"][k]]
+            if c:
+                x, y = st.pos[objs, 0], st.pos[objs, 1]
+                assert np.all((r[0] <= x) & (x <= r[2]) & (r[1] <= y) & (y <= r[3]))
+            members.append(objs)
+        cand = set(np.concatenate(members).tolist()) if members else set()
+        assert set(want_sets[qi].tolist()) <= cand
+
+
+def test_subqueries_degenerate_queries():
+    lv = _leaf_table([(0, 0)])
+    assert len(oracle.subqueries(lv, [np.nan, 0, 1, 1])[0]) == 0
+    assert len(oracle.subqueries(lv, [0.6, 0, 0.5, 1])[0]) == 0
+    li, cov = oracle.subqueries(lv, [-np.inf, -np.inf, np.inf, np.inf])
+    assert list(li) == [0] and list(cov) == [0]      # cell 0 is never strictly inside
+
+
+@pytest.mark.parametrize("level,side", [(7, 0.04), (8, 0.06)])
+def test_subquery_counts_eq_nr_isect(level, side):
+    """Eq. nr_isect (uniform grid): |Q_I| ~ sum(perimeter)/cell_side.  On one
+    axis a side-s interval placed at random meets s/cell + 1 cells on average, so
+    covering + intersecting = (k+1)^2 per query on average (k = s / cell) and
+    the boundary ring has (k+1)^2 - (k-1)^2 = 4k cells, which is exactly
+    perimeter / cell_side."""
+    G = 1 << level
+    leaves = _leaf_table([(level, z) for z in range(G * G)])
+    rng = np.random.default_rng(level)
+    c = rng.uniform(0.1, 0.9, (40, 2)).astype(np.float32)
+    rects = workloads.squares_around(c, side)
+    n_i = n_c = 0
+    for r in rects:
+        li, cov = oracle.subqueries(leaves, r)
+        n_c += int(cov.sum())
+        n_i += int(len(cov) - cov.sum())
+    cell = 1.0 / G
+    k = side / cell
+    est_i = len(rects) * 4 * side / cell
+    assert abs(n_i - est_i) / est_i < 0.06
+    assert abs((n_i + n_c) - len(rects) * (k + 1) ** 2) / (n_i + n_c) < 0.06
+
+
+# ----------------------------------------------------------------------------
+# Bitmap layout of a result
+# ----------------------------------------------------------------------------
+def test_bitmap_layout():
+    off = np.array([0, 3, 3, 5], np.uint64)
+    ids = np.array([0, 31, 32, 1, 70], np.uint32)
+    w = oracle.bitmap(off, ids, 71)
+    assert w.shape == (3, 3)
+    assert list(w[0]) == [1 | (1 << 31), 1, 0]
+    assert list(w[1]) == [0, 0, 0]
+    assert list(w[2]) == [2, 0, 1 << 6]
