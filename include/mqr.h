@@ -1,0 +1,199 @@
+/*
+ * mqr.h -- C ABI of libmqr: repeated range queries over moving objects on one
+ * GB300 GPU (sm_103a).
+ *
+ * The library answers, tick after tick, the spatial join between the latest
+ * known positions of a population of moving objects and the range queries
+ * issued during the tick (Lettich et al., "Manycore processing of repeated
+ * range queries over massive moving objects observations", Sec. 2.4 "Problem
+ * statement").  It indexes the objects with a point-region quadtree whose
+ * leaves hold at most leaf_cap objects (Def. "MBR partitioning into a
+ * quadtree-induced regular grid", Alg. 1), splits every query over the leaves
+ * it meets (Def. "Mapping functions"), tests intersecting subqueries against
+ * the leaf's objects into 32-bit bitmap words (Sec. 5.5, Alg. 2), and decodes
+ * the words plus the covering subqueries into the result (Sec. 5.6 Alg. 4,
+ * Sec. 5.7).
+ *
+ * Conventions shared by every entry point:
+ *  - Every call returns an mqr_status; nothing aborts the process.  On an
+ *    error, mqr_last_error() returns a message (thread-local, valid until the
+ *    next call on the same thread).
+ *  - Pointers named *_dev are CUDA device pointers (or managed memory) owned
+ *    by the caller; pointers named *_host are host pointers owned by the
+ *    caller.  The library never frees caller memory and keeps no pointer to
+ *    it after the call returns.
+ *  - All device work is enqueued on the context's stream (see mqr_create_ex);
+ *    device inputs must stay valid until that stream reaches the call's work,
+ *    which mqr_tick waits for before returning.
+ *  - A context is not thread-safe: one thread at a time per context.
+ *  - Coordinates are IEEE float32; a query (xa, ya, xb, yb) is the CLOSED
+ *    rectangle xa <= x <= xb, ya <= y <= yb (Def. 1).  A query with a NaN
+ *    corner, or with xa > xb or ya > yb, has an empty result.  NaN object
+ *    coordinates never match; infinite ones match only infinite edges.
+ */
+#ifndef MQR_H
+#define MQR_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct mqr_ctx mqr_ctx;
+
+typedef enum {
+    MQR_OK = 0,
+    MQR_ERR_INVALID_ARG = 1, /* bad pointer, size, kind or id                */
+    MQR_ERR_OOM = 2,         /* device or host allocation failed             */
+    MQR_ERR_CAPACITY = 3,    /* output buffer too small: *out_count = needed */
+    MQR_ERR_CUDA = 4,        /* a CUDA call failed (message has the detail)  */
+    MQR_ERR_TIMEOUT = 5,     /* a bounded device-side wait gave up           */
+    MQR_ERR_INTERNAL = 6
+} mqr_status;
+
+/* The indexed space: objects outside it are still answered exactly (their
+ * cell index is clamped to the border cells). */
+typedef struct {
+    float xmin, ymin, xmax, ymax;
+} mqr_rect;
+
+/* Result layouts written by mqr_tick.  R = total number of (query, object)
+ * results of the tick, Q = number of queries, W = ceil(max_objects / 32).
+ *  PAIRS         out_dev: uint32 pairs (qidx, id), R of them (8*R bytes),
+ *                grouped by query in ascending qidx; order inside a query
+ *                unspecified.
+ *  PAIRS_SORTED  as PAIRS, ascending in (qidx, id).
+ *  CSR           out_dev: uint32 ids, R of them (4*R bytes), grouped by query
+ *                in ascending qidx; offsets_dev (required) gets uint64[Q+1]
+ *                with the start of every query's list.  Order inside a query
+ *                unspecified.
+ *  CSR_SORTED    as CSR, ids ascending inside each query.
+ *  BITMAP        out_dev: Q rows of W uint32 words (4*Q*W bytes); bit
+ *                (id mod 32) of word id/32 of row qidx is 1 iff object id is
+ *                in the result of query qidx.  Padding bits are 0.
+ *  COUNT         no id output (out_dev may be NULL); only *out_count and, if
+ *                given, offsets_dev.
+ * offsets_dev, when non-NULL, receives the per-query offsets for every kind.
+ * The sorted kinds are limited to R < 2^30. */
+typedef enum {
+    MQR_OUT_PAIRS = 0,
+    MQR_OUT_PAIRS_SORTED = 1,
+    MQR_OUT_CSR = 2,
+    MQR_OUT_CSR_SORTED = 3,
+    MQR_OUT_BITMAP = 4,
+    MQR_OUT_COUNT = 5
+} mqr_out_kind;
+
+typedef enum {
+    MQR_INDEX_QUADTREE = 0,     /* PR-quadtree, leaves hold <= leaf_cap objects (Alg. 1) */
+    MQR_INDEX_UNIFORM_GRID = 1  /* uniform grid of 2^grid_level cells per axis (Def. uniform grid) */
+} mqr_index_kind;
+
+typedef struct {
+    uint32_t max_objects;  /* object ids are in [0, max_objects)                      */
+    uint32_t leaf_cap;     /* th_quad: a quadrant holding more objects is split        */
+    int32_t index_kind;    /* mqr_index_kind                                           */
+    uint32_t grid_level;   /* uniform grid only: 1..15                                 */
+    int32_t covering;      /* 1 (default): covering subqueries skip containment tests
+                              (Sec. 5.7); 0: every subquery is tested                  */
+    int32_t reserved[3];   /* must be 0                                                */
+} mqr_config;
+
+/* Counters of the last completed tick (Sec. 6.x metrics). */
+typedef struct {
+    uint64_t n_objects;          /* objects present (ever updated)                 */
+    uint64_t n_queries;
+    uint64_t n_leaves;           /* non-empty index cells                          */
+    uint64_t max_level;          /* deepest leaf level (l_deep)                    */
+    uint64_t n_sub_intersecting; /* |Q_I|                                          */
+    uint64_t n_sub_covering;     /* covering subqueries, counted per leaf          */
+    uint64_t n_covering_runs;    /* covering subqueries after merging adjacent leaves */
+    uint64_t n_tests;            /* sum over cells of |Q_I^c| * |P^c|              */
+    uint64_t n_filter_items;     /* warp work items of the filtering kernel        */
+    uint64_t n_bitmap_words;     /* 32-bit words of the filtering bitmaps          */
+    uint64_t n_results;          /* R                                              */
+    uint64_t n_results_covering; /* results coming from covering subqueries        */
+    uint64_t n_retries;          /* internal buffer growths during the tick        */
+} mqr_stats;
+
+/* Fill *cfg with defaults: max_objects = 1<<20, leaf_cap = 128, quadtree,
+ * grid_level = 8, covering = 1. */
+mqr_status mqr_config_default(mqr_config *cfg);
+
+/* Create a context over `bounds` with a PR-quadtree index of leaf capacity
+ * `leaf_cap` (th_quad, Def. quadtree grid) for object ids in
+ * [0, max_objects).  Uses the CUDA device current on the calling thread and a
+ * stream the context creates.  *out receives the context; destroy it with
+ * mqr_destroy.  Errors: INVALID_ARG (NULL out, leaf_cap == 0, bounds not
+ * finite or empty), OOM, CUDA. */
+mqr_status mqr_create(mqr_rect bounds, uint32_t leaf_cap, uint32_t max_objects, mqr_ctx **out);
+
+/* As mqr_create with every knob of mqr_config.  `cuda_stream` is a
+ * cudaStream_t the caller owns (NULL: the context creates its own); all work
+ * of the context is enqueued on it. */
+mqr_status mqr_create_ex(mqr_rect bounds, const mqr_config *cfg, void *cuda_stream, mqr_ctx **out);
+
+/* Apply position updates (Sec. 2.2 "Batch processing"): object ids_dev[i]
+ * moves to (xy_dev[2i], xy_dev[2i+1]).  Within one call the LAST occurrence
+ * of a repeated id wins; across calls the later call wins.  An object is
+ * present from its first update on.  All calls made before an mqr_tick
+ * belong to that tick; the tick answers against the state at its start
+ * (timeslice semantics, Sec. 2.3), so calls made after mqr_tick returns
+ * belong to the next tick.  ids_dev: uint32[n] device; xy_dev: float32[2n]
+ * device, interleaved (x, y).  Asynchronous: returns once enqueued.  Ids
+ * >= max_objects are ignored and reported as INVALID_ARG by the next
+ * mqr_tick.  n == 0 is a no-op. */
+mqr_status mqr_apply_updates(mqr_ctx *ctx, const uint32_t *ids_dev, const float *xy_dev, uint32_t n);
+
+/* As mqr_apply_updates with host buffers (copied to the device on the
+ * context's stream before the call returns; page-locked buffers copy fastest). */
+mqr_status mqr_apply_updates_host(mqr_ctx *ctx, const uint32_t *ids_host, const float *xy_host, uint32_t n);
+
+/* Answer Q queries against the current state (one tick, Sec. 2.4):
+ * rects_dev: float32[4Q] device, (xa, ya, xb, yb) per query; the query index
+ * qidx is its position in rects_dev.  kind: an mqr_out_kind.  out_dev /
+ * out_capacity_bytes: caller's device output buffer (see mqr_out_kind).
+ * out_count (host, required): receives the number of results R (pairs or ids)
+ * or, for BITMAP, the number of words Q*W.  offsets_dev: NULL or uint64[Q+1]
+ * device.  Blocks until the tick's work on the stream is complete.
+ * Errors: INVALID_ARG, CAPACITY (buffer too small; *out_count holds the
+ * size needed, nothing usable was written; call again with a larger buffer),
+ * TIMEOUT, CUDA, OOM. */
+mqr_status mqr_tick(mqr_ctx *ctx, const float *rects_dev, uint32_t Q, int kind,
+                    void *out_dev, uint64_t out_capacity_bytes, uint64_t *out_count,
+                    uint64_t *offsets_dev);
+
+/* As mqr_tick with host buffers: rects_host is copied in, the result is
+ * copied to out_host (and offsets_host if non-NULL) before the call returns. */
+mqr_status mqr_tick_host(mqr_ctx *ctx, const float *rects_host, uint32_t Q, int kind,
+                         void *out_host, uint64_t out_capacity_bytes, uint64_t *out_count,
+                         uint64_t *offsets_host);
+
+/* Counters of the last completed tick. */
+mqr_status mqr_get_stats(const mqr_ctx *ctx, mqr_stats *out);
+
+/* Copy the last tick's non-empty quadtree leaves (Alg. 1 output, Morton
+ * order) to the host: 4 uint32 per leaf {level, z, begin, end}, where z is
+ * the leaf's Morton code at its level and [begin, end) its run of objects in
+ * the tick's Morton-sorted object order.  *n receives the number of leaves;
+ * if cap (in leaves) is too small, CAPACITY is returned and nothing copied. */
+mqr_status mqr_get_leaves(mqr_ctx *ctx, uint32_t *leaves_host, uint64_t cap, uint64_t *n);
+
+/* Copy the last tick's Morton-sorted objects (Alg. 1 GPUradixSort output) to
+ * the host: keys_host[k] = 30-bit Morton code at l_max = 15, ids_host[k] =
+ * object id, for the *n present objects.  Either pointer may be NULL. */
+mqr_status mqr_get_sorted(mqr_ctx *ctx, uint32_t *keys_host, uint32_t *ids_host, uint64_t cap, uint64_t *n);
+
+/* Message of the last failed call on this thread ("" if none). */
+const char *mqr_last_error(void);
+
+/* Release the context and everything it allocated.  NULL is a no-op. */
+void mqr_destroy(mqr_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MQR_H */

@@ -21,6 +21,7 @@ from __future__ import annotations
 
 import ctypes
 import os
+import platform
 import subprocess
 import sys
 
@@ -28,14 +29,14 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "mqr_oracle.c")
-_LIB = os.path.join(_HERE, "libmqr_oracle.so")
+_LIB = os.path.join(_HERE, "libmqr_oracle.%s.so" % platform.machine())
 _FLAGS = ["-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared"]
 
 _lib = None
 
 
 def build(force: bool = False) -> str:
-    """Compile ``mqr_oracle.c`` into ``libmqr_oracle.so`` next to it."""
+    """Compile ``mqr_oracle.c`` into ``libmqr_oracle.<machine>.so`` next to it."""
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
         tmp = _LIB + ".tmp%d" % os.getpid()
         subprocess.check_call(["gcc", *_FLAGS, "-o", tmp, _SRC, "-lm"])

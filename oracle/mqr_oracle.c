@@ -212,22 +212,60 @@ int64_t orc_join_grid(const float *pos, const uint8_t *present, uint32_t nmax,
     return (int64_t)v.n;
 }
 
-/* Per-query result counts only (same grid walk, no id list): used to check
- * large workloads on every query while ids are checked on a sample. */
+/* Per-query result counts only (Def. 1 through the same uniform grid, no id
+ * list): used to check large workloads on every query while ids are checked
+ * on a sample. */
 int64_t orc_count_grid(const float *pos, const uint8_t *present, uint32_t nmax,
                        const float *rects, uint32_t Q,
                        double x0, double y0, double x1, double y1,
                        double cell_side, uint64_t *counts)
 {
-    uint64_t *off = (uint64_t *)malloc(((size_t)Q + 1) * sizeof(uint64_t));
-    if (!off) return -1;
-    uint32_t *ids = 0;
-    int64_t r = orc_join_grid(pos, present, nmax, rects, Q, x0, y0, x1, y1, cell_side, off, &ids);
-    if (r >= 0)
-        for (uint32_t q = 0; q < Q; ++q) counts[q] = off[q + 1] - off[q];
-    free(ids);
-    free(off);
-    return r;
+    if (!(cell_side > 0.0)) cell_side = 1e-12;
+    double gx = floor((x1 - x0) / cell_side), gy = floor((y1 - y0) / cell_side);
+    uint32_t GX = gx < 1.0 ? 1u : (gx > 4096.0 ? 4096u : (uint32_t)gx);
+    uint32_t GY = gy < 1.0 ? 1u : (gy > 4096.0 ? 4096u : (uint32_t)gy);
+    double cwx = (x1 - x0) / GX, cwy = (y1 - y0) / GY;
+    size_t ncell = (size_t)GX * GY;
+    uint64_t *cstart = (uint64_t *)calloc(ncell + 1, sizeof(uint64_t));
+    uint32_t *cell_of = (uint32_t *)malloc((size_t)(nmax ? nmax : 1) * sizeof(uint32_t));
+    if (!cstart || !cell_of) { free(cstart); free(cell_of); return -1; }
+    uint64_t npres = 0;
+    for (uint32_t id = 0; id < nmax; ++id) {
+        if (!present[id]) continue;
+        uint32_t ci = orc_grid_cell(pos[2 * (size_t)id], x0, cwx, GX);
+        uint32_t cj = orc_grid_cell(pos[2 * (size_t)id + 1], y0, cwy, GY);
+        cell_of[id] = cj * GX + ci;
+        cstart[cell_of[id] + 1]++;
+        npres++;
+    }
+    for (size_t c = 0; c < ncell; ++c) cstart[c + 1] += cstart[c];
+    uint32_t *cell_ids = (uint32_t *)malloc((size_t)(npres ? npres : 1) * sizeof(uint32_t));
+    uint64_t *fill = (uint64_t *)malloc(ncell * sizeof(uint64_t));
+    if (!cell_ids || !fill) { free(cstart); free(cell_of); free(cell_ids); free(fill); return -1; }
+    memcpy(fill, cstart, ncell * sizeof(uint64_t));
+    for (uint32_t id = 0; id < nmax; ++id)
+        if (present[id]) cell_ids[fill[cell_of[id]]++] = id;
+    uint64_t total = 0;
+    for (uint32_t q = 0; q < Q; ++q) {
+        const float *r = rects + 4 * (size_t)q;
+        uint64_t cnt = 0;
+        if (!orc_query_is_empty(r)) {
+            uint32_t i0 = orc_grid_cell(r[0], x0, cwx, GX), i1 = orc_grid_cell(r[2], x0, cwx, GX);
+            uint32_t j0 = orc_grid_cell(r[1], y0, cwy, GY), j1 = orc_grid_cell(r[3], y0, cwy, GY);
+            for (uint32_t cj = j0; cj <= j1; ++cj)
+                for (uint32_t ci = i0; ci <= i1; ++ci) {
+                    size_t c = (size_t)cj * GX + ci;
+                    for (uint64_t k = cstart[c]; k < cstart[c + 1]; ++k) {
+                        uint32_t id = cell_ids[k];
+                        cnt += (uint64_t)orc_in_rect(pos[2 * (size_t)id], pos[2 * (size_t)id + 1], r);
+                    }
+                }
+        }
+        counts[q] = cnt;
+        total += cnt;
+    }
+    free(cstart); free(cell_of); free(cell_ids); free(fill);
+    return (int64_t)total;
 }
 
 /* Query-major bitmap of a CSR result (reading of the bitmap layout of the

@@ -1,0 +1,322 @@
+// k_join.cu -- the join kernels: filtering into bitmap words (Sec. 5.5,
+// Alg. 2), the result-count scan (Sec. 5.6), and the decoding of bitmap words
+// plus the covering-subquery expansion into the output (Sec. 5.6 Alg. 4,
+// Sec. 5.7).
+#include "mqr_internal.cuh"
+
+namespace mqr {
+
+__device__ __forceinline__ bool tick_buffers_ok(const Info *info, const Caps &caps) {
+    return info->n_sub <= caps.sub && info->n_sub_i <= caps.sub_i && info->n_words <= caps.words;
+}
+
+// ---------------------------------------------------------------------------
+// a10: filtering.  A work item is (leaf, chunk of <= 256 of its objects,
+// group of <= 32 of its intersecting subqueries) and is processed by one
+// warp: lane j holds objects j, 32+j, ..., 224+j of the chunk in registers,
+// the group's rectangles are broadcast one at a time, and for every 32-object
+// word __ballot_sync of the closed-rectangle test (Def. 1) yields the 32-bit
+// bitmap word directly in the linearized row-major layout (row = subquery,
+// Sec. 5.5 Fig. 9b), so no interlaced bitmap and no linearization pass are
+// needed.  Lane s keeps the words of subquery s and writes them as one
+// contiguous run; popcounts give the subquery's result count.
+// Objects past the chunk are loaded as NaN, which fails every comparison.
+// ---------------------------------------------------------------------------
+constexpr int kFilterThreads = 256;
+
+__global__ void __launch_bounds__(kFilterThreads)
+filter_kernel(const float4 *__restrict__ rects, const float2 *__restrict__ sxy,
+              const uint32_t *__restrict__ leaf_beg, const uint32_t *__restrict__ leaf_sub_off,
+              const uint32_t *__restrict__ leaf_word_off, const uint32_t *__restrict__ leaf_item_off,
+              const uint32_t *__restrict__ isub, const uint32_t *__restrict__ sub_q,
+              uint32_t *__restrict__ sub_res, uint32_t *__restrict__ bitmap, Caps caps,
+              const Info *info) {
+    if (!tick_buffers_ok(info, caps)) return;
+    const uint32_t L = (uint32_t)info->n_leaves;
+    const uint32_t items = (uint32_t)info->n_items;
+    const int lane = threadIdx.x & 31;
+    const uint32_t nwarps = gridDim.x * (kFilterThreads / 32);
+    const float qnan = __int_as_float(0x7fc00000);
+
+    for (uint32_t item = (blockIdx.x * kFilterThreads + threadIdx.x) >> 5; item < items; item += nwarps) {
+        // leaf = last l with leaf_item_off[l] <= item
+        uint32_t a = 0, b = L;
+        while (b - a > 1) {
+            uint32_t m = (a + b) >> 1;
+            if (__ldg(leaf_item_off + m) <= item) a = m; else b = m;
+        }
+        const uint32_t leaf = a;
+        const uint32_t r = item - __ldg(leaf_item_off + leaf);
+        const uint32_t soff = __ldg(leaf_sub_off + leaf);
+        const uint32_t nsub = __ldg(leaf_sub_off + leaf + 1) - soff;
+        const uint32_t beg = __ldg(leaf_beg + leaf);
+        const uint32_t nobj = __ldg(leaf_beg + leaf + 1) - beg;
+        const uint32_t ngroups = (nsub + 31u) >> 5;
+        const uint32_t c = r / ngroups, g = r - c * ngroups;
+        const uint32_t nchunk = (nobj + 255u) >> 8;
+        const uint32_t nw_leaf = (nobj + 31u) >> 5;
+        const uint32_t obase = beg + c * 256u;
+        const uint32_t ocnt = min(256u, nobj - c * 256u);
+        const uint32_t nwc = (ocnt + 31u) >> 5;
+
+        float x[8], y[8];
+#pragma unroll
+        for (int wd = 0; wd < 8; ++wd) {
+            uint32_t idx = wd * 32 + lane;
+            if (idx < ocnt) {
+                float2 p = __ldg(sxy + obase + idx);
+                x[wd] = p.x;
+                y[wd] = p.y;
+            } else {
+                x[wd] = qnan;
+                y[wd] = qnan;
+            }
+        }
+        const uint32_t s0 = g * 32u;
+        const uint32_t ns = min(32u, nsub - s0);
+        uint32_t myk = 0;
+        float4 myr = make_float4(qnan, qnan, qnan, qnan);
+        if ((uint32_t)lane < ns) {
+            myk = __ldg(isub + soff + s0 + lane);
+            myr = __ldg(rects + __ldg(sub_q + myk));
+        }
+        uint32_t w[8];
+#pragma unroll
+        for (int wd = 0; wd < 8; ++wd) w[wd] = 0;
+        for (uint32_t s = 0; s < ns; ++s) {
+            const float xa = __shfl_sync(0xffffffffu, myr.x, s);
+            const float ya = __shfl_sync(0xffffffffu, myr.y, s);
+            const float xb = __shfl_sync(0xffffffffu, myr.z, s);
+            const float yb = __shfl_sync(0xffffffffu, myr.w, s);
+            const bool mine = (uint32_t)lane == s;
+#pragma unroll
+            for (int wd = 0; wd < 8; ++wd) {
+                if ((uint32_t)wd < nwc) {
+                    bool in = (xa <= x[wd]) & (x[wd] <= xb) & (ya <= y[wd]) & (y[wd] <= yb);
+                    uint32_t bw = __ballot_sync(0xffffffffu, in);
+                    if (mine) w[wd] = bw;
+                }
+            }
+        }
+        if ((uint32_t)lane < ns) {
+            uint32_t cnt = 0;
+            const uint32_t row = __ldg(leaf_word_off + leaf) + (s0 + lane) * nw_leaf + c * 8u;
+#pragma unroll
+            for (int wd = 0; wd < 8; ++wd) {
+                if ((uint32_t)wd < nwc) {
+                    bitmap[row + wd] = w[wd];
+                    cnt += __popc(w[wd]);
+                }
+            }
+            if (nchunk == 1) sub_res[myk] = cnt;
+            else atomicAdd(sub_res + myk, cnt);
+        }
+    }
+}
+
+void launch_filter(cudaStream_t st, int num_sms, const float4 *rects, const float2 *sxy,
+                   const uint32_t *leaf_beg, const uint32_t *leaf_sub_off,
+                   const uint32_t *leaf_word_off, const uint32_t *leaf_item_off,
+                   const uint32_t *isub, const uint32_t *sub_q, uint32_t *sub_res,
+                   uint32_t *bitmap, Caps caps, const Info *info) {
+    filter_kernel<<<num_sms * 8, kFilterThreads, 0, st>>>(rects, sxy, leaf_beg, leaf_sub_off,
+                                                          leaf_word_off, leaf_item_off, isub, sub_q,
+                                                          sub_res, bitmap, caps, info);
+}
+
+// ---------------------------------------------------------------------------
+// a11: exclusive scan of the per-subquery result counts (query-major order)
+// into 64-bit output offsets; R = out_off[n_sub].
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(kResThreads)
+result_scan_kernel(const uint32_t *__restrict__ sub_res, const uint32_t *__restrict__ sub_leaf,
+                   unsigned long long *__restrict__ out_off, unsigned long long *status,
+                   uint32_t *tile_counter, Caps caps, Info *info) {
+    __shared__ unsigned long long s_scan[kResThreads / 32 + 1];
+    __shared__ unsigned long long s_cov;
+    __shared__ uint32_t s_tile;
+    __shared__ unsigned long long s_prefix;
+    const int tid = threadIdx.x;
+    if (tid == 0) { s_tile = atomicAdd(tile_counter, 1u); s_cov = 0; }
+    __syncthreads();
+    if (!tick_buffers_ok(info, caps)) return;
+    const uint32_t tile = s_tile;
+    const uint32_t nsub = (uint32_t)info->n_sub;
+    const uint32_t base = tile * kResTile;
+    if (base >= nsub) {
+        if (tile == 0 && tid == 0) out_off[0] = 0;
+        return;
+    }
+    const uint32_t kb = base + tid * kResItems;
+    uint32_t v[kResItems];
+    unsigned long long t = 0, cov = 0;
+#pragma unroll
+    for (int e = 0; e < kResItems; ++e) {
+        uint32_t k = kb + e;
+        v[e] = k < nsub ? sub_res[k] : 0u;
+        t += v[e];
+        if (k < nsub && (sub_leaf[k] & 0x80000000u)) cov += v[e];
+    }
+    unsigned long long total;
+    unsigned long long off = block_excl_scan<kResThreads>(t, &total, s_scan);
+    if (tid == 0) s_prefix = lookback<unsigned long long>(status, tile, total, &info->err);
+    cov = warp_sum(cov);
+    if ((tid & 31) == 0 && cov) atomicAdd(&s_cov, cov);
+    __syncthreads();
+    off += s_prefix;
+#pragma unroll
+    for (int e = 0; e < kResItems; ++e) {
+        uint32_t k = kb + e;
+        if (k < nsub) out_off[k] = off;
+        off += v[e];
+    }
+    if (tid == 0) {
+        if (s_cov) atomicAdd(&info->n_results_cov, s_cov);
+        if (base + kResTile >= nsub) {
+            out_off[nsub] = s_prefix + total;
+            info->n_results = s_prefix + total;
+        }
+    }
+}
+
+void launch_result_scan(cudaStream_t st, unsigned long long sub_cap, const uint32_t *sub_res,
+                        const uint32_t *sub_leaf, unsigned long long *out_off,
+                        unsigned long long *status, uint32_t *tile_counter, Caps caps, Info *info) {
+    unsigned long long tiles = (sub_cap + kResTile - 1) / kResTile;
+    if (tiles == 0) tiles = 1;
+    result_scan_kernel<<<(unsigned)tiles, kResThreads, 0, st>>>(sub_res, sub_leaf, out_off, status,
+                                                               tile_counter, caps, info);
+}
+
+// ---------------------------------------------------------------------------
+// a12 + a13: emit the results.  One warp per subquery record, records taken
+// in query-major order so that the output is written front to back.
+//  - covering run: the run's objects are one contiguous range of the sorted
+//    ids; copy it (Sec. 5.7 covering expansion, done here on the device).
+//  - intersecting: read the subquery's bitmap row 32 words at a time and, per
+//    word, let lane j with bit j set write at run + popc(word & lanemask_lt)
+//    (Alg. 4: lane i writes the i-th positive of the word, coalesced).
+// ---------------------------------------------------------------------------
+template <int KIND>
+__device__ __forceinline__ void emit_one(void *out, unsigned long long pos, uint32_t q, uint32_t id,
+                                         uint32_t wpr) {
+    if (KIND == kEmitPairs) {
+        reinterpret_cast<uint2 *>(out)[pos] = make_uint2(q, id);
+    } else if (KIND == kEmitIds) {
+        reinterpret_cast<uint32_t *>(out)[pos] = id;
+    } else if (KIND == kEmitBitmap) {
+        atomicOr(reinterpret_cast<uint32_t *>(out) + (size_t)q * wpr + (id >> 5), 1u << (id & 31u));
+    } else {
+        reinterpret_cast<unsigned long long *>(out)[pos] = ((unsigned long long)q << 32) | id;
+    }
+}
+
+constexpr int kEmitThreads = 256;
+
+template <int KIND>
+__global__ void __launch_bounds__(kEmitThreads)
+emit_kernel(const uint32_t *__restrict__ sub_q, const uint32_t *__restrict__ sub_leaf,
+            const uint32_t *__restrict__ sub_len, const uint32_t *__restrict__ sub_bm,
+            const unsigned long long *__restrict__ out_off, const uint32_t *__restrict__ leaf_beg,
+            const uint32_t *__restrict__ sid, const uint32_t *__restrict__ bitmap, void *out,
+            uint32_t wpr, Caps caps, const Info *info) {
+    if (!tick_buffers_ok(info, caps)) return;
+    if (KIND != kEmitBitmap && info->n_results > caps.out) return;
+    const uint32_t nsub = (uint32_t)info->n_sub;
+    const int lane = threadIdx.x & 31;
+    const uint32_t lt = lanemask_lt();
+    const uint32_t nwarps = gridDim.x * (kEmitThreads / 32);
+    for (uint32_t k = (blockIdx.x * kEmitThreads + threadIdx.x) >> 5; k < nsub; k += nwarps) {
+        const uint32_t q = __ldg(sub_q + k);
+        const uint32_t sl = __ldg(sub_leaf + k);
+        const unsigned long long off = __ldg(out_off + k);
+        if (sl & 0x80000000u) {
+            const uint32_t first = sl & 0x7fffffffu;
+            const uint32_t b = __ldg(leaf_beg + first);
+            const uint32_t n = __ldg(leaf_beg + first + __ldg(sub_len + k)) - b;
+            for (uint32_t i = lane; i < n; i += 32) emit_one<KIND>(out, off + i, q, __ldg(sid + b + i), wpr);
+        } else {
+            const uint32_t b = __ldg(leaf_beg + sl);
+            const uint32_t n = __ldg(leaf_beg + sl + 1) - b;
+            const uint32_t nw = (n + 31u) >> 5;
+            const uint32_t row = __ldg(sub_bm + k);
+            unsigned long long run = off;
+            for (uint32_t w0 = 0; w0 < nw; w0 += 32) {
+                const uint32_t myw = (w0 + lane < nw) ? __ldg(bitmap + row + w0 + lane) : 0u;
+                const uint32_t nj = min(32u, nw - w0);
+                for (uint32_t j = 0; j < nj; ++j) {
+                    const uint32_t word = __shfl_sync(0xffffffffu, myw, j);
+                    if (word == 0u) continue;
+                    if ((word >> lane) & 1u)
+                        emit_one<KIND>(out, run + __popc(word & lt), q, __ldg(sid + b + (w0 + j) * 32u + lane), wpr);
+                    run += __popc(word);
+                }
+            }
+        }
+    }
+}
+
+void launch_emit(cudaStream_t st, int num_sms, int emit_kind, const uint32_t *sub_q,
+                 const uint32_t *sub_leaf, const uint32_t *sub_len, const uint32_t *sub_bm,
+                 const unsigned long long *out_off, const uint32_t *leaf_beg,
+                 const uint32_t *sid, const uint32_t *bitmap, void *out, uint32_t wpr,
+                 Caps caps, const Info *info) {
+    const int grid = num_sms * 8;
+    switch (emit_kind) {
+        case kEmitPairs:
+            emit_kernel<kEmitPairs><<<grid, kEmitThreads, 0, st>>>(sub_q, sub_leaf, sub_len, sub_bm, out_off,
+                                                                   leaf_beg, sid, bitmap, out, wpr, caps, info);
+            break;
+        case kEmitIds:
+            emit_kernel<kEmitIds><<<grid, kEmitThreads, 0, st>>>(sub_q, sub_leaf, sub_len, sub_bm, out_off,
+                                                                 leaf_beg, sid, bitmap, out, wpr, caps, info);
+            break;
+        case kEmitBitmap:
+            emit_kernel<kEmitBitmap><<<grid, kEmitThreads, 0, st>>>(sub_q, sub_leaf, sub_len, sub_bm, out_off,
+                                                                    leaf_beg, sid, bitmap, out, wpr, caps, info);
+            break;
+        default:
+            emit_kernel<kEmitKeys64><<<grid, kEmitThreads, 0, st>>>(sub_q, sub_leaf, sub_len, sub_bm, out_off,
+                                                                    leaf_beg, sid, bitmap, out, wpr, caps, info);
+            break;
+    }
+}
+
+// Per-query offsets: the first subquery record of query q starts its list.
+__global__ void query_offsets_kernel(uint32_t Q, const uint32_t *__restrict__ sub_off,
+                                     const unsigned long long *__restrict__ out_off,
+                                     unsigned long long *__restrict__ offsets, Caps caps,
+                                     const Info *info) {
+    if (!tick_buffers_ok(info, caps)) return;
+    for (uint32_t q = blockIdx.x * blockDim.x + threadIdx.x; q <= Q; q += gridDim.x * blockDim.x)
+        offsets[q] = out_off[sub_off[q]];
+}
+
+void launch_query_offsets(cudaStream_t st, uint32_t Q, const uint32_t *sub_off,
+                          const unsigned long long *out_off, unsigned long long *offsets,
+                          Caps caps, const Info *info) {
+    uint32_t g = (Q + 1 + 255) / 256;
+    if (g > 4096) g = 4096;
+    query_offsets_kernel<<<g, 256, 0, st>>>(Q, sub_off, out_off, offsets, caps, info);
+}
+
+// Sorted (qidx << 32 | id) keys to the requested layout.
+__global__ void keys_to_output_kernel(const unsigned long long *__restrict__ keys, uint64_t n,
+                                      int as_pairs, void *out) {
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n;
+         i += (uint64_t)gridDim.x * blockDim.x) {
+        unsigned long long k = keys[i];
+        if (as_pairs) reinterpret_cast<uint2 *>(out)[i] = make_uint2((uint32_t)(k >> 32), (uint32_t)k);
+        else reinterpret_cast<uint32_t *>(out)[i] = (uint32_t)k;
+    }
+}
+
+void launch_keys_to_output(cudaStream_t st, const unsigned long long *keys, uint64_t n,
+                           int as_pairs, void *out) {
+    if (n == 0) return;
+    uint64_t g = (n + 255) / 256;
+    if (g > 8192) g = 8192;
+    keys_to_output_kernel<<<(unsigned)g, 256, 0, st>>>(keys, n, as_pairs, out);
+}
+
+}  // namespace mqr

@@ -1,0 +1,707 @@
+// mqr_api.cu -- the C ABI of libmqr (declared in include/mqr.h): context,
+// device memory, and the per-tick pipeline
+//   a2 Morton keys -> a3 onesweep sort (4 passes) -> a4 leaves ->
+//   a5/a6 query count + scan -> a8 leaf scans -> a7 query write ->
+//   a10 filter -> a11 result scan -> a12/a13 emit (-> a14 sort/layout)
+// all enqueued on the context's stream with one host synchronisation at the
+// end of the tick (the result count sizes the caller's output).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+
+#include "../../include/mqr.h"
+#include "mqr_internal.cuh"
+
+using namespace mqr;
+
+namespace {
+
+thread_local std::string g_err;
+
+mqr_status fail(mqr_status s, const std::string &msg) {
+    g_err = msg;
+    return s;
+}
+
+mqr_status cuda_fail(cudaError_t e, const char *what) {
+    std::string m = std::string(what) + ": " + cudaGetErrorString(e);
+    return fail(e == cudaErrorMemoryAllocation ? MQR_ERR_OOM : MQR_ERR_CUDA, m);
+}
+
+#define MQR_CUDA(call)                                         \
+    do {                                                       \
+        cudaError_t e_ = (call);                               \
+        if (e_ != cudaSuccess) return cuda_fail(e_, #call);    \
+    } while (0)
+
+// A device buffer that only grows (contents are not preserved on growth).
+template <typename T>
+struct DevBuf {
+    T *p = nullptr;
+    size_t n = 0;
+    cudaError_t ensure(size_t want) {
+        if (want <= n) return cudaSuccess;
+        if (p) cudaFree(p);
+        p = nullptr;
+        n = 0;
+        cudaError_t e = cudaMalloc(&p, want * sizeof(T));
+        if (e == cudaSuccess) n = want;
+        return e;
+    }
+    void release() {
+        if (p) cudaFree(p);
+        p = nullptr;
+        n = 0;
+    }
+};
+
+size_t grow_to(unsigned long long need) { return (size_t)(need + need / 4 + 1024); }
+
+}  // namespace
+
+struct mqr_ctx {
+    int device = 0;
+    int num_sms = 148;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    mqr_config cfg{};
+    mqr_rect bounds{};
+    float sx = 0.f, sy = 0.f;
+    uint32_t nmax = 0;
+    unsigned long long epoch = 0;
+
+    // resident state
+    DevBuf<float2> pos;
+    DevBuf<unsigned long long> stamp;
+    // sort
+    DevBuf<unsigned long long> keysA, keysB;
+    DevBuf<uint32_t> skey, sid;
+    DevBuf<float2> sxy;
+    // leaves
+    DevBuf<uint32_t> leaf_lo, leaf_hi, leaf_beg, leaf_nsub, leaf_sub_off, leaf_word_off,
+        leaf_item_off, leaf_cursor;
+    DevBuf<uint8_t> mk_a, mk_b;
+    // per query / subquery
+    DevBuf<uint32_t> sub_off, sub_q, sub_leaf, sub_len, sub_res, sub_bm, isub, bitmap;
+    DevBuf<unsigned long long> out_off;
+    // zero-initialised arena: Info, histograms, tile counters, look-back status
+    DevBuf<unsigned char> arena;
+    // staging for the host-buffer entry points and the sorted output kinds
+    DevBuf<uint32_t> up_ids;
+    DevBuf<float2> up_xy;
+    DevBuf<float4> q_rects;
+    DevBuf<unsigned char> out_stage;
+    DevBuf<unsigned long long> off_stage, sortA, sortB;
+    DevBuf<unsigned char> sort_arena;
+    DevBuf<unsigned long long> upd_err;  // sticky error word of the update kernels
+
+    Info *info_host = nullptr;  // pinned
+    Info last{};
+    unsigned long long last_q = 0, retries = 0;
+    bool have_tick = false;
+};
+
+namespace {
+
+// Arena layout for one tick.
+struct Arena {
+    size_t info, hist, counters, st_sort, st_leaf, st_lscan, st_query, st_res, total;
+    uint32_t sort_tiles, leaf_tiles, lscan_tiles, query_tiles, res_tiles;
+};
+
+Arena arena_layout(uint32_t nmax, uint32_t Q, unsigned long long sub_cap) {
+    Arena a{};
+    a.sort_tiles = (nmax + kSortTile - 1) / kSortTile;
+    a.leaf_tiles = (nmax + kLeafTile - 1) / kLeafTile;
+    a.lscan_tiles = (nmax + kLeafScanTile - 1) / kLeafScanTile;
+    a.query_tiles = (Q + kQueryTile - 1) / kQueryTile;
+    a.res_tiles = (uint32_t)((sub_cap + kResTile - 1) / kResTile) + 1;
+    size_t o = 0;
+    auto take = [&](size_t bytes) {
+        size_t r = o;
+        o += (bytes + 255) & ~(size_t)255;
+        return r;
+    };
+    a.info = take(sizeof(Info));
+    a.hist = take(8 * 256 * sizeof(uint32_t));
+    a.counters = take(16 * sizeof(uint32_t));
+    a.st_sort = take((size_t)4 * 256 * a.sort_tiles * sizeof(uint32_t));
+    a.st_leaf = take((size_t)a.leaf_tiles * sizeof(uint32_t));
+    a.st_lscan = take((size_t)3 * a.lscan_tiles * sizeof(uint32_t));
+    a.st_query = take((size_t)a.query_tiles * sizeof(uint32_t));
+    a.st_res = take((size_t)a.res_tiles * sizeof(unsigned long long));
+    a.total = o;
+    return a;
+}
+
+template <typename T>
+T *at(mqr_ctx *c, size_t off) {
+    return reinterpret_cast<T *>(c->arena.p + off);
+}
+
+mqr_status check_launch(const char *what) {
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, what);
+    return MQR_OK;
+}
+
+bool finite_rect(const mqr_rect &b) {
+    return std::isfinite(b.xmin) && std::isfinite(b.ymin) && std::isfinite(b.xmax) &&
+           std::isfinite(b.ymax) && b.xmax > b.xmin && b.ymax > b.ymin;
+}
+
+// scale = 2^15 / (hi - lo), each operation rounded to float32.
+float fp32_scale(float lo, float hi) {
+    volatile float w = hi - lo;
+    volatile float s = 32768.0f / w;
+    return s;
+}
+
+uint32_t bitmap_words_per_row(uint32_t nmax) { return (nmax + 31u) / 32u; }
+
+size_t out_elem_bytes(int kind) {
+    switch (kind) {
+        case MQR_OUT_PAIRS:
+        case MQR_OUT_PAIRS_SORTED: return 8;
+        case MQR_OUT_CSR:
+        case MQR_OUT_CSR_SORTED: return 4;
+        default: return 4;
+    }
+}
+
+// Enqueue the whole pipeline up to the result scan (and the emit when the
+// caller's buffer is given).  Returns after enqueueing.
+mqr_status enqueue_tick(mqr_ctx *c, const float4 *rects, uint32_t Q, int emit_kind, void *out,
+                        unsigned long long out_cap_elems, unsigned long long *offsets,
+                        const Arena &a, Caps &caps) {
+    cudaStream_t st = c->stream;
+    Info *info = at<Info>(c, a.info);
+    uint32_t *hist = at<uint32_t>(c, a.hist);
+    uint32_t *ctr = at<uint32_t>(c, a.counters);
+    unsigned long long *err = &info->err;
+    const float x0 = c->bounds.xmin, y0 = c->bounds.ymin;
+    const uint32_t nmax = c->nmax;
+    const int cov = c->cfg.covering ? 1 : 0;
+
+    MQR_CUDA(cudaMemsetAsync(c->arena.p, 0, a.total, st));
+    // Carry the update kernels' sticky error bits into this tick.
+    MQR_CUDA(cudaMemcpyAsync(&info->err, c->upd_err.p, sizeof(unsigned long long),
+                             cudaMemcpyDeviceToDevice, st));
+    MQR_CUDA(cudaMemsetAsync(c->upd_err.p, 0, sizeof(unsigned long long), st));
+    if (Q == 0) MQR_CUDA(cudaMemsetAsync(c->sub_off.p, 0, sizeof(uint32_t), st));
+
+    // a2 + a3: keys and the 4-pass onesweep sort of (key << 32 | id).
+    launch_morton_keys(st, c->pos.p, c->stamp.p, nmax, x0, y0, c->sx, c->sy, c->keysA.p, hist, info);
+    uint32_t *st_sort = at<uint32_t>(c, a.st_sort);
+    const size_t pass_status = (size_t)256 * a.sort_tiles;
+    unsigned long long *src = c->keysA.p, *dst = c->keysB.p;
+    for (int p = 0; p < 4; ++p) {
+        bool fin = p == 3;
+        launch_onesweep_pass(st, src, dst, nmax, 32 + 8 * p, hist + 256 * p, st_sort + pass_status * p,
+                             ctr + p, err, fin, c->pos.p, c->skey.p, c->sid.p, c->sxy.p);
+        std::swap(src, dst);
+    }
+    // a4
+    launch_build_leaves(st, c->skey.p, nmax, c->cfg.leaf_cap,
+                        c->cfg.index_kind == MQR_INDEX_UNIFORM_GRID, c->cfg.grid_level, c->mk_a.p,
+                        c->mk_b.p, at<uint32_t>(c, a.st_leaf), ctr + 4, c->leaf_lo.p, c->leaf_hi.p,
+                        c->leaf_beg.p, c->leaf_nsub.p, info);
+    // a5 + a6
+    launch_query_count(st, rects, Q, x0, y0, c->sx, c->sy, c->leaf_lo.p, c->leaf_hi.p, c->leaf_beg.p,
+                       cov, c->sub_off.p, c->leaf_nsub.p, at<uint32_t>(c, a.st_query), ctr + 5, info);
+    // a8 scans
+    launch_leaf_scan(st, nmax, c->leaf_beg.p, c->leaf_nsub.p, c->leaf_sub_off.p, c->leaf_word_off.p,
+                     c->leaf_item_off.p, c->leaf_cursor.p, at<uint32_t>(c, a.st_lscan), ctr + 6, info);
+    // a7
+    caps.sub = c->sub_q.n;
+    caps.sub_i = c->isub.n;
+    caps.words = std::min<size_t>(c->bitmap.n, 0xffffffffull);
+    caps.out = out_cap_elems;
+    launch_query_write(st, rects, Q, x0, y0, c->sx, c->sy, c->leaf_lo.p, c->leaf_hi.p, c->leaf_beg.p,
+                       cov, c->sub_off.p, c->leaf_sub_off.p, c->leaf_word_off.p, c->leaf_cursor.p,
+                       c->sub_q.p, c->sub_leaf.p, c->sub_len.p, c->sub_res.p, c->sub_bm.p, c->isub.p,
+                       caps, info);
+    // a10
+    launch_filter(st, c->num_sms, rects, c->sxy.p, c->leaf_beg.p, c->leaf_sub_off.p,
+                  c->leaf_word_off.p, c->leaf_item_off.p, c->isub.p, c->sub_q.p, c->sub_res.p,
+                  c->bitmap.p, caps, info);
+    // a11
+    launch_result_scan(st, caps.sub, c->sub_res.p, c->sub_leaf.p, c->out_off.p,
+                       at<unsigned long long>(c, a.st_res), ctr + 7, caps, info);
+    // a12 + a13
+    if (out != nullptr && emit_kind >= 0)
+        launch_emit(st, c->num_sms, emit_kind, c->sub_q.p, c->sub_leaf.p, c->sub_len.p, c->sub_bm.p,
+                    c->out_off.p, c->leaf_beg.p, c->sid.p, c->bitmap.p, out,
+                    bitmap_words_per_row(nmax), caps, info);
+    if (offsets != nullptr) launch_query_offsets(st, Q, c->sub_off.p, c->out_off.p, offsets, caps, info);
+    return check_launch("tick kernels");
+}
+
+// Make sure every per-tick buffer that depends on Q or on the capacities
+// exists.
+mqr_status ensure_tick_buffers(mqr_ctx *c, uint32_t Q) {
+    size_t sub0 = std::max<size_t>(4096, (size_t)Q * 4);
+    MQR_CUDA(c->sub_off.ensure((size_t)Q + 1));
+    if (c->sub_q.n == 0) {
+        MQR_CUDA(c->sub_q.ensure(sub0));
+        MQR_CUDA(c->sub_leaf.ensure(sub0));
+        MQR_CUDA(c->sub_len.ensure(sub0));
+        MQR_CUDA(c->sub_res.ensure(sub0));
+        MQR_CUDA(c->sub_bm.ensure(sub0));
+        MQR_CUDA(c->out_off.ensure(sub0 + 1));
+        MQR_CUDA(c->isub.ensure(sub0));
+        MQR_CUDA(c->bitmap.ensure(std::max<size_t>(1 << 16, (size_t)Q * 16)));
+    }
+    return MQR_OK;
+}
+
+mqr_status grow_sub(mqr_ctx *c, unsigned long long need) {
+    size_t n = grow_to(need);
+    c->sub_q.release(); c->sub_leaf.release(); c->sub_len.release(); c->sub_res.release();
+    c->sub_bm.release(); c->out_off.release();
+    MQR_CUDA(c->sub_q.ensure(n));
+    MQR_CUDA(c->sub_leaf.ensure(n));
+    MQR_CUDA(c->sub_len.ensure(n));
+    MQR_CUDA(c->sub_res.ensure(n));
+    MQR_CUDA(c->sub_bm.ensure(n));
+    MQR_CUDA(c->out_off.ensure(n + 1));
+    return MQR_OK;
+}
+
+// Run the pipeline until every internal buffer was large enough; leaves the
+// tick's device state valid and c->last filled.  `out` may be null (then
+// nothing is emitted).
+mqr_status run_tick(mqr_ctx *c, const float4 *rects, uint32_t Q, int emit_kind, void *out,
+                    unsigned long long out_cap_elems, unsigned long long *offsets) {
+    mqr_status s = ensure_tick_buffers(c, Q);
+    if (s != MQR_OK) return s;
+    c->retries = 0;
+    for (int attempt = 0; attempt < 8; ++attempt) {
+        Arena a = arena_layout(c->nmax, Q, c->sub_q.n);
+        MQR_CUDA(c->arena.ensure(a.total));
+        Caps caps{};
+        s = enqueue_tick(c, rects, Q, emit_kind, out, out_cap_elems, offsets, a, caps);
+        if (s != MQR_OK) return s;
+        MQR_CUDA(cudaMemcpyAsync(c->info_host, c->arena.p + a.info, sizeof(Info), cudaMemcpyDeviceToHost,
+                                 c->stream));
+        MQR_CUDA(cudaStreamSynchronize(c->stream));
+        Info in = *c->info_host;
+        c->last = in;
+        c->last_q = Q;
+        c->have_tick = true;
+        if (in.err & kErrTimeout)
+            return fail(MQR_ERR_TIMEOUT, "a device-side wait exceeded its deadline");
+        if (in.err & kErrInternal) return fail(MQR_ERR_INTERNAL, "device index out of range");
+        if (in.err & kErrBadId) {
+            return fail(MQR_ERR_INVALID_ARG,
+                        "an update id was >= max_objects (ignored); the tick was answered without it");
+        }
+        bool again = false;
+        if (in.n_sub > caps.sub) {
+            s = grow_sub(c, in.n_sub);
+            if (s != MQR_OK) return s;
+            again = true;
+        } else {
+            if (in.n_sub_i > caps.sub_i) {
+                c->isub.release();
+                MQR_CUDA(c->isub.ensure(grow_to(in.n_sub_i)));
+                again = true;
+            }
+            if (in.n_words > caps.words) {
+                if (in.n_words > 0xffffffffull)
+                    return fail(MQR_ERR_CAPACITY, "more than 2^32 bitmap words in one tick");
+                c->bitmap.release();
+                MQR_CUDA(c->bitmap.ensure(grow_to(in.n_words)));
+                again = true;
+            }
+        }
+        if (!again) return MQR_OK;
+        ++c->retries;
+    }
+    return fail(MQR_ERR_INTERNAL, "buffer growth did not converge");
+}
+
+// Sort n keys (qidx << 32 | id) in sortA: digits over the id bits and the
+// qidx bits only.  Result ends in *result.
+mqr_status sort_result_keys(mqr_ctx *c, uint64_t n, uint32_t Q, unsigned long long **result) {
+    *result = c->sortA.p;
+    if (n <= 1) return MQR_OK;
+    int shifts[8], nd = 0;
+    uint32_t idbits = 1;
+    while (idbits < 32 && (1ull << idbits) < c->nmax) ++idbits;
+    uint32_t qbits = 1;
+    while (qbits < 32 && (1ull << qbits) < Q) ++qbits;
+    for (uint32_t b = 0; b < idbits; b += 8) shifts[nd++] = (int)b;
+    for (uint32_t b = 0; b < qbits; b += 8) shifts[nd++] = 32 + (int)b;
+    uint32_t tiles = (uint32_t)((n + kSortTile - 1) / kSortTile);
+    size_t hist_off = 0, ctr_off = 8 * 256 * sizeof(uint32_t);
+    size_t st_off = ctr_off + 256;
+    size_t total = st_off + (size_t)nd * 256 * tiles * sizeof(uint32_t);
+    MQR_CUDA(c->sort_arena.ensure(total));
+    MQR_CUDA(cudaMemsetAsync(c->sort_arena.p, 0, total, c->stream));
+    uint32_t *hist = reinterpret_cast<uint32_t *>(c->sort_arena.p + hist_off);
+    uint32_t *ctr = reinterpret_cast<uint32_t *>(c->sort_arena.p + ctr_off);
+    uint32_t *stp = reinterpret_cast<uint32_t *>(c->sort_arena.p + st_off);
+    launch_key_histograms(c->stream, c->sortA.p, (uint32_t)n, shifts, nd, hist);
+    unsigned long long *src = c->sortA.p, *dst = c->sortB.p;
+    // error word of this sort: a dedicated slot in its counters block
+    unsigned long long *err = reinterpret_cast<unsigned long long *>(ctr + 12);
+    for (int d = 0; d < nd; ++d) {
+        launch_onesweep_pass(c->stream, src, dst, (uint32_t)n, shifts[d], hist + 256 * d,
+                             stp + (size_t)256 * tiles * d, ctr + d, err, false, nullptr, nullptr,
+                             nullptr, nullptr);
+        std::swap(src, dst);
+    }
+    *result = src;
+    mqr_status s = check_launch("result sort");
+    if (s != MQR_OK) return s;
+    unsigned long long herr = 0;
+    MQR_CUDA(cudaMemcpyAsync(&herr, err, sizeof(herr), cudaMemcpyDeviceToHost, c->stream));
+    MQR_CUDA(cudaStreamSynchronize(c->stream));
+    if (herr & kErrTimeout) return fail(MQR_ERR_TIMEOUT, "a device-side wait exceeded its deadline");
+    if (herr) return fail(MQR_ERR_INTERNAL, "device index out of range in the result sort");
+    return MQR_OK;
+}
+
+mqr_status tick_device(mqr_ctx *c, const float *rects_dev, uint32_t Q, int kind, void *out_dev,
+                       uint64_t cap_bytes, uint64_t *out_count, uint64_t *offsets_dev) {
+    const float4 *rects = reinterpret_cast<const float4 *>(rects_dev);
+    unsigned long long *offs = reinterpret_cast<unsigned long long *>(offsets_dev);
+    const uint32_t wpr = bitmap_words_per_row(c->nmax);
+    if (kind == MQR_OUT_BITMAP) {
+        uint64_t words = (uint64_t)Q * wpr;
+        *out_count = words;
+        if (cap_bytes < words * 4) return fail(MQR_ERR_CAPACITY, "bitmap output buffer too small");
+        if (words && out_dev == nullptr) return fail(MQR_ERR_INVALID_ARG, "out_dev is NULL");
+        if (words) MQR_CUDA(cudaMemsetAsync(out_dev, 0, words * 4, c->stream));
+        return run_tick(c, rects, Q, kEmitBitmap, out_dev, words, offs);
+    }
+    if (kind == MQR_OUT_COUNT) {
+        mqr_status s = run_tick(c, rects, Q, -1, nullptr, 0, offs);
+        *out_count = c->last.n_results;
+        return s;
+    }
+    if (kind == MQR_OUT_PAIRS || kind == MQR_OUT_CSR) {
+        const size_t eb = out_elem_bytes(kind);
+        unsigned long long cap_elems = cap_bytes / eb;
+        mqr_status s = run_tick(c, rects, Q, kind == MQR_OUT_PAIRS ? kEmitPairs : kEmitIds,
+                                out_dev, out_dev ? cap_elems : 0, offs);
+        *out_count = c->last.n_results;
+        if (s != MQR_OK) return s;
+        if (c->last.n_results > cap_elems || (c->last.n_results && out_dev == nullptr))
+            return fail(MQR_ERR_CAPACITY, "output buffer too small for the tick's results");
+        return MQR_OK;
+    }
+    // sorted kinds: count first, then emit (qidx, id) keys, sort, lay out.
+    mqr_status s = run_tick(c, rects, Q, -1, nullptr, 0, offs);
+    *out_count = c->last.n_results;
+    if (s != MQR_OK) return s;
+    const uint64_t R = c->last.n_results;
+    const size_t eb = out_elem_bytes(kind);
+    if (R > cap_bytes / eb || (R && out_dev == nullptr))
+        return fail(MQR_ERR_CAPACITY, "output buffer too small for the tick's results");
+    if (R >= (1ull << 30)) return fail(MQR_ERR_INVALID_ARG, "sorted output kinds are limited to R < 2^30");
+    if (R == 0) return MQR_OK;
+    MQR_CUDA(c->sortA.ensure(R));
+    MQR_CUDA(c->sortB.ensure(R));
+    Arena a = arena_layout(c->nmax, Q, c->sub_q.n);
+    Caps caps{c->sub_q.n, c->isub.n, std::min<size_t>(c->bitmap.n, 0xffffffffull), R};
+    Info *info = at<Info>(c, a.info);
+    launch_emit(c->stream, c->num_sms, kEmitKeys64, c->sub_q.p, c->sub_leaf.p, c->sub_len.p,
+                c->sub_bm.p, c->out_off.p, c->leaf_beg.p, c->sid.p, c->bitmap.p, c->sortA.p, wpr, caps,
+                info);
+    s = check_launch("emit keys");
+    if (s != MQR_OK) return s;
+    unsigned long long *sorted = nullptr;
+    s = sort_result_keys(c, R, Q, &sorted);
+    if (s != MQR_OK) return s;
+    launch_keys_to_output(c->stream, sorted, R, kind == MQR_OUT_PAIRS_SORTED, out_dev);
+    s = check_launch("layout");
+    if (s != MQR_OK) return s;
+    MQR_CUDA(cudaStreamSynchronize(c->stream));
+    return MQR_OK;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// C ABI
+// ---------------------------------------------------------------------------
+extern "C" {
+
+const char *mqr_last_error(void) { return g_err.c_str(); }
+
+mqr_status mqr_config_default(mqr_config *cfg) {
+    if (!cfg) return fail(MQR_ERR_INVALID_ARG, "cfg is NULL");
+    std::memset(cfg, 0, sizeof(*cfg));
+    cfg->max_objects = 1u << 20;
+    cfg->leaf_cap = 128;
+    cfg->index_kind = MQR_INDEX_QUADTREE;
+    cfg->grid_level = 8;
+    cfg->covering = 1;
+    return MQR_OK;
+}
+
+void mqr_destroy(mqr_ctx *c) {
+    if (!c) return;
+    int prev = 0;
+    cudaGetDevice(&prev);
+    cudaSetDevice(c->device);
+    if (c->stream) cudaStreamSynchronize(c->stream);
+    DevBuf<float2> *f2[] = {&c->pos, &c->sxy, &c->up_xy};
+    for (auto *b : f2) b->release();
+    DevBuf<unsigned long long> *u64s[] = {&c->stamp, &c->keysA, &c->keysB, &c->out_off, &c->off_stage,
+                                          &c->sortA, &c->sortB};
+    for (auto *b : u64s) b->release();
+    DevBuf<uint32_t> *u32s[] = {&c->skey, &c->sid, &c->leaf_lo, &c->leaf_hi, &c->leaf_beg, &c->leaf_nsub,
+                                &c->leaf_sub_off, &c->leaf_word_off, &c->leaf_item_off, &c->leaf_cursor,
+                                &c->sub_off, &c->sub_q, &c->sub_leaf, &c->sub_len, &c->sub_res,
+                                &c->sub_bm, &c->isub, &c->bitmap, &c->up_ids};
+    for (auto *b : u32s) b->release();
+    c->mk_a.release();
+    c->mk_b.release();
+    c->arena.release();
+    c->sort_arena.release();
+    c->upd_err.release();
+    c->q_rects.release();
+    c->out_stage.release();
+    if (c->info_host) cudaFreeHost(c->info_host);
+    if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
+    cudaSetDevice(prev);
+    delete c;
+}
+
+mqr_status mqr_create_ex(mqr_rect bounds, const mqr_config *cfg, void *cuda_stream, mqr_ctx **out) {
+    if (!out) return fail(MQR_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if (!cfg) return fail(MQR_ERR_INVALID_ARG, "cfg is NULL");
+    if (!finite_rect(bounds)) return fail(MQR_ERR_INVALID_ARG, "bounds must be finite with xmax > xmin, ymax > ymin");
+    if (cfg->leaf_cap == 0) return fail(MQR_ERR_INVALID_ARG, "leaf_cap must be >= 1");
+    if (cfg->index_kind != MQR_INDEX_QUADTREE && cfg->index_kind != MQR_INDEX_UNIFORM_GRID)
+        return fail(MQR_ERR_INVALID_ARG, "unknown index_kind");
+    if (cfg->index_kind == MQR_INDEX_UNIFORM_GRID && (cfg->grid_level < 1 || cfg->grid_level > 15))
+        return fail(MQR_ERR_INVALID_ARG, "grid_level must be in 1..15");
+    if (cfg->max_objects >= (1u << 30)) return fail(MQR_ERR_INVALID_ARG, "max_objects must be < 2^30");
+    if (cfg->reserved[0] || cfg->reserved[1] || cfg->reserved[2])
+        return fail(MQR_ERR_INVALID_ARG, "reserved fields must be 0");
+    float sx = fp32_scale(bounds.xmin, bounds.xmax), sy = fp32_scale(bounds.ymin, bounds.ymax);
+    if (!std::isfinite(sx) || !std::isfinite(sy) || !(sx > 0.f) || !(sy > 0.f))
+        return fail(MQR_ERR_INVALID_ARG, "bounds too small for float32 cell scaling");
+
+    mqr_ctx *c = new (std::nothrow) mqr_ctx();
+    if (!c) return fail(MQR_ERR_OOM, "host allocation failed");
+    c->cfg = *cfg;
+    c->bounds = bounds;
+    c->sx = sx;
+    c->sy = sy;
+    c->nmax = cfg->max_objects;
+    auto bail = [&](cudaError_t e, const char *what) {
+        mqr_status s = cuda_fail(e, what);
+        mqr_destroy(c);
+        return s;
+    };
+    cudaError_t e;
+    if ((e = cudaGetDevice(&c->device)) != cudaSuccess) return bail(e, "cudaGetDevice");
+    if ((e = cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device)) != cudaSuccess)
+        return bail(e, "cudaDeviceGetAttribute");
+    if (cuda_stream) {
+        c->stream = reinterpret_cast<cudaStream_t>(cuda_stream);
+    } else {
+        if ((e = cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking)) != cudaSuccess)
+            return bail(e, "cudaStreamCreate");
+        c->own_stream = true;
+    }
+    const size_t n = std::max<size_t>(c->nmax, 1);
+    if ((e = c->pos.ensure(n)) || (e = c->stamp.ensure(n)) || (e = c->keysA.ensure(n)) ||
+        (e = c->keysB.ensure(n)) || (e = c->skey.ensure(n)) || (e = c->sid.ensure(n)) ||
+        (e = c->sxy.ensure(n)) || (e = c->leaf_lo.ensure(n)) || (e = c->leaf_hi.ensure(n)) ||
+        (e = c->leaf_beg.ensure(n + 1)) || (e = c->leaf_nsub.ensure(n)) ||
+        (e = c->leaf_sub_off.ensure(n + 1)) || (e = c->leaf_word_off.ensure(n + 1)) ||
+        (e = c->leaf_item_off.ensure(n + 1)) || (e = c->leaf_cursor.ensure(n)) ||
+        (e = c->upd_err.ensure(1)))
+        return bail(e, "cudaMalloc (object state)");
+    if (cfg->index_kind == MQR_INDEX_QUADTREE && cfg->leaf_cap > (uint32_t)kLeafCapSmem &&
+        cfg->leaf_cap < c->nmax) {
+        if ((e = c->mk_a.ensure(2 * n + 2)) || (e = c->mk_b.ensure(2 * n + 2)))
+            return bail(e, "cudaMalloc (window tables)");
+    }
+    if ((e = cudaMemsetAsync(c->stamp.p, 0, n * sizeof(unsigned long long), c->stream)) ||
+        (e = cudaMemsetAsync(c->pos.p, 0, n * sizeof(float2), c->stream)) ||
+        (e = cudaMemsetAsync(c->upd_err.p, 0, sizeof(unsigned long long), c->stream)))
+        return bail(e, "cudaMemset");
+    if ((e = cudaMallocHost(&c->info_host, sizeof(Info))) != cudaSuccess) return bail(e, "cudaMallocHost");
+    if ((e = cudaStreamSynchronize(c->stream)) != cudaSuccess) return bail(e, "cudaStreamSynchronize");
+    *out = c;
+    return MQR_OK;
+}
+
+mqr_status mqr_create(mqr_rect bounds, uint32_t leaf_cap, uint32_t max_objects, mqr_ctx **out) {
+    mqr_config cfg;
+    mqr_config_default(&cfg);
+    cfg.leaf_cap = leaf_cap;
+    cfg.max_objects = max_objects;
+    return mqr_create_ex(bounds, &cfg, nullptr, out);
+}
+
+mqr_status mqr_apply_updates(mqr_ctx *c, const uint32_t *ids_dev, const float *xy_dev, uint32_t n) {
+    if (!c) return fail(MQR_ERR_INVALID_ARG, "ctx is NULL");
+    if (n == 0) return MQR_OK;
+    if (!ids_dev || !xy_dev) return fail(MQR_ERR_INVALID_ARG, "ids_dev / xy_dev is NULL");
+    MQR_CUDA(cudaSetDevice(c->device));
+    ++c->epoch;
+    launch_apply_updates(c->stream, ids_dev, reinterpret_cast<const float2 *>(xy_dev), n, c->nmax,
+                         c->epoch, c->stamp.p, c->pos.p, c->upd_err.p);
+    return check_launch("apply_updates");
+}
+
+mqr_status mqr_apply_updates_host(mqr_ctx *c, const uint32_t *ids_host, const float *xy_host, uint32_t n) {
+    if (!c) return fail(MQR_ERR_INVALID_ARG, "ctx is NULL");
+    if (n == 0) return MQR_OK;
+    if (!ids_host || !xy_host) return fail(MQR_ERR_INVALID_ARG, "ids_host / xy_host is NULL");
+    MQR_CUDA(cudaSetDevice(c->device));
+    MQR_CUDA(c->up_ids.ensure(n));
+    MQR_CUDA(c->up_xy.ensure(n));
+    MQR_CUDA(cudaMemcpyAsync(c->up_ids.p, ids_host, (size_t)n * 4, cudaMemcpyHostToDevice, c->stream));
+    MQR_CUDA(cudaMemcpyAsync(c->up_xy.p, xy_host, (size_t)n * 8, cudaMemcpyHostToDevice, c->stream));
+    mqr_status s = mqr_apply_updates(c, c->up_ids.p, reinterpret_cast<const float *>(c->up_xy.p), n);
+    if (s != MQR_OK) return s;
+    // the host buffers may be reused as soon as we return
+    MQR_CUDA(cudaStreamSynchronize(c->stream));
+    return MQR_OK;
+}
+
+static mqr_status tick_args(mqr_ctx *c, const void *rects, uint32_t Q, int kind, uint64_t *out_count) {
+    if (!c) return fail(MQR_ERR_INVALID_ARG, "ctx is NULL");
+    if (!out_count) return fail(MQR_ERR_INVALID_ARG, "out_count is NULL");
+    if (Q > 0 && !rects) return fail(MQR_ERR_INVALID_ARG, "rects is NULL");
+    if (Q >= (1u << 30)) return fail(MQR_ERR_INVALID_ARG, "Q must be < 2^30");
+    if (kind < MQR_OUT_PAIRS || kind > MQR_OUT_COUNT) return fail(MQR_ERR_INVALID_ARG, "unknown output kind");
+    return MQR_OK;
+}
+
+mqr_status mqr_tick(mqr_ctx *c, const float *rects_dev, uint32_t Q, int kind, void *out_dev,
+                    uint64_t out_capacity_bytes, uint64_t *out_count, uint64_t *offsets_dev) {
+    mqr_status s = tick_args(c, rects_dev, Q, kind, out_count);
+    if (s != MQR_OK) return s;
+    if ((kind == MQR_OUT_CSR || kind == MQR_OUT_CSR_SORTED) && !offsets_dev)
+        return fail(MQR_ERR_INVALID_ARG, "CSR output needs offsets_dev");
+    *out_count = 0;
+    MQR_CUDA(cudaSetDevice(c->device));
+    return tick_device(c, rects_dev, Q, kind, out_dev, out_capacity_bytes, out_count, offsets_dev);
+}
+
+mqr_status mqr_tick_host(mqr_ctx *c, const float *rects_host, uint32_t Q, int kind, void *out_host,
+                         uint64_t out_capacity_bytes, uint64_t *out_count, uint64_t *offsets_host) {
+    mqr_status s = tick_args(c, rects_host, Q, kind, out_count);
+    if (s != MQR_OK) return s;
+    if ((kind == MQR_OUT_CSR || kind == MQR_OUT_CSR_SORTED) && !offsets_host)
+        return fail(MQR_ERR_INVALID_ARG, "CSR output needs offsets_host");
+    *out_count = 0;
+    MQR_CUDA(cudaSetDevice(c->device));
+    MQR_CUDA(c->q_rects.ensure(std::max<size_t>(Q, 1)));
+    if (Q) MQR_CUDA(cudaMemcpyAsync(c->q_rects.p, rects_host, (size_t)Q * 16, cudaMemcpyHostToDevice, c->stream));
+    uint64_t *offs_dev = nullptr;
+    if (offsets_host) {
+        MQR_CUDA(c->off_stage.ensure((size_t)Q + 1));
+        offs_dev = reinterpret_cast<uint64_t *>(c->off_stage.p);
+    }
+    const float *rd = reinterpret_cast<const float *>(c->q_rects.p);
+    // Device staging buffer: as large as the caller's buffer allows, grown on
+    // demand (the tick's device state stays valid, so only the output is
+    // produced again after a growth).
+    size_t want = out_capacity_bytes;
+    if (kind == MQR_OUT_BITMAP) want = std::min<uint64_t>(want, (uint64_t)Q * bitmap_words_per_row(c->nmax) * 4);
+    if (kind == MQR_OUT_COUNT) want = 0;
+    size_t have = std::min(c->out_stage.n, want);
+    s = tick_device(c, rd, Q, kind, have ? c->out_stage.p : nullptr, have, out_count, offs_dev);
+    if (s == MQR_ERR_CAPACITY && kind != MQR_OUT_COUNT) {
+        uint64_t need = kind == MQR_OUT_BITMAP ? *out_count * 4 : *out_count * out_elem_bytes(kind);
+        if (need > out_capacity_bytes) return s;
+        MQR_CUDA(c->out_stage.ensure(std::max<size_t>(need, 1)));
+        s = tick_device(c, rd, Q, kind, c->out_stage.p, need, out_count, offs_dev);
+    }
+    if (s != MQR_OK) return s;
+    uint64_t bytes = kind == MQR_OUT_BITMAP ? *out_count * 4
+                     : (kind == MQR_OUT_COUNT ? 0 : *out_count * out_elem_bytes(kind));
+    if (bytes) {
+        if (!out_host) return fail(MQR_ERR_INVALID_ARG, "out_host is NULL");
+        MQR_CUDA(cudaMemcpyAsync(out_host, c->out_stage.p, bytes, cudaMemcpyDeviceToHost, c->stream));
+    }
+    if (offsets_host)
+        MQR_CUDA(cudaMemcpyAsync(offsets_host, offs_dev, ((size_t)Q + 1) * 8, cudaMemcpyDeviceToHost, c->stream));
+    MQR_CUDA(cudaStreamSynchronize(c->stream));
+    return MQR_OK;
+}
+
+mqr_status mqr_get_stats(const mqr_ctx *c, mqr_stats *o) {
+    if (!c || !o) return fail(MQR_ERR_INVALID_ARG, "NULL argument");
+    const Info &in = c->last;
+    std::memset(o, 0, sizeof(*o));
+    o->n_objects = in.n_present;
+    o->n_queries = c->last_q;
+    o->n_leaves = in.n_leaves;
+    o->max_level = in.max_level;
+    o->n_sub_intersecting = in.n_sub_i;
+    o->n_sub_covering = in.n_sub_c;
+    o->n_covering_runs = in.n_runs;
+    o->n_tests = in.n_tests;
+    o->n_filter_items = in.n_items;
+    o->n_bitmap_words = in.n_words;
+    o->n_results = in.n_results;
+    o->n_results_covering = in.n_results_cov;
+    o->n_retries = c->retries;
+    return MQR_OK;
+}
+
+mqr_status mqr_get_leaves(mqr_ctx *c, uint32_t *leaves_host, uint64_t cap, uint64_t *n) {
+    if (!c || !n) return fail(MQR_ERR_INVALID_ARG, "NULL argument");
+    if (!c->have_tick) return fail(MQR_ERR_INVALID_ARG, "no tick has completed yet");
+    const uint64_t L = c->last.n_leaves;
+    *n = L;
+    if (L == 0) return MQR_OK;
+    if (cap < L || !leaves_host) return fail(MQR_ERR_CAPACITY, "leaves_host too small");
+    MQR_CUDA(cudaSetDevice(c->device));
+    uint32_t *lo = new (std::nothrow) uint32_t[3 * L + 1];
+    if (!lo) return fail(MQR_ERR_OOM, "host allocation failed");
+    uint32_t *hi = lo + L, *beg = lo + 2 * L;
+    cudaError_t e = cudaMemcpyAsync(lo, c->leaf_lo.p, L * 4, cudaMemcpyDeviceToHost, c->stream);
+    if (!e) e = cudaMemcpyAsync(hi, c->leaf_hi.p, L * 4, cudaMemcpyDeviceToHost, c->stream);
+    if (!e) e = cudaMemcpyAsync(beg, c->leaf_beg.p, (L + 1) * 4, cudaMemcpyDeviceToHost, c->stream);
+    if (!e) e = cudaStreamSynchronize(c->stream);
+    if (e) {
+        delete[] lo;
+        return cuda_fail(e, "mqr_get_leaves copy");
+    }
+    for (uint64_t k = 0; k < L; ++k) {
+        uint32_t span = hi[k] - lo[k] + 1u;
+        uint32_t s = 0;
+        while ((1ull << (2 * (s + 1))) <= span) ++s;
+        leaves_host[4 * k + 0] = 15u - s;
+        leaves_host[4 * k + 1] = s >= 15 ? 0u : lo[k] >> (2 * s);
+        leaves_host[4 * k + 2] = beg[k];
+        leaves_host[4 * k + 3] = beg[k + 1];
+    }
+    delete[] lo;
+    return MQR_OK;
+}
+
+mqr_status mqr_get_sorted(mqr_ctx *c, uint32_t *keys_host, uint32_t *ids_host, uint64_t cap, uint64_t *n) {
+    if (!c || !n) return fail(MQR_ERR_INVALID_ARG, "NULL argument");
+    if (!c->have_tick) return fail(MQR_ERR_INVALID_ARG, "no tick has completed yet");
+    const uint64_t N = c->last.n_present;
+    *n = N;
+    if (N == 0) return MQR_OK;
+    if (cap < N) return fail(MQR_ERR_CAPACITY, "buffers too small");
+    MQR_CUDA(cudaSetDevice(c->device));
+    if (keys_host) MQR_CUDA(cudaMemcpyAsync(keys_host, c->skey.p, N * 4, cudaMemcpyDeviceToHost, c->stream));
+    if (ids_host) MQR_CUDA(cudaMemcpyAsync(ids_host, c->sid.p, N * 4, cudaMemcpyDeviceToHost, c->stream));
+    MQR_CUDA(cudaStreamSynchronize(c->stream));
+    return MQR_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,297 @@
+// mqr_internal.cuh -- shared device helpers and kernel launchers of libmqr.
+//
+// Layout in HBM (one context, N = max_objects slots):
+//   pos      float2[N]      last-known position per object id (Sec. 2.2)
+//   stamp    u64[N]         (update epoch << 32 | index) of the winning update;
+//                           0 = object never updated (absent)
+//   keysA/B  u64[N]         radix-sort ping-pong: (morton30 << 32) | id, bit 62
+//                           set for absent slots so they sort last
+//   skey/sid u32[N]         Morton-sorted keys and ids of present objects
+//   sxy      float2[N]      positions in Morton-sorted order (SoA-by-record,
+//                           Sec. 4.4 structure of vectors)
+//   leaf_lo/hi u32[L]       Morton interval [lo, hi] of each non-empty leaf
+//   leaf_beg u32[L+1]       first sorted object of each leaf (cell boundary
+//                           table, Sec. 4.4)
+//   per query, per subquery and per leaf work arrays (see mqr_api.cu)
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace mqr {
+
+constexpr int kLevels = 15;                 // l_max: 15 bits per axis, 30-bit keys
+constexpr uint32_t kCells = 1u << kLevels;  // cells per axis of the l_max grid
+constexpr uint32_t kAbsentKey = 1u << 30;   // key of an absent slot (sorts last)
+
+// Sticky error bits reported through Info::err.
+constexpr unsigned long long kErrTimeout = 1ull;   // a bounded wait gave up
+constexpr unsigned long long kErrBadId = 2ull;     // update id >= max_objects
+constexpr unsigned long long kErrInternal = 4ull;  // an index left its range
+
+// Device-side counters of one tick (zeroed at the start of every tick).
+struct Info {
+    unsigned long long n_present;
+    unsigned long long n_leaves;
+    unsigned long long max_level;
+    unsigned long long n_sub;       // subquery records (intersecting + covering runs)
+    unsigned long long n_sub_i;     // intersecting subqueries
+    unsigned long long n_sub_c;     // covering subqueries counted per leaf
+    unsigned long long n_runs;      // covering runs
+    unsigned long long n_tests;     // containment tests of the filter
+    unsigned long long n_items;     // filter work items
+    unsigned long long n_words;     // bitmap words
+    unsigned long long n_results;   // R
+    unsigned long long n_results_cov;
+    unsigned long long err;
+    unsigned long long pad[3];
+};
+
+// Capacities of the growable per-tick buffers (host-chosen, passed by value).
+struct Caps {
+    unsigned long long sub;      // subquery records
+    unsigned long long sub_i;    // intersecting subqueries (isub list)
+    unsigned long long words;    // bitmap words
+    unsigned long long out;      // output elements (pairs / ids / bitmap words)
+};
+
+// ---------------------------------------------------------------------------
+// Cell function and Morton codes (Alg. 1 GPUcalculateMortonHash)
+// ---------------------------------------------------------------------------
+// i = min(floor((v - lo) * scale), 2^15 - 1), NaN and negatives to 0; the two
+// roundings are explicit so that objects and query corners share one
+// monotone map (exact containment follows from monotonicity).
+__device__ __forceinline__ uint32_t cell_of(float v, float lo, float scale) {
+    float t = __fmul_rn(__fsub_rn(v, lo), scale);
+    if (!(t >= 0.0f)) return 0u;
+    if (t >= 32767.0f) return kCells - 1;
+    return (uint32_t)t;
+}
+
+// Spread the 15 low bits of v to the even bit positions.
+__host__ __device__ __forceinline__ uint32_t spread15(uint32_t v) {
+    v &= 0x7fffu;
+    v = (v | (v << 8)) & 0x00ff00ffu;
+    v = (v | (v << 4)) & 0x0f0f0f0fu;
+    v = (v | (v << 2)) & 0x33333333u;
+    v = (v | (v << 1)) & 0x55555555u;
+    return v;
+}
+__host__ __device__ __forceinline__ uint32_t compact15(uint32_t v) {
+    v &= 0x55555555u;
+    v = (v | (v >> 1)) & 0x33333333u;
+    v = (v | (v >> 2)) & 0x0f0f0f0fu;
+    v = (v | (v >> 4)) & 0x00ff00ffu;
+    v = (v | (v >> 8)) & 0x0000ffffu;
+    return v;
+}
+// x index in the even bits, y index in the odd bits.
+__host__ __device__ __forceinline__ uint32_t morton2(uint32_t i, uint32_t j) {
+    return spread15(i) | (spread15(j) << 1);
+}
+
+// Depth of the deepest quadtree node containing both keys (0..15).
+__device__ __forceinline__ uint32_t shared_depth(uint32_t a, uint32_t b) {
+    uint32_t x = a ^ b;
+    return x == 0u ? 15u : (uint32_t)(__clz(x) - 2) >> 1;
+}
+
+// ---------------------------------------------------------------------------
+// Warp / block scans
+// ---------------------------------------------------------------------------
+template <typename T>
+__device__ __forceinline__ T warp_incl_scan(T v) {
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        T u = __shfl_up_sync(0xffffffffu, v, d);
+        if (lane >= d) v += u;
+    }
+    return v;
+}
+
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v) {
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) v += __shfl_xor_sync(0xffffffffu, v, d);
+    return v;
+}
+
+// Exclusive scan over the block (NT threads); *total receives the sum.
+// smem: at least NT/32 + 1 elements.  Contains __syncthreads.
+template <int NT, typename T>
+__device__ __forceinline__ T block_excl_scan(T v, T *total, T *smem) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    T inc = warp_incl_scan(v);
+    if (lane == 31) smem[warp] = inc;
+    __syncthreads();
+    if (warp == 0) {
+        T s = lane < NT / 32 ? smem[lane] : T(0);
+        T si = warp_incl_scan(s);
+        if (lane < NT / 32) smem[lane] = si - s;
+        if (lane == NT / 32 - 1) smem[NT / 32] = si;
+    }
+    __syncthreads();
+    T res = smem[warp] + inc - v;
+    *total = smem[NT / 32];
+    __syncthreads();
+    return res;
+}
+
+// ---------------------------------------------------------------------------
+// Decoupled look-back for single-pass scans.  A status word packs a 2-bit
+// flag (1 = tile aggregate, 2 = inclusive prefix) above the value.  Waits are
+// bounded by a wall-clock deadline; on expiry the kernel records kErrTimeout
+// and carries on with a partial sum (its output is then discarded by the host).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+constexpr unsigned long long kWaitNs = 2000000000ull;  // 2 s
+
+template <typename T> struct StatusBits;
+template <> struct StatusBits<uint32_t> {
+    static constexpr uint32_t kShift = 30, kMask = (1u << 30) - 1;
+};
+template <> struct StatusBits<unsigned long long> {
+    static constexpr unsigned kShift = 62;
+    static constexpr unsigned long long kMask = (1ull << 62) - 1;
+};
+
+__device__ __forceinline__ uint32_t status_load(const uint32_t *p) {
+    return *(const volatile uint32_t *)p;
+}
+__device__ __forceinline__ unsigned long long status_load(const unsigned long long *p) {
+    return *(const volatile unsigned long long *)p;
+}
+__device__ __forceinline__ void status_store(uint32_t *p, uint32_t v) { atomicExch(p, v); }
+__device__ __forceinline__ void status_store(unsigned long long *p, unsigned long long v) { atomicExch(p, v); }
+
+// Called by ONE thread of tile `tile`: publishes `agg`, returns the exclusive
+// prefix of all earlier tiles, then publishes the inclusive prefix.
+template <typename T>
+__device__ T lookback(T *status, uint32_t tile, T agg, unsigned long long *err) {
+    using B = StatusBits<T>;
+    if (tile == 0) {
+        status_store(status, (T(2) << B::kShift) | agg);
+        return T(0);
+    }
+    status_store(status + tile, (T(1) << B::kShift) | agg);
+    T sum = 0;
+    long j = (long)tile - 1;
+    unsigned long long t0 = 0;
+    unsigned spins = 0;
+    while (j >= 0) {
+        T v = status_load(status + j);
+        T flag = v >> B::kShift;
+        if (flag == 0) {
+            if ((++spins & 63u) == 0) {
+                unsigned long long now = global_ns();
+                if (t0 == 0) t0 = now;
+                else if (now - t0 > kWaitNs) { atomicOr(err, kErrTimeout); break; }
+            }
+            continue;
+        }
+        sum += v & B::kMask;
+        if (flag == 2) break;
+        --j;
+    }
+    status_store(status + tile, (T(2) << B::kShift) | (sum + agg));
+    return sum;
+}
+
+__device__ __forceinline__ uint32_t lanemask_lt() {
+    uint32_t m;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+    return m;
+}
+
+// ---------------------------------------------------------------------------
+// Launchers (host functions; all enqueue on `st`)
+// ---------------------------------------------------------------------------
+// a1: apply updates, last occurrence wins.
+void launch_apply_updates(cudaStream_t st, const uint32_t *ids, const float2 *xy, uint32_t n,
+                          uint32_t nmax, unsigned long long epoch, unsigned long long *stamp,
+                          float2 *pos, unsigned long long *err);
+
+// a2: Morton keys of every slot + digit histograms of the 4 sort passes.
+void launch_morton_keys(cudaStream_t st, const float2 *pos, const unsigned long long *stamp,
+                        uint32_t nmax, float x0, float y0, float sx, float sy,
+                        unsigned long long *keys, uint32_t *hist4x256, Info *info);
+
+// a3: one onesweep pass over n u64 keys, 8-bit digit at `shift`.  The final
+// pass of the object sort (`final_obj`) writes skey/sid/sxy instead of `out`.
+constexpr int kSortThreads = 256, kSortItems = 16, kSortTile = kSortThreads * kSortItems;
+void launch_onesweep_pass(cudaStream_t st, const unsigned long long *in, unsigned long long *out,
+                          uint32_t n, int shift, const uint32_t *hist256, uint32_t *status,
+                          uint32_t *tile_counter, unsigned long long *err, bool final_obj,
+                          const float2 *pos, uint32_t *skey, uint32_t *sid, float2 *sxy);
+// Histograms (nd digit passes at shifts[]) of n u64 keys, for generic sorts.
+void launch_key_histograms(cudaStream_t st, const unsigned long long *keys, uint32_t n,
+                           const int *shifts_host, int nd, uint32_t *hist);
+
+// a4: leaves.  level_mode: 0 = quadtree (capacity rule), 1 = uniform grid at
+// `grid_level`.  Writes leaf_lo/leaf_hi/leaf_beg and Info::n_leaves/max_level.
+constexpr int kLeafThreads = 256, kLeafTile = 2048, kLeafCapSmem = 16384;
+void launch_build_leaves(cudaStream_t st, const uint32_t *skey, uint32_t nmax, uint32_t cap,
+                         int uniform_grid, uint32_t grid_level, uint8_t *mk_a, uint8_t *mk_b,
+                         uint32_t *status, uint32_t *tile_counter, uint32_t *leaf_lo,
+                         uint32_t *leaf_hi, uint32_t *leaf_beg, uint32_t *leaf_nsub, Info *info);
+
+// a5 + a6: per-query subquery counts + exclusive scan (sub_off[Q+1]), and the
+// per-leaf intersecting-subquery histogram leaf_nsub.
+constexpr int kQueryThreads = 256, kQueryItems = 4, kQueryTile = kQueryThreads * kQueryItems;
+void launch_query_count(cudaStream_t st, const float4 *rects, uint32_t Q, float x0, float y0,
+                        float sx, float sy, const uint32_t *leaf_lo, const uint32_t *leaf_hi,
+                        const uint32_t *leaf_beg, int covering, uint32_t *sub_off,
+                        uint32_t *leaf_nsub, uint32_t *status, uint32_t *tile_counter, Info *info);
+
+// a8: scans over leaves -> leaf_sub_off, leaf_word_off, leaf_item_off, cursor.
+constexpr int kLeafScanThreads = 256, kLeafScanItems = 8, kLeafScanTile = kLeafScanThreads * kLeafScanItems;
+void launch_leaf_scan(cudaStream_t st, uint32_t nmax, const uint32_t *leaf_beg,
+                      const uint32_t *leaf_nsub, uint32_t *leaf_sub_off, uint32_t *leaf_word_off,
+                      uint32_t *leaf_item_off, uint32_t *leaf_cursor, uint32_t *status3,
+                      uint32_t *tile_counter, Info *info);
+
+// a7 (+ a8 scatter): write subquery records, covering runs, isub lists.
+void launch_query_write(cudaStream_t st, const float4 *rects, uint32_t Q, float x0, float y0,
+                        float sx, float sy, const uint32_t *leaf_lo, const uint32_t *leaf_hi,
+                        const uint32_t *leaf_beg, int covering, const uint32_t *sub_off,
+                        const uint32_t *leaf_sub_off, const uint32_t *leaf_word_off,
+                        uint32_t *leaf_cursor, uint32_t *sub_q, uint32_t *sub_leaf,
+                        uint32_t *sub_len, uint32_t *sub_res, uint32_t *sub_bm, uint32_t *isub,
+                        Caps caps, Info *info);
+
+// a10: filtering into bitmap words + per-subquery counts.
+void launch_filter(cudaStream_t st, int num_sms, const float4 *rects, const float2 *sxy,
+                   const uint32_t *leaf_beg, const uint32_t *leaf_sub_off,
+                   const uint32_t *leaf_word_off, const uint32_t *leaf_item_off,
+                   const uint32_t *isub, const uint32_t *sub_q, uint32_t *sub_res,
+                   uint32_t *bitmap, Caps caps, const Info *info);
+
+// a11: result offsets out_off[k] (u64, exclusive) over subquery records.
+constexpr int kResThreads = 256, kResItems = 8, kResTile = kResThreads * kResItems;
+void launch_result_scan(cudaStream_t st, unsigned long long sub_cap, const uint32_t *sub_res,
+                        const uint32_t *sub_leaf, unsigned long long *out_off,
+                        unsigned long long *status, uint32_t *tile_counter, Caps caps, Info *info);
+
+// a12 + a13: emit results in query-major order.
+enum EmitKind { kEmitPairs = 0, kEmitIds = 1, kEmitBitmap = 2, kEmitKeys64 = 3 };
+void launch_emit(cudaStream_t st, int num_sms, int emit_kind, const uint32_t *sub_q,
+                 const uint32_t *sub_leaf, const uint32_t *sub_len, const uint32_t *sub_bm,
+                 const unsigned long long *out_off, const uint32_t *leaf_beg,
+                 const uint32_t *sid, const uint32_t *bitmap, void *out, uint32_t bitmap_words_per_row,
+                 Caps caps, const Info *info);
+
+// Per-query offsets from subquery offsets: off[q] = out_off[sub_off[q]].
+void launch_query_offsets(cudaStream_t st, uint32_t Q, const uint32_t *sub_off,
+                          const unsigned long long *out_off, unsigned long long *offsets,
+                          Caps caps, const Info *info);
+
+// (qidx << 32 | id) keys -> pairs (qidx, id) or ids.
+void launch_keys_to_output(cudaStream_t st, const unsigned long long *keys, uint64_t n,
+                           int as_pairs, void *out);
+
+}  // namespace mqr

@@ -1,0 +1,277 @@
+"""Thin ctypes binding of libmqr (include/mqr.h): same names, argument
+marshalling only.  Every step of the join runs in the CUDA library; this
+module never computes results itself.  If libmqr.so is missing the functions
+raise -- there is no fallback.
+
+Device arguments accept torch CUDA tensors (their data_ptr is passed) or raw
+integer device pointers.  Host-buffer entry points accept numpy arrays.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libmqr.so")
+
+MQR_OK, MQR_ERR_INVALID_ARG, MQR_ERR_OOM, MQR_ERR_CAPACITY, MQR_ERR_CUDA, MQR_ERR_TIMEOUT, MQR_ERR_INTERNAL = range(7)
+MQR_OUT_PAIRS, MQR_OUT_PAIRS_SORTED, MQR_OUT_CSR, MQR_OUT_CSR_SORTED, MQR_OUT_BITMAP, MQR_OUT_COUNT = range(6)
+MQR_INDEX_QUADTREE, MQR_INDEX_UNIFORM_GRID = 0, 1
+
+KINDS = {"pairs": MQR_OUT_PAIRS, "pairs_sorted": MQR_OUT_PAIRS_SORTED, "csr": MQR_OUT_CSR,
+         "csr_sorted": MQR_OUT_CSR_SORTED, "bitmap": MQR_OUT_BITMAP, "count": MQR_OUT_COUNT}
+
+# Every symbol include/mqr.h declares.
+EXPORTS = ["mqr_config_default", "mqr_create", "mqr_create_ex", "mqr_apply_updates",
+           "mqr_apply_updates_host", "mqr_tick", "mqr_tick_host", "mqr_get_stats", "mqr_get_leaves",
+           "mqr_get_sorted", "mqr_last_error", "mqr_destroy"]
+
+
+class MqrError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__("mqr status %d: %s" % (status, msg))
+        self.status = status
+
+
+class mqr_rect(ctypes.Structure):
+    _fields_ = [("xmin", ctypes.c_float), ("ymin", ctypes.c_float),
+                ("xmax", ctypes.c_float), ("ymax", ctypes.c_float)]
+
+
+class mqr_config(ctypes.Structure):
+    _fields_ = [("max_objects", ctypes.c_uint32), ("leaf_cap", ctypes.c_uint32),
+                ("index_kind", ctypes.c_int32), ("grid_level", ctypes.c_uint32),
+                ("covering", ctypes.c_int32), ("reserved", ctypes.c_int32 * 3)]
+
+
+class mqr_stats(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_uint64) for n in (
+        "n_objects", "n_queries", "n_leaves", "max_level", "n_sub_intersecting", "n_sub_covering",
+        "n_covering_runs", "n_tests", "n_filter_items", "n_bitmap_words", "n_results",
+        "n_results_covering", "n_retries")]
+
+    def as_dict(self):
+        return {n: int(getattr(self, n)) for n, _ in self._fields_}
+
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load libmqr.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError("libmqr.so is not built (call __graft_entry__.build()); "
+                           "there is no CPU fallback")
+    lib = ctypes.CDLL(path)
+    P, u32, u64, i32 = ctypes.c_void_p, ctypes.c_uint32, ctypes.c_uint64, ctypes.c_int
+    pctx = ctypes.POINTER(P)
+    sig = {
+        "mqr_config_default": ([ctypes.POINTER(mqr_config)], i32),
+        "mqr_create": ([mqr_rect, u32, u32, pctx], i32),
+        "mqr_create_ex": ([mqr_rect, ctypes.POINTER(mqr_config), P, pctx], i32),
+        "mqr_apply_updates": ([P, P, P, u32], i32),
+        "mqr_apply_updates_host": ([P, P, P, u32], i32),
+        "mqr_tick": ([P, P, u32, i32, P, u64, ctypes.POINTER(u64), P], i32),
+        "mqr_tick_host": ([P, P, u32, i32, P, u64, ctypes.POINTER(u64), P], i32),
+        "mqr_get_stats": ([P, ctypes.POINTER(mqr_stats)], i32),
+        "mqr_get_leaves": ([P, P, u64, ctypes.POINTER(u64)], i32),
+        "mqr_get_sorted": ([P, P, P, u64, ctypes.POINTER(u64)], i32),
+        "mqr_last_error": ([], ctypes.c_char_p),
+        "mqr_destroy": ([P], None),
+    }
+    for name, (args, res) in sig.items():
+        f = getattr(lib, name)
+        f.argtypes = args
+        f.restype = res
+    _lib = lib
+    return lib
+
+
+def _ptr(x):
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    if hasattr(x, "data_ptr"):
+        if not x.is_cuda:
+            raise ValueError("expected a CUDA tensor")
+        if not x.is_contiguous():
+            raise ValueError("expected a contiguous tensor")
+        return x.data_ptr()
+    raise TypeError("expected a torch CUDA tensor or an int device pointer")
+
+
+def _hptr(a):
+    if a is None:
+        return None
+    if not isinstance(a, np.ndarray) or not a.flags["C_CONTIGUOUS"]:
+        raise ValueError("expected a C-contiguous numpy array")
+    return a.ctypes.data
+
+
+def _check(status):
+    if status != MQR_OK:
+        raise MqrError(status, load().mqr_last_error().decode())
+    return status
+
+
+# -- same names as the C ABI -------------------------------------------------
+def mqr_config_default():
+    cfg = mqr_config()
+    _check(load().mqr_config_default(ctypes.byref(cfg)))
+    return cfg
+
+
+def mqr_create(bounds, leaf_cap, max_objects):
+    ctx = ctypes.c_void_p()
+    _check(load().mqr_create(mqr_rect(*bounds), leaf_cap, max_objects, ctypes.byref(ctx)))
+    return ctx
+
+
+def mqr_create_ex(bounds, cfg: mqr_config, cuda_stream=None):
+    ctx = ctypes.c_void_p()
+    _check(load().mqr_create_ex(mqr_rect(*bounds), ctypes.byref(cfg), cuda_stream, ctypes.byref(ctx)))
+    return ctx
+
+
+def mqr_apply_updates(ctx, ids_dev, xy_dev, n=None):
+    n = int(ids_dev.shape[0]) if n is None else n
+    _check(load().mqr_apply_updates(ctx, _ptr(ids_dev), _ptr(xy_dev), n))
+
+
+def mqr_apply_updates_host(ctx, ids_host, xy_host):
+    n = int(ids_host.shape[0])
+    _check(load().mqr_apply_updates_host(ctx, _hptr(ids_host), _hptr(xy_host), n))
+
+
+def mqr_tick(ctx, rects_dev, Q, kind, out_dev, out_capacity_bytes, offsets_dev=None, check=True):
+    """Returns (status, out_count)."""
+    cnt = ctypes.c_uint64(0)
+    st = load().mqr_tick(ctx, _ptr(rects_dev), Q, kind, _ptr(out_dev), out_capacity_bytes,
+                         ctypes.byref(cnt), _ptr(offsets_dev))
+    if check and st not in (MQR_OK, MQR_ERR_CAPACITY):
+        _check(st)
+    return st, int(cnt.value)
+
+
+def mqr_tick_host(ctx, rects_host, Q, kind, out_host, out_capacity_bytes, offsets_host=None, check=True):
+    cnt = ctypes.c_uint64(0)
+    st = load().mqr_tick_host(ctx, _hptr(rects_host), Q, kind, _hptr(out_host), out_capacity_bytes,
+                              ctypes.byref(cnt), _hptr(offsets_host))
+    if check and st not in (MQR_OK, MQR_ERR_CAPACITY):
+        _check(st)
+    return st, int(cnt.value)
+
+
+def mqr_get_stats(ctx):
+    s = mqr_stats()
+    _check(load().mqr_get_stats(ctx, ctypes.byref(s)))
+    return s.as_dict()
+
+
+def mqr_get_leaves(ctx):
+    n = ctypes.c_uint64(0)
+    st = load().mqr_get_leaves(ctx, None, 0, ctypes.byref(n))
+    if st not in (MQR_OK, MQR_ERR_CAPACITY):
+        _check(st)
+    out = np.zeros((int(n.value), 4), np.uint32)
+    if n.value:
+        _check(load().mqr_get_leaves(ctx, out.ctypes.data, out.shape[0], ctypes.byref(n)))
+    return out
+
+
+def mqr_get_sorted(ctx):
+    n = ctypes.c_uint64(0)
+    st = load().mqr_get_sorted(ctx, None, None, 0, ctypes.byref(n))
+    if st not in (MQR_OK, MQR_ERR_CAPACITY):
+        _check(st)
+    keys = np.zeros(int(n.value), np.uint32)
+    ids = np.zeros(int(n.value), np.uint32)
+    if n.value:
+        _check(load().mqr_get_sorted(ctx, keys.ctypes.data, ids.ctypes.data, keys.shape[0], ctypes.byref(n)))
+    return keys, ids
+
+
+def mqr_last_error():
+    return load().mqr_last_error().decode()
+
+
+def mqr_destroy(ctx):
+    if ctx:
+        load().mqr_destroy(ctx)
+
+
+# -- convenience wrapper ------------------------------------------------------
+class Index:
+    """Owns one mqr context; torch tensors in, torch tensors out."""
+
+    def __init__(self, bounds=(0.0, 0.0, 1.0, 1.0), leaf_cap=128, max_objects=1 << 20,
+                 index_kind=MQR_INDEX_QUADTREE, grid_level=8, covering=True, stream=None):
+        import torch
+        self._torch = torch
+        cfg = mqr_config_default()
+        cfg.max_objects = max_objects
+        cfg.leaf_cap = min(int(leaf_cap), 0xFFFFFFFF)
+        cfg.index_kind = index_kind
+        cfg.grid_level = grid_level
+        cfg.covering = 1 if covering else 0
+        self.max_objects = max_objects
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        self.ctx = mqr_create_ex(bounds, cfg, ctypes.c_void_p(self.stream.cuda_stream))
+        self._out = None
+
+    def close(self):
+        if self.ctx:
+            mqr_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def apply_updates(self, ids, xy):
+        mqr_apply_updates(self.ctx, ids, xy, int(ids.shape[0]))
+
+    def tick(self, rects, kind="pairs"):
+        """Answer the queries; returns (result, offsets) as CUDA tensors.
+        pairs/pairs_sorted -> int32[R, 2] (qidx, id); csr/csr_sorted -> int32[R];
+        bitmap -> int32[Q, ceil(max_objects/32)]; count -> None.  Values are
+        uint32 reinterpreted as int32."""
+        torch = self._torch
+        k = KINDS[kind]
+        Q = int(rects.shape[0])
+        offs = torch.empty(Q + 1, dtype=torch.int64, device=rects.device)
+        if k == MQR_OUT_BITMAP:
+            W = (self.max_objects + 31) // 32
+            out = torch.empty((Q, W), dtype=torch.int32, device=rects.device)
+            mqr_tick(self.ctx, rects, Q, k, out, out.numel() * 4, offs)
+            return out, offs
+        if k == MQR_OUT_COUNT:
+            mqr_tick(self.ctx, rects, Q, k, None, 0, offs)
+            return None, offs
+        elem = 8 if k in (MQR_OUT_PAIRS, MQR_OUT_PAIRS_SORTED) else 4
+        if self._out is None:
+            self._out = torch.empty(max(1 << 16, 8 * Q) * 2, dtype=torch.int32, device=rects.device)
+        st, cnt = mqr_tick(self.ctx, rects, Q, k, self._out, self._out.numel() * 4, offs)
+        if st == MQR_ERR_CAPACITY:
+            self._out = torch.empty(max(cnt * elem // 4 + 1024, 1), dtype=torch.int32, device=rects.device)
+            st, cnt = mqr_tick(self.ctx, rects, Q, k, self._out, self._out.numel() * 4, offs)
+            _check(st)
+        res = self._out[: cnt * elem // 4]
+        return (res.view(cnt, 2) if elem == 8 else res), offs
+
+    def stats(self):
+        return mqr_get_stats(self.ctx)
+
+    def leaves(self):
+        return mqr_get_leaves(self.ctx)
+
+    def sorted_objects(self):
+        return mqr_get_sorted(self.ctx)
