@@ -1,0 +1,471 @@
+"""Benchmark: repeated range queries over moving objects on GB300.
+
+One step = one tick of the whole hot path: the tick's position updates of
+every object (mqr_apply_updates) followed by the spatial join of the tick's
+queries through the PR-quadtree (mqr_tick), pair-list output.
+
+Default workload (N=1): 4,000,000 objects, 90% in 64 Gaussian hotspots (sigma
+log-uniform 0.002-0.02) and 10% uniform, random walk sigma 0.0005 with
+hotspot drift 0.001/tick, 400,000 square queries per tick of side
+log-uniform 0.0005-0.005 centred on objects, leaf_cap 128, pairs output.
+
+Prints ONE JSON line (rank 0).  `--impl reference` times the CPU oracle
+instead (bounded samples of the same workload).  Multi-GPU (torchrun): every
+rank runs an independent replica world (weak scaling, no collective on the
+data path); a barrier brackets the timed region and the max over ranks is
+reported.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "traffic.json")
+FALLBACK_HBM_GBS = 6800.0
+
+WORKLOADS = {
+    "hotspot4m": dict(kind="hotspot", n=4_000_000, q=400_000, cap=128,
+                      desc="hotspot-4M: 4,000,000 objects (90% in 64 Gaussian hotspots, sigma log-uniform "
+                           "0.002-0.02; 10% uniform), random walk sigma 0.0005, hotspot drift 0.001/tick, "
+                           "400,000 square queries/tick of side log-uniform 0.0005-0.005 centred on objects, "
+                           "leaf_cap 128 (fixed), pair-list output"),
+    "uniform1m": dict(kind="uniform", n=1_000_000, q=100_000, cap=128,
+                      desc="uniform-1M: 1,000,000 uniform objects, random walk sigma 0.0005, 100,000 queries/tick "
+                           "of side 0.002 centred on objects, leaf_cap 128, pair-list output"),
+    "uniform16k": dict(kind="small", n=16384, q=1024, cap=64,
+                       desc="uniform-16K: 16,384 uniform objects, 1,024 queries of side 0.01, leaf_cap 64"),
+}
+
+
+def log(*a):
+    print(*a, file=sys.stderr, flush=True)
+
+
+# ----------------------------------------------------------------------------
+# workload
+# ----------------------------------------------------------------------------
+def make_world(name, seed):
+    from paper_1411_3212_gb300 import workloads
+    w = WORKLOADS[name]
+    if w["kind"] == "hotspot":
+        return workloads.HotspotWalk(n=w["n"], q=w["q"], seed=seed)
+    if w["kind"] == "uniform":
+        return workloads.UniformWalk(n=w["n"], q=w["q"], seed=seed)
+
+    class Small:
+        def __init__(self):
+            self.t = 0
+
+        def next_tick(self):
+            self.t += 1
+            return workloads.uniform_small(seed=seed + self.t)
+    return Small()
+
+
+def gen_ticks(name, seed, count):
+    world = make_world(name, seed)
+    return [world.next_tick() for _ in range(count)]
+
+
+# ----------------------------------------------------------------------------
+# algorithmic bytes per phase (the data the method must move)
+# ----------------------------------------------------------------------------
+def phase_bytes(s, n_updates, nmax):
+    N, Q = s["n_objects"], s["n_queries"]
+    R, W = s["n_results"], s["n_bitmap_words"]
+    S, SI = s["n_sub_intersecting"] + s["n_covering_runs"], s["n_sub_intersecting"]
+    return {
+        "updates": 20 * n_updates,                       # read id+xy, write xy
+        "keys": 16 * nmax,                               # read xy, write key
+        "sort": 3 * 16 * nmax + 32 * nmax,               # 3 x (read+write 8B), last: read 8B + gather 8B + write 16B
+        "leaves": 4 * N + 12 * s["n_leaves"],
+        "query_blocks": 32 * Q + 24 * s["n_pairs"],     # rects in; cells, offsets, pair records out
+        "candidates": 8 * s["n_candidates"] + 16 * S,   # leaf intervals in; subquery records out
+        "group": 16 * s["n_leaves"] + 4 * S + 8 * SI,
+        "filter": 8 * s["n_filter_loads"] + 24 * SI + 4 * W,
+        "result_scan": 12 * S,
+        "emit": 12 * R + 4 * W + 24 * S,                 # write 8B pair + read 4B id per result
+    }
+
+
+def source_hash():
+    h = hashlib.sha256()
+    for f in sorted(os.listdir(os.path.join(ROOT, "paper_1411_3212_gb300", "csrc"))):
+        with open(os.path.join(ROOT, "paper_1411_3212_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def read_peaks():
+    try:
+        with open(PEAKS_FILE) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+def read_traffic(kernel):
+    """Per-launch DRAM bytes of `kernel` from a committed ncu summary, if the
+    CUDA sources have not changed since it was taken."""
+    try:
+        with open(TRAFFIC_FILE) as f:
+            t = json.load(f)
+        e = t.get(kernel)
+        if e and e.get("source_hash") == source_hash() and e.get("workload") == "hotspot4m":
+            return float(e["dram_bytes_per_launch"])
+    except Exception:
+        pass
+    return None
+
+
+# ----------------------------------------------------------------------------
+# clocks sampled during the timed region
+# ----------------------------------------------------------------------------
+class Clocks:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.idx = gpu_index
+        self.p = None
+
+    def start(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.idx), "--query-gpu=" + self.FIELDS,
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return None
+        self.p.terminate()
+        try:
+            out, _ = self.p.communicate(timeout=5)
+        except Exception:
+            self.p.kill()
+            out, _ = self.p.communicate()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ----------------------------------------------------------------------------
+# distributed helpers (replicas only)
+# ----------------------------------------------------------------------------
+def dist_setup(n_gpus):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        if torch.cuda.is_available():
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend=backend)
+        return dist, rank, world, local
+    return None, rank, world, local
+
+
+def barrier(dist, dev):
+    import torch
+    if dist is not None:
+        dist.barrier()
+    if dev is not None:
+        torch.cuda.synchronize()
+
+
+def reduce_max(dist, x, dev):
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.float64, device=dev if dev is not None else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ----------------------------------------------------------------------------
+# CPU baseline: the oracle as it stands, on a bounded sample
+# ----------------------------------------------------------------------------
+def oracle_sample_rate(st, rects, q_total, sample_q, cell):
+    import oracle
+    rng = np.random.default_rng(1234)
+    pick = np.sort(rng.choice(rects.shape[0], size=min(sample_q, rects.shape[0]), replace=False))
+    t0 = time.perf_counter()
+    oracle.join_grid(st, rects[:0], cell_side=cell)         # grid build only
+    t1 = time.perf_counter()
+    oracle.join_grid(st, rects[pick], cell_side=cell)       # build + sampled queries
+    t2 = time.perf_counter()
+    build = t1 - t0
+    per_query = max((t2 - t1) - build, 0.0) / len(pick)
+    tick = build + per_query * q_total
+    return q_total / tick, t2 - t0, len(pick)
+
+
+def cpu_baseline(ticks, name, nmax, sample_q):
+    import oracle
+    st = oracle.State(nmax)
+    for t in ticks:
+        st.apply_updates(t.ids, t.xy)
+    t = ticks[-1]
+    val, secs, nq = oracle_sample_rate(st, t.rects, t.rects.shape[0], sample_q, cell=0.002)
+    return {"value": val, "unit": "queries/s", "cores": 1, "kind": "oracle",
+            "sample": "one tick of %s: single-threaded C uniform-grid join (cell 0.002); full grid build "
+                      "over all %d objects + %d of the %d queries (random sample), per-tick time "
+                      "extrapolated as build + per-query time x all queries; %.1f s of CPU work"
+                      % (name, nmax, nq, t.rects.shape[0], secs)}
+
+
+def run_reference(args, name):
+    """--impl reference: the CPU oracle on bounded samples of the workload."""
+    import oracle
+    dist, rank, world, local = dist_setup(args.gpus)
+    if rank != 0:
+        return
+    w = WORKLOADS[name]
+    ticks = gen_ticks(name, 0, args.warmup + args.steps)
+    st = oracle.State(w["n"])
+    sample_q = args.ref_sample
+    rates, times = [], []
+    for i, t in enumerate(ticks):
+        st.apply_updates(t.ids, t.xy)
+        rate, secs, nq = oracle_sample_rate(st, t.rects, t.rects.shape[0], sample_q, cell=0.002)
+        if i >= args.warmup:
+            rates.append(rate)
+            times.append(w["q"] / rate)
+    value = w["q"] * len(times) / sum(times)
+    ms = 1000.0 * sum(times) / len(times)
+    sample = ("per step: the tick's updates applied to the oracle state, then a single-threaded C "
+              "uniform-grid join (cell 0.002) of a random %d of the %d queries after a full grid build; "
+              "step time extrapolated to all queries" % (sample_q, w["q"]))
+    line = {"impl": "reference", "metric": "queries/s at 4M skewed objects" if name == "hotspot4m" else "queries/s",
+            "value": value, "unit": "queries/s", "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": w["desc"], "objects": w["n"], "queries_per_tick": w["q"],
+                       "leaf_cap": w["cap"], "parallelism": "replicas"},
+            "cpu_baseline": {"value": value, "unit": "queries/s", "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": "queries/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ----------------------------------------------------------------------------
+# GPU arm
+# ----------------------------------------------------------------------------
+def run_gpu(args, name):
+    import torch
+    from paper_1411_3212_gb300 import mqr
+
+    dist, rank, world, local = dist_setup(args.gpus)
+    dev = torch.device("cuda", local if world > 1 else 0)
+    torch.cuda.set_device(dev)
+    w = WORKLOADS[name]
+    nmax, Q = w["n"], w["q"]
+
+    t_gen = time.perf_counter()
+    ticks = gen_ticks(name, 1000 * rank, args.warmup + args.steps)
+    log("rank %d: generated %d ticks in %.1f s" % (rank, len(ticks), time.perf_counter() - t_gen))
+
+    ids_d = torch.from_numpy(ticks[0].ids.view(np.int32)).to(dev)
+    xy_d = [torch.from_numpy(t.xy).to(dev) for t in ticks]
+    rect_d = [torch.from_numpy(t.rects).to(dev) for t in ticks]
+    flush = torch.empty(args.flush_mb * (1 << 20) // 4, dtype=torch.int32, device=dev)
+
+    idx = mqr.Index(bounds=(0.0, 0.0, 1.0, 1.0), leaf_cap=w["cap"], max_objects=nmax)
+    kind = mqr.KINDS[args.kind]
+    elem = 8 if kind in (mqr.MQR_OUT_PAIRS, mqr.MQR_OUT_PAIRS_SORTED) else 4
+    out = torch.empty(1, dtype=torch.int32, device=dev)
+    offs = torch.empty(Q + 1, dtype=torch.int64, device=dev) if args.offsets else None
+
+    def step(i):
+        nonlocal out
+        idx.apply_updates(ids_d, xy_d[i])
+        st, cnt = mqr.mqr_tick(idx.ctx, rect_d[i], Q, kind, out, out.numel() * 4, offs)
+        if st == mqr.MQR_ERR_CAPACITY:                  # only during warm-up
+            out = torch.empty(int(cnt * elem * 1.3) // 4 + 1024, dtype=torch.int32, device=dev)
+            st, cnt = mqr.mqr_tick(idx.ctx, rect_d[i], Q, kind, out, out.numel() * 4, offs)
+        mqr._check(st)
+        return cnt
+
+    for i in range(args.warmup):
+        step(i)
+    torch.cuda.synchronize()
+
+    idx.set_timing(True)
+    clocks = Clocks(local if world > 1 else 0)
+    stream = torch.cuda.current_stream()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    bytes_acc = {}
+    results = 0
+    clocks.start()
+    barrier(dist, dev)
+    t_wall = time.perf_counter()
+    for k in range(args.steps):
+        i = args.warmup + k
+        flush.zero_()                                   # L2 flush between timed steps
+        evs[k][0].record(stream)
+        results += step(i)
+        evs[k][1].record(stream)
+        s = idx.stats()
+        for ph, b in phase_bytes(s, nmax, nmax).items():
+            bytes_acc[ph] = bytes_acc.get(ph, 0) + b
+    barrier(dist, dev)
+    wall = time.perf_counter() - t_wall
+    clk = clocks.stop()
+    step_ms = [a.elapsed_time(b) for a, b in evs]
+    timing = idx.timing()
+    stats = idx.stats()
+    idx.set_timing(False)
+
+    total_ms = reduce_max(dist, sum(step_ms), dev)
+    mean_ms = total_ms / args.steps
+    value = world * Q * args.steps / (total_ms / 1000.0)
+
+    # roofline of the dominant kernel phase
+    kern = {p: timing["ms"][p] for p in bytes_acc if timing["launches"].get(p, 0) > 0}
+    dom = max(kern, key=kern.get)
+    launches = timing["launches"][dom]
+    per_launch_ms = timing["ms"][dom] / launches
+    per_launch_bytes = bytes_acc[dom] / launches
+    peak, peak_kind = read_peaks()
+    achieved = per_launch_bytes / (per_launch_ms / 1000.0) / 1e9
+    kernel_names = {"emit": "emit_kernel", "filter": "filter_kernel", "sort": "onesweep_kernel",
+                    "query_blocks": "query_blocks_kernel", "candidates": "candidates_kernel",
+                    "group": "leaf_scan_kernel+scatter_kernel",
+                    "leaves": "leaves_kernel", "keys": "morton_kernel", "updates": "stamp_kernel+write_winner_kernel",
+                    "result_scan": "result_scan_kernel"}
+    roofline = {"bound": "hbm", "kernel": kernel_names.get(dom, dom), "phase": dom,
+                "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "peak_source": "%s (MEASURED_PEAKS.json hbm_gbs)" % peak_kind if peak_kind == "measured" else "fallback 6.8 TB/s",
+                "traffic": read_traffic(kernel_names.get(dom, dom)),
+                "algorithmic_bytes_per_launch": per_launch_bytes, "launch_ms": per_launch_ms}
+    join = ["filter", "emit"]
+    join_ms = sum(timing["ms"][p] for p in join)
+    join_bytes = sum(bytes_acc[p] for p in join)
+    join_gbs = join_bytes / (join_ms / 1000.0) / 1e9 if join_ms > 0 else 0.0
+    phases = {p: {"ms_per_tick": timing["ms"][p] / max(timing["ticks"], 1),
+                  "launches_per_tick": timing["launches"][p] / max(timing["ticks"], 1),
+                  "GB/s": (bytes_acc[p] / (timing["ms"][p] / 1000.0) / 1e9) if p in bytes_acc and timing["ms"][p] > 0 else None}
+              for p in mqr.PHASES if timing["launches"][p] > 0}
+    gpu_launches = int(sum(timing["launches"].values()))
+
+    # end to end through the host-buffer entry points
+    e2e = None
+    if not args.no_e2e:
+        e2e = run_e2e(args, idx, ticks, kind, elem, Q, stats["n_results"], dev)
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(ticks, name, nmax, args.cpu_sample)
+
+    idx.close()
+    if rank != 0:
+        return
+    srt = sorted(step_ms)
+    line = {
+        "metric": "queries/s at 4M skewed objects" if name == "hotspot4m" else "queries/s",
+        "value": value, "unit": "queries/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": mean_ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32", "data": "synthetic",
+        "config": {"workload": w["desc"], "objects": nmax, "queries_per_tick": Q, "leaf_cap": w["cap"],
+                   "output": args.kind, "parallelism": "replicas" if world > 1 else "single-gpu",
+                   "l2": "flushed (%d MB write) between timed steps" % args.flush_mb},
+        "tick_latency_ms": {"p50": srt[len(srt) // 2], "p99": srt[min(len(srt) - 1, int(0.99 * len(srt)))],
+                            "max": srt[-1]},
+        "join_kernels": {"phases": join, "GB/s": join_gbs, "frac_of_peak": join_gbs / peak},
+        "roofline": roofline,
+        "cpu_baseline": cpu,
+        "e2e": e2e,
+        "gpu_launches": gpu_launches,
+        "clocks": clk,
+        "phases": phases,
+        "stats": stats,
+        "wall_s": wall,
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_e2e(args, idx, ticks, kind, elem, Q, r_hint, dev):
+    import torch
+    from paper_1411_3212_gb300 import mqr
+    n = ticks[0].ids.shape[0]
+    ids_h = torch.from_numpy(ticks[0].ids.view(np.int32)).pin_memory().numpy().view(np.uint32)
+    xy_h = [torch.from_numpy(t.xy).pin_memory().numpy() for t in ticks]
+    rect_h = [torch.from_numpy(t.rects).pin_memory().numpy() for t in ticks]
+    cap_elems = int(r_hint * 1.5) + 4096
+    out_h = torch.empty(cap_elems * elem // 4, dtype=torch.int32).pin_memory().numpy()
+    steps = min(args.steps, len(ticks))
+    # warm the staging buffers
+    mqr.mqr_apply_updates_host(idx.ctx, ids_h, xy_h[0])
+    mqr.mqr_tick_host(idx.ctx, rect_h[0], Q, kind, out_h, out_h.nbytes)
+    times, d2h = [], []
+    for k in range(steps):
+        t0 = time.perf_counter()
+        mqr.mqr_apply_updates_host(idx.ctx, ids_h, xy_h[k])
+        st, cnt = mqr.mqr_tick_host(idx.ctx, rect_h[k], Q, kind, out_h, out_h.nbytes)
+        times.append(time.perf_counter() - t0)
+        mqr._check(st)
+        d2h.append(cnt * elem)
+    return {"value": Q * steps / sum(times), "unit": "queries/s",
+            "h2d_bytes_per_step": int(n * 12 + Q * 16), "d2h_bytes_per_step": int(sum(d2h) / steps),
+            "ms_per_step": 1000.0 * sum(times) / steps, "steps": steps,
+            "api": "mqr_apply_updates_host + mqr_tick_host (pinned host buffers)"}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="mine", choices=["mine", "reference"])
+    ap.add_argument("--workload", default="hotspot4m", choices=sorted(WORKLOADS))
+    ap.add_argument("--kind", default="pairs", choices=["pairs", "csr", "count"])
+    ap.add_argument("--offsets", action="store_true", help="also write per-query offsets")
+    ap.add_argument("--flush-mb", type=int, default=256)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-sample", type=int, default=100000)
+    ap.add_argument("--ref-sample", type=int, default=10000)
+    args = ap.parse_args()
+    if args.warmup < 3:
+        log("warm-up raised to 3 steps")
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args, args.workload)
+    else:
+        run_gpu(args, args.workload)
+
+
+if __name__ == "__main__":
+    main()

@@ -116,7 +116,34 @@ typedef struct {
     uint64_t n_results;          /* R                                              */
     uint64_t n_results_covering; /* results coming from covering subqueries        */
     uint64_t n_retries;          /* internal buffer growths during the tick        */
+    uint64_t n_filter_loads;     /* object records loaded by the filtering kernel  */
+    uint64_t n_pairs;            /* (query, block) pairs of query splitting        */
+    uint64_t n_candidates;       /* (query, leaf) candidates classified            */
 } mqr_stats;
+
+/* Pipeline phases timed by mqr_set_timing (CUDA events on the context's
+ * stream around each phase's kernels). */
+typedef enum {
+    MQR_PHASE_UPDATES = 0,     /* position updates (Sec. 2.2)                  */
+    MQR_PHASE_KEYS = 1,        /* Morton keys + sort histograms (Alg. 1)       */
+    MQR_PHASE_SORT = 2,        /* radix sort of the objects (Alg. 1)           */
+    MQR_PHASE_LEAVES = 3,      /* quadtree / grid leaves (Alg. 1)              */
+    MQR_PHASE_QUERY_BLOCKS = 4,/* query splitting: lookup table, blocks, scan (Sec. 5.3) */
+    MQR_PHASE_GROUP = 5,       /* grouping subqueries by leaf (Sec. 5.3 sorting) */
+    MQR_PHASE_CANDIDATES = 6,  /* query splitting: candidates -> subqueries      */
+    MQR_PHASE_FILTER = 7,      /* filtering into bitmap words (Sec. 5.5)        */
+    MQR_PHASE_RESULT_SCAN = 8, /* result-count scan (Sec. 5.6)                  */
+    MQR_PHASE_EMIT = 9,        /* decoding + covering expansion (Sec. 5.6, 5.7) */
+    MQR_PHASE_OFFSETS = 10,    /* per-query offsets                             */
+    MQR_PHASE_OUTPUT_SORT = 11,/* sorted output kinds                           */
+    MQR_NUM_PHASES = 12
+} mqr_phase;
+
+typedef struct {
+    double ms[MQR_NUM_PHASES];         /* accumulated device time per phase      */
+    uint64_t launches[MQR_NUM_PHASES]; /* kernels launched per phase             */
+    uint64_t ticks;                    /* ticks accumulated                      */
+} mqr_timing;
 
 /* Fill *cfg with defaults: max_objects = 1<<20, leaf_cap = 128, quadtree,
  * grid_level = 8, covering = 1. */
@@ -185,6 +212,14 @@ mqr_status mqr_get_leaves(mqr_ctx *ctx, uint32_t *leaves_host, uint64_t cap, uin
  * the host: keys_host[k] = 30-bit Morton code at l_max = 15, ids_host[k] =
  * object id, for the *n present objects.  Either pointer may be NULL. */
 mqr_status mqr_get_sorted(mqr_ctx *ctx, uint32_t *keys_host, uint32_t *ids_host, uint64_t cap, uint64_t *n);
+
+/* Enable (1) or disable (0) per-phase timing; enabling resets the
+ * accumulators.  Timing adds two event records per phase to the stream. */
+mqr_status mqr_set_timing(mqr_ctx *ctx, int enable);
+
+/* Per-phase device time and kernel-launch counts accumulated over the ticks
+ * completed since timing was enabled. */
+mqr_status mqr_get_timing(const mqr_ctx *ctx, mqr_timing *out);
 
 /* Message of the last failed call on this thread ("" if none). */
 const char *mqr_last_error(void);

@@ -89,6 +89,11 @@ struct mqr_ctx {
     // per query / subquery
     DevBuf<uint32_t> sub_off, sub_q, sub_leaf, sub_len, sub_res, sub_bm, isub, bitmap;
     DevBuf<unsigned long long> out_off;
+    // query splitting: coarse lookup table, per-query cells, (query, block) pairs
+    DevBuf<uint32_t> zmap, pair_q, pair_first, pair_blo;
+    DevBuf<uint2> qcells;
+    DevBuf<unsigned long long> cand_off, pair_off;
+    unsigned long long cand_tiles = 0;
     // zero-initialised arena: Info, histograms, tile counters, look-back status
     DevBuf<unsigned char> arena;
     // staging for the host-buffer entry points and the sorted output kinds
@@ -102,6 +107,16 @@ struct mqr_ctx {
 
     Info *info_host = nullptr;  // pinned
     Info last{};
+    // per-phase timing (mqr_set_timing)
+    bool timing = false;
+    cudaEvent_t ev[MQR_NUM_PHASES][2] = {};
+    bool ev_used[MQR_NUM_PHASES] = {};
+    uint64_t ev_launches[MQR_NUM_PHASES] = {};
+    static constexpr int kMaxPendingUpdates = 64;
+    cudaEvent_t up_ev[kMaxPendingUpdates][2] = {};
+    int up_pending = 0;
+    uint64_t up_launches = 0;
+    mqr_timing acc{};
     unsigned long long last_q = 0, retries = 0;
     bool have_tick = false;
 };
@@ -110,16 +125,18 @@ namespace {
 
 // Arena layout for one tick.
 struct Arena {
-    size_t info, hist, counters, st_sort, st_leaf, st_lscan, st_query, st_res, total;
-    uint32_t sort_tiles, leaf_tiles, lscan_tiles, query_tiles, res_tiles;
+    size_t info, hist, counters, st_sort, st_leaf, st_lscan, st_qb_p, st_qb_c, st_cand, st_res, total;
+    uint32_t sort_tiles, leaf_tiles, lscan_tiles, qb_tiles, res_tiles;
+    unsigned long long cand_tiles;
 };
 
-Arena arena_layout(uint32_t nmax, uint32_t Q, unsigned long long sub_cap) {
+Arena arena_layout(uint32_t nmax, uint32_t Q, unsigned long long sub_cap, unsigned long long cand_tiles) {
     Arena a{};
     a.sort_tiles = (nmax + kSortTile - 1) / kSortTile;
     a.leaf_tiles = (nmax + kLeafTile - 1) / kLeafTile;
     a.lscan_tiles = (nmax + kLeafScanTile - 1) / kLeafScanTile;
-    a.query_tiles = (Q + kQueryTile - 1) / kQueryTile;
+    a.qb_tiles = (Q + kQBThreads - 1) / kQBThreads;
+    a.cand_tiles = cand_tiles;
     a.res_tiles = (uint32_t)((sub_cap + kResTile - 1) / kResTile) + 1;
     size_t o = 0;
     auto take = [&](size_t bytes) {
@@ -133,7 +150,9 @@ Arena arena_layout(uint32_t nmax, uint32_t Q, unsigned long long sub_cap) {
     a.st_sort = take((size_t)4 * 256 * a.sort_tiles * sizeof(uint32_t));
     a.st_leaf = take((size_t)a.leaf_tiles * sizeof(uint32_t));
     a.st_lscan = take((size_t)3 * a.lscan_tiles * sizeof(uint32_t));
-    a.st_query = take((size_t)a.query_tiles * sizeof(uint32_t));
+    a.st_qb_p = take((size_t)a.qb_tiles * sizeof(uint32_t));
+    a.st_qb_c = take((size_t)a.qb_tiles * sizeof(unsigned long long));
+    a.st_cand = take((size_t)a.cand_tiles * sizeof(uint32_t));
     a.st_res = take((size_t)a.res_tiles * sizeof(unsigned long long));
     a.total = o;
     return a;
@@ -148,6 +167,41 @@ mqr_status check_launch(const char *what) {
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, what);
     return MQR_OK;
+}
+
+// Phase timing: events around each phase's kernels when enabled.
+void phase_begin(mqr_ctx *c, int p) {
+    if (!c->timing) return;
+    cudaEventRecord(c->ev[p][0], c->stream);
+}
+void phase_end(mqr_ctx *c, int p, uint64_t launches) {
+    if (!c->timing) return;
+    cudaEventRecord(c->ev[p][1], c->stream);
+    c->ev_used[p] = true;
+    c->ev_launches[p] = launches;
+}
+// Called after the stream has been synchronised: fold the recorded phases
+// (and the update calls since the last tick) into the accumulators.
+void phases_collect(mqr_ctx *c, bool count_tick) {
+    if (!c->timing) return;
+    for (int p = 0; p < MQR_NUM_PHASES; ++p) {
+        if (!c->ev_used[p]) continue;
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, c->ev[p][0], c->ev[p][1]) == cudaSuccess) {
+            c->acc.ms[p] += ms;
+            c->acc.launches[p] += c->ev_launches[p];
+        }
+        c->ev_used[p] = false;
+    }
+    for (int k = 0; k < c->up_pending; ++k) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, c->up_ev[k][0], c->up_ev[k][1]) == cudaSuccess)
+            c->acc.ms[MQR_PHASE_UPDATES] += ms;
+    }
+    c->acc.launches[MQR_PHASE_UPDATES] += c->up_launches;
+    c->up_pending = 0;
+    c->up_launches = 0;
+    if (count_tick) c->acc.ticks++;
 }
 
 bool finite_rect(const mqr_rect &b) {
@@ -196,49 +250,85 @@ mqr_status enqueue_tick(mqr_ctx *c, const float4 *rects, uint32_t Q, int emit_ki
     if (Q == 0) MQR_CUDA(cudaMemsetAsync(c->sub_off.p, 0, sizeof(uint32_t), st));
 
     // a2 + a3: keys and the 4-pass onesweep sort of (key << 32 | id).
+    phase_begin(c, MQR_PHASE_KEYS);
     launch_morton_keys(st, c->pos.p, c->stamp.p, nmax, x0, y0, c->sx, c->sy, c->keysA.p, hist, info);
+    phase_end(c, MQR_PHASE_KEYS, nmax ? 1 : 0);
     uint32_t *st_sort = at<uint32_t>(c, a.st_sort);
     const size_t pass_status = (size_t)256 * a.sort_tiles;
     unsigned long long *src = c->keysA.p, *dst = c->keysB.p;
+    phase_begin(c, MQR_PHASE_SORT);
     for (int p = 0; p < 4; ++p) {
         bool fin = p == 3;
         launch_onesweep_pass(st, src, dst, nmax, 32 + 8 * p, hist + 256 * p, st_sort + pass_status * p,
                              ctr + p, err, fin, c->pos.p, c->skey.p, c->sid.p, c->sxy.p);
         std::swap(src, dst);
     }
+    phase_end(c, MQR_PHASE_SORT, nmax ? 4 : 0);
     // a4
-    launch_build_leaves(st, c->skey.p, nmax, c->cfg.leaf_cap,
-                        c->cfg.index_kind == MQR_INDEX_UNIFORM_GRID, c->cfg.grid_level, c->mk_a.p,
-                        c->mk_b.p, at<uint32_t>(c, a.st_leaf), ctr + 4, c->leaf_lo.p, c->leaf_hi.p,
-                        c->leaf_beg.p, c->leaf_nsub.p, info);
-    // a5 + a6
-    launch_query_count(st, rects, Q, x0, y0, c->sx, c->sy, c->leaf_lo.p, c->leaf_hi.p, c->leaf_beg.p,
-                       cov, c->sub_off.p, c->leaf_nsub.p, at<uint32_t>(c, a.st_query), ctr + 5, info);
-    // a8 scans
-    launch_leaf_scan(st, nmax, c->leaf_beg.p, c->leaf_nsub.p, c->leaf_sub_off.p, c->leaf_word_off.p,
-                     c->leaf_item_off.p, c->leaf_cursor.p, at<uint32_t>(c, a.st_lscan), ctr + 6, info);
-    // a7
+    phase_begin(c, MQR_PHASE_LEAVES);
+    const uint32_t cap = c->cfg.leaf_cap;
+    const bool ug = c->cfg.index_kind == MQR_INDEX_UNIFORM_GRID;
+    launch_build_leaves(st, c->skey.p, nmax, cap, ug, c->cfg.grid_level, c->mk_a.p, c->mk_b.p,
+                        at<uint32_t>(c, a.st_leaf), ctr + 4, c->leaf_lo.p, c->leaf_hi.p, c->leaf_beg.p,
+                        c->leaf_nsub.p, info);
+    uint64_t leaf_launches = nmax ? 1 : 0;
+    if (nmax && !ug && cap > (uint32_t)kLeafCapSmem && cap < nmax) {
+        int kexp = 0;
+        while ((2ull << kexp) <= (unsigned long long)cap + 1) ++kexp;
+        leaf_launches += 1 + kexp;
+    }
+    phase_end(c, MQR_PHASE_LEAVES, leaf_launches);
+    // a5 + a6: coarse lookup table, blocks and candidate counts per query
     caps.sub = c->sub_q.n;
     caps.sub_i = c->isub.n;
     caps.words = std::min<size_t>(c->bitmap.n, 0xffffffffull);
     caps.out = out_cap_elems;
-    launch_query_write(st, rects, Q, x0, y0, c->sx, c->sy, c->leaf_lo.p, c->leaf_hi.p, c->leaf_beg.p,
-                       cov, c->sub_off.p, c->leaf_sub_off.p, c->leaf_word_off.p, c->leaf_cursor.p,
-                       c->sub_q.p, c->sub_leaf.p, c->sub_len.p, c->sub_res.p, c->sub_bm.p, c->isub.p,
-                       caps, info);
+    caps.cand_tiles = a.cand_tiles;
+    phase_begin(c, MQR_PHASE_QUERY_BLOCKS);
+    launch_zmap(st, c->leaf_hi.p, info, c->zmap.p);
+    launch_query_blocks(st, rects, Q, x0, y0, c->sx, c->sy, c->leaf_lo.p, c->leaf_hi.p, c->zmap.p,
+                        c->qcells.p, c->cand_off.p, c->pair_q.p, c->pair_first.p, c->pair_blo.p,
+                        c->pair_off.p, at<uint32_t>(c, a.st_qb_p), at<unsigned long long>(c, a.st_qb_c),
+                        ctr + 5, info);
+    phase_end(c, MQR_PHASE_QUERY_BLOCKS, Q ? 2 : 1);
+    // a7: candidates -> subquery records
+    phase_begin(c, MQR_PHASE_CANDIDATES);
+    launch_candidates(st, c->num_sms, Q, cov, c->leaf_lo.p, c->leaf_hi.p, c->leaf_beg.p, c->qcells.p,
+                      c->cand_off.p, c->pair_q.p, c->pair_first.p, c->pair_blo.p, c->pair_off.p,
+                      c->sub_q.p, c->sub_leaf.p, c->sub_len.p, c->sub_res.p, c->sub_off.p, c->leaf_nsub.p,
+                      at<uint32_t>(c, a.st_cand), ctr + 8, caps, info);
+    phase_end(c, MQR_PHASE_CANDIDATES, 1);
+    // a8: group intersecting subqueries by leaf
+    phase_begin(c, MQR_PHASE_GROUP);
+    launch_leaf_scan(st, nmax, c->leaf_beg.p, c->leaf_nsub.p, c->leaf_sub_off.p, c->leaf_word_off.p,
+                     c->leaf_item_off.p, c->leaf_cursor.p, at<uint32_t>(c, a.st_lscan), ctr + 6, info);
+    launch_scatter(st, c->num_sms, c->sub_leaf.p, c->leaf_beg.p, c->leaf_sub_off.p, c->leaf_word_off.p,
+                   c->leaf_cursor.p, c->sub_bm.p, c->isub.p, caps, info);
+    phase_end(c, MQR_PHASE_GROUP, nmax ? 2 : 1);
     // a10
+    phase_begin(c, MQR_PHASE_FILTER);
     launch_filter(st, c->num_sms, rects, c->sxy.p, c->leaf_beg.p, c->leaf_sub_off.p,
                   c->leaf_word_off.p, c->leaf_item_off.p, c->isub.p, c->sub_q.p, c->sub_res.p,
                   c->bitmap.p, caps, info);
+    phase_end(c, MQR_PHASE_FILTER, 1);
     // a11
+    phase_begin(c, MQR_PHASE_RESULT_SCAN);
     launch_result_scan(st, caps.sub, c->sub_res.p, c->sub_leaf.p, c->out_off.p,
                        at<unsigned long long>(c, a.st_res), ctr + 7, caps, info);
+    phase_end(c, MQR_PHASE_RESULT_SCAN, 1);
     // a12 + a13
-    if (out != nullptr && emit_kind >= 0)
+    if (out != nullptr && emit_kind >= 0) {
+        phase_begin(c, MQR_PHASE_EMIT);
         launch_emit(st, c->num_sms, emit_kind, c->sub_q.p, c->sub_leaf.p, c->sub_len.p, c->sub_bm.p,
                     c->out_off.p, c->leaf_beg.p, c->sid.p, c->bitmap.p, out,
                     bitmap_words_per_row(nmax), caps, info);
-    if (offsets != nullptr) launch_query_offsets(st, Q, c->sub_off.p, c->out_off.p, offsets, caps, info);
+        phase_end(c, MQR_PHASE_EMIT, 1);
+    }
+    if (offsets != nullptr) {
+        phase_begin(c, MQR_PHASE_OFFSETS);
+        launch_query_offsets(st, Q, c->sub_off.p, c->out_off.p, offsets, caps, info);
+        phase_end(c, MQR_PHASE_OFFSETS, 1);
+    }
     return check_launch("tick kernels");
 }
 
@@ -247,6 +337,14 @@ mqr_status enqueue_tick(mqr_ctx *c, const float4 *rects, uint32_t Q, int emit_ki
 mqr_status ensure_tick_buffers(mqr_ctx *c, uint32_t Q) {
     size_t sub0 = std::max<size_t>(4096, (size_t)Q * 4);
     MQR_CUDA(c->sub_off.ensure((size_t)Q + 1));
+    MQR_CUDA(c->zmap.ensure(kZCells + 1));
+    MQR_CUDA(c->qcells.ensure(std::max<size_t>(Q, 1)));
+    MQR_CUDA(c->cand_off.ensure((size_t)Q + 1));
+    MQR_CUDA(c->pair_q.ensure((size_t)Q * 9 + 1));
+    MQR_CUDA(c->pair_first.ensure((size_t)Q * 9 + 1));
+    MQR_CUDA(c->pair_blo.ensure((size_t)Q * 9 + 1));
+    MQR_CUDA(c->pair_off.ensure((size_t)Q * 9 + 1));
+    c->cand_tiles = std::max<unsigned long long>(c->cand_tiles, std::max<unsigned long long>(1024, Q / 4));
     if (c->sub_q.n == 0) {
         MQR_CUDA(c->sub_q.ensure(sub0));
         MQR_CUDA(c->sub_leaf.ensure(sub0));
@@ -282,7 +380,7 @@ mqr_status run_tick(mqr_ctx *c, const float4 *rects, uint32_t Q, int emit_kind, 
     if (s != MQR_OK) return s;
     c->retries = 0;
     for (int attempt = 0; attempt < 8; ++attempt) {
-        Arena a = arena_layout(c->nmax, Q, c->sub_q.n);
+        Arena a = arena_layout(c->nmax, Q, c->sub_q.n, c->cand_tiles);
         MQR_CUDA(c->arena.ensure(a.total));
         Caps caps{};
         s = enqueue_tick(c, rects, Q, emit_kind, out, out_cap_elems, offsets, a, caps);
@@ -302,7 +400,11 @@ mqr_status run_tick(mqr_ctx *c, const float4 *rects, uint32_t Q, int emit_kind, 
                         "an update id was >= max_objects (ignored); the tick was answered without it");
         }
         bool again = false;
-        if (in.n_sub > caps.sub) {
+        const unsigned long long need_tiles = (in.n_cand + kCandTile - 1) / kCandTile;
+        if (need_tiles > caps.cand_tiles) {
+            c->cand_tiles = grow_to(need_tiles);
+            again = true;
+        } else if (in.n_sub > caps.sub) {
             s = grow_sub(c, in.n_sub);
             if (s != MQR_OK) return s;
             again = true;
@@ -320,7 +422,10 @@ mqr_status run_tick(mqr_ctx *c, const float4 *rects, uint32_t Q, int emit_kind, 
                 again = true;
             }
         }
-        if (!again) return MQR_OK;
+        if (!again) {
+            phases_collect(c, true);
+            return MQR_OK;
+        }
         ++c->retries;
     }
     return fail(MQR_ERR_INTERNAL, "buffer growth did not converge");
@@ -409,9 +514,10 @@ mqr_status tick_device(mqr_ctx *c, const float *rects_dev, uint32_t Q, int kind,
     if (R == 0) return MQR_OK;
     MQR_CUDA(c->sortA.ensure(R));
     MQR_CUDA(c->sortB.ensure(R));
-    Arena a = arena_layout(c->nmax, Q, c->sub_q.n);
-    Caps caps{c->sub_q.n, c->isub.n, std::min<size_t>(c->bitmap.n, 0xffffffffull), R};
+    Arena a = arena_layout(c->nmax, Q, c->sub_q.n, c->cand_tiles);
+    Caps caps{c->sub_q.n, c->isub.n, std::min<size_t>(c->bitmap.n, 0xffffffffull), R, c->cand_tiles};
     Info *info = at<Info>(c, a.info);
+    phase_begin(c, MQR_PHASE_OUTPUT_SORT);
     launch_emit(c->stream, c->num_sms, kEmitKeys64, c->sub_q.p, c->sub_leaf.p, c->sub_len.p,
                 c->sub_bm.p, c->out_off.p, c->leaf_beg.p, c->sid.p, c->bitmap.p, c->sortA.p, wpr, caps,
                 info);
@@ -421,9 +527,11 @@ mqr_status tick_device(mqr_ctx *c, const float *rects_dev, uint32_t Q, int kind,
     s = sort_result_keys(c, R, Q, &sorted);
     if (s != MQR_OK) return s;
     launch_keys_to_output(c->stream, sorted, R, kind == MQR_OUT_PAIRS_SORTED, out_dev);
+    phase_end(c, MQR_PHASE_OUTPUT_SORT, 0);
     s = check_launch("layout");
     if (s != MQR_OK) return s;
     MQR_CUDA(cudaStreamSynchronize(c->stream));
+    phases_collect(c, false);
     return MQR_OK;
 }
 
@@ -461,8 +569,12 @@ void mqr_destroy(mqr_ctx *c) {
     DevBuf<uint32_t> *u32s[] = {&c->skey, &c->sid, &c->leaf_lo, &c->leaf_hi, &c->leaf_beg, &c->leaf_nsub,
                                 &c->leaf_sub_off, &c->leaf_word_off, &c->leaf_item_off, &c->leaf_cursor,
                                 &c->sub_off, &c->sub_q, &c->sub_leaf, &c->sub_len, &c->sub_res,
-                                &c->sub_bm, &c->isub, &c->bitmap, &c->up_ids};
+                                &c->sub_bm, &c->isub, &c->bitmap, &c->up_ids, &c->zmap, &c->pair_q,
+                                &c->pair_first, &c->pair_blo};
     for (auto *b : u32s) b->release();
+    c->qcells.release();
+    c->cand_off.release();
+    c->pair_off.release();
     c->mk_a.release();
     c->mk_b.release();
     c->arena.release();
@@ -470,6 +582,12 @@ void mqr_destroy(mqr_ctx *c) {
     c->upd_err.release();
     c->q_rects.release();
     c->out_stage.release();
+    for (int p = 0; p < MQR_NUM_PHASES; ++p)
+        for (int k = 0; k < 2; ++k)
+            if (c->ev[p][k]) cudaEventDestroy(c->ev[p][k]);
+    for (int p = 0; p < mqr_ctx::kMaxPendingUpdates; ++p)
+        for (int k = 0; k < 2; ++k)
+            if (c->up_ev[p][k]) cudaEventDestroy(c->up_ev[p][k]);
     if (c->info_host) cudaFreeHost(c->info_host);
     if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
     cudaSetDevice(prev);
@@ -554,8 +672,15 @@ mqr_status mqr_apply_updates(mqr_ctx *c, const uint32_t *ids_dev, const float *x
     if (!ids_dev || !xy_dev) return fail(MQR_ERR_INVALID_ARG, "ids_dev / xy_dev is NULL");
     MQR_CUDA(cudaSetDevice(c->device));
     ++c->epoch;
+    const bool timed = c->timing && c->up_pending < mqr_ctx::kMaxPendingUpdates;
+    if (timed) cudaEventRecord(c->up_ev[c->up_pending][0], c->stream);
     launch_apply_updates(c->stream, ids_dev, reinterpret_cast<const float2 *>(xy_dev), n, c->nmax,
                          c->epoch, c->stamp.p, c->pos.p, c->upd_err.p);
+    if (timed) {
+        cudaEventRecord(c->up_ev[c->up_pending][1], c->stream);
+        ++c->up_pending;
+    }
+    if (c->timing) c->up_launches += 2;
     return check_launch("apply_updates");
 }
 
@@ -655,6 +780,9 @@ mqr_status mqr_get_stats(const mqr_ctx *c, mqr_stats *o) {
     o->n_results = in.n_results;
     o->n_results_covering = in.n_results_cov;
     o->n_retries = c->retries;
+    o->n_filter_loads = in.n_item_objs;
+    o->n_pairs = in.n_pairs;
+    o->n_candidates = in.n_cand;
     return MQR_OK;
 }
 
@@ -701,6 +829,29 @@ mqr_status mqr_get_sorted(mqr_ctx *c, uint32_t *keys_host, uint32_t *ids_host, u
     if (keys_host) MQR_CUDA(cudaMemcpyAsync(keys_host, c->skey.p, N * 4, cudaMemcpyDeviceToHost, c->stream));
     if (ids_host) MQR_CUDA(cudaMemcpyAsync(ids_host, c->sid.p, N * 4, cudaMemcpyDeviceToHost, c->stream));
     MQR_CUDA(cudaStreamSynchronize(c->stream));
+    return MQR_OK;
+}
+
+mqr_status mqr_set_timing(mqr_ctx *c, int enable) {
+    if (!c) return fail(MQR_ERR_INVALID_ARG, "ctx is NULL");
+    MQR_CUDA(cudaSetDevice(c->device));
+    if (enable && !c->ev[0][0]) {
+        for (int p = 0; p < MQR_NUM_PHASES; ++p)
+            for (int k = 0; k < 2; ++k) MQR_CUDA(cudaEventCreate(&c->ev[p][k]));
+        for (int p = 0; p < mqr_ctx::kMaxPendingUpdates; ++p)
+            for (int k = 0; k < 2; ++k) MQR_CUDA(cudaEventCreate(&c->up_ev[p][k]));
+    }
+    c->timing = enable != 0;
+    std::memset(&c->acc, 0, sizeof(c->acc));
+    std::memset(c->ev_used, 0, sizeof(c->ev_used));
+    c->up_pending = 0;
+    c->up_launches = 0;
+    return MQR_OK;
+}
+
+mqr_status mqr_get_timing(const mqr_ctx *c, mqr_timing *out) {
+    if (!c || !out) return fail(MQR_ERR_INVALID_ARG, "NULL argument");
+    *out = c->acc;
     return MQR_OK;
 }
 

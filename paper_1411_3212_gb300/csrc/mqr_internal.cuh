@@ -44,7 +44,9 @@ struct Info {
     unsigned long long n_results;   // R
     unsigned long long n_results_cov;
     unsigned long long err;
-    unsigned long long pad[3];
+    unsigned long long n_item_objs;  // objects loaded by the filter (sum over items)
+    unsigned long long n_pairs;      // (query, block) pairs of query splitting
+    unsigned long long n_cand;       // candidate (query, leaf) pairs
 };
 
 // Capacities of the growable per-tick buffers (host-chosen, passed by value).
@@ -53,6 +55,7 @@ struct Caps {
     unsigned long long sub_i;    // intersecting subqueries (isub list)
     unsigned long long words;    // bitmap words
     unsigned long long out;      // output elements (pairs / ids / bitmap words)
+    unsigned long long cand_tiles;  // look-back status slots of the candidate pass
 };
 
 // ---------------------------------------------------------------------------
@@ -240,13 +243,29 @@ void launch_build_leaves(cudaStream_t st, const uint32_t *skey, uint32_t nmax, u
                          uint32_t *status, uint32_t *tile_counter, uint32_t *leaf_lo,
                          uint32_t *leaf_hi, uint32_t *leaf_beg, uint32_t *leaf_nsub, Info *info);
 
-// a5 + a6: per-query subquery counts + exclusive scan (sub_off[Q+1]), and the
-// per-leaf intersecting-subquery histogram leaf_nsub.
-constexpr int kQueryThreads = 256, kQueryItems = 4, kQueryTile = kQueryThreads * kQueryItems;
-void launch_query_count(cudaStream_t st, const float4 *rects, uint32_t Q, float x0, float y0,
-                        float sx, float sy, const uint32_t *leaf_lo, const uint32_t *leaf_hi,
-                        const uint32_t *leaf_beg, int covering, uint32_t *sub_off,
-                        uint32_t *leaf_nsub, uint32_t *status, uint32_t *tile_counter, Info *info);
+// Query splitting (a5-a7).  Coarse lookup level and tile shapes.
+constexpr int kZLevel = 8;
+constexpr uint32_t kZCells = 1u << (2 * kZLevel);
+constexpr int kZShift = 2 * (kLevels - kZLevel);
+constexpr int kQBThreads = 256;                       // queries per tile of query_blocks
+constexpr int kCandThreads = 256, kCandItems = 4, kCandTile = kCandThreads * kCandItems;
+
+void launch_zmap(cudaStream_t st, const uint32_t *leaf_hi, const Info *info, uint32_t *zmap);
+// a5 + a6: blocks, leaf ranges and candidate counts per query, scanned.
+void launch_query_blocks(cudaStream_t st, const float4 *rects, uint32_t Q, float x0, float y0, float sx,
+                         float sy, const uint32_t *leaf_lo, const uint32_t *leaf_hi, const uint32_t *zmap,
+                         uint2 *qcells, unsigned long long *cand_off, uint32_t *pair_q,
+                         uint32_t *pair_first, uint32_t *pair_blo, unsigned long long *pair_off,
+                         uint32_t *status_p, unsigned long long *status_c, uint32_t *tile_counter,
+                         Info *info);
+// a7: candidates -> subquery records (query-major), sub_off[Q+1], leaf_nsub.
+void launch_candidates(cudaStream_t st, int num_sms, uint32_t Q, int covering, const uint32_t *leaf_lo,
+                       const uint32_t *leaf_hi, const uint32_t *leaf_beg, const uint2 *qcells,
+                       const unsigned long long *cand_off, const uint32_t *pair_q,
+                       const uint32_t *pair_first, const uint32_t *pair_blo,
+                       const unsigned long long *pair_off, uint32_t *sub_q, uint32_t *sub_leaf,
+                       uint32_t *sub_len, uint32_t *sub_res, uint32_t *sub_off, uint32_t *leaf_nsub,
+                       uint32_t *status, uint32_t *tile_counter, Caps caps, Info *info);
 
 // a8: scans over leaves -> leaf_sub_off, leaf_word_off, leaf_item_off, cursor.
 constexpr int kLeafScanThreads = 256, kLeafScanItems = 8, kLeafScanTile = kLeafScanThreads * kLeafScanItems;
@@ -255,14 +274,10 @@ void launch_leaf_scan(cudaStream_t st, uint32_t nmax, const uint32_t *leaf_beg,
                       uint32_t *leaf_item_off, uint32_t *leaf_cursor, uint32_t *status3,
                       uint32_t *tile_counter, Info *info);
 
-// a7 (+ a8 scatter): write subquery records, covering runs, isub lists.
-void launch_query_write(cudaStream_t st, const float4 *rects, uint32_t Q, float x0, float y0,
-                        float sx, float sy, const uint32_t *leaf_lo, const uint32_t *leaf_hi,
-                        const uint32_t *leaf_beg, int covering, const uint32_t *sub_off,
-                        const uint32_t *leaf_sub_off, const uint32_t *leaf_word_off,
-                        uint32_t *leaf_cursor, uint32_t *sub_q, uint32_t *sub_leaf,
-                        uint32_t *sub_len, uint32_t *sub_res, uint32_t *sub_bm, uint32_t *isub,
-                        Caps caps, Info *info);
+// a8 scatter: intersecting subqueries into their leaf's list + bitmap rows.
+void launch_scatter(cudaStream_t st, int num_sms, const uint32_t *sub_leaf, const uint32_t *leaf_beg,
+                    const uint32_t *leaf_sub_off, const uint32_t *leaf_word_off, uint32_t *leaf_cursor,
+                    uint32_t *sub_bm, uint32_t *isub, Caps caps, const Info *info);
 
 // a10: filtering into bitmap words + per-subquery counts.
 void launch_filter(cudaStream_t st, int num_sms, const float4 *rects, const float2 *sxy,

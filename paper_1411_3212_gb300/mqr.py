@@ -26,7 +26,10 @@ KINDS = {"pairs": MQR_OUT_PAIRS, "pairs_sorted": MQR_OUT_PAIRS_SORTED, "csr": MQ
 # Every symbol include/mqr.h declares.
 EXPORTS = ["mqr_config_default", "mqr_create", "mqr_create_ex", "mqr_apply_updates",
            "mqr_apply_updates_host", "mqr_tick", "mqr_tick_host", "mqr_get_stats", "mqr_get_leaves",
-           "mqr_get_sorted", "mqr_last_error", "mqr_destroy"]
+           "mqr_get_sorted", "mqr_set_timing", "mqr_get_timing", "mqr_last_error", "mqr_destroy"]
+
+PHASES = ["updates", "keys", "sort", "leaves", "query_blocks", "group", "candidates", "filter",
+          "result_scan", "emit", "offsets", "output_sort"]
 
 
 class MqrError(RuntimeError):
@@ -50,10 +53,19 @@ class mqr_stats(ctypes.Structure):
     _fields_ = [(n, ctypes.c_uint64) for n in (
         "n_objects", "n_queries", "n_leaves", "max_level", "n_sub_intersecting", "n_sub_covering",
         "n_covering_runs", "n_tests", "n_filter_items", "n_bitmap_words", "n_results",
-        "n_results_covering", "n_retries")]
+        "n_results_covering", "n_retries", "n_filter_loads", "n_pairs", "n_candidates")]
 
     def as_dict(self):
         return {n: int(getattr(self, n)) for n, _ in self._fields_}
+
+
+class mqr_timing(ctypes.Structure):
+    _fields_ = [("ms", ctypes.c_double * 12), ("launches", ctypes.c_uint64 * 12), ("ticks", ctypes.c_uint64)]
+
+    def as_dict(self):
+        return {"ms": {PHASES[i]: float(self.ms[i]) for i in range(12)},
+                "launches": {PHASES[i]: int(self.launches[i]) for i in range(12)},
+                "ticks": int(self.ticks)}
 
 
 _lib = None
@@ -81,6 +93,8 @@ def load(path: str = LIB_PATH):
         "mqr_get_stats": ([P, ctypes.POINTER(mqr_stats)], i32),
         "mqr_get_leaves": ([P, P, u64, ctypes.POINTER(u64)], i32),
         "mqr_get_sorted": ([P, P, P, u64, ctypes.POINTER(u64)], i32),
+        "mqr_set_timing": ([P, i32], i32),
+        "mqr_get_timing": ([P, ctypes.POINTER(mqr_timing)], i32),
         "mqr_last_error": ([], ctypes.c_char_p),
         "mqr_destroy": ([P], None),
     }
@@ -197,6 +211,16 @@ def mqr_get_sorted(ctx):
     return keys, ids
 
 
+def mqr_set_timing(ctx, enable):
+    _check(load().mqr_set_timing(ctx, 1 if enable else 0))
+
+
+def mqr_get_timing(ctx):
+    t = mqr_timing()
+    _check(load().mqr_get_timing(ctx, ctypes.byref(t)))
+    return t.as_dict()
+
+
 def mqr_last_error():
     return load().mqr_last_error().decode()
 
@@ -269,6 +293,12 @@ class Index:
 
     def stats(self):
         return mqr_get_stats(self.ctx)
+
+    def set_timing(self, enable=True):
+        mqr_set_timing(self.ctx, enable)
+
+    def timing(self):
+        return mqr_get_timing(self.ctx)
 
     def leaves(self):
         return mqr_get_leaves(self.ctx)
