@@ -76,6 +76,7 @@ typedef struct {
  *  COUNT         no id output (out_dev may be NULL); only *out_count and, if
  *                given, offsets_dev.
  * offsets_dev, when non-NULL, receives the per-query offsets for every kind.
+ * out_dev must be 16-byte aligned (cudaMalloc and torch allocations are).
  * The sorted kinds are limited to R < 2^30. */
 typedef enum {
     MQR_OUT_PAIRS = 0,

@@ -203,7 +203,7 @@ onesweep_kernel(const unsigned long long *__restrict__ in, unsigned long long *_
     uint32_t dstart = block_excl_scan<kSortThreads>(c, &tot, s_scan);
     uint32_t gstart = block_excl_scan<kSortThreads>(hist256[tid], &tot, s_scan);
     s_dstart[tid] = dstart;
-    uint32_t prefix = lookback<uint32_t>(status + (size_t)tid * num_tiles, tile, c, err);
+    uint32_t prefix = lookback1<uint32_t>(status + (size_t)tid * num_tiles, tile, c, err);
     s_gbase[tid] = gstart + prefix - dstart;
     __syncthreads();
 
@@ -371,7 +371,10 @@ leaves_kernel(const uint32_t *__restrict__ K, uint32_t cap, int uniform_grid, ui
     }
     uint32_t total;
     uint32_t off = block_excl_scan<kLeafThreads>(cnt, &total, s_scan);
-    if (tid == 0) s_prefix = lookback<uint32_t>(status, tile, total, &info->err);
+    if (tid < 32) {
+        const uint32_t pre = lookback_warp<uint32_t>(status, tile, total, &info->err);
+        if (tid == 0) s_prefix = pre;
+    }
     __syncthreads();
     uint32_t idx = s_prefix + off;
 #pragma unroll

@@ -7,7 +7,8 @@
 namespace mqr {
 
 __device__ __forceinline__ bool tick_buffers_ok(const Info *info, const Caps &caps) {
-    return info->n_sub <= caps.sub && info->n_sub_i <= caps.sub_i && info->n_words <= caps.words;
+    return info->n_sub <= caps.sub && info->n_sub_i <= caps.sub_i && info->n_words <= caps.words &&
+           info->n_items <= caps.items;
 }
 
 // ---------------------------------------------------------------------------
@@ -28,24 +29,18 @@ __global__ void __launch_bounds__(kFilterThreads)
 filter_kernel(const float4 *__restrict__ rects, const float2 *__restrict__ sxy,
               const uint32_t *__restrict__ leaf_beg, const uint32_t *__restrict__ leaf_sub_off,
               const uint32_t *__restrict__ leaf_word_off, const uint32_t *__restrict__ leaf_item_off,
-              const uint32_t *__restrict__ isub, const uint32_t *__restrict__ sub_q,
+              const uint32_t *__restrict__ item_leaf, const uint32_t *__restrict__ isub,
+              const uint32_t *__restrict__ sub_q,
               uint32_t *__restrict__ sub_res, uint32_t *__restrict__ bitmap, Caps caps,
               const Info *info) {
     if (!tick_buffers_ok(info, caps)) return;
-    const uint32_t L = (uint32_t)info->n_leaves;
     const uint32_t items = (uint32_t)info->n_items;
     const int lane = threadIdx.x & 31;
     const uint32_t nwarps = gridDim.x * (kFilterThreads / 32);
     const float qnan = __int_as_float(0x7fc00000);
 
     for (uint32_t item = (blockIdx.x * kFilterThreads + threadIdx.x) >> 5; item < items; item += nwarps) {
-        // leaf = last l with leaf_item_off[l] <= item
-        uint32_t a = 0, b = L;
-        while (b - a > 1) {
-            uint32_t m = (a + b) >> 1;
-            if (__ldg(leaf_item_off + m) <= item) a = m; else b = m;
-        }
-        const uint32_t leaf = a;
+        const uint32_t leaf = __ldg(item_leaf + item);
         const uint32_t r = item - __ldg(leaf_item_off + leaf);
         const uint32_t soff = __ldg(leaf_sub_off + leaf);
         const uint32_t nsub = __ldg(leaf_sub_off + leaf + 1) - soff;
@@ -117,11 +112,11 @@ filter_kernel(const float4 *__restrict__ rects, const float2 *__restrict__ sxy,
 void launch_filter(cudaStream_t st, int num_sms, const float4 *rects, const float2 *sxy,
                    const uint32_t *leaf_beg, const uint32_t *leaf_sub_off,
                    const uint32_t *leaf_word_off, const uint32_t *leaf_item_off,
-                   const uint32_t *isub, const uint32_t *sub_q, uint32_t *sub_res,
-                   uint32_t *bitmap, Caps caps, const Info *info) {
+                   const uint32_t *item_leaf, const uint32_t *isub, const uint32_t *sub_q,
+                   uint32_t *sub_res, uint32_t *bitmap, Caps caps, const Info *info) {
     filter_kernel<<<num_sms * 8, kFilterThreads, 0, st>>>(rects, sxy, leaf_beg, leaf_sub_off,
-                                                          leaf_word_off, leaf_item_off, isub, sub_q,
-                                                          sub_res, bitmap, caps, info);
+                                                          leaf_word_off, leaf_item_off, item_leaf, isub,
+                                                          sub_q, sub_res, bitmap, caps, info);
 }
 
 // ---------------------------------------------------------------------------
@@ -159,7 +154,10 @@ result_scan_kernel(const uint32_t *__restrict__ sub_res, const uint32_t *__restr
     }
     unsigned long long total;
     unsigned long long off = block_excl_scan<kResThreads>(t, &total, s_scan);
-    if (tid == 0) s_prefix = lookback<unsigned long long>(status, tile, total, &info->err);
+    if (tid < 32) {
+        const unsigned long long pre = lookback_warp<unsigned long long>(status, tile, total, &info->err);
+        if (tid == 0) s_prefix = pre;
+    }
     cov = warp_sum(cov);
     if ((tid & 31) == 0 && cov) atomicAdd(&s_cov, cov);
     __syncthreads();
@@ -213,6 +211,34 @@ __device__ __forceinline__ void emit_one(void *out, unsigned long long pos, uint
 
 constexpr int kEmitThreads = 256;
 
+// Copy a covering run: ids sid[b..b+n) with query q to output slots off...
+template <int KIND>
+__device__ __forceinline__ void emit_run(void *out, unsigned long long off, uint32_t q,
+                                         const uint32_t *__restrict__ sid, uint32_t b, uint32_t n,
+                                         uint32_t wpr, int lane) {
+    if (KIND == kEmitPairs) {
+        // 16-byte stores of two pairs once the output slot is even
+        if (n == 0) return;
+        if (off & 1ull) {
+            if (lane == 0) emit_one<KIND>(out, off, q, __ldg(sid + b), wpr);
+            ++off; ++b; --n;
+        }
+        const uint32_t n2 = n >> 1;
+        uint4 *o4 = reinterpret_cast<uint4 *>(out) + (off >> 1);
+        for (uint32_t i = lane; i < n2; i += 32) {
+            const uint32_t a0 = __ldg(sid + b + 2 * i), a1 = __ldg(sid + b + 2 * i + 1);
+            o4[i] = make_uint4(q, a0, q, a1);
+        }
+        if ((n & 1u) && lane == 0) emit_one<KIND>(out, off + n - 1, q, __ldg(sid + b + n - 1), wpr);
+    } else {
+        for (uint32_t i = lane; i < n; i += 32) emit_one<KIND>(out, off + i, q, __ldg(sid + b + i), wpr);
+    }
+}
+
+// One warp per batch of 32 consecutive subquery records (query-major order,
+// so the output is written front to back): lane j loads the metadata of
+// record j of the batch, then the warp handles the records one by one with
+// the metadata broadcast by shuffles.
 template <int KIND>
 __global__ void __launch_bounds__(kEmitThreads)
 emit_kernel(const uint32_t *__restrict__ sub_q, const uint32_t *__restrict__ sub_leaf,
@@ -226,30 +252,46 @@ emit_kernel(const uint32_t *__restrict__ sub_q, const uint32_t *__restrict__ sub
     const int lane = threadIdx.x & 31;
     const uint32_t lt = lanemask_lt();
     const uint32_t nwarps = gridDim.x * (kEmitThreads / 32);
-    for (uint32_t k = (blockIdx.x * kEmitThreads + threadIdx.x) >> 5; k < nsub; k += nwarps) {
-        const uint32_t q = __ldg(sub_q + k);
-        const uint32_t sl = __ldg(sub_leaf + k);
-        const unsigned long long off = __ldg(out_off + k);
-        if (sl & 0x80000000u) {
+    const uint32_t nbatch = (nsub + 31u) >> 5;
+    for (uint32_t batch = (blockIdx.x * kEmitThreads + threadIdx.x) >> 5; batch < nbatch; batch += nwarps) {
+        const uint32_t k = batch * 32u + lane;
+        uint32_t q = 0, sl = 0, bm = 0, b = 0, e = 0;
+        unsigned long long off = 0;
+        if (k < nsub) {
+            q = __ldg(sub_q + k);
+            sl = __ldg(sub_leaf + k);
+            off = __ldg(out_off + k);
             const uint32_t first = sl & 0x7fffffffu;
-            const uint32_t b = __ldg(leaf_beg + first);
-            const uint32_t n = __ldg(leaf_beg + first + __ldg(sub_len + k)) - b;
-            for (uint32_t i = lane; i < n; i += 32) emit_one<KIND>(out, off + i, q, __ldg(sid + b + i), wpr);
-        } else {
-            const uint32_t b = __ldg(leaf_beg + sl);
-            const uint32_t n = __ldg(leaf_beg + sl + 1) - b;
-            const uint32_t nw = (n + 31u) >> 5;
-            const uint32_t row = __ldg(sub_bm + k);
-            unsigned long long run = off;
-            for (uint32_t w0 = 0; w0 < nw; w0 += 32) {
-                const uint32_t myw = (w0 + lane < nw) ? __ldg(bitmap + row + w0 + lane) : 0u;
-                const uint32_t nj = min(32u, nw - w0);
-                for (uint32_t j = 0; j < nj; ++j) {
-                    const uint32_t word = __shfl_sync(0xffffffffu, myw, j);
-                    if (word == 0u) continue;
-                    if ((word >> lane) & 1u)
-                        emit_one<KIND>(out, run + __popc(word & lt), q, __ldg(sid + b + (w0 + j) * 32u + lane), wpr);
-                    run += __popc(word);
+            uint32_t len = 1;
+            if (sl & 0x80000000u) len = __ldg(sub_len + k);
+            else bm = __ldg(sub_bm + k);
+            b = __ldg(leaf_beg + first);
+            e = __ldg(leaf_beg + first + len);
+        }
+        const uint32_t nrec = min(32u, nsub - batch * 32u);
+        for (uint32_t j = 0; j < nrec; ++j) {
+            const uint32_t qj = __shfl_sync(0xffffffffu, q, j);
+            const uint32_t slj = __shfl_sync(0xffffffffu, sl, j);
+            const uint32_t bj = __shfl_sync(0xffffffffu, b, j);
+            const uint32_t ej = __shfl_sync(0xffffffffu, e, j);
+            const unsigned long long offj = __shfl_sync(0xffffffffu, off, j);
+            if (slj & 0x80000000u) {
+                emit_run<KIND>(out, offj, qj, sid, bj, ej - bj, wpr, lane);
+            } else {
+                const uint32_t row = __shfl_sync(0xffffffffu, bm, j);
+                const uint32_t nw = (ej - bj + 31u) >> 5;
+                unsigned long long run = offj;
+                for (uint32_t w0 = 0; w0 < nw; w0 += 32) {
+                    const uint32_t myw = (w0 + lane < nw) ? __ldg(bitmap + row + w0 + lane) : 0u;
+                    const uint32_t nj = min(32u, nw - w0);
+                    for (uint32_t jj = 0; jj < nj; ++jj) {
+                        const uint32_t word = __shfl_sync(0xffffffffu, myw, jj);
+                        if (word == 0u) continue;
+                        if ((word >> lane) & 1u)
+                            emit_one<KIND>(out, run + __popc(word & lt), qj,
+                                           __ldg(sid + bj + (w0 + jj) * 32u + lane), wpr);
+                        run += __popc(word);
+                    }
                 }
             }
         }
@@ -282,22 +324,30 @@ void launch_emit(cudaStream_t st, int num_sms, int emit_kind, const uint32_t *su
     }
 }
 
-// Per-query offsets: the first subquery record of query q starts its list.
-__global__ void query_offsets_kernel(uint32_t Q, const uint32_t *__restrict__ sub_off,
+// Per-query offsets: the first record of query q is the first record of its
+// first (query, block) pair (queries without pairs take the next pair's).
+__global__ void query_offsets_kernel(uint32_t Q, const uint32_t *__restrict__ qpair,
+                                     const uint32_t *__restrict__ pair_rec,
                                      const unsigned long long *__restrict__ out_off,
                                      unsigned long long *__restrict__ offsets, Caps caps,
                                      const Info *info) {
     if (!tick_buffers_ok(info, caps)) return;
-    for (uint32_t q = blockIdx.x * blockDim.x + threadIdx.x; q <= Q; q += gridDim.x * blockDim.x)
-        offsets[q] = out_off[sub_off[q]];
+    const unsigned long long nsub = info->n_sub;
+    for (uint32_t q = blockIdx.x * blockDim.x + threadIdx.x; q <= Q; q += gridDim.x * blockDim.x) {
+        if (Q == 0 || nsub == 0) {
+            offsets[q] = 0;
+            continue;
+        }
+        offsets[q] = out_off[pair_rec[qpair[q]]];
+    }
 }
 
-void launch_query_offsets(cudaStream_t st, uint32_t Q, const uint32_t *sub_off,
+void launch_query_offsets(cudaStream_t st, uint32_t Q, const uint32_t *qpair, const uint32_t *pair_rec,
                           const unsigned long long *out_off, unsigned long long *offsets,
                           Caps caps, const Info *info) {
     uint32_t g = (Q + 1 + 255) / 256;
     if (g > 4096) g = 4096;
-    query_offsets_kernel<<<g, 256, 0, st>>>(Q, sub_off, out_off, offsets, caps, info);
+    query_offsets_kernel<<<g, 256, 0, st>>>(Q, qpair, pair_rec, out_off, offsets, caps, info);
 }
 
 // Sorted (qidx << 32 | id) keys to the requested layout.

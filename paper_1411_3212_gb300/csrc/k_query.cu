@@ -117,7 +117,8 @@ query_blocks_kernel(const float4 *__restrict__ rects, uint32_t Q, float x0, floa
                     const uint32_t *__restrict__ zmap, uint2 *__restrict__ qcells,
                     unsigned long long *__restrict__ cand_off, uint32_t *__restrict__ pair_q,
                     uint32_t *__restrict__ pair_first, uint32_t *__restrict__ pair_blo,
-                    unsigned long long *__restrict__ pair_off, uint32_t *status_p,
+                    unsigned long long *__restrict__ pair_off, uint32_t *__restrict__ qpair,
+                    uint32_t *__restrict__ tile_p0, unsigned long long tile_cap, uint32_t *status_p,
                     unsigned long long *status_c, uint32_t *tile_counter, Info *info) {
     __shared__ uint32_t s_scan32[kQBThreads / 32 + 1];
     __shared__ unsigned long long s_scan64[kQBThreads / 32 + 1];
@@ -164,14 +165,20 @@ query_blocks_kernel(const float4 *__restrict__ rects, uint32_t Q, float x0, floa
     unsigned long long tot_c;
     const uint32_t off_p = block_excl_scan<kQBThreads>(npairs, &tot_p, s_scan32);
     const unsigned long long off_c = block_excl_scan<kQBThreads>(ncand, &tot_c, s_scan64);
-    if (tid == 0) {
-        s_pp = lookback<uint32_t>(status_p, tile, tot_p, &info->err);
-        s_pc = lookback<unsigned long long>(status_c, tile, tot_c, &info->err);
+    if (tid < 32) {
+        const uint32_t pp = lookback_warp<uint32_t>(status_p, tile, tot_p, &info->err);
+        if (tid == 0) s_pp = pp;
+    } else if (tid < 64) {
+        const unsigned long long pc = lookback_warp<unsigned long long>(status_c, tile, tot_c, &info->err);
+        if (tid == 32) s_pc = pc;
     }
     __syncthreads();
     uint32_t p = s_pp + off_p;
     unsigned long long co = s_pc + off_c;
-    if (q < Q) cand_off[q] = co;
+    if (q < Q) {
+        cand_off[q] = co;
+        qpair[q] = p;
+    }
 #pragma unroll
     for (int b = 0; b < 9; ++b) {
         if (cnt[b] == 0) continue;
@@ -179,6 +186,9 @@ query_blocks_kernel(const float4 *__restrict__ rects, uint32_t Q, float x0, floa
         pair_first[p] = first[b];
         pair_blo[p] = blo9[b];
         pair_off[p] = co;
+        // warp tiles of 32 candidates whose first candidate falls in this pair
+        for (unsigned long long t = (co + 31) >> 5; (t << 5) < co + cnt[b] && t < tile_cap; ++t)
+            tile_p0[t] = p;
         co += cnt[b];
         ++p;
     }
@@ -186,6 +196,7 @@ query_blocks_kernel(const float4 *__restrict__ rects, uint32_t Q, float x0, floa
         const uint32_t np = s_pp + tot_p;
         const unsigned long long nc = s_pc + tot_c;
         cand_off[Q] = nc;
+        qpair[Q] = np;
         pair_off[np] = nc;
         info->n_pairs = np;
         info->n_cand = nc;
@@ -200,258 +211,240 @@ void launch_query_blocks(cudaStream_t st, const float4 *rects, uint32_t Q, float
                          float sy, const uint32_t *leaf_lo, const uint32_t *leaf_hi, const uint32_t *zmap,
                          uint2 *qcells, unsigned long long *cand_off, uint32_t *pair_q,
                          uint32_t *pair_first, uint32_t *pair_blo, unsigned long long *pair_off,
+                         uint32_t *qpair, uint32_t *tile_p0, unsigned long long tile_cap,
                          uint32_t *status_p, unsigned long long *status_c, uint32_t *tile_counter,
                          Info *info) {
     if (Q == 0) return;
     uint32_t tiles = (Q + kQBThreads - 1) / kQBThreads;
     query_blocks_kernel<<<tiles, kQBThreads, 0, st>>>(rects, Q, x0, y0, sx, sy, leaf_lo, leaf_hi, zmap,
                                                       qcells, cand_off, pair_q, pair_first, pair_blo,
-                                                      pair_off, status_p, status_c, tile_counter, info);
+                                                      pair_off, qpair, tile_p0, tile_cap, status_p,
+                                                      status_c, tile_counter, info);
 }
 
 // ---------------------------------------------------------------------------
-// a7: candidate leaves -> subquery records.  Tiles of kCandTile candidates
-// (taken in order by a persistent grid) map each candidate to its pair,
-// classify it, and compact the subqueries with a single-pass scan into
-// records in query-major order.  Consecutive covering leaves of one pair form
-// one covering run (their objects are one contiguous range of the sorted
-// objects).  Record k: sub_q[k] = query, sub_leaf[k] = first leaf (bit 31 set
-// for a covering run), sub_len[k] = run length, sub_res[k] = result count
-// (covering: the run's objects; intersecting: 0, filled by the filter).
+// a7: candidate leaves -> subquery records, in warp tiles of 32 consecutive
+// candidates (no shared memory, no block barriers).  The pairs touching a
+// tile are the 32 pairs from tile_p0[t] on (every pair has >= 1 candidate);
+// lane j loads pair tile_p0[t] + j, the pair starts inside the tile are
+// gathered in one bit mask, and the pair of lane L is found by a popcount.
+// Consecutive covering leaves of one pair inside one tile form one covering
+// run (their objects are one contiguous range of the sorted objects).
+// Count pass -> scan of the per-tile record counts -> write pass.  Record k:
+// sub_q[k] = query, sub_leaf[k] = first leaf (bit 31 set for a covering run),
+// sub_len[k] = run length, sub_res[k] = result count (covering: the run's
+// objects; intersecting: 0, filled by the filter).  Records are in
+// query-major order.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ int classify_candidate(unsigned long long cand, uint32_t p,
-                                                  const uint32_t *__restrict__ pair_q,
-                                                  const uint32_t *__restrict__ pair_first,
-                                                  const uint32_t *__restrict__ pair_blo,
-                                                  const unsigned long long *__restrict__ pair_off,
-                                                  const uint2 *__restrict__ qcells,
-                                                  const uint32_t *__restrict__ leaf_lo,
-                                                  const uint32_t *__restrict__ leaf_hi, int covering) {
-    uint32_t i0, i1, j0, j1;
-    unpack_cells(__ldg(qcells + __ldg(pair_q + p)), i0, i1, j0, j1);
-    const uint32_t l = __ldg(pair_first + p) + (uint32_t)(cand - __ldg(pair_off + p));
-    int cl = classify(i0, i1, j0, j1, block_log2(i0, i1, j0, j1), __ldg(pair_blo + p), __ldg(leaf_lo + l),
-                      __ldg(leaf_hi + l));
-    return (cl == 2 && !covering) ? 1 : cl;
+struct CandLane {
+    bool valid;
+    int code;          // 0 none, 1 intersecting, 2 covering
+    bool cont;         // covering and continuing the run of the previous lane
+    uint32_t q, leaf, p_rel;
+    uint32_t po_j;     // lane j's pair: offset of its first candidate in the tile
+    bool pj_starts;    // lane j's pair starts inside this tile
+};
+
+__device__ __forceinline__ CandLane cand_lane(unsigned long long t, unsigned long long ncand, uint32_t npairs,
+                                              int covering, const uint32_t *__restrict__ tile_p0,
+                                              const uint32_t *__restrict__ pair_q,
+                                              const uint32_t *__restrict__ pair_first,
+                                              const uint32_t *__restrict__ pair_blo,
+                                              const unsigned long long *__restrict__ pair_off,
+                                              const uint2 *__restrict__ qcells,
+                                              const uint32_t *__restrict__ leaf_lo,
+                                              const uint32_t *__restrict__ leaf_hi) {
+    const uint32_t lane = threadIdx.x & 31;
+    const unsigned long long c0 = t << 5;
+    const uint32_t p0 = __ldg(tile_p0 + t);
+    const uint32_t pj = p0 + lane;
+    uint32_t q_j = 0, f_j = 0, b_j = 0;
+    unsigned long long po = ~0ull;
+    if (pj < npairs) {
+        po = __ldg(pair_off + pj);
+        q_j = __ldg(pair_q + pj);
+        f_j = __ldg(pair_first + pj);
+        b_j = __ldg(pair_blo + pj);
+    }
+    CandLane r;
+    r.pj_starts = pj < npairs && po >= c0 && po < c0 + 32;
+    r.po_j = r.pj_starts ? (uint32_t)(po - c0) : 0u;
+    const uint32_t bit = (r.pj_starts && lane > 0) ? (1u << r.po_j) : 0u;
+    const uint32_t start_mask = __reduce_or_sync(0xffffffffu, bit);
+    uint32_t le;
+    asm("mov.u32 %0, %%lanemask_le;" : "=r"(le));
+    r.p_rel = __popc(start_mask & le);
+    const unsigned long long c = c0 + lane;
+    r.valid = c < ncand;
+    r.q = __shfl_sync(0xffffffffu, q_j, r.p_rel);
+    const uint32_t first = __shfl_sync(0xffffffffu, f_j, r.p_rel);
+    const uint32_t blo = __shfl_sync(0xffffffffu, b_j, r.p_rel);
+    const unsigned long long pstart = __shfl_sync(0xffffffffu, po, r.p_rel);
+    r.code = 0;
+    r.leaf = 0;
+    if (r.valid) {
+        r.leaf = first + (uint32_t)(c - pstart);
+        uint32_t i0, i1, j0, j1;
+        unpack_cells(__ldg(qcells + r.q), i0, i1, j0, j1);
+        r.code = classify(i0, i1, j0, j1, block_log2(i0, i1, j0, j1), blo, __ldg(leaf_lo + r.leaf),
+                          __ldg(leaf_hi + r.leaf));
+        if (r.code == 2 && !covering) r.code = 1;
+    }
+    const int prev = __shfl_up_sync(0xffffffffu, r.code, 1);
+    const bool is_start = r.valid && c == pstart;
+    r.cont = r.code == 2 && lane > 0 && !is_start && prev == 2;
+    return r;
 }
 
-__global__ void __launch_bounds__(kCandThreads)
-candidates_kernel(uint32_t Q, int covering, const uint32_t *__restrict__ leaf_lo,
-                  const uint32_t *__restrict__ leaf_hi, const uint32_t *__restrict__ leaf_beg,
-                  const uint2 *__restrict__ qcells, const unsigned long long *__restrict__ cand_off,
-                  const uint32_t *__restrict__ pair_q, const uint32_t *__restrict__ pair_first,
-                  const uint32_t *__restrict__ pair_blo, const unsigned long long *__restrict__ pair_off,
-                  uint32_t *__restrict__ sub_q, uint32_t *__restrict__ sub_leaf,
-                  uint32_t *__restrict__ sub_len, uint32_t *__restrict__ sub_res,
-                  uint32_t *__restrict__ sub_off, uint32_t *__restrict__ leaf_nsub, uint32_t *status,
-                  uint32_t *tile_counter, Caps caps, Info *info) {
-    constexpr int T = kCandTile, PER = kCandItems;
-    __shared__ unsigned long long s_poff[T + 2];
-    __shared__ uint32_t s_pq[T + 1], s_pfirst[T + 1], s_pblo[T + 1];
-    __shared__ uint8_t s_code[T];
-    __shared__ uint16_t s_pj[T];
-    __shared__ uint32_t s_rec[T + 1];
-    __shared__ uint32_t s_scan[kCandThreads / 32 + 1];
-    __shared__ unsigned long long s_red[4];
-    __shared__ uint32_t s_tile, s_p0, s_prefix, s_qa;
-    __shared__ int s_prev_cov;
-
-    const int tid = threadIdx.x;
+__global__ void __launch_bounds__(256)
+cand_count_kernel(int covering, const uint32_t *__restrict__ tile_p0, const uint32_t *__restrict__ pair_q,
+                  const uint32_t *__restrict__ pair_first, const uint32_t *__restrict__ pair_blo,
+                  const unsigned long long *__restrict__ pair_off, const uint2 *__restrict__ qcells,
+                  const uint32_t *__restrict__ leaf_lo, const uint32_t *__restrict__ leaf_hi,
+                  const uint32_t *__restrict__ leaf_beg, uint32_t *__restrict__ tile_cnt,
+                  uint32_t *__restrict__ leaf_nsub, Caps caps, Info *info) {
+    __shared__ unsigned long long s_red[3];
+    if (threadIdx.x < 3) s_red[threadIdx.x] = 0;
+    __syncthreads();
     const unsigned long long ncand = info->n_cand;
     const uint32_t npairs = (uint32_t)info->n_pairs;
-    if (ncand == 0) {
-        for (uint32_t q = blockIdx.x * blockDim.x + tid; q <= Q; q += gridDim.x * blockDim.x) sub_off[q] = 0;
-        return;
-    }
-    const unsigned long long ntiles = (ncand + T - 1) / T;
-    if (ntiles > caps.cand_tiles) return;     // the host sees n_cand, grows the status array, retries
-    for (;;) {
-        if (tid == 0) s_tile = atomicAdd(tile_counter, 1u);
-        if (tid < 4) s_red[tid] = 0;
-        __syncthreads();
-        const uint32_t tile = s_tile;
-        if (tile >= ntiles) break;
-        const unsigned long long c0 = (unsigned long long)tile * T;
-        const uint32_t cn = (uint32_t)min((unsigned long long)T, ncand - c0);
-        if (tid == 0) {
-            // last pair with pair_off[p] <= c0
-            uint32_t a = 0, b = npairs;
-            while (b - a > 1) {
-                uint32_t m = (a + b) >> 1;
-                if (pair_off[m] <= c0) a = m; else b = m;
-            }
-            s_p0 = a;
-        }
-        __syncthreads();
-        const uint32_t p0 = s_p0;
-        const uint32_t np = min((uint32_t)T + 1u, npairs - p0);      // pairs p0 .. p0+np-1
-        for (uint32_t j = tid; j <= np; j += kCandThreads) {
-            s_poff[j] = pair_off[p0 + j];                                // pair_off[npairs] = ncand
-            if (j < np) {
-                s_pq[j] = pair_q[p0 + j];
-                s_pfirst[j] = pair_first[p0 + j];
-                s_pblo[j] = pair_blo[p0 + j];
-            }
-        }
-        if (tid == 0) {
-            // classification of the candidate just before the tile, if it belongs to pair p0
-            s_prev_cov = 0;
-            if (c0 > 0 && c0 - 1 >= pair_off[p0])
-                s_prev_cov = classify_candidate(c0 - 1, p0, pair_q, pair_first, pair_blo, pair_off, qcells,
-                                                leaf_lo, leaf_hi, covering) == 2;
-        }
-        __syncthreads();
-
-        // classify this thread's candidates (blocked: tid*PER .. +PER)
-        uint32_t nrec = 0;
-        unsigned long long n_i = 0, n_c = 0, tests = 0;
-#pragma unroll
-        for (int e = 0; e < PER; ++e) {
-            const uint32_t loc = tid * PER + e;
-            if (loc >= cn) break;
-            const unsigned long long cand = c0 + loc;
-            uint32_t a = 0, b = np;                                   // last j with s_poff[j] <= cand
-            while (b - a > 1) {
-                uint32_t m = (a + b) >> 1;
-                if (s_poff[m] <= cand) a = m; else b = m;
-            }
-            uint32_t i0, i1, j0, j1;
-            unpack_cells(__ldg(qcells + s_pq[a]), i0, i1, j0, j1);
-            const uint32_t l = s_pfirst[a] + (uint32_t)(cand - s_poff[a]);
-            int cl = classify(i0, i1, j0, j1, block_log2(i0, i1, j0, j1), s_pblo[a], __ldg(leaf_lo + l),
-                              __ldg(leaf_hi + l));
-            if (cl == 2 && !covering) cl = 1;
-            s_code[loc] = (uint8_t)cl;
-            s_pj[loc] = (uint16_t)a;
-        }
-        __syncthreads();
-        // records: intersecting candidates and heads of covering runs
-        uint32_t rflags = 0;
-#pragma unroll
-        for (int e = 0; e < PER; ++e) {
-            const uint32_t loc = tid * PER + e;
-            if (loc >= cn) break;
-            const int cl = s_code[loc];
-            bool rec = false;
-            if (cl == 1) {
-                rec = true;
-            } else if (cl == 2) {
-                const unsigned long long cand = c0 + loc;
-                const uint32_t a = s_pj[loc];
-                bool cont;
-                if (cand == s_poff[a]) cont = false;                     // first candidate of its pair
-                else if (loc == 0) cont = s_prev_cov;
-                else cont = s_code[loc - 1] == 2;
-                rec = !cont;
-            }
-            if (rec) {
-                rflags |= 1u << e;
-                ++nrec;
-            }
-        }
-        uint32_t total;
-        uint32_t off = block_excl_scan<kCandThreads>(nrec, &total, s_scan);
-        if (tid == 0) s_prefix = lookback<uint32_t>(status, tile, total, &info->err);
-        // exclusive record prefix at every candidate position of the tile
-#pragma unroll
-        for (int e = 0; e < PER; ++e) {
-            const uint32_t loc = tid * PER + e;
-            if (loc < cn) s_rec[loc] = off;
-            if (rflags & (1u << e)) ++off;
-        }
-        if (tid == 0) s_rec[cn] = total;
-        __syncthreads();
-        const uint32_t prefix = s_prefix;
-
-        // write the records
-#pragma unroll
-        for (int e = 0; e < PER; ++e) {
-            const uint32_t loc = tid * PER + e;
-            if (loc >= cn) break;
-            const int cl = s_code[loc];
-            if (cl == 2) ++n_c;
-            if (!(rflags & (1u << e))) continue;
-            const unsigned long long cand = c0 + loc;
-            const uint32_t a = s_pj[loc];
-            const uint32_t q = s_pq[a];
-            const uint32_t l = s_pfirst[a] + (uint32_t)(cand - s_poff[a]);
-            const uint32_t k = prefix + s_rec[loc];
-            if (cl == 1) {
+    const unsigned long long ntiles = (ncand + 31) >> 5;
+    const uint32_t lane = threadIdx.x & 31;
+    unsigned long long n_i = 0, n_c = 0, tests = 0;
+    if (ntiles <= caps.cand_tiles) {
+        const unsigned long long nw = (unsigned long long)gridDim.x * (blockDim.x >> 5);
+        for (unsigned long long t = (blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x) >> 5; t < ntiles;
+             t += nw) {
+            CandLane r = cand_lane(t, ncand, npairs, covering, tile_p0, pair_q, pair_first, pair_blo, pair_off,
+                                   qcells, leaf_lo, leaf_hi);
+            const bool rec = r.code == 1 || (r.code == 2 && !r.cont);
+            const uint32_t m = __ballot_sync(0xffffffffu, rec);
+            if (lane == 0) tile_cnt[t] = __popc(m);
+            if (r.code == 1) {
                 ++n_i;
-                atomicAdd(leaf_nsub + l, 1u);
-                tests += __ldg(leaf_beg + l + 1) - __ldg(leaf_beg + l);
-                if (k < caps.sub) {
-                    sub_q[k] = q;
-                    sub_leaf[k] = l;
-                    sub_len[k] = 1;
-                    sub_res[k] = 0;
-                }
-            } else {
-                // run length: following candidates of the same pair that are covering
-                uint32_t len = 1;
-                const unsigned long long pend = s_poff[a + 1];
-                unsigned long long nx = cand + 1;
-                while (nx < pend) {
-                    int cl2;
-                    if (nx < c0 + cn) cl2 = s_code[nx - c0];
-                    else cl2 = classify_candidate(nx, p0 + a, pair_q, pair_first, pair_blo, pair_off, qcells,
-                                                  leaf_lo, leaf_hi, covering);
-                    if (cl2 != 2) break;
-                    ++len;
-                    ++nx;
-                }
-                if (k < caps.sub) {
-                    sub_q[k] = q;
-                    sub_leaf[k] = l | 0x80000000u;
-                    sub_len[k] = len;
-                    sub_res[k] = __ldg(leaf_beg + l + len) - __ldg(leaf_beg + l);
-                }
+                atomicAdd(leaf_nsub + r.leaf, 1u);
+                tests += __ldg(leaf_beg + r.leaf + 1) - __ldg(leaf_beg + r.leaf);
+            } else if (r.code == 2) {
+                ++n_c;
             }
         }
-        n_i = warp_sum(n_i); n_c = warp_sum(n_c); tests = warp_sum(tests);
-        if ((tid & 31) == 0) {
-            atomicAdd(&s_red[0], n_i);
-            atomicAdd(&s_red[1], n_c);
-            atomicAdd(&s_red[3], tests);
-        }
-        // per-query first record: queries whose first candidate lies in this tile
-        if (tid == 0) {
-            uint32_t a = 0, b = Q;                                     // first q with cand_off[q] >= c0
-            while (a < b) {
-                uint32_t m = (a + b) >> 1;
-                if (cand_off[m] >= c0) b = m; else a = m + 1;
-            }
-            s_qa = a;
-        }
-        __syncthreads();
-        const bool last_tile = c0 + cn == ncand;
-        for (uint32_t q = s_qa + tid; q <= Q; q += kCandThreads) {
-            const unsigned long long co = cand_off[q];
-            if (co >= c0 + cn && !(last_tile && co == ncand)) break;
-            sub_off[q] = prefix + (co >= c0 + cn ? total : s_rec[co - c0]);
-        }
-        if (tid == 0) {
-            if (s_red[0]) atomicAdd(&info->n_sub_i, s_red[0]);
-            if (s_red[1]) atomicAdd(&info->n_sub_c, s_red[1]);
-            if (s_red[3]) atomicAdd(&info->n_tests, s_red[3]);
-            if (total > s_red[0]) atomicAdd(&info->n_runs, (unsigned long long)(total - s_red[0]));
-            if (last_tile) info->n_sub = prefix + total;
-        }
-        __syncthreads();
+    }
+    n_i = warp_sum(n_i); n_c = warp_sum(n_c); tests = warp_sum(tests);
+    if (lane == 0) {
+        if (n_i) atomicAdd(&s_red[0], n_i);
+        if (n_c) atomicAdd(&s_red[1], n_c);
+        if (tests) atomicAdd(&s_red[2], tests);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        if (s_red[0]) atomicAdd(&info->n_sub_i, s_red[0]);
+        if (s_red[1]) atomicAdd(&info->n_sub_c, s_red[1]);
+        if (s_red[2]) atomicAdd(&info->n_tests, s_red[2]);
     }
 }
 
-void launch_candidates(cudaStream_t st, int num_sms, uint32_t Q, int covering, const uint32_t *leaf_lo,
-                       const uint32_t *leaf_hi, const uint32_t *leaf_beg, const uint2 *qcells,
-                       const unsigned long long *cand_off, const uint32_t *pair_q,
-                       const uint32_t *pair_first, const uint32_t *pair_blo,
-                       const unsigned long long *pair_off, uint32_t *sub_q, uint32_t *sub_leaf,
-                       uint32_t *sub_len, uint32_t *sub_res, uint32_t *sub_off, uint32_t *leaf_nsub,
-                       uint32_t *status, uint32_t *tile_counter, Caps caps, Info *info) {
-    candidates_kernel<<<num_sms * 4, kCandThreads, 0, st>>>(Q, covering, leaf_lo, leaf_hi, leaf_beg, qcells,
-                                                            cand_off, pair_q, pair_first, pair_blo, pair_off,
-                                                            sub_q, sub_leaf, sub_len, sub_res, sub_off,
-                                                            leaf_nsub, status, tile_counter, caps, info);
+// Exclusive scan of the per-tile record counts -> tile_off; n_sub = total.
+__global__ void __launch_bounds__(256)
+tile_scan_kernel(const uint32_t *__restrict__ tile_cnt, uint32_t *__restrict__ tile_off, uint32_t *status,
+                 uint32_t *tile_counter, Caps caps, Info *info) {
+    __shared__ uint32_t s_scan[256 / 32 + 1];
+    __shared__ uint32_t s_tile, s_prefix;
+    const int tid = threadIdx.x;
+    if (tid == 0) s_tile = atomicAdd(tile_counter, 1u);
+    __syncthreads();
+    const unsigned long long ntiles = (info->n_cand + 31) >> 5;
+    if (ntiles > caps.cand_tiles) return;
+    const uint32_t blk = s_tile;
+    const unsigned long long base = (unsigned long long)blk * 2048;
+    if (base >= ntiles) return;
+    uint32_t v[8], t = 0;
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
+        const unsigned long long i = base + tid * 8 + e;
+        v[e] = i < ntiles ? tile_cnt[i] : 0u;
+        t += v[e];
+    }
+    uint32_t total;
+    uint32_t off = block_excl_scan<256>(t, &total, s_scan);
+    if (tid < 32) {
+        const uint32_t pre = lookback_warp<uint32_t>(status, blk, total, &info->err);
+        if (tid == 0) s_prefix = pre;
+    }
+    __syncthreads();
+    off += s_prefix;
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
+        const unsigned long long i = base + tid * 8 + e;
+        if (i < ntiles) tile_off[i] = off;
+        off += v[e];
+    }
+    if (tid == 0 && base + 2048 >= ntiles) info->n_sub = s_prefix + total;
+}
+
+__global__ void __launch_bounds__(256)
+cand_write_kernel(int covering, const uint32_t *__restrict__ tile_p0, const uint32_t *__restrict__ pair_q,
+                  const uint32_t *__restrict__ pair_first, const uint32_t *__restrict__ pair_blo,
+                  const unsigned long long *__restrict__ pair_off, const uint2 *__restrict__ qcells,
+                  const uint32_t *__restrict__ leaf_lo, const uint32_t *__restrict__ leaf_hi,
+                  const uint32_t *__restrict__ leaf_beg, const uint32_t *__restrict__ tile_off,
+                  uint32_t *__restrict__ sub_q, uint32_t *__restrict__ sub_leaf, uint32_t *__restrict__ sub_len,
+                  uint32_t *__restrict__ sub_res, uint32_t *__restrict__ pair_rec, Caps caps,
+                  const Info *info) {
+    const unsigned long long ncand = info->n_cand;
+    const uint32_t npairs = (uint32_t)info->n_pairs;
+    const unsigned long long ntiles = (ncand + 31) >> 5;
+    if (ntiles > caps.cand_tiles) return;
+    const uint32_t nsub = (uint32_t)info->n_sub;
+    if (blockIdx.x == 0 && threadIdx.x == 0) pair_rec[npairs] = nsub;
+    const uint32_t lane = threadIdx.x & 31;
+    const uint32_t lt = lanemask_lt();
+    const unsigned long long nw = (unsigned long long)gridDim.x * (blockDim.x >> 5);
+    for (unsigned long long t = (blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x) >> 5; t < ntiles;
+         t += nw) {
+        CandLane r = cand_lane(t, ncand, npairs, covering, tile_p0, pair_q, pair_first, pair_blo, pair_off,
+                               qcells, leaf_lo, leaf_hi);
+        const bool rec = r.code == 1 || (r.code == 2 && !r.cont);
+        const uint32_t m = __ballot_sync(0xffffffffu, rec);
+        const uint32_t notcont = __ballot_sync(0xffffffffu, !(r.valid && r.cont));
+        const uint32_t base = __ldg(tile_off + t);
+        // the first record of every pair that starts in this tile
+        if (r.pj_starts) pair_rec[__ldg(tile_p0 + t) + lane] = base + __popc(m & ((1u << r.po_j) - 1u));
+        if (!rec) continue;
+        const uint32_t k = base + __popc(m & lt);
+        if (k >= caps.sub) continue;
+        if (r.code == 1) {
+            sub_q[k] = r.q;
+            sub_leaf[k] = r.leaf;
+            sub_len[k] = 1;
+            sub_res[k] = 0;
+        } else {
+            const uint32_t after = notcont & ~(lt | (1u << lane));   // later lanes that end the run
+            const uint32_t end = after ? (uint32_t)(__ffs(after) - 1) : 32u;
+            const uint32_t len = end - lane;
+            sub_q[k] = r.q;
+            sub_leaf[k] = r.leaf | 0x80000000u;
+            sub_len[k] = len;
+            sub_res[k] = __ldg(leaf_beg + r.leaf + len) - __ldg(leaf_beg + r.leaf);
+        }
+    }
+}
+
+void launch_candidates(cudaStream_t st, int num_sms, int covering, const uint32_t *tile_p0,
+                       const uint32_t *pair_q, const uint32_t *pair_first, const uint32_t *pair_blo,
+                       const unsigned long long *pair_off, const uint2 *qcells, const uint32_t *leaf_lo,
+                       const uint32_t *leaf_hi, const uint32_t *leaf_beg, uint32_t *tile_cnt,
+                       uint32_t *tile_off, uint32_t *leaf_nsub, uint32_t *sub_q, uint32_t *sub_leaf,
+                       uint32_t *sub_len, uint32_t *sub_res, uint32_t *pair_rec, uint32_t *status,
+                       uint32_t *tile_counter, Caps caps, Info *info) {
+    cand_count_kernel<<<num_sms * 8, 256, 0, st>>>(covering, tile_p0, pair_q, pair_first, pair_blo, pair_off,
+                                                   qcells, leaf_lo, leaf_hi, leaf_beg, tile_cnt, leaf_nsub,
+                                                   caps, info);
+    const unsigned long long scan_blocks = (caps.cand_tiles + 2047) / 2048;
+    tile_scan_kernel<<<(unsigned)(scan_blocks ? scan_blocks : 1), 256, 0, st>>>(tile_cnt, tile_off, status,
+                                                                              tile_counter, caps, info);
+    cand_write_kernel<<<num_sms * 8, 256, 0, st>>>(covering, tile_p0, pair_q, pair_first, pair_blo, pair_off,
+                                                   qcells, leaf_lo, leaf_hi, leaf_beg, tile_off, sub_q,
+                                                   sub_leaf, sub_len, sub_res, pair_rec, caps, info);
 }
 
 // ---------------------------------------------------------------------------
@@ -465,7 +458,8 @@ __global__ void __launch_bounds__(kLeafScanThreads)
 leaf_scan_kernel(const uint32_t *__restrict__ leaf_beg, const uint32_t *__restrict__ leaf_nsub,
                  uint32_t *__restrict__ leaf_sub_off, uint32_t *__restrict__ leaf_word_off,
                  uint32_t *__restrict__ leaf_item_off, uint32_t *__restrict__ leaf_cursor,
-                 uint32_t *status3, uint32_t num_tiles, uint32_t *tile_counter, Info *info) {
+                 uint32_t *__restrict__ item_leaf, uint32_t *status3, uint32_t num_tiles,
+                 uint32_t *tile_counter, Caps caps, Info *info) {
     __shared__ uint32_t s_scan[kLeafScanThreads / 32 + 1];
     __shared__ uint32_t s_tile, s_p[3];
     const int tid = threadIdx.x;
@@ -500,9 +494,11 @@ leaf_scan_kernel(const uint32_t *__restrict__ leaf_beg, const uint32_t *__restri
     uint32_t o_i = block_excl_scan<kLeafScanThreads>(t_i, &tot_i, s_scan);
     objs = warp_sum(objs);
     if ((tid & 31) == 0 && objs) atomicAdd(&info->n_item_objs, objs);
-    if (tid < 3) {
-        uint32_t agg = tid == 0 ? tot_s : (tid == 1 ? tot_w : tot_i);
-        s_p[tid] = lookback<uint32_t>(status3 + (size_t)tid * num_tiles, tile, agg, &info->err);
+    if (tid < 96) {
+        const int w = tid >> 5;
+        const uint32_t agg = w == 0 ? tot_s : (w == 1 ? tot_w : tot_i);
+        const uint32_t pre = lookback_warp<uint32_t>(status3 + (size_t)w * num_tiles, tile, agg, &info->err);
+        if ((tid & 31) == 0) s_p[w] = pre;
     }
     __syncthreads();
     o_s += s_p[0]; o_w += s_p[1]; o_i += s_p[2];
@@ -514,6 +510,8 @@ leaf_scan_kernel(const uint32_t *__restrict__ leaf_beg, const uint32_t *__restri
             leaf_cursor[l] = o_s;
             leaf_word_off[l] = o_w;
             leaf_item_off[l] = o_i;
+            for (uint32_t t = 0; t < ni[e]; ++t)
+                if (o_i + t < caps.items) item_leaf[o_i + t] = l;
         }
         o_s += ns[e]; o_w += nw[e]; o_i += ni[e];
     }
@@ -528,13 +526,14 @@ leaf_scan_kernel(const uint32_t *__restrict__ leaf_beg, const uint32_t *__restri
 
 void launch_leaf_scan(cudaStream_t st, uint32_t nmax, const uint32_t *leaf_beg,
                       const uint32_t *leaf_nsub, uint32_t *leaf_sub_off, uint32_t *leaf_word_off,
-                      uint32_t *leaf_item_off, uint32_t *leaf_cursor, uint32_t *status3,
-                      uint32_t *tile_counter, Info *info) {
+                      uint32_t *leaf_item_off, uint32_t *leaf_cursor, uint32_t *item_leaf,
+                      uint32_t *status3, uint32_t *tile_counter, Caps caps, Info *info) {
     if (nmax == 0) return;
     uint32_t tiles = (nmax + kLeafScanTile - 1) / kLeafScanTile;
     leaf_scan_kernel<<<tiles, kLeafScanThreads, 0, st>>>(leaf_beg, leaf_nsub, leaf_sub_off,
                                                          leaf_word_off, leaf_item_off, leaf_cursor,
-                                                         status3, tiles, tile_counter, info);
+                                                         item_leaf, status3, tiles, tile_counter, caps,
+                                                         info);
 }
 
 // ---------------------------------------------------------------------------
@@ -546,7 +545,9 @@ scatter_kernel(const uint32_t *__restrict__ sub_leaf, const uint32_t *__restrict
                const uint32_t *__restrict__ leaf_sub_off, const uint32_t *__restrict__ leaf_word_off,
                uint32_t *__restrict__ leaf_cursor, uint32_t *__restrict__ sub_bm,
                uint32_t *__restrict__ isub, Caps caps, const Info *info) {
-    if (info->n_sub > caps.sub || info->n_sub_i > caps.sub_i || info->n_words > caps.words) return;
+    if (info->n_sub > caps.sub || info->n_sub_i > caps.sub_i || info->n_words > caps.words ||
+        info->n_items > caps.items)
+        return;
     const uint32_t nsub = (uint32_t)info->n_sub;
     for (uint32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < nsub; k += gridDim.x * blockDim.x) {
         const uint32_t sl = sub_leaf[k];

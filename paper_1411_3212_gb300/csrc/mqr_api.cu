@@ -87,10 +87,10 @@ struct mqr_ctx {
         leaf_item_off, leaf_cursor;
     DevBuf<uint8_t> mk_a, mk_b;
     // per query / subquery
-    DevBuf<uint32_t> sub_off, sub_q, sub_leaf, sub_len, sub_res, sub_bm, isub, bitmap;
+    DevBuf<uint32_t> sub_q, sub_leaf, sub_len, sub_res, sub_bm, isub, bitmap, item_leaf;
     DevBuf<unsigned long long> out_off;
     // query splitting: coarse lookup table, per-query cells, (query, block) pairs
-    DevBuf<uint32_t> zmap, pair_q, pair_first, pair_blo;
+    DevBuf<uint32_t> zmap, pair_q, pair_first, pair_blo, pair_rec, qpair, tile_p0, tile_cnt, tile_off;
     DevBuf<uint2> qcells;
     DevBuf<unsigned long long> cand_off, pair_off;
     unsigned long long cand_tiles = 0;
@@ -152,7 +152,7 @@ Arena arena_layout(uint32_t nmax, uint32_t Q, unsigned long long sub_cap, unsign
     a.st_lscan = take((size_t)3 * a.lscan_tiles * sizeof(uint32_t));
     a.st_qb_p = take((size_t)a.qb_tiles * sizeof(uint32_t));
     a.st_qb_c = take((size_t)a.qb_tiles * sizeof(unsigned long long));
-    a.st_cand = take((size_t)a.cand_tiles * sizeof(uint32_t));
+    a.st_cand = take((size_t)((a.cand_tiles + kCandScanTile - 1) / kCandScanTile + 1) * sizeof(uint32_t));
     a.st_res = take((size_t)a.res_tiles * sizeof(unsigned long long));
     a.total = o;
     return a;
@@ -247,7 +247,6 @@ mqr_status enqueue_tick(mqr_ctx *c, const float4 *rects, uint32_t Q, int emit_ki
     MQR_CUDA(cudaMemcpyAsync(&info->err, c->upd_err.p, sizeof(unsigned long long),
                              cudaMemcpyDeviceToDevice, st));
     MQR_CUDA(cudaMemsetAsync(c->upd_err.p, 0, sizeof(unsigned long long), st));
-    if (Q == 0) MQR_CUDA(cudaMemsetAsync(c->sub_off.p, 0, sizeof(uint32_t), st));
 
     // a2 + a3: keys and the 4-pass onesweep sort of (key << 32 | id).
     phase_begin(c, MQR_PHASE_KEYS);
@@ -284,31 +283,33 @@ mqr_status enqueue_tick(mqr_ctx *c, const float4 *rects, uint32_t Q, int emit_ki
     caps.words = std::min<size_t>(c->bitmap.n, 0xffffffffull);
     caps.out = out_cap_elems;
     caps.cand_tiles = a.cand_tiles;
+    caps.items = c->item_leaf.n;
     phase_begin(c, MQR_PHASE_QUERY_BLOCKS);
     launch_zmap(st, c->leaf_hi.p, info, c->zmap.p);
     launch_query_blocks(st, rects, Q, x0, y0, c->sx, c->sy, c->leaf_lo.p, c->leaf_hi.p, c->zmap.p,
                         c->qcells.p, c->cand_off.p, c->pair_q.p, c->pair_first.p, c->pair_blo.p,
-                        c->pair_off.p, at<uint32_t>(c, a.st_qb_p), at<unsigned long long>(c, a.st_qb_c),
-                        ctr + 5, info);
+                        c->pair_off.p, c->qpair.p, c->tile_p0.p, a.cand_tiles,
+                        at<uint32_t>(c, a.st_qb_p), at<unsigned long long>(c, a.st_qb_c), ctr + 5, info);
     phase_end(c, MQR_PHASE_QUERY_BLOCKS, Q ? 2 : 1);
     // a7: candidates -> subquery records
     phase_begin(c, MQR_PHASE_CANDIDATES);
-    launch_candidates(st, c->num_sms, Q, cov, c->leaf_lo.p, c->leaf_hi.p, c->leaf_beg.p, c->qcells.p,
-                      c->cand_off.p, c->pair_q.p, c->pair_first.p, c->pair_blo.p, c->pair_off.p,
-                      c->sub_q.p, c->sub_leaf.p, c->sub_len.p, c->sub_res.p, c->sub_off.p, c->leaf_nsub.p,
-                      at<uint32_t>(c, a.st_cand), ctr + 8, caps, info);
-    phase_end(c, MQR_PHASE_CANDIDATES, 1);
+    launch_candidates(st, c->num_sms, cov, c->tile_p0.p, c->pair_q.p, c->pair_first.p, c->pair_blo.p,
+                      c->pair_off.p, c->qcells.p, c->leaf_lo.p, c->leaf_hi.p, c->leaf_beg.p, c->tile_cnt.p,
+                      c->tile_off.p, c->leaf_nsub.p, c->sub_q.p, c->sub_leaf.p, c->sub_len.p, c->sub_res.p,
+                      c->pair_rec.p, at<uint32_t>(c, a.st_cand), ctr + 8, caps, info);
+    phase_end(c, MQR_PHASE_CANDIDATES, 3);
     // a8: group intersecting subqueries by leaf
     phase_begin(c, MQR_PHASE_GROUP);
     launch_leaf_scan(st, nmax, c->leaf_beg.p, c->leaf_nsub.p, c->leaf_sub_off.p, c->leaf_word_off.p,
-                     c->leaf_item_off.p, c->leaf_cursor.p, at<uint32_t>(c, a.st_lscan), ctr + 6, info);
+                     c->leaf_item_off.p, c->leaf_cursor.p, c->item_leaf.p, at<uint32_t>(c, a.st_lscan),
+                     ctr + 6, caps, info);
     launch_scatter(st, c->num_sms, c->sub_leaf.p, c->leaf_beg.p, c->leaf_sub_off.p, c->leaf_word_off.p,
                    c->leaf_cursor.p, c->sub_bm.p, c->isub.p, caps, info);
     phase_end(c, MQR_PHASE_GROUP, nmax ? 2 : 1);
     // a10
     phase_begin(c, MQR_PHASE_FILTER);
     launch_filter(st, c->num_sms, rects, c->sxy.p, c->leaf_beg.p, c->leaf_sub_off.p,
-                  c->leaf_word_off.p, c->leaf_item_off.p, c->isub.p, c->sub_q.p, c->sub_res.p,
+                  c->leaf_word_off.p, c->leaf_item_off.p, c->item_leaf.p, c->isub.p, c->sub_q.p, c->sub_res.p,
                   c->bitmap.p, caps, info);
     phase_end(c, MQR_PHASE_FILTER, 1);
     // a11
@@ -326,7 +327,7 @@ mqr_status enqueue_tick(mqr_ctx *c, const float4 *rects, uint32_t Q, int emit_ki
     }
     if (offsets != nullptr) {
         phase_begin(c, MQR_PHASE_OFFSETS);
-        launch_query_offsets(st, Q, c->sub_off.p, c->out_off.p, offsets, caps, info);
+        launch_query_offsets(st, Q, c->qpair.p, c->pair_rec.p, c->out_off.p, offsets, caps, info);
         phase_end(c, MQR_PHASE_OFFSETS, 1);
     }
     return check_launch("tick kernels");
@@ -336,15 +337,19 @@ mqr_status enqueue_tick(mqr_ctx *c, const float4 *rects, uint32_t Q, int emit_ki
 // exists.
 mqr_status ensure_tick_buffers(mqr_ctx *c, uint32_t Q) {
     size_t sub0 = std::max<size_t>(4096, (size_t)Q * 4);
-    MQR_CUDA(c->sub_off.ensure((size_t)Q + 1));
     MQR_CUDA(c->zmap.ensure(kZCells + 1));
     MQR_CUDA(c->qcells.ensure(std::max<size_t>(Q, 1)));
     MQR_CUDA(c->cand_off.ensure((size_t)Q + 1));
+    MQR_CUDA(c->qpair.ensure((size_t)Q + 1));
     MQR_CUDA(c->pair_q.ensure((size_t)Q * 9 + 1));
     MQR_CUDA(c->pair_first.ensure((size_t)Q * 9 + 1));
     MQR_CUDA(c->pair_blo.ensure((size_t)Q * 9 + 1));
     MQR_CUDA(c->pair_off.ensure((size_t)Q * 9 + 1));
-    c->cand_tiles = std::max<unsigned long long>(c->cand_tiles, std::max<unsigned long long>(1024, Q / 4));
+    MQR_CUDA(c->pair_rec.ensure((size_t)Q * 9 + 2));
+    c->cand_tiles = std::max<unsigned long long>(c->cand_tiles, std::max<unsigned long long>(1 << 16, 2ull * Q));
+    MQR_CUDA(c->tile_p0.ensure(c->cand_tiles));
+    MQR_CUDA(c->tile_cnt.ensure(c->cand_tiles));
+    MQR_CUDA(c->tile_off.ensure(c->cand_tiles));
     if (c->sub_q.n == 0) {
         MQR_CUDA(c->sub_q.ensure(sub0));
         MQR_CUDA(c->sub_leaf.ensure(sub0));
@@ -354,6 +359,7 @@ mqr_status ensure_tick_buffers(mqr_ctx *c, uint32_t Q) {
         MQR_CUDA(c->out_off.ensure(sub0 + 1));
         MQR_CUDA(c->isub.ensure(sub0));
         MQR_CUDA(c->bitmap.ensure(std::max<size_t>(1 << 16, (size_t)Q * 16)));
+        MQR_CUDA(c->item_leaf.ensure(std::max<size_t>(1 << 16, (size_t)Q)));
     }
     return MQR_OK;
 }
@@ -400,9 +406,13 @@ mqr_status run_tick(mqr_ctx *c, const float4 *rects, uint32_t Q, int emit_kind, 
                         "an update id was >= max_objects (ignored); the tick was answered without it");
         }
         bool again = false;
-        const unsigned long long need_tiles = (in.n_cand + kCandTile - 1) / kCandTile;
+        const unsigned long long need_tiles = (in.n_cand + 31) / 32;
         if (need_tiles > caps.cand_tiles) {
             c->cand_tiles = grow_to(need_tiles);
+            c->tile_p0.release(); c->tile_cnt.release(); c->tile_off.release();
+            MQR_CUDA(c->tile_p0.ensure(c->cand_tiles));
+            MQR_CUDA(c->tile_cnt.ensure(c->cand_tiles));
+            MQR_CUDA(c->tile_off.ensure(c->cand_tiles));
             again = true;
         } else if (in.n_sub > caps.sub) {
             s = grow_sub(c, in.n_sub);
@@ -412,6 +422,11 @@ mqr_status run_tick(mqr_ctx *c, const float4 *rects, uint32_t Q, int emit_kind, 
             if (in.n_sub_i > caps.sub_i) {
                 c->isub.release();
                 MQR_CUDA(c->isub.ensure(grow_to(in.n_sub_i)));
+                again = true;
+            }
+            if (in.n_items > caps.items) {
+                c->item_leaf.release();
+                MQR_CUDA(c->item_leaf.ensure(grow_to(in.n_items)));
                 again = true;
             }
             if (in.n_words > caps.words) {
@@ -492,6 +507,8 @@ mqr_status tick_device(mqr_ctx *c, const float *rects_dev, uint32_t Q, int kind,
         return s;
     }
     if (kind == MQR_OUT_PAIRS || kind == MQR_OUT_CSR) {
+        if (out_dev && (reinterpret_cast<uintptr_t>(out_dev) & 15u))
+            return fail(MQR_ERR_INVALID_ARG, "out_dev must be 16-byte aligned");
         const size_t eb = out_elem_bytes(kind);
         unsigned long long cap_elems = cap_bytes / eb;
         mqr_status s = run_tick(c, rects, Q, kind == MQR_OUT_PAIRS ? kEmitPairs : kEmitIds,
@@ -515,7 +532,8 @@ mqr_status tick_device(mqr_ctx *c, const float *rects_dev, uint32_t Q, int kind,
     MQR_CUDA(c->sortA.ensure(R));
     MQR_CUDA(c->sortB.ensure(R));
     Arena a = arena_layout(c->nmax, Q, c->sub_q.n, c->cand_tiles);
-    Caps caps{c->sub_q.n, c->isub.n, std::min<size_t>(c->bitmap.n, 0xffffffffull), R, c->cand_tiles};
+    Caps caps{c->sub_q.n, c->isub.n, std::min<size_t>(c->bitmap.n, 0xffffffffull), R, c->cand_tiles,
+              c->item_leaf.n};
     Info *info = at<Info>(c, a.info);
     phase_begin(c, MQR_PHASE_OUTPUT_SORT);
     launch_emit(c->stream, c->num_sms, kEmitKeys64, c->sub_q.p, c->sub_leaf.p, c->sub_len.p,
@@ -568,9 +586,10 @@ void mqr_destroy(mqr_ctx *c) {
     for (auto *b : u64s) b->release();
     DevBuf<uint32_t> *u32s[] = {&c->skey, &c->sid, &c->leaf_lo, &c->leaf_hi, &c->leaf_beg, &c->leaf_nsub,
                                 &c->leaf_sub_off, &c->leaf_word_off, &c->leaf_item_off, &c->leaf_cursor,
-                                &c->sub_off, &c->sub_q, &c->sub_leaf, &c->sub_len, &c->sub_res,
-                                &c->sub_bm, &c->isub, &c->bitmap, &c->up_ids, &c->zmap, &c->pair_q,
-                                &c->pair_first, &c->pair_blo};
+                                &c->sub_q, &c->sub_leaf, &c->sub_len, &c->sub_res,
+                                &c->sub_bm, &c->isub, &c->bitmap, &c->item_leaf, &c->up_ids, &c->zmap, &c->pair_q,
+                                &c->pair_first, &c->pair_blo, &c->pair_rec, &c->qpair, &c->tile_p0,
+                                &c->tile_cnt, &c->tile_off};
     for (auto *b : u32s) b->release();
     c->qcells.release();
     c->cand_off.release();
@@ -773,7 +792,7 @@ mqr_status mqr_get_stats(const mqr_ctx *c, mqr_stats *o) {
     o->max_level = in.max_level;
     o->n_sub_intersecting = in.n_sub_i;
     o->n_sub_covering = in.n_sub_c;
-    o->n_covering_runs = in.n_runs;
+    o->n_covering_runs = in.n_sub - in.n_sub_i;
     o->n_tests = in.n_tests;
     o->n_filter_items = in.n_items;
     o->n_bitmap_words = in.n_words;

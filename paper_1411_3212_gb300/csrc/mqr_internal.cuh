@@ -55,7 +55,8 @@ struct Caps {
     unsigned long long sub_i;    // intersecting subqueries (isub list)
     unsigned long long words;    // bitmap words
     unsigned long long out;      // output elements (pairs / ids / bitmap words)
-    unsigned long long cand_tiles;  // look-back status slots of the candidate pass
+    unsigned long long cand_tiles;  // warp tiles (32 candidates) the candidate buffers can hold
+    unsigned long long items;       // filter work items (item -> leaf map)
 };
 
 // ---------------------------------------------------------------------------
@@ -143,9 +144,11 @@ __device__ __forceinline__ T block_excl_scan(T v, T *total, T *smem) {
 
 // ---------------------------------------------------------------------------
 // Decoupled look-back for single-pass scans.  A status word packs a 2-bit
-// flag (1 = tile aggregate, 2 = inclusive prefix) above the value.  Waits are
-// bounded by a wall-clock deadline; on expiry the kernel records kErrTimeout
-// and carries on with a partial sum (its output is then discarded by the host).
+// flag (1 = tile aggregate, 2 = inclusive prefix) above the value.  Tiles are
+// numbered in the order their blocks start (an atomic counter), so a tile
+// only ever waits for tiles already running.  Waits are bounded by a
+// wall-clock deadline; on expiry the kernel records kErrTimeout and carries on
+// with a partial sum (its output is then discarded by the host).
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ unsigned long long global_ns() {
     unsigned long long t;
@@ -172,10 +175,64 @@ __device__ __forceinline__ unsigned long long status_load(const unsigned long lo
 __device__ __forceinline__ void status_store(uint32_t *p, uint32_t v) { atomicExch(p, v); }
 __device__ __forceinline__ void status_store(unsigned long long *p, unsigned long long v) { atomicExch(p, v); }
 
-// Called by ONE thread of tile `tile`: publishes `agg`, returns the exclusive
-// prefix of all earlier tiles, then publishes the inclusive prefix.
+// Warp-wide look-back, called by all 32 lanes of one warp of tile `tile`:
+// publishes `agg`, examines the 32 nearest earlier tiles per step (one per
+// lane), and returns (to every lane) the exclusive prefix of all earlier
+// tiles, then publishes the inclusive prefix.
 template <typename T>
-__device__ T lookback(T *status, uint32_t tile, T agg, unsigned long long *err) {
+__device__ T lookback_warp(T *status, uint32_t tile, T agg, unsigned long long *err) {
+    using B = StatusBits<T>;
+    const int lane = threadIdx.x & 31;
+    if (tile == 0) {
+        if (lane == 0) status_store(status, (T(2) << B::kShift) | agg);
+        return T(0);
+    }
+    if (lane == 0) status_store(status + tile, (T(1) << B::kShift) | agg);
+    T sum = 0;
+    long j = (long)tile - 1;
+    unsigned long long t0 = 0;
+    unsigned spins = 0;
+    bool expired = false;
+    for (;;) {
+        const long idx = j - lane;
+        T v = idx < 0 ? (T(2) << B::kShift) : status_load(status + idx);
+        for (;;) {
+            const bool inval = (v >> B::kShift) == 0;
+            if (!__any_sync(0xffffffffu, inval)) break;
+            __nanosleep(64);
+            if (inval) v = status_load(status + idx);
+            if ((++spins & 63u) == 0) {
+                if (lane == 0) {
+                    unsigned long long now = global_ns();
+                    if (t0 == 0) t0 = now;
+                    else if (now - t0 > kWaitNs) expired = true;
+                }
+                expired = __shfl_sync(0xffffffffu, expired, 0);
+                if (expired) break;
+            }
+        }
+        if (expired) {
+            if (lane == 0) atomicOr(err, kErrTimeout);
+            break;
+        }
+        const T flag = v >> B::kShift, val = v & B::kMask;
+        const uint32_t incl = __ballot_sync(0xffffffffu, flag == 2);
+        if (incl) {
+            const int first = __ffs(incl) - 1;
+            sum += warp_sum(lane <= first ? val : T(0));
+            break;
+        }
+        sum += warp_sum(val);
+        j -= 32;
+    }
+    if (lane == 0) status_store(status + tile, (T(2) << B::kShift) | (sum + agg));
+    return sum;
+}
+
+// Per-thread look-back for the radix sort, where every thread scans the
+// status of its own digit (consecutive tiles adjacent in memory).
+template <typename T>
+__device__ T lookback1(T *status, uint32_t tile, T agg, unsigned long long *err) {
     using B = StatusBits<T>;
     if (tile == 0) {
         status_store(status, (T(2) << B::kShift) | agg);
@@ -187,14 +244,18 @@ __device__ T lookback(T *status, uint32_t tile, T agg, unsigned long long *err) 
     unsigned long long t0 = 0;
     unsigned spins = 0;
     while (j >= 0) {
-        T v = status_load(status + j);
-        T flag = v >> B::kShift;
+        const T v = status_load(status + j);
+        const T flag = v >> B::kShift;
         if (flag == 0) {
             if ((++spins & 63u) == 0) {
-                unsigned long long now = global_ns();
+                const unsigned long long now = global_ns();
                 if (t0 == 0) t0 = now;
-                else if (now - t0 > kWaitNs) { atomicOr(err, kErrTimeout); break; }
+                else if (now - t0 > kWaitNs) {
+                    atomicOr(err, kErrTimeout);
+                    break;
+                }
             }
+            __nanosleep(32);
             continue;
         }
         sum += v & B::kMask;
@@ -248,7 +309,7 @@ constexpr int kZLevel = 8;
 constexpr uint32_t kZCells = 1u << (2 * kZLevel);
 constexpr int kZShift = 2 * (kLevels - kZLevel);
 constexpr int kQBThreads = 256;                       // queries per tile of query_blocks
-constexpr int kCandThreads = 256, kCandItems = 4, kCandTile = kCandThreads * kCandItems;
+constexpr int kCandScanTile = 2048;                   // warp tiles per block of the tile-count scan
 
 void launch_zmap(cudaStream_t st, const uint32_t *leaf_hi, const Info *info, uint32_t *zmap);
 // a5 + a6: blocks, leaf ranges and candidate counts per query, scanned.
@@ -256,23 +317,25 @@ void launch_query_blocks(cudaStream_t st, const float4 *rects, uint32_t Q, float
                          float sy, const uint32_t *leaf_lo, const uint32_t *leaf_hi, const uint32_t *zmap,
                          uint2 *qcells, unsigned long long *cand_off, uint32_t *pair_q,
                          uint32_t *pair_first, uint32_t *pair_blo, unsigned long long *pair_off,
+                         uint32_t *qpair, uint32_t *tile_p0, unsigned long long tile_cap,
                          uint32_t *status_p, unsigned long long *status_c, uint32_t *tile_counter,
                          Info *info);
-// a7: candidates -> subquery records (query-major), sub_off[Q+1], leaf_nsub.
-void launch_candidates(cudaStream_t st, int num_sms, uint32_t Q, int covering, const uint32_t *leaf_lo,
-                       const uint32_t *leaf_hi, const uint32_t *leaf_beg, const uint2 *qcells,
-                       const unsigned long long *cand_off, const uint32_t *pair_q,
-                       const uint32_t *pair_first, const uint32_t *pair_blo,
-                       const unsigned long long *pair_off, uint32_t *sub_q, uint32_t *sub_leaf,
-                       uint32_t *sub_len, uint32_t *sub_res, uint32_t *sub_off, uint32_t *leaf_nsub,
-                       uint32_t *status, uint32_t *tile_counter, Caps caps, Info *info);
+// a7: candidates (warp tiles of 32) -> subquery records (query-major), the
+// first record of every pair (pair_rec[npairs+1]) and leaf_nsub.
+void launch_candidates(cudaStream_t st, int num_sms, int covering, const uint32_t *tile_p0,
+                       const uint32_t *pair_q, const uint32_t *pair_first, const uint32_t *pair_blo,
+                       const unsigned long long *pair_off, const uint2 *qcells, const uint32_t *leaf_lo,
+                       const uint32_t *leaf_hi, const uint32_t *leaf_beg, uint32_t *tile_cnt,
+                       uint32_t *tile_off, uint32_t *leaf_nsub, uint32_t *sub_q, uint32_t *sub_leaf,
+                       uint32_t *sub_len, uint32_t *sub_res, uint32_t *pair_rec, uint32_t *status,
+                       uint32_t *tile_counter, Caps caps, Info *info);
 
 // a8: scans over leaves -> leaf_sub_off, leaf_word_off, leaf_item_off, cursor.
 constexpr int kLeafScanThreads = 256, kLeafScanItems = 8, kLeafScanTile = kLeafScanThreads * kLeafScanItems;
 void launch_leaf_scan(cudaStream_t st, uint32_t nmax, const uint32_t *leaf_beg,
                       const uint32_t *leaf_nsub, uint32_t *leaf_sub_off, uint32_t *leaf_word_off,
-                      uint32_t *leaf_item_off, uint32_t *leaf_cursor, uint32_t *status3,
-                      uint32_t *tile_counter, Info *info);
+                      uint32_t *leaf_item_off, uint32_t *leaf_cursor, uint32_t *item_leaf,
+                      uint32_t *status3, uint32_t *tile_counter, Caps caps, Info *info);
 
 // a8 scatter: intersecting subqueries into their leaf's list + bitmap rows.
 void launch_scatter(cudaStream_t st, int num_sms, const uint32_t *sub_leaf, const uint32_t *leaf_beg,
@@ -283,8 +346,8 @@ void launch_scatter(cudaStream_t st, int num_sms, const uint32_t *sub_leaf, cons
 void launch_filter(cudaStream_t st, int num_sms, const float4 *rects, const float2 *sxy,
                    const uint32_t *leaf_beg, const uint32_t *leaf_sub_off,
                    const uint32_t *leaf_word_off, const uint32_t *leaf_item_off,
-                   const uint32_t *isub, const uint32_t *sub_q, uint32_t *sub_res,
-                   uint32_t *bitmap, Caps caps, const Info *info);
+                   const uint32_t *item_leaf, const uint32_t *isub, const uint32_t *sub_q,
+                   uint32_t *sub_res, uint32_t *bitmap, Caps caps, const Info *info);
 
 // a11: result offsets out_off[k] (u64, exclusive) over subquery records.
 constexpr int kResThreads = 256, kResItems = 8, kResTile = kResThreads * kResItems;
@@ -300,8 +363,8 @@ void launch_emit(cudaStream_t st, int num_sms, int emit_kind, const uint32_t *su
                  const uint32_t *sid, const uint32_t *bitmap, void *out, uint32_t bitmap_words_per_row,
                  Caps caps, const Info *info);
 
-// Per-query offsets from subquery offsets: off[q] = out_off[sub_off[q]].
-void launch_query_offsets(cudaStream_t st, uint32_t Q, const uint32_t *sub_off,
+// Per-query offsets: off[q] = out_off[pair_rec[qpair[q]]].
+void launch_query_offsets(cudaStream_t st, uint32_t Q, const uint32_t *qpair, const uint32_t *pair_rec,
                           const unsigned long long *out_off, unsigned long long *offsets,
                           Caps caps, const Info *info);
 
