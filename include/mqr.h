@@ -222,6 +222,28 @@ mqr_status mqr_set_timing(mqr_ctx *ctx, int enable);
  * completed since timing was enabled. */
 mqr_status mqr_get_timing(const mqr_ctx *ctx, mqr_timing *out);
 
+/* Largest n accepted by mqr_sort_objects_noalloc. */
+#define MQR_NOALLOC_MAX_OBJECTS 262144u
+
+/* Allocation-free Morton sort of n objects, for callers that cannot allocate
+ * device memory: embedders that own all device memory (a fixed budget or their
+ * own pool) and latency-critical loops that cannot afford the device-wide
+ * synchronisation cudaMalloc / cudaFree may cause.  The paper has no
+ * counterpart: this is a library convenience, not a step of the method.
+ * Objects 0..n-1 are at (xy_dev[2i], xy_dev[2i+1]) (float32, device, all
+ * present); on return keys_out_dev[k] (uint32, device) holds the k-th
+ * smallest Morton key at l_max = 15 over `bounds` and ids_out_dev[k] its
+ * object id (ties in id order) -- the same order mqr_get_sorted reports for a
+ * context holding those objects.  Scratch memory is a fixed array of about
+ * 4.3 MB held by every GPU that loads the library until the process exits;
+ * n > MQR_NOALLOC_MAX_OBJECTS is rejected with INVALID_ARG.  The first call
+ * on a device looks the array's address up (cudaGetSymbolAddress), so make it
+ * before any stream capture.  All calls share the array: calls that overlap
+ * on the GPU (e.g. on different streams) race.  Blocks until done.  Errors:
+ * INVALID_ARG, CUDA, TIMEOUT, INTERNAL.  cuda_stream: a cudaStream_t or NULL. */
+mqr_status mqr_sort_objects_noalloc(mqr_rect bounds, const float *xy_dev, uint32_t n,
+                                    uint32_t *keys_out_dev, uint32_t *ids_out_dev, void *cuda_stream);
+
 /* Message of the last failed call on this thread ("" if none). */
 const char *mqr_last_error(void);
 

@@ -64,6 +64,8 @@ size_t grow_to(unsigned long long need) { return (size_t)(need + need / 4 + 1024
 
 }  // namespace
 
+void mqr::set_last_error(const std::string &msg) { g_err = msg; }
+
 struct mqr_ctx {
     int device = 0;
     int num_sms = 148;

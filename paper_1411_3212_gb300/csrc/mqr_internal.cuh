@@ -18,6 +18,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <string>
+
 namespace mqr {
 
 constexpr int kLevels = 15;                 // l_max: 15 bits per axis, 30-bit keys
@@ -271,6 +273,9 @@ __device__ __forceinline__ uint32_t lanemask_lt() {
     asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
     return m;
 }
+
+// Message returned by mqr_last_error() on the calling thread.
+void set_last_error(const std::string &msg);
 
 // ---------------------------------------------------------------------------
 // Launchers (host functions; all enqueue on `st`)

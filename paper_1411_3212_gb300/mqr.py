@@ -26,7 +26,10 @@ KINDS = {"pairs": MQR_OUT_PAIRS, "pairs_sorted": MQR_OUT_PAIRS_SORTED, "csr": MQ
 # Every symbol include/mqr.h declares.
 EXPORTS = ["mqr_config_default", "mqr_create", "mqr_create_ex", "mqr_apply_updates",
            "mqr_apply_updates_host", "mqr_tick", "mqr_tick_host", "mqr_get_stats", "mqr_get_leaves",
-           "mqr_get_sorted", "mqr_set_timing", "mqr_get_timing", "mqr_last_error", "mqr_destroy"]
+           "mqr_get_sorted", "mqr_set_timing", "mqr_get_timing", "mqr_sort_objects_noalloc",
+           "mqr_last_error", "mqr_destroy"]
+
+MQR_NOALLOC_MAX_OBJECTS = 262144
 
 PHASES = ["updates", "keys", "sort", "leaves", "query_blocks", "group", "candidates", "filter",
           "result_scan", "emit", "offsets", "output_sort"]
@@ -95,6 +98,7 @@ def load(path: str = LIB_PATH):
         "mqr_get_sorted": ([P, P, P, u64, ctypes.POINTER(u64)], i32),
         "mqr_set_timing": ([P, i32], i32),
         "mqr_get_timing": ([P, ctypes.POINTER(mqr_timing)], i32),
+        "mqr_sort_objects_noalloc": ([mqr_rect, P, u32, P, P, P], i32),
         "mqr_last_error": ([], ctypes.c_char_p),
         "mqr_destroy": ([P], None),
     }
@@ -219,6 +223,11 @@ def mqr_get_timing(ctx):
     t = mqr_timing()
     _check(load().mqr_get_timing(ctx, ctypes.byref(t)))
     return t.as_dict()
+
+
+def mqr_sort_objects_noalloc(bounds, xy_dev, n, keys_out_dev, ids_out_dev, cuda_stream=None):
+    _check(load().mqr_sort_objects_noalloc(mqr_rect(*bounds), _ptr(xy_dev), n, _ptr(keys_out_dev),
+                                           _ptr(ids_out_dev), cuda_stream))
 
 
 def mqr_last_error():
