@@ -121,6 +121,7 @@ struct mqr_ctx {
     mqr_timing acc{};
     unsigned long long last_q = 0, retries = 0;
     bool have_tick = false;
+    bool bad_id = false;   // an update id >= max_objects was seen since the last report
 };
 
 namespace {
@@ -403,10 +404,7 @@ mqr_status run_tick(mqr_ctx *c, const float4 *rects, uint32_t Q, int emit_kind, 
         if (in.err & kErrTimeout)
             return fail(MQR_ERR_TIMEOUT, "a device-side wait exceeded its deadline");
         if (in.err & kErrInternal) return fail(MQR_ERR_INTERNAL, "device index out of range");
-        if (in.err & kErrBadId) {
-            return fail(MQR_ERR_INVALID_ARG,
-                        "an update id was >= max_objects (ignored); the tick was answered without it");
-        }
+        if (in.err & kErrBadId) c->bad_id = true;
         bool again = false;
         const unsigned long long need_tiles = (in.n_cand + 31) / 32;
         if (need_tiles > caps.cand_tiles) {
@@ -490,8 +488,8 @@ mqr_status sort_result_keys(mqr_ctx *c, uint64_t n, uint32_t Q, unsigned long lo
     return MQR_OK;
 }
 
-mqr_status tick_device(mqr_ctx *c, const float *rects_dev, uint32_t Q, int kind, void *out_dev,
-                       uint64_t cap_bytes, uint64_t *out_count, uint64_t *offsets_dev) {
+mqr_status tick_device_impl(mqr_ctx *c, const float *rects_dev, uint32_t Q, int kind, void *out_dev,
+                            uint64_t cap_bytes, uint64_t *out_count, uint64_t *offsets_dev) {
     const float4 *rects = reinterpret_cast<const float4 *>(rects_dev);
     unsigned long long *offs = reinterpret_cast<unsigned long long *>(offsets_dev);
     const uint32_t wpr = bitmap_words_per_row(c->nmax);
@@ -553,6 +551,19 @@ mqr_status tick_device(mqr_ctx *c, const float *rects_dev, uint32_t Q, int kind,
     MQR_CUDA(cudaStreamSynchronize(c->stream));
     phases_collect(c, false);
     return MQR_OK;
+}
+
+// The tick itself, then the deferred report of ignored update ids (the tick
+// was answered completely, without those updates).
+mqr_status tick_device(mqr_ctx *c, const float *rects_dev, uint32_t Q, int kind, void *out_dev,
+                       uint64_t cap_bytes, uint64_t *out_count, uint64_t *offsets_dev) {
+    mqr_status s = tick_device_impl(c, rects_dev, Q, kind, out_dev, cap_bytes, out_count, offsets_dev);
+    if (s == MQR_OK && c->bad_id) {
+        c->bad_id = false;
+        return fail(MQR_ERR_INVALID_ARG,
+                    "an update id was >= max_objects (ignored); the tick was answered without it");
+    }
+    return s;
 }
 
 }  // namespace

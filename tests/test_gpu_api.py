@@ -1,0 +1,167 @@
+"""C-ABI behaviour on the GPU: output kinds, host-buffer entry points,
+capacity and id errors, timing counters."""
+import ctypes
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1411_3212_gb300 import workloads
+from tests.gpu_util import assert_same_csr, oracle_state, to_dev, torch_dev
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def case():
+    w = workloads.HotspotWalk(n=30000, q=2000, hotspots=6, side_lo=0.001, side_hi=0.03, seed=21)
+    t = w.next_tick()
+    st = oracle_state(30000, [(t.ids, t.xy)])
+    return t, oracle.join_grid(st, t.rects, cell_side=0.005)
+
+
+def mk(n, cap=32):
+    from paper_1411_3212_gb300 import mqr
+    return mqr, mqr.Index(bounds=(0.0, 0.0, 1.0, 1.0), leaf_cap=cap, max_objects=n)
+
+
+def test_pairs_sorted_kind(case):
+    torch, dev = torch_dev()
+    t, (woff, wids) = case
+    mqr, idx = mk(30000)
+    idx.apply_updates(to_dev(t.ids, dev), to_dev(t.xy, dev))
+    res, offs = idx.tick(to_dev(t.rects, dev), kind="pairs_sorted")
+    p = res.cpu().numpy().view(np.uint32)
+    want_q = np.repeat(np.arange(t.rects.shape[0], dtype=np.uint32), np.diff(woff.astype(np.int64)))
+    np.testing.assert_array_equal(p[:, 0], want_q)
+    np.testing.assert_array_equal(p[:, 1], wids)
+    np.testing.assert_array_equal(offs.cpu().numpy().view(np.uint64), woff)
+    idx.close()
+
+
+def test_csr_unsorted_kind_is_a_permutation_per_query(case):
+    torch, dev = torch_dev()
+    t, (woff, wids) = case
+    mqr, idx = mk(30000)
+    idx.apply_updates(to_dev(t.ids, dev), to_dev(t.xy, dev))
+    res, offs = idx.tick(to_dev(t.rects, dev), kind="csr")
+    ids = res.cpu().numpy().view(np.uint32)
+    off = offs.cpu().numpy().view(np.uint64)
+    np.testing.assert_array_equal(off, woff)
+    for q in range(t.rects.shape[0]):
+        a, b = int(off[q]), int(off[q + 1])
+        np.testing.assert_array_equal(np.sort(ids[a:b]), wids[a:b])
+    idx.close()
+
+
+def test_host_entry_points(case):
+    torch, dev = torch_dev()
+    t, want = case
+    from paper_1411_3212_gb300 import mqr
+    ctx = mqr.mqr_create((0.0, 0.0, 1.0, 1.0), 32, 30000)
+    try:
+        mqr.mqr_apply_updates_host(ctx, np.ascontiguousarray(t.ids), np.ascontiguousarray(t.xy))
+        Q = t.rects.shape[0]
+        offs = np.zeros(Q + 1, np.uint64)
+        out = np.zeros(16, np.uint32)                    # far too small: CAPACITY with the size needed
+        st, cnt = mqr.mqr_tick_host(ctx, np.ascontiguousarray(t.rects), Q, mqr.MQR_OUT_CSR_SORTED, out,
+                                    out.nbytes, offs)
+        assert st == mqr.MQR_ERR_CAPACITY and cnt == want[1].shape[0]
+        out = np.zeros(cnt, np.uint32)
+        st, cnt = mqr.mqr_tick_host(ctx, np.ascontiguousarray(t.rects), Q, mqr.MQR_OUT_CSR_SORTED, out,
+                                    out.nbytes, offs)
+        assert st == mqr.MQR_OK
+        assert_same_csr((offs, out), want)
+        bm = np.zeros((Q, (30000 + 31) // 32), np.uint32)
+        st, cnt = mqr.mqr_tick_host(ctx, np.ascontiguousarray(t.rects), Q, mqr.MQR_OUT_BITMAP, bm, bm.nbytes)
+        assert st == mqr.MQR_OK
+        np.testing.assert_array_equal(bm, oracle.bitmap(*want, 30000))
+    finally:
+        mqr.mqr_destroy(ctx)
+
+
+def test_device_capacity_error_then_retry(case):
+    torch, dev = torch_dev()
+    t, want = case
+    from paper_1411_3212_gb300 import mqr
+    mqr_, idx = mk(30000)
+    idx.apply_updates(to_dev(t.ids, dev), to_dev(t.xy, dev))
+    Q = t.rects.shape[0]
+    rd = to_dev(t.rects, dev)
+    small = torch.empty(64, dtype=torch.int32, device=dev)
+    st, cnt = mqr.mqr_tick(idx.ctx, rd, Q, mqr.MQR_OUT_PAIRS, small, small.numel() * 4)
+    assert st == mqr.MQR_ERR_CAPACITY and cnt == want[1].shape[0]
+    big = torch.empty(2 * cnt, dtype=torch.int32, device=dev)
+    st, cnt2 = mqr.mqr_tick(idx.ctx, rd, Q, mqr.MQR_OUT_PAIRS, big, big.numel() * 4)
+    assert st == mqr.MQR_OK and cnt2 == cnt
+    idx.close()
+
+
+def test_bad_update_id_is_reported_and_ignored():
+    torch, dev = torch_dev()
+    from paper_1411_3212_gb300 import mqr
+    mqr_, idx = mk(100, cap=4)
+    ids = np.array([0, 1, 100, 2], np.uint32)             # 100 >= max_objects
+    xy = np.array([[0.1, 0.1], [0.2, 0.2], [0.3, 0.3], [0.4, 0.4]], np.float32)
+    idx.apply_updates(to_dev(ids, dev), to_dev(xy, dev))
+    with pytest.raises(mqr.MqrError, match="max_objects"):
+        idx.tick(to_dev(np.array([[0, 0, 1, 1]], np.float32), dev), kind="csr_sorted")
+    # the error is reported once; the valid updates were applied
+    res, offs = idx.tick(to_dev(np.array([[0, 0, 1, 1]], np.float32), dev), kind="csr_sorted")
+    np.testing.assert_array_equal(res.cpu().numpy(), [0, 1, 2])
+    idx.close()
+
+
+def test_misaligned_output_rejected(case):
+    torch, dev = torch_dev()
+    t, want = case
+    from paper_1411_3212_gb300 import mqr
+    mqr_, idx = mk(30000)
+    idx.apply_updates(to_dev(t.ids, dev), to_dev(t.xy, dev))
+    buf = torch.empty(1 << 20, dtype=torch.int32, device=dev)
+    with pytest.raises(mqr.MqrError, match="aligned"):
+        mqr.mqr_tick(idx.ctx, to_dev(t.rects, dev), t.rects.shape[0], mqr.MQR_OUT_PAIRS,
+                     buf.data_ptr() + 4, buf.numel() * 4 - 4)
+    idx.close()
+
+
+def test_timing_counters(case):
+    torch, dev = torch_dev()
+    t, want = case
+    mqr, idx = mk(30000)
+    idx.set_timing(True)
+    for _ in range(2):
+        idx.apply_updates(to_dev(t.ids, dev), to_dev(t.xy, dev))
+        idx.tick(to_dev(t.rects, dev), kind="pairs")
+    tm = idx.timing()
+    assert tm["ticks"] >= 2
+    for ph in ["updates", "keys", "sort", "leaves", "query_blocks", "candidates", "group", "filter",
+               "result_scan", "emit"]:
+        assert tm["launches"][ph] > 0 and tm["ms"][ph] > 0.0, ph
+    idx.close()
+
+
+def test_uniform_grid_subquery_counts_match_oracle(case):
+    """The uniform-grid variant (every leaf at grid_level) splits queries
+    exactly as g(q) over the grid's non-empty cells."""
+    torch, dev = torch_dev()
+    t, want = case
+    from paper_1411_3212_gb300 import mqr
+    idx = mqr.Index(bounds=(0.0, 0.0, 1.0, 1.0), leaf_cap=1, max_objects=30000, index_kind=1, grid_level=7)
+    idx.apply_updates(to_dev(t.ids, dev), to_dev(t.xy, dev))
+    idx.tick(to_dev(t.rects, dev), kind="count")
+    s = idx.stats()
+    lv = idx.leaves()
+    assert np.all(lv[:, 0] == 7)
+    dt = np.dtype([("level", np.uint32), ("z", np.uint32), ("begin", np.uint32), ("end", np.uint32)])
+    table = np.zeros(len(lv), dt)
+    table["level"], table["z"], table["begin"], table["end"] = lv[:, 0], lv[:, 1], lv[:, 2], lv[:, 3]
+    n_i = n_c = 0
+    for r in t.rects[:500]:
+        li, cov = oracle.subqueries(table, r)
+        n_c += int(cov.sum())
+        n_i += int(len(cov) - cov.sum())
+    idx.tick(to_dev(t.rects[:500], dev), kind="count")
+    s = idx.stats()
+    assert s["n_sub_intersecting"] == n_i and s["n_sub_covering"] == n_c
+    idx.close()
