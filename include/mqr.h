@@ -5,14 +5,14 @@
  * The library answers, tick after tick, the spatial join between the latest
  * known positions of a population of moving objects and the range queries
  * issued during the tick (Lettich et al., "Manycore processing of repeated
- * range queries over massive moving objects observations", Sec. 2.4 "Problem
+ * range queries over massive moving objects observations", Sec. 2.5 "Problem
  * statement").  It indexes the objects with a point-region quadtree whose
  * leaves hold at most leaf_cap objects (Def. "MBR partitioning into a
  * quadtree-induced regular grid", Alg. 1), splits every query over the leaves
  * it meets (Def. "Mapping functions"), tests intersecting subqueries against
- * the leaf's objects into 32-bit bitmap words (Sec. 5.5, Alg. 2), and decodes
- * the words plus the covering subqueries into the result (Sec. 5.6 Alg. 4,
- * Sec. 5.7).
+ * the leaf's objects into 32-bit bitmap words (Sec. 5.4, Alg. 2), and decodes
+ * the words plus the covering subqueries into the result (Sec. 5.5 Alg. 4,
+ * Sec. 5.6).
  *
  * Conventions shared by every entry point:
  *  - Every call returns an mqr_status; nothing aborts the process.  On an
@@ -98,11 +98,11 @@ typedef struct {
     int32_t index_kind;    /* mqr_index_kind                                           */
     uint32_t grid_level;   /* uniform grid only: 1..15                                 */
     int32_t covering;      /* 1 (default): covering subqueries skip containment tests
-                              (Sec. 5.7); 0: every subquery is tested                  */
+                              (Sec. 5.6); 0: every subquery is tested                  */
     int32_t reserved[3];   /* must be 0                                                */
 } mqr_config;
 
-/* Counters of the last completed tick (Sec. 6.x metrics). */
+/* Counters of the last completed tick (Sec. 7 metrics). */
 typedef struct {
     uint64_t n_objects;          /* objects present (ever updated)                 */
     uint64_t n_queries;
@@ -132,9 +132,9 @@ typedef enum {
     MQR_PHASE_QUERY_BLOCKS = 4,/* query splitting: lookup table, blocks, scan (Sec. 5.3) */
     MQR_PHASE_GROUP = 5,       /* grouping subqueries by leaf (Sec. 5.3 sorting) */
     MQR_PHASE_CANDIDATES = 6,  /* query splitting: candidates -> subqueries      */
-    MQR_PHASE_FILTER = 7,      /* filtering into bitmap words (Sec. 5.5)        */
-    MQR_PHASE_RESULT_SCAN = 8, /* result-count scan (Sec. 5.6)                  */
-    MQR_PHASE_EMIT = 9,        /* decoding + covering expansion (Sec. 5.6, 5.7) */
+    MQR_PHASE_FILTER = 7,      /* filtering into bitmap words (Sec. 5.4)        */
+    MQR_PHASE_RESULT_SCAN = 8, /* result-count scan (Sec. 5.5)                  */
+    MQR_PHASE_EMIT = 9,        /* decoding + covering expansion (Sec. 5.5, 5.6) */
     MQR_PHASE_OFFSETS = 10,    /* per-query offsets                             */
     MQR_PHASE_OUTPUT_SORT = 11,/* sorted output kinds                           */
     MQR_NUM_PHASES = 12
@@ -179,7 +179,7 @@ mqr_status mqr_apply_updates(mqr_ctx *ctx, const uint32_t *ids_dev, const float 
  * context's stream before the call returns; page-locked buffers copy fastest). */
 mqr_status mqr_apply_updates_host(mqr_ctx *ctx, const uint32_t *ids_host, const float *xy_host, uint32_t n);
 
-/* Answer Q queries against the current state (one tick, Sec. 2.4):
+/* Answer Q queries against the current state (one tick, Sec. 2.5):
  * rects_dev: float32[4Q] device, (xa, ya, xb, yb) per query; the query index
  * qidx is its position in rects_dev.  kind: an mqr_out_kind.  out_dev /
  * out_capacity_bytes: caller's device output buffer (see mqr_out_kind).

@@ -12,7 +12,7 @@ Functions (each citing the paper passage its C routine follows):
   join_brute     -- Def. 1 by testing every (query, object) pair.
   count_grid     -- per-query result counts (Def. 1).
   bitmap         -- query x object bitmap of a result (bitmap layout of the
-                    filtering phase, Sec. 5.5, taken over the whole Q x N).
+                    filtering phase, Sec. 5.4, taken over the whole Q x N).
   cell / scale / morton / keys -- Morton codes at l_max = 15 (Alg. 1).
   quadtree       -- Alg. 1 PR-quadtree leaves, level by level.
   subqueries     -- Def. "Mapping functions" g(q), intersecting/covering.

@@ -1,7 +1,7 @@
-// k_join.cu -- the join kernels: filtering into bitmap words (Sec. 5.5,
-// Alg. 2), the result-count scan (Sec. 5.6), and the decoding of bitmap words
-// plus the covering-subquery expansion into the output (Sec. 5.6 Alg. 4,
-// Sec. 5.7).
+// k_join.cu -- the join kernels: filtering into bitmap words (Sec. 5.4,
+// Alg. 2), the result-count scan (Sec. 5.5), and the decoding of bitmap words
+// plus the covering-subquery expansion into the output (Sec. 5.5 Alg. 4,
+// Sec. 5.6).
 #include "mqr_internal.cuh"
 
 namespace mqr {
@@ -18,7 +18,7 @@ __device__ __forceinline__ bool tick_buffers_ok(const Info *info, const Caps &ca
 // the group's rectangles are broadcast one at a time, and for every 32-object
 // word __ballot_sync of the closed-rectangle test (Def. 1) yields the 32-bit
 // bitmap word directly in the linearized row-major layout (row = subquery,
-// Sec. 5.5 Fig. 9b), so no interlaced bitmap and no linearization pass are
+// Sec. 5.4 Fig. 9b), so no interlaced bitmap and no linearization pass are
 // needed.  Lane s keeps the words of subquery s and writes them as one
 // contiguous run; popcounts give the subquery's result count.
 // Objects past the chunk are loaded as NaN, which fails every comparison.
@@ -190,7 +190,7 @@ void launch_result_scan(cudaStream_t st, unsigned long long sub_cap, const uint3
 // a12 + a13: emit the results.  One warp per subquery record, records taken
 // in query-major order so that the output is written front to back.
 //  - covering run: the run's objects are one contiguous range of the sorted
-//    ids; copy it (Sec. 5.7 covering expansion, done here on the device).
+//    ids; copy it (Sec. 5.6 covering expansion, done here on the device).
 //  - intersecting: read the subquery's bitmap row 32 words at a time and, per
 //    word, let lane j with bit j set write at run + popc(word & lanemask_lt)
 //    (Alg. 4: lane i writes the i-th positive of the word, coalesced).

@@ -450,7 +450,7 @@ void launch_candidates(cudaStream_t st, int num_sms, int covering, const uint32_
 // ---------------------------------------------------------------------------
 // a8: per-leaf scans.  For leaf l with n objects and s intersecting
 // subqueries: its subquery list starts at leaf_sub_off[l]; its bitmap (s rows
-// of ceil(n/32) words, row-major: the linearized layout of Sec. 5.5) starts
+// of ceil(n/32) words, row-major: the linearized layout of Sec. 5.4) starts
 // at leaf_word_off[l]; its filter work items (ceil(n/256) object chunks x
 // ceil(s/32) subquery groups) start at leaf_item_off[l].
 // ---------------------------------------------------------------------------
