@@ -41,6 +41,9 @@ WORKLOADS = {
                            "0.002-0.02; 10% uniform), random walk sigma 0.0005, hotspot drift 0.001/tick, "
                            "400,000 square queries/tick of side log-uniform 0.0005-0.005 centred on objects, "
                            "leaf_cap 128 (fixed), pair-list output"),
+    "hotspot2m": dict(kind="hotspot", n=2_000_000, q=200_000, cap=128,
+                      desc="hotspot-2M: the hotspot-4M recipe at 2,000,000 objects and 200,000 queries/tick "
+                           "(profiling size)"),
     "hotspot1m": dict(kind="hotspot", n=1_000_000, q=100_000, cap=128,
                       desc="hotspot-1M: the hotspot-4M recipe at 1,000,000 objects and 100,000 queries/tick "
                            "(profiling size)"),

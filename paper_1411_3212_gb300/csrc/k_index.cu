@@ -140,12 +140,13 @@ void launch_key_histograms(cudaStream_t st, const unsigned long long *keys, uint
 // that consecutive threads write consecutive addresses.
 // Status layout: status[digit * num_tiles + tile].
 // ---------------------------------------------------------------------------
-template <bool FINAL>
+template <bool FINAL, bool PRE>
 __global__ void __launch_bounds__(kSortThreads)
 onesweep_kernel(const unsigned long long *__restrict__ in, unsigned long long *__restrict__ out,
                 uint32_t n, int shift, const uint32_t *__restrict__ hist256, uint32_t *status,
                 uint32_t *tile_counter, unsigned long long *err, const float2 *__restrict__ pos,
-                uint32_t *__restrict__ skey, uint32_t *__restrict__ sid, float2 *__restrict__ sxy) {
+                uint32_t *__restrict__ skey, uint32_t *__restrict__ sid, float2 *__restrict__ sxy,
+                const uint32_t *__restrict__ tile_offs) {
     constexpr int W = kSortThreads / 32;
     __shared__ unsigned long long s_keys[kSortTile];
     __shared__ uint32_t s_whist[W][256];
@@ -155,10 +156,10 @@ onesweep_kernel(const unsigned long long *__restrict__ in, unsigned long long *_
     __shared__ uint32_t s_tile;
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    if (tid == 0) s_tile = atomicAdd(tile_counter, 1u);
+    if (!PRE && tid == 0) s_tile = atomicAdd(tile_counter, 1u);
     for (int i = tid; i < W * 256; i += kSortThreads) (&s_whist[0][0])[i] = 0;
     __syncthreads();
-    const uint32_t tile = s_tile;
+    const uint32_t tile = PRE ? blockIdx.x : s_tile;
     const uint32_t num_tiles = (n + kSortTile - 1) / kSortTile;
     const uint32_t base = tile * kSortTile;
     const uint32_t wbase = base + warp * 32 * kSortItems;
@@ -201,10 +202,15 @@ onesweep_kernel(const unsigned long long *__restrict__ in, unsigned long long *_
     }
     uint32_t tot;
     uint32_t dstart = block_excl_scan<kSortThreads>(c, &tot, s_scan);
-    uint32_t gstart = block_excl_scan<kSortThreads>(hist256[tid], &tot, s_scan);
     s_dstart[tid] = dstart;
-    uint32_t prefix = lookback1<uint32_t>(status + (size_t)tid * num_tiles, tile, c, err);
-    s_gbase[tid] = gstart + prefix - dstart;
+    if (PRE) {
+        // output start of this tile's keys of digit tid, from the tile-histogram scan
+        s_gbase[tid] = tile_offs[(size_t)tid * num_tiles + tile] - dstart;
+    } else {
+        uint32_t gstart = block_excl_scan<kSortThreads>(hist256[tid], &tot, s_scan);
+        uint32_t prefix = lookback1<uint32_t>(status + (size_t)tid * num_tiles, tile, c, err);
+        s_gbase[tid] = gstart + prefix - dstart;
+    }
     __syncthreads();
 
 #pragma unroll
@@ -245,11 +251,77 @@ void launch_onesweep_pass(cudaStream_t st, const unsigned long long *in, unsigne
     if (n == 0) return;
     uint32_t tiles = (n + kSortTile - 1) / kSortTile;
     if (final_obj)
-        onesweep_kernel<true><<<tiles, kSortThreads, 0, st>>>(in, out, n, shift, hist256, status,
-                                                             tile_counter, err, pos, skey, sid, sxy);
+        onesweep_kernel<true, false><<<tiles, kSortThreads, 0, st>>>(in, out, n, shift, hist256, status,
+                                                                    tile_counter, err, pos, skey, sid, sxy,
+                                                                    nullptr);
     else
-        onesweep_kernel<false><<<tiles, kSortThreads, 0, st>>>(in, out, n, shift, hist256, status,
-                                                              tile_counter, err, pos, skey, sid, sxy);
+        onesweep_kernel<false, false><<<tiles, kSortThreads, 0, st>>>(in, out, n, shift, hist256, status,
+                                                                     tile_counter, err, pos, skey, sid, sxy,
+                                                                     nullptr);
+}
+
+// ---------------------------------------------------------------------------
+// a3, look-back-free pass (when every tile of a pass runs in one wave the
+// decoupled look-back degenerates into a serial walk): per-tile digit counts,
+// then one block per digit scans its counts over the tiles (adding the
+// digit's global start), then the same stable rank-and-scatter tile kernel
+// reads its offsets instead of looking back.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(kSortThreads)
+tile_hist_kernel(const unsigned long long *__restrict__ in, uint32_t n, int shift,
+                 uint32_t *__restrict__ counts) {
+    __shared__ uint32_t s_h[256];
+    const uint32_t tiles = (n + kSortTile - 1) / kSortTile;
+    s_h[threadIdx.x] = 0;
+    __syncthreads();
+    const uint32_t base = blockIdx.x * kSortTile;
+#pragma unroll 4
+    for (int it = 0; it < kSortItems; ++it) {
+        const uint32_t i = base + it * kSortThreads + threadIdx.x;
+        if (i < n) atomicAdd(&s_h[(uint32_t)(in[i] >> shift) & 255u], 1u);
+    }
+    __syncthreads();
+    counts[(size_t)threadIdx.x * tiles + blockIdx.x] = s_h[threadIdx.x];
+}
+
+__global__ void __launch_bounds__(256)
+digit_scan_kernel(const uint32_t *__restrict__ counts, const uint32_t *__restrict__ hist256, uint32_t n,
+                  uint32_t *__restrict__ offs) {
+    __shared__ uint32_t s_scan[256 / 32 + 1];
+    __shared__ uint32_t s_base;
+    const uint32_t tiles = (n + kSortTile - 1) / kSortTile;
+    const uint32_t d = blockIdx.x;
+    uint32_t tot;
+    const uint32_t g = block_excl_scan<256>(hist256[threadIdx.x], &tot, s_scan);
+    if (threadIdx.x == d) s_base = g;
+    __syncthreads();
+    uint32_t carry = s_base;
+    const uint32_t *cd = counts + (size_t)d * tiles;
+    uint32_t *od = offs + (size_t)d * tiles;
+    for (uint32_t t0 = 0; t0 < tiles; t0 += 256) {
+        const uint32_t t = t0 + threadIdx.x;
+        const uint32_t v = t < tiles ? cd[t] : 0u;
+        uint32_t chunk;
+        const uint32_t ex = block_excl_scan<256>(v, &chunk, s_scan);
+        if (t < tiles) od[t] = carry + ex;
+        carry += chunk;
+    }
+}
+
+void launch_sort_pass_pre(cudaStream_t st, const unsigned long long *in, unsigned long long *out, uint32_t n,
+                          int shift, const uint32_t *hist256, uint32_t *counts, uint32_t *offs,
+                          unsigned long long *err, bool final_obj, const float2 *pos, uint32_t *skey,
+                          uint32_t *sid, float2 *sxy) {
+    if (n == 0) return;
+    const uint32_t tiles = (n + kSortTile - 1) / kSortTile;
+    tile_hist_kernel<<<tiles, kSortThreads, 0, st>>>(in, n, shift, counts);
+    digit_scan_kernel<<<256, 256, 0, st>>>(counts, hist256, n, offs);
+    if (final_obj)
+        onesweep_kernel<true, true><<<tiles, kSortThreads, 0, st>>>(in, out, n, shift, hist256, nullptr,
+                                                                   nullptr, err, pos, skey, sid, sxy, offs);
+    else
+        onesweep_kernel<false, true><<<tiles, kSortThreads, 0, st>>>(in, out, n, shift, hist256, nullptr,
+                                                                    nullptr, err, pos, skey, sid, sxy, offs);
 }
 
 // ---------------------------------------------------------------------------

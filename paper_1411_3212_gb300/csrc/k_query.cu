@@ -120,6 +120,7 @@ query_blocks_kernel(const float4 *__restrict__ rects, uint32_t Q, float x0, floa
                     unsigned long long *__restrict__ pair_off, uint32_t *__restrict__ qpair,
                     uint32_t *__restrict__ tile_p0, unsigned long long tile_cap, uint32_t *status_p,
                     unsigned long long *status_c, uint32_t *tile_counter, Info *info) {
+    // one thread per (query, block slot): kQBQueries queries x 9 slots per block
     __shared__ uint32_t s_scan32[kQBThreads / 32 + 1];
     __shared__ unsigned long long s_scan64[kQBThreads / 32 + 1];
     __shared__ uint32_t s_tile, s_pp;
@@ -129,42 +130,33 @@ query_blocks_kernel(const float4 *__restrict__ rects, uint32_t Q, float x0, floa
     __syncthreads();
     const uint32_t tile = s_tile;
     const uint32_t L = (uint32_t)info->n_leaves;
-    const uint32_t q = tile * kQBThreads + tid;
+    const uint32_t slot = (uint32_t)tid % 9u, ql = (uint32_t)tid / 9u;
+    const uint32_t q = tile * kQBQueries + ql;
+    const bool qvalid = ql < (uint32_t)kQBQueries && q < Q;
 
-    uint32_t first[9], cnt[9], blo9[9];
-    uint32_t npairs = 0;
-    unsigned long long ncand = 0;
-#pragma unroll
-    for (int b = 0; b < 9; ++b) cnt[b] = 0;
+    uint32_t f = 0, cnt = 0, blo = 0;
     QCells c;
-    if (q < Q && L > 0 && query_cells(rects[q], x0, y0, sx, sy, c)) {
+    const bool qok = qvalid && L > 0 && query_cells(rects[q], x0, y0, sx, sy, c);
+    if (qok) {
         const uint32_t k = block_log2(c.i0, c.i1, c.j0, c.j1);
-        const uint32_t bi_lo = c.i0 >> k, bi_hi = c.i1 >> k, bj_lo = c.j0 >> k, bj_hi = c.j1 >> k;
-        qcells[q] = make_uint2(c.i0 | (c.i1 << 16), c.j0 | (c.j1 << 16));
-#pragma unroll
-        for (int dj = 0; dj < 3; ++dj) {
-#pragma unroll
-            for (int di = 0; di < 3; ++di) {
-                const int b = dj * 3 + di;
-                if (bi_lo + di > bi_hi || bj_lo + dj > bj_hi) continue;
-                const uint32_t blo = morton2((bi_lo + di) << k, (bj_lo + dj) << k);
-                const uint32_t bhi = blo + ((1u << (2 * k)) - 1u);
-                const uint32_t f = leaf_at_or_after(blo, leaf_hi, zmap);
-                if (f >= L || __ldg(leaf_lo + f) > bhi) continue;
+        const uint32_t bi = (c.i0 >> k) + slot % 3u, bj = (c.j0 >> k) + slot / 3u;
+        if (slot == 0) qcells[q] = make_uint2(c.i0 | (c.i1 << 16), c.j0 | (c.j1 << 16));
+        if (bi <= (c.i1 >> k) && bj <= (c.j1 >> k)) {
+            blo = morton2(bi << k, bj << k);
+            const uint32_t bhi = blo + ((1u << (2 * k)) - 1u);
+            f = leaf_at_or_after(blo, leaf_hi, zmap);
+            if (f < L && __ldg(leaf_lo + f) <= bhi) {
                 const uint32_t g = leaf_at_or_after(bhi, leaf_hi, zmap);
                 const uint32_t last = (g < L && __ldg(leaf_lo + g) <= bhi) ? g : g - 1u;
-                first[b] = f;
-                cnt[b] = last - f + 1u;
-                blo9[b] = blo;
-                ++npairs;
-                ncand += cnt[b];
+                cnt = last - f + 1u;
             }
         }
     }
+    const uint32_t has = cnt > 0u ? 1u : 0u;
     uint32_t tot_p;
     unsigned long long tot_c;
-    const uint32_t off_p = block_excl_scan<kQBThreads>(npairs, &tot_p, s_scan32);
-    const unsigned long long off_c = block_excl_scan<kQBThreads>(ncand, &tot_c, s_scan64);
+    const uint32_t off_p = block_excl_scan<kQBThreads>(has, &tot_p, s_scan32);
+    const unsigned long long off_c = block_excl_scan<kQBThreads>((unsigned long long)cnt, &tot_c, s_scan64);
     if (tid < 32) {
         const uint32_t pp = lookback_warp<uint32_t>(status_p, tile, tot_p, &info->err);
         if (tid == 0) s_pp = pp;
@@ -173,26 +165,21 @@ query_blocks_kernel(const float4 *__restrict__ rects, uint32_t Q, float x0, floa
         if (tid == 32) s_pc = pc;
     }
     __syncthreads();
-    uint32_t p = s_pp + off_p;
-    unsigned long long co = s_pc + off_c;
-    if (q < Q) {
+    const uint32_t p = s_pp + off_p;
+    const unsigned long long co = s_pc + off_c;
+    if (qvalid && slot == 0) {
         cand_off[q] = co;
         qpair[q] = p;
     }
-#pragma unroll
-    for (int b = 0; b < 9; ++b) {
-        if (cnt[b] == 0) continue;
+    if (has) {
         pair_q[p] = q;
-        pair_first[p] = first[b];
-        pair_blo[p] = blo9[b];
+        pair_first[p] = f;
+        pair_blo[p] = blo;
         pair_off[p] = co;
         // warp tiles of 32 candidates whose first candidate falls in this pair
-        for (unsigned long long t = (co + 31) >> 5; (t << 5) < co + cnt[b] && t < tile_cap; ++t)
-            tile_p0[t] = p;
-        co += cnt[b];
-        ++p;
+        for (unsigned long long t = (co + 31) >> 5; (t << 5) < co + cnt && t < tile_cap; ++t) tile_p0[t] = p;
     }
-    if (tid == 0 && (tile + 1) * (uint32_t)kQBThreads >= Q) {
+    if (tid == 0 && (tile + 1) * (uint32_t)kQBQueries >= Q) {
         const uint32_t np = s_pp + tot_p;
         const unsigned long long nc = s_pc + tot_c;
         cand_off[Q] = nc;
@@ -215,7 +202,7 @@ void launch_query_blocks(cudaStream_t st, const float4 *rects, uint32_t Q, float
                          uint32_t *status_p, unsigned long long *status_c, uint32_t *tile_counter,
                          Info *info) {
     if (Q == 0) return;
-    uint32_t tiles = (Q + kQBThreads - 1) / kQBThreads;
+    uint32_t tiles = (Q + kQBQueries - 1) / kQBQueries;
     query_blocks_kernel<<<tiles, kQBThreads, 0, st>>>(rects, Q, x0, y0, sx, sy, leaf_lo, leaf_hi, zmap,
                                                       qcells, cand_off, pair_q, pair_first, pair_blo,
                                                       pair_off, qpair, tile_p0, tile_cap, status_p,

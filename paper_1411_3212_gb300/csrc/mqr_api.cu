@@ -82,7 +82,7 @@ struct mqr_ctx {
     DevBuf<unsigned long long> stamp;
     // sort
     DevBuf<unsigned long long> keysA, keysB;
-    DevBuf<uint32_t> skey, sid;
+    DevBuf<uint32_t> skey, sid, sort_counts, sort_offs;
     DevBuf<float2> sxy;
     // leaves
     DevBuf<uint32_t> leaf_lo, leaf_hi, leaf_beg, leaf_nsub, leaf_sub_off, leaf_word_off,
@@ -128,7 +128,7 @@ namespace {
 
 // Arena layout for one tick.
 struct Arena {
-    size_t info, hist, counters, st_sort, st_leaf, st_lscan, st_qb_p, st_qb_c, st_cand, st_res, total;
+    size_t info, hist, counters, st_leaf, st_lscan, st_qb_p, st_qb_c, st_cand, st_res, total;
     uint32_t sort_tiles, leaf_tiles, lscan_tiles, qb_tiles, res_tiles;
     unsigned long long cand_tiles;
 };
@@ -138,7 +138,7 @@ Arena arena_layout(uint32_t nmax, uint32_t Q, unsigned long long sub_cap, unsign
     a.sort_tiles = (nmax + kSortTile - 1) / kSortTile;
     a.leaf_tiles = (nmax + kLeafTile - 1) / kLeafTile;
     a.lscan_tiles = (nmax + kLeafScanTile - 1) / kLeafScanTile;
-    a.qb_tiles = (Q + kQBThreads - 1) / kQBThreads;
+    a.qb_tiles = (Q + kQBQueries - 1) / kQBQueries;
     a.cand_tiles = cand_tiles;
     a.res_tiles = (uint32_t)((sub_cap + kResTile - 1) / kResTile) + 1;
     size_t o = 0;
@@ -150,7 +150,6 @@ Arena arena_layout(uint32_t nmax, uint32_t Q, unsigned long long sub_cap, unsign
     a.info = take(sizeof(Info));
     a.hist = take(8 * 256 * sizeof(uint32_t));
     a.counters = take(16 * sizeof(uint32_t));
-    a.st_sort = take((size_t)4 * 256 * a.sort_tiles * sizeof(uint32_t));
     a.st_leaf = take((size_t)a.leaf_tiles * sizeof(uint32_t));
     a.st_lscan = take((size_t)3 * a.lscan_tiles * sizeof(uint32_t));
     a.st_qb_p = take((size_t)a.qb_tiles * sizeof(uint32_t));
@@ -255,17 +254,15 @@ mqr_status enqueue_tick(mqr_ctx *c, const float4 *rects, uint32_t Q, int emit_ki
     phase_begin(c, MQR_PHASE_KEYS);
     launch_morton_keys(st, c->pos.p, c->stamp.p, nmax, x0, y0, c->sx, c->sy, c->keysA.p, hist, info);
     phase_end(c, MQR_PHASE_KEYS, nmax ? 1 : 0);
-    uint32_t *st_sort = at<uint32_t>(c, a.st_sort);
-    const size_t pass_status = (size_t)256 * a.sort_tiles;
     unsigned long long *src = c->keysA.p, *dst = c->keysB.p;
     phase_begin(c, MQR_PHASE_SORT);
     for (int p = 0; p < 4; ++p) {
-        bool fin = p == 3;
-        launch_onesweep_pass(st, src, dst, nmax, 32 + 8 * p, hist + 256 * p, st_sort + pass_status * p,
-                             ctr + p, err, fin, c->pos.p, c->skey.p, c->sid.p, c->sxy.p);
+        const bool fin = p == 3;
+        launch_sort_pass_pre(st, src, dst, nmax, 32 + 8 * p, hist + 256 * p, c->sort_counts.p, c->sort_offs.p,
+                             err, fin, c->pos.p, c->skey.p, c->sid.p, c->sxy.p);
         std::swap(src, dst);
     }
-    phase_end(c, MQR_PHASE_SORT, nmax ? 4 : 0);
+    phase_end(c, MQR_PHASE_SORT, nmax ? 12 : 0);
     // a4
     phase_begin(c, MQR_PHASE_LEAVES);
     const uint32_t cap = c->cfg.leaf_cap;
@@ -597,7 +594,7 @@ void mqr_destroy(mqr_ctx *c) {
     DevBuf<unsigned long long> *u64s[] = {&c->stamp, &c->keysA, &c->keysB, &c->out_off, &c->off_stage,
                                           &c->sortA, &c->sortB};
     for (auto *b : u64s) b->release();
-    DevBuf<uint32_t> *u32s[] = {&c->skey, &c->sid, &c->leaf_lo, &c->leaf_hi, &c->leaf_beg, &c->leaf_nsub,
+    DevBuf<uint32_t> *u32s[] = {&c->skey, &c->sid, &c->sort_counts, &c->sort_offs, &c->leaf_lo, &c->leaf_hi, &c->leaf_beg, &c->leaf_nsub,
                                 &c->leaf_sub_off, &c->leaf_word_off, &c->leaf_item_off, &c->leaf_cursor,
                                 &c->sub_q, &c->sub_leaf, &c->sub_len, &c->sub_res,
                                 &c->sub_bm, &c->isub, &c->bitmap, &c->item_leaf, &c->up_ids, &c->zmap, &c->pair_q,
@@ -673,6 +670,8 @@ mqr_status mqr_create_ex(mqr_rect bounds, const mqr_config *cfg, void *cuda_stre
         (e = c->leaf_beg.ensure(n + 1)) || (e = c->leaf_nsub.ensure(n)) ||
         (e = c->leaf_sub_off.ensure(n + 1)) || (e = c->leaf_word_off.ensure(n + 1)) ||
         (e = c->leaf_item_off.ensure(n + 1)) || (e = c->leaf_cursor.ensure(n)) ||
+        (e = c->sort_counts.ensure((size_t)256 * ((n + kSortTile - 1) / kSortTile))) ||
+        (e = c->sort_offs.ensure((size_t)256 * ((n + kSortTile - 1) / kSortTile))) ||
         (e = c->upd_err.ensure(1)))
         return bail(e, "cudaMalloc (object state)");
     if (cfg->index_kind == MQR_INDEX_QUADTREE && cfg->leaf_cap > (uint32_t)kLeafCapSmem &&

@@ -297,6 +297,13 @@ void launch_onesweep_pass(cudaStream_t st, const unsigned long long *in, unsigne
                           uint32_t n, int shift, const uint32_t *hist256, uint32_t *status,
                           uint32_t *tile_counter, unsigned long long *err, bool final_obj,
                           const float2 *pos, uint32_t *skey, uint32_t *sid, float2 *sxy);
+// The same pass without look-back: per-tile digit counts (counts/offs hold
+// 256 x ceil(n / kSortTile) u32 each), a per-digit scan over the tiles, then
+// the rank-and-scatter tile kernel with the precomputed offsets.
+void launch_sort_pass_pre(cudaStream_t st, const unsigned long long *in, unsigned long long *out, uint32_t n,
+                          int shift, const uint32_t *hist256, uint32_t *counts, uint32_t *offs,
+                          unsigned long long *err, bool final_obj, const float2 *pos, uint32_t *skey,
+                          uint32_t *sid, float2 *sxy);
 // Histograms (nd digit passes at shifts[]) of n u64 keys, for generic sorts.
 void launch_key_histograms(cudaStream_t st, const unsigned long long *keys, uint32_t n,
                            const int *shifts_host, int nd, uint32_t *hist);
@@ -313,7 +320,8 @@ void launch_build_leaves(cudaStream_t st, const uint32_t *skey, uint32_t nmax, u
 constexpr int kZLevel = 8;
 constexpr uint32_t kZCells = 1u << (2 * kZLevel);
 constexpr int kZShift = 2 * (kLevels - kZLevel);
-constexpr int kQBThreads = 256;                       // queries per tile of query_blocks
+constexpr int kQBThreads = 256;                       // threads per block of query_blocks
+constexpr int kQBQueries = kQBThreads / 9;            // queries per block (9 block slots each)
 constexpr int kCandScanTile = 2048;                   // warp tiles per block of the tile-count scan
 
 void launch_zmap(cudaStream_t st, const uint32_t *leaf_hi, const Info *info, uint32_t *zmap);
