@@ -32,7 +32,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
-TRAFFIC_FILE = os.path.join(ROOT, "profiles", "traffic.json")
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "emit_kernel_traffic.txt")
 FALLBACK_HBM_GBS = 6800.0
 
 WORKLOADS = {
@@ -124,14 +124,18 @@ def read_peaks():
 
 
 def read_traffic(kernel):
-    """Per-launch DRAM bytes of `kernel` from a committed ncu summary, if the
-    CUDA sources have not changed since it was taken."""
+    """Per-launch DRAM bytes of `kernel` from the committed ncu summary, if the
+    CUDA sources have not changed since it was taken (else None)."""
     try:
+        kv = {}
         with open(TRAFFIC_FILE) as f:
-            t = json.load(f)
-        e = t.get(kernel)
-        if e and e.get("source_hash") == source_hash() and e.get("workload") == "hotspot4m":
-            return float(e["dram_bytes_per_launch"])
+            for line in f:
+                line = line.strip()
+                if line and not line.startswith("#") and "=" in line:
+                    k, v = line.split("=", 1)
+                    kv[k.strip()] = v.strip()
+        if kv.get("kernel") == kernel and kv.get("source_hash") == source_hash() and kv.get("workload") == "hotspot4m":
+            return float(kv["dram_bytes_per_launch"])
     except Exception:
         pass
     return None
@@ -152,7 +156,7 @@ class Clocks:
     def start(self):
         try:
             self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.idx), "--query-gpu=" + self.FIELDS,
-                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                       "--format=csv,noheader,nounits", "-lms", "25"],
                                       stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except Exception:
             self.p = None
@@ -300,7 +304,8 @@ def run_gpu(args, name):
     nmax, Q = w["n"], w["q"]
 
     t_gen = time.perf_counter()
-    ticks = gen_ticks(name, 1000 * rank, args.warmup + args.steps)
+    uniq = min(args.steps, args.unique_ticks)          # timed steps cycle over these ticks
+    ticks = gen_ticks(name, 1000 * rank, args.warmup + uniq)
     log("rank %d: generated %d ticks in %.1f s" % (rank, len(ticks), time.perf_counter() - t_gen))
 
     ids_d = torch.from_numpy(ticks[0].ids.view(np.int32)).to(dev)
@@ -338,7 +343,7 @@ def run_gpu(args, name):
     barrier(dist, dev)
     t_wall = time.perf_counter()
     for k in range(args.steps):
-        i = args.warmup + k
+        i = args.warmup + (k % uniq)
         flush.zero_()                                   # L2 flush between timed steps
         evs[k][0].record(stream)
         results += step(i)
@@ -406,7 +411,8 @@ def run_gpu(args, name):
         "dtype": "f32", "data": "synthetic",
         "config": {"workload": w["desc"], "objects": nmax, "queries_per_tick": Q, "leaf_cap": w["cap"],
                    "output": args.kind, "parallelism": "replicas" if world > 1 else "single-gpu",
-                   "l2": "flushed (%d MB write) between timed steps" % args.flush_mb},
+                   "l2": "flushed (%d MB write) between timed steps" % args.flush_mb,
+                   "ticks": "%d distinct generated ticks, cycled over the %d timed steps" % (uniq, args.steps)},
         "tick_latency_ms": {"p50": srt[len(srt) // 2], "p99": srt[min(len(srt) - 1, int(0.99 * len(srt)))],
                             "max": srt[-1]},
         "join_kernels": {"phases": join, "GB/s": join_gbs, "frac_of_peak": join_gbs / peak},
@@ -452,7 +458,8 @@ def run_e2e(args, idx, ticks, kind, elem, Q, r_hint, dev):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--unique-ticks", type=int, default=20, help="distinct ticks the timed steps cycle over")
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="mine", choices=["mine", "reference"])
     ap.add_argument("--workload", default="hotspot4m", choices=sorted(WORKLOADS))
