@@ -149,7 +149,7 @@ onesweep_kernel(const unsigned long long *__restrict__ in, unsigned long long *_
                 const uint32_t *__restrict__ tile_offs) {
     constexpr int W = kSortThreads / 32;
     __shared__ unsigned long long s_keys[kSortTile];
-    __shared__ uint32_t s_whist[W][256];
+    __shared__ uint16_t s_whist[W][256];   // per-warp digit counts (<= 32 * kSortItems)
     __shared__ uint32_t s_dstart[256];
     __shared__ uint32_t s_gbase[256];
     __shared__ uint32_t s_scan[W + 1];
@@ -191,25 +191,29 @@ onesweep_kernel(const unsigned long long *__restrict__ in, unsigned long long *_
     }
     __syncthreads();
 
-    // Per digit (thread tid == digit): exclusive prefix over warps, tile-local
-    // digit starts, global digit start, look-back over earlier tiles.
+    // Per digit (thread tid == digit, tid < 256): exclusive prefix over warps,
+    // tile-local digit starts, output start of the tile's keys of that digit.
     uint32_t c = 0;
+    if (tid < 256) {
 #pragma unroll
-    for (int w = 0; w < W; ++w) {
-        uint32_t v = s_whist[w][tid];
-        s_whist[w][tid] = c;
-        c += v;
+        for (int w = 0; w < W; ++w) {
+            uint32_t v = s_whist[w][tid];
+            s_whist[w][tid] = c;
+            c += v;
+        }
     }
     uint32_t tot;
     uint32_t dstart = block_excl_scan<kSortThreads>(c, &tot, s_scan);
-    s_dstart[tid] = dstart;
+    if (tid < 256) s_dstart[tid] = dstart;
     if (PRE) {
         // output start of this tile's keys of digit tid, from the tile-histogram scan
-        s_gbase[tid] = tile_offs[(size_t)tid * num_tiles + tile] - dstart;
+        if (tid < 256) s_gbase[tid] = tile_offs[(size_t)tid * num_tiles + tile] - dstart;
     } else {
-        uint32_t gstart = block_excl_scan<kSortThreads>(hist256[tid], &tot, s_scan);
-        uint32_t prefix = lookback1<uint32_t>(status + (size_t)tid * num_tiles, tile, c, err);
-        s_gbase[tid] = gstart + prefix - dstart;
+        uint32_t gstart = block_excl_scan<kSortThreads>(tid < 256 ? hist256[tid] : 0u, &tot, s_scan);
+        if (tid < 256) {
+            uint32_t prefix = lookback1<uint32_t>(status + (size_t)tid * num_tiles, tile, c, err);
+            s_gbase[tid] = gstart + prefix - dstart;
+        }
     }
     __syncthreads();
 
@@ -272,7 +276,7 @@ tile_hist_kernel(const unsigned long long *__restrict__ in, uint32_t n, int shif
                  uint32_t *__restrict__ counts) {
     __shared__ uint32_t s_h[256];
     const uint32_t tiles = (n + kSortTile - 1) / kSortTile;
-    s_h[threadIdx.x] = 0;
+    for (int i = threadIdx.x; i < 256; i += kSortThreads) s_h[i] = 0;
     __syncthreads();
     const uint32_t base = blockIdx.x * kSortTile;
 #pragma unroll 4
@@ -281,7 +285,7 @@ tile_hist_kernel(const unsigned long long *__restrict__ in, uint32_t n, int shif
         if (i < n) atomicAdd(&s_h[(uint32_t)(in[i] >> shift) & 255u], 1u);
     }
     __syncthreads();
-    counts[(size_t)threadIdx.x * tiles + blockIdx.x] = s_h[threadIdx.x];
+    for (int i = threadIdx.x; i < 256; i += kSortThreads) counts[(size_t)i * tiles + blockIdx.x] = s_h[i];
 }
 
 __global__ void __launch_bounds__(256)
@@ -366,7 +370,8 @@ __global__ void __launch_bounds__(kLeafThreads)
 leaves_kernel(const uint32_t *__restrict__ K, uint32_t cap, int uniform_grid, uint32_t grid_level,
               int kexp, const uint8_t *__restrict__ Mk_global, uint32_t *status,
               uint32_t *tile_counter, uint32_t *__restrict__ leaf_lo, uint32_t *__restrict__ leaf_hi,
-              uint32_t *__restrict__ leaf_beg, uint32_t *__restrict__ leaf_nsub, Info *info) {
+              uint32_t *__restrict__ leaf_beg, uint32_t *__restrict__ leaf_nsub, uint2 *__restrict__ leaf_box,
+              Info *info) {
     extern __shared__ uint8_t dsm[];
     __shared__ uint8_t s_L[kLeafTile + 1];
     __shared__ uint32_t s_scan[kLeafThreads / 32 + 1];
@@ -461,6 +466,7 @@ leaves_kernel(const uint32_t *__restrict__ K, uint32_t cap, int uniform_grid, ui
         leaf_hi[idx] = lo + span;
         leaf_beg[idx] = (uint32_t)p;
         leaf_nsub[idx] = 0;
+        leaf_box[idx] = make_uint2(compact15(lo) | (compact15(lo >> 1) << 16), kLevels - L);
         ++idx;
     }
     maxl = __reduce_max_sync(0xffffffffu, maxl);
@@ -474,7 +480,8 @@ leaves_kernel(const uint32_t *__restrict__ K, uint32_t cap, int uniform_grid, ui
 void launch_build_leaves(cudaStream_t st, const uint32_t *skey, uint32_t nmax, uint32_t cap,
                          int uniform_grid, uint32_t grid_level, uint8_t *mk_a, uint8_t *mk_b,
                          uint32_t *status, uint32_t *tile_counter, uint32_t *leaf_lo,
-                         uint32_t *leaf_hi, uint32_t *leaf_beg, uint32_t *leaf_nsub, Info *info) {
+                         uint32_t *leaf_hi, uint32_t *leaf_beg, uint32_t *leaf_nsub, uint2 *leaf_box,
+                         Info *info) {
     if (nmax == 0) return;
     uint32_t tiles = (nmax + kLeafTile - 1) / kLeafTile;
     int kexp = 0;
@@ -497,7 +504,7 @@ void launch_build_leaves(cudaStream_t st, const uint32_t *skey, uint32_t nmax, u
     }
     leaves_kernel<<<tiles, kLeafThreads, dyn, st>>>(skey, cap, uniform_grid, grid_level, kexp, mk,
                                                     status, tile_counter, leaf_lo, leaf_hi, leaf_beg,
-                                                    leaf_nsub, info);
+                                                    leaf_nsub, leaf_box, info);
 }
 
 }  // namespace mqr

@@ -25,6 +25,27 @@ __device__ __forceinline__ bool tick_buffers_ok(const Info *info, const Caps &ca
 // ---------------------------------------------------------------------------
 constexpr int kFilterThreads = 256;
 
+// The closed-rectangle tests of one item: for each of the ns subqueries (the
+// rectangle of lane s broadcast to the warp) and each of the NW object words,
+// the ballot of the 32 lanes' tests is the bitmap word; lane s keeps its own.
+template <int NW>
+__device__ __forceinline__ void filter_words(const float (&x)[8], const float (&y)[8], float4 myr, uint32_t ns,
+                                             int lane, uint32_t (&w)[8]) {
+    for (uint32_t s = 0; s < ns; ++s) {
+        const float xa = __shfl_sync(0xffffffffu, myr.x, s);
+        const float ya = __shfl_sync(0xffffffffu, myr.y, s);
+        const float xb = __shfl_sync(0xffffffffu, myr.z, s);
+        const float yb = __shfl_sync(0xffffffffu, myr.w, s);
+        const bool mine = (uint32_t)lane == s;
+#pragma unroll
+        for (int wd = 0; wd < NW; ++wd) {
+            const bool in = (xa <= x[wd]) & (x[wd] <= xb) & (ya <= y[wd]) & (y[wd] <= yb);
+            const uint32_t bw = __ballot_sync(0xffffffffu, in);
+            if (mine) w[wd] = bw;
+        }
+    }
+}
+
 __global__ void __launch_bounds__(kFilterThreads)
 filter_kernel(const float4 *__restrict__ rects, const float2 *__restrict__ sxy,
               const uint32_t *__restrict__ leaf_beg, const uint32_t *__restrict__ leaf_sub_off,
@@ -78,20 +99,15 @@ filter_kernel(const float4 *__restrict__ rects, const float2 *__restrict__ sxy,
         uint32_t w[8];
 #pragma unroll
         for (int wd = 0; wd < 8; ++wd) w[wd] = 0;
-        for (uint32_t s = 0; s < ns; ++s) {
-            const float xa = __shfl_sync(0xffffffffu, myr.x, s);
-            const float ya = __shfl_sync(0xffffffffu, myr.y, s);
-            const float xb = __shfl_sync(0xffffffffu, myr.z, s);
-            const float yb = __shfl_sync(0xffffffffu, myr.w, s);
-            const bool mine = (uint32_t)lane == s;
-#pragma unroll
-            for (int wd = 0; wd < 8; ++wd) {
-                if ((uint32_t)wd < nwc) {
-                    bool in = (xa <= x[wd]) & (x[wd] <= xb) & (ya <= y[wd]) & (y[wd] <= yb);
-                    uint32_t bw = __ballot_sync(0xffffffffu, in);
-                    if (mine) w[wd] = bw;
-                }
-            }
+        switch (nwc) {                      // the chunk's word count, fixed per item
+            case 1: filter_words<1>(x, y, myr, ns, lane, w); break;
+            case 2: filter_words<2>(x, y, myr, ns, lane, w); break;
+            case 3: filter_words<3>(x, y, myr, ns, lane, w); break;
+            case 4: filter_words<4>(x, y, myr, ns, lane, w); break;
+            case 5: filter_words<5>(x, y, myr, ns, lane, w); break;
+            case 6: filter_words<6>(x, y, myr, ns, lane, w); break;
+            case 7: filter_words<7>(x, y, myr, ns, lane, w); break;
+            default: filter_words<8>(x, y, myr, ns, lane, w); break;
         }
         if ((uint32_t)lane < ns) {
             uint32_t cnt = 0;

@@ -75,9 +75,7 @@ __device__ __forceinline__ uint32_t leaf_at_or_after(uint32_t z, const uint32_t 
 // the leaf table (leaves and blocks are both aligned quadtree quadrants).
 __device__ __forceinline__ uint32_t block_log2(uint32_t i0, uint32_t i1, uint32_t j0, uint32_t j1) {
     const uint32_t e = max(i1 - i0, j1 - j0) + 1u;
-    uint32_t k = 0;
-    while ((2u << k) < e) ++k;
-    return k;
+    return e <= 1u ? 0u : 31u - __clz(e - 1u);       // = ceil(log2 e) - 1
 }
 
 __device__ __forceinline__ void unpack_cells(uint2 qc, uint32_t &i0, uint32_t &i1, uint32_t &j0, uint32_t &j1) {
@@ -92,15 +90,15 @@ __device__ __forceinline__ void unpack_cells(uint2 qc, uint32_t &i0, uint32_t &i
 // Sec. 5.3 Fig. 8).  Covering iff the leaf's cells lie strictly inside the
 // rectangle on both axes (Def. "Mapping functions"): then every object of the
 // leaf passes the FP32 test of Def. 1, the cell function being monotone.
+// blk: the block's lower-left cell (i | j << 16); box: the leaf's lower-left
+// cell (i | j << 16) and the log2 of its side in cells.
 __device__ __forceinline__ int classify(uint32_t i0, uint32_t i1, uint32_t j0, uint32_t j1, uint32_t k,
-                                        uint32_t blo, uint32_t lo, uint32_t hi) {
-    const uint32_t span = hi - lo + 1u;
-    const uint32_t s = (31u - __clz(span)) >> 1;
-    const uint32_t bi0 = compact15(lo), bj0 = compact15(lo >> 1);
-    const uint32_t bi1 = bi0 + (1u << s) - 1u, bj1 = bj0 + (1u << s) - 1u;
+                                        uint32_t blk, uint2 box) {
+    const uint32_t bi0 = box.x & 0xffffu, bj0 = box.x >> 16;
+    const uint32_t bi1 = bi0 + (1u << box.y) - 1u, bj1 = bj0 + (1u << box.y) - 1u;
     if (bi1 < i0 || bi0 > i1 || bj1 < j0 || bj0 > j1) return 0;
     const uint32_t ci = max(bi0, i0), cj = max(bj0, j0);
-    const uint32_t Bi0 = compact15(blo), Bj0 = compact15(blo >> 1);
+    const uint32_t Bi0 = blk & 0xffffu, Bj0 = blk >> 16;
     if (ci < Bi0 || ci > Bi0 + (1u << k) - 1u || cj < Bj0 || cj > Bj0 + (1u << k) - 1u) return 0;
     return (bi0 > i0 && bi1 < i1 && bj0 > j0 && bj1 < j1) ? 2 : 1;
 }
@@ -134,7 +132,7 @@ query_blocks_kernel(const float4 *__restrict__ rects, uint32_t Q, float x0, floa
     const uint32_t q = tile * kQBQueries + ql;
     const bool qvalid = ql < (uint32_t)kQBQueries && q < Q;
 
-    uint32_t f = 0, cnt = 0, blo = 0;
+    uint32_t f = 0, cnt = 0, blk = 0;
     QCells c;
     const bool qok = qvalid && L > 0 && query_cells(rects[q], x0, y0, sx, sy, c);
     if (qok) {
@@ -142,7 +140,8 @@ query_blocks_kernel(const float4 *__restrict__ rects, uint32_t Q, float x0, floa
         const uint32_t bi = (c.i0 >> k) + slot % 3u, bj = (c.j0 >> k) + slot / 3u;
         if (slot == 0) qcells[q] = make_uint2(c.i0 | (c.i1 << 16), c.j0 | (c.j1 << 16));
         if (bi <= (c.i1 >> k) && bj <= (c.j1 >> k)) {
-            blo = morton2(bi << k, bj << k);
+            blk = (bi << k) | ((bj << k) << 16);
+            const uint32_t blo = morton2(bi << k, bj << k);
             const uint32_t bhi = blo + ((1u << (2 * k)) - 1u);
             f = leaf_at_or_after(blo, leaf_hi, zmap);
             if (f < L && __ldg(leaf_lo + f) <= bhi) {
@@ -174,7 +173,7 @@ query_blocks_kernel(const float4 *__restrict__ rects, uint32_t Q, float x0, floa
     if (has) {
         pair_q[p] = q;
         pair_first[p] = f;
-        pair_blo[p] = blo;
+        pair_blo[p] = blk;
         pair_off[p] = co;
         // warp tiles of 32 candidates whose first candidate falls in this pair
         for (unsigned long long t = (co + 31) >> 5; (t << 5) < co + cnt && t < tile_cap; ++t) tile_p0[t] = p;
@@ -239,8 +238,7 @@ __device__ __forceinline__ CandLane cand_lane(unsigned long long t, unsigned lon
                                               const uint32_t *__restrict__ pair_blo,
                                               const unsigned long long *__restrict__ pair_off,
                                               const uint2 *__restrict__ qcells,
-                                              const uint32_t *__restrict__ leaf_lo,
-                                              const uint32_t *__restrict__ leaf_hi) {
+                                              const uint2 *__restrict__ leaf_box) {
     const uint32_t lane = threadIdx.x & 31;
     const unsigned long long c0 = t << 5;
     const uint32_t p0 = __ldg(tile_p0 + t);
@@ -265,7 +263,7 @@ __device__ __forceinline__ CandLane cand_lane(unsigned long long t, unsigned lon
     r.valid = c < ncand;
     r.q = __shfl_sync(0xffffffffu, q_j, r.p_rel);
     const uint32_t first = __shfl_sync(0xffffffffu, f_j, r.p_rel);
-    const uint32_t blo = __shfl_sync(0xffffffffu, b_j, r.p_rel);
+    const uint32_t blo = __shfl_sync(0xffffffffu, b_j, r.p_rel);   // block corner
     const unsigned long long pstart = __shfl_sync(0xffffffffu, po, r.p_rel);
     r.code = 0;
     r.leaf = 0;
@@ -273,8 +271,7 @@ __device__ __forceinline__ CandLane cand_lane(unsigned long long t, unsigned lon
         r.leaf = first + (uint32_t)(c - pstart);
         uint32_t i0, i1, j0, j1;
         unpack_cells(__ldg(qcells + r.q), i0, i1, j0, j1);
-        r.code = classify(i0, i1, j0, j1, block_log2(i0, i1, j0, j1), blo, __ldg(leaf_lo + r.leaf),
-                          __ldg(leaf_hi + r.leaf));
+        r.code = classify(i0, i1, j0, j1, block_log2(i0, i1, j0, j1), blo, __ldg(leaf_box + r.leaf));
         if (r.code == 2 && !covering) r.code = 1;
     }
     const int prev = __shfl_up_sync(0xffffffffu, r.code, 1);
@@ -287,7 +284,7 @@ __global__ void __launch_bounds__(256)
 cand_count_kernel(int covering, const uint32_t *__restrict__ tile_p0, const uint32_t *__restrict__ pair_q,
                   const uint32_t *__restrict__ pair_first, const uint32_t *__restrict__ pair_blo,
                   const unsigned long long *__restrict__ pair_off, const uint2 *__restrict__ qcells,
-                  const uint32_t *__restrict__ leaf_lo, const uint32_t *__restrict__ leaf_hi,
+                  const uint2 *__restrict__ leaf_box,
                   const uint32_t *__restrict__ leaf_beg, uint32_t *__restrict__ tile_cnt,
                   uint32_t *__restrict__ leaf_nsub, Caps caps, Info *info) {
     __shared__ unsigned long long s_red[3];
@@ -303,7 +300,7 @@ cand_count_kernel(int covering, const uint32_t *__restrict__ tile_p0, const uint
         for (unsigned long long t = (blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x) >> 5; t < ntiles;
              t += nw) {
             CandLane r = cand_lane(t, ncand, npairs, covering, tile_p0, pair_q, pair_first, pair_blo, pair_off,
-                                   qcells, leaf_lo, leaf_hi);
+                                   qcells, leaf_box);
             const bool rec = r.code == 1 || (r.code == 2 && !r.cont);
             const uint32_t m = __ballot_sync(0xffffffffu, rec);
             if (lane == 0) tile_cnt[t] = __popc(m);
@@ -372,7 +369,7 @@ __global__ void __launch_bounds__(256)
 cand_write_kernel(int covering, const uint32_t *__restrict__ tile_p0, const uint32_t *__restrict__ pair_q,
                   const uint32_t *__restrict__ pair_first, const uint32_t *__restrict__ pair_blo,
                   const unsigned long long *__restrict__ pair_off, const uint2 *__restrict__ qcells,
-                  const uint32_t *__restrict__ leaf_lo, const uint32_t *__restrict__ leaf_hi,
+                  const uint2 *__restrict__ leaf_box,
                   const uint32_t *__restrict__ leaf_beg, const uint32_t *__restrict__ tile_off,
                   uint32_t *__restrict__ sub_q, uint32_t *__restrict__ sub_leaf, uint32_t *__restrict__ sub_len,
                   uint32_t *__restrict__ sub_res, uint32_t *__restrict__ pair_rec, Caps caps,
@@ -389,7 +386,7 @@ cand_write_kernel(int covering, const uint32_t *__restrict__ tile_p0, const uint
     for (unsigned long long t = (blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x) >> 5; t < ntiles;
          t += nw) {
         CandLane r = cand_lane(t, ncand, npairs, covering, tile_p0, pair_q, pair_first, pair_blo, pair_off,
-                               qcells, leaf_lo, leaf_hi);
+                               qcells, leaf_box);
         const bool rec = r.code == 1 || (r.code == 2 && !r.cont);
         const uint32_t m = __ballot_sync(0xffffffffu, rec);
         const uint32_t notcont = __ballot_sync(0xffffffffu, !(r.valid && r.cont));
@@ -418,19 +415,19 @@ cand_write_kernel(int covering, const uint32_t *__restrict__ tile_p0, const uint
 
 void launch_candidates(cudaStream_t st, int num_sms, int covering, const uint32_t *tile_p0,
                        const uint32_t *pair_q, const uint32_t *pair_first, const uint32_t *pair_blo,
-                       const unsigned long long *pair_off, const uint2 *qcells, const uint32_t *leaf_lo,
-                       const uint32_t *leaf_hi, const uint32_t *leaf_beg, uint32_t *tile_cnt,
+                       const unsigned long long *pair_off, const uint2 *qcells, const uint2 *leaf_box,
+                       const uint32_t *leaf_beg, uint32_t *tile_cnt,
                        uint32_t *tile_off, uint32_t *leaf_nsub, uint32_t *sub_q, uint32_t *sub_leaf,
                        uint32_t *sub_len, uint32_t *sub_res, uint32_t *pair_rec, uint32_t *status,
                        uint32_t *tile_counter, Caps caps, Info *info) {
     cand_count_kernel<<<num_sms * 8, 256, 0, st>>>(covering, tile_p0, pair_q, pair_first, pair_blo, pair_off,
-                                                   qcells, leaf_lo, leaf_hi, leaf_beg, tile_cnt, leaf_nsub,
+                                                   qcells, leaf_box, leaf_beg, tile_cnt, leaf_nsub,
                                                    caps, info);
     const unsigned long long scan_blocks = (caps.cand_tiles + 2047) / 2048;
     tile_scan_kernel<<<(unsigned)(scan_blocks ? scan_blocks : 1), 256, 0, st>>>(tile_cnt, tile_off, status,
                                                                               tile_counter, caps, info);
     cand_write_kernel<<<num_sms * 8, 256, 0, st>>>(covering, tile_p0, pair_q, pair_first, pair_blo, pair_off,
-                                                   qcells, leaf_lo, leaf_hi, leaf_beg, tile_off, sub_q,
+                                                   qcells, leaf_box, leaf_beg, tile_off, sub_q,
                                                    sub_leaf, sub_len, sub_res, pair_rec, caps, info);
 }
 

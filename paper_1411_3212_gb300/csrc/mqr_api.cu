@@ -88,6 +88,7 @@ struct mqr_ctx {
     DevBuf<uint32_t> leaf_lo, leaf_hi, leaf_beg, leaf_nsub, leaf_sub_off, leaf_word_off,
         leaf_item_off, leaf_cursor;
     DevBuf<uint8_t> mk_a, mk_b;
+    DevBuf<uint2> leaf_box;
     // per query / subquery
     DevBuf<uint32_t> sub_q, sub_leaf, sub_len, sub_res, sub_bm, isub, bitmap, item_leaf;
     DevBuf<unsigned long long> out_off;
@@ -269,7 +270,7 @@ mqr_status enqueue_tick(mqr_ctx *c, const float4 *rects, uint32_t Q, int emit_ki
     const bool ug = c->cfg.index_kind == MQR_INDEX_UNIFORM_GRID;
     launch_build_leaves(st, c->skey.p, nmax, cap, ug, c->cfg.grid_level, c->mk_a.p, c->mk_b.p,
                         at<uint32_t>(c, a.st_leaf), ctr + 4, c->leaf_lo.p, c->leaf_hi.p, c->leaf_beg.p,
-                        c->leaf_nsub.p, info);
+                        c->leaf_nsub.p, c->leaf_box.p, info);
     uint64_t leaf_launches = nmax ? 1 : 0;
     if (nmax && !ug && cap > (uint32_t)kLeafCapSmem && cap < nmax) {
         int kexp = 0;
@@ -294,7 +295,7 @@ mqr_status enqueue_tick(mqr_ctx *c, const float4 *rects, uint32_t Q, int emit_ki
     // a7: candidates -> subquery records
     phase_begin(c, MQR_PHASE_CANDIDATES);
     launch_candidates(st, c->num_sms, cov, c->tile_p0.p, c->pair_q.p, c->pair_first.p, c->pair_blo.p,
-                      c->pair_off.p, c->qcells.p, c->leaf_lo.p, c->leaf_hi.p, c->leaf_beg.p, c->tile_cnt.p,
+                      c->pair_off.p, c->qcells.p, c->leaf_box.p, c->leaf_beg.p, c->tile_cnt.p,
                       c->tile_off.p, c->leaf_nsub.p, c->sub_q.p, c->sub_leaf.p, c->sub_len.p, c->sub_res.p,
                       c->pair_rec.p, at<uint32_t>(c, a.st_cand), ctr + 8, caps, info);
     phase_end(c, MQR_PHASE_CANDIDATES, 3);
@@ -602,6 +603,7 @@ void mqr_destroy(mqr_ctx *c) {
                                 &c->tile_cnt, &c->tile_off};
     for (auto *b : u32s) b->release();
     c->qcells.release();
+    c->leaf_box.release();
     c->cand_off.release();
     c->pair_off.release();
     c->mk_a.release();
@@ -672,7 +674,7 @@ mqr_status mqr_create_ex(mqr_rect bounds, const mqr_config *cfg, void *cuda_stre
         (e = c->leaf_item_off.ensure(n + 1)) || (e = c->leaf_cursor.ensure(n)) ||
         (e = c->sort_counts.ensure((size_t)256 * ((n + kSortTile - 1) / kSortTile))) ||
         (e = c->sort_offs.ensure((size_t)256 * ((n + kSortTile - 1) / kSortTile))) ||
-        (e = c->upd_err.ensure(1)))
+        (e = c->upd_err.ensure(1)) || (e = c->leaf_box.ensure(n)))
         return bail(e, "cudaMalloc (object state)");
     if (cfg->index_kind == MQR_INDEX_QUADTREE && cfg->leaf_cap > (uint32_t)kLeafCapSmem &&
         cfg->leaf_cap < c->nmax) {

@@ -12,6 +12,8 @@
 //   leaf_lo/hi u32[L]       Morton interval [lo, hi] of each non-empty leaf
 //   leaf_beg u32[L+1]       first sorted object of each leaf (cell boundary
 //                           table, Sec. 4.4)
+//   leaf_box uint2[L]       lower-left cell (i | j << 16) and log2 side of each
+//                           leaf
 //   per query, per subquery and per leaf work arrays (see mqr_api.cu)
 #pragma once
 
@@ -292,7 +294,7 @@ void launch_morton_keys(cudaStream_t st, const float2 *pos, const unsigned long 
 
 // a3: one onesweep pass over n u64 keys, 8-bit digit at `shift`.  The final
 // pass of the object sort (`final_obj`) writes skey/sid/sxy instead of `out`.
-constexpr int kSortThreads = 256, kSortItems = 16, kSortTile = kSortThreads * kSortItems;
+constexpr int kSortThreads = 512, kSortItems = 8, kSortTile = kSortThreads * kSortItems;
 void launch_onesweep_pass(cudaStream_t st, const unsigned long long *in, unsigned long long *out,
                           uint32_t n, int shift, const uint32_t *hist256, uint32_t *status,
                           uint32_t *tile_counter, unsigned long long *err, bool final_obj,
@@ -314,7 +316,8 @@ constexpr int kLeafThreads = 256, kLeafTile = 2048, kLeafCapSmem = 16384;
 void launch_build_leaves(cudaStream_t st, const uint32_t *skey, uint32_t nmax, uint32_t cap,
                          int uniform_grid, uint32_t grid_level, uint8_t *mk_a, uint8_t *mk_b,
                          uint32_t *status, uint32_t *tile_counter, uint32_t *leaf_lo,
-                         uint32_t *leaf_hi, uint32_t *leaf_beg, uint32_t *leaf_nsub, Info *info);
+                         uint32_t *leaf_hi, uint32_t *leaf_beg, uint32_t *leaf_nsub, uint2 *leaf_box,
+                         Info *info);
 
 // Query splitting (a5-a7).  Coarse lookup level and tile shapes.
 constexpr int kZLevel = 8;
@@ -337,8 +340,8 @@ void launch_query_blocks(cudaStream_t st, const float4 *rects, uint32_t Q, float
 // first record of every pair (pair_rec[npairs+1]) and leaf_nsub.
 void launch_candidates(cudaStream_t st, int num_sms, int covering, const uint32_t *tile_p0,
                        const uint32_t *pair_q, const uint32_t *pair_first, const uint32_t *pair_blo,
-                       const unsigned long long *pair_off, const uint2 *qcells, const uint32_t *leaf_lo,
-                       const uint32_t *leaf_hi, const uint32_t *leaf_beg, uint32_t *tile_cnt,
+                       const unsigned long long *pair_off, const uint2 *qcells, const uint2 *leaf_box,
+                       const uint32_t *leaf_beg, uint32_t *tile_cnt,
                        uint32_t *tile_off, uint32_t *leaf_nsub, uint32_t *sub_q, uint32_t *sub_leaf,
                        uint32_t *sub_len, uint32_t *sub_res, uint32_t *pair_rec, uint32_t *status,
                        uint32_t *tile_counter, Caps caps, Info *info);
