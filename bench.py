@@ -123,9 +123,11 @@ def read_peaks():
         return FALLBACK_HBM_GBS, "fallback"
 
 
-def read_traffic(kernel):
-    """Per-launch DRAM bytes of `kernel` from the committed ncu summary, if the
-    CUDA sources have not changed since it was taken (else None)."""
+def read_traffic(kernel, results_per_launch):
+    """Per-launch DRAM bytes of `kernel` from the committed ncu summary, scaled
+    by the results the timed launches processed (the captured launch is a
+    different tick), if the CUDA sources have not changed since it was taken
+    (else None)."""
     try:
         kv = {}
         with open(TRAFFIC_FILE) as f:
@@ -135,7 +137,7 @@ def read_traffic(kernel):
                     k, v = line.split("=", 1)
                     kv[k.strip()] = v.strip()
         if kv.get("kernel") == kernel and kv.get("source_hash") == source_hash() and kv.get("workload") == "hotspot4m":
-            return float(kv["dram_bytes_per_launch"])
+            return float(kv["dram_bytes_per_launch"]) * results_per_launch / float(kv["results"])
     except Exception:
         pass
     return None
@@ -379,7 +381,7 @@ def run_gpu(args, name):
     roofline = {"bound": "hbm", "kernel": kernel_names.get(dom, dom), "phase": dom,
                 "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                 "peak_source": "%s (MEASURED_PEAKS.json hbm_gbs)" % peak_kind if peak_kind == "measured" else "fallback 6.8 TB/s",
-                "traffic": read_traffic(kernel_names.get(dom, dom)),
+                "traffic": read_traffic(kernel_names.get(dom, dom), results / max(args.steps, 1)),
                 "algorithmic_bytes_per_launch": per_launch_bytes, "launch_ms": per_launch_ms}
     join = ["filter", "emit"]
     join_ms = sum(timing["ms"][p] for p in join)
