@@ -225,9 +225,29 @@ __device__ __forceinline__ void emit_one(void *out, unsigned long long pos, uint
     }
 }
 
+// The same, at slot rel of a record whose first slot is base (32-bit offset
+// arithmetic inside a record).
+template <int KIND>
+__device__ __forceinline__ void emit_rel(void *out, unsigned long long base, uint32_t rel, uint32_t q, uint32_t id,
+                                         uint32_t wpr) {
+    if (KIND == kEmitPairs) {
+        (reinterpret_cast<uint2 *>(out) + base)[rel] = make_uint2(q, id);
+    } else if (KIND == kEmitIds) {
+        (reinterpret_cast<uint32_t *>(out) + base)[rel] = id;
+    } else if (KIND == kEmitBitmap) {
+        atomicOr(reinterpret_cast<uint32_t *>(out) + (size_t)q * wpr + (id >> 5), 1u << (id & 31u));
+    } else {
+        (reinterpret_cast<unsigned long long *>(out) + base)[rel] = ((unsigned long long)q << 32) | id;
+    }
+}
+
 constexpr int kEmitThreads = 256;
+constexpr int kEmitWarps = kEmitThreads / 32;
+constexpr int kRunSteps = 2;      // strided warp steps issued together in a covering run
 
 // Copy a covering run: ids sid[b..b+n) with query q to output slots off...
+// kRunSteps strided steps of the warp are issued together (loads first) so
+// that each lane keeps several id loads in flight.
 template <int KIND>
 __device__ __forceinline__ void emit_run(void *out, unsigned long long off, uint32_t q,
                                          const uint32_t *__restrict__ sid, uint32_t b, uint32_t n,
@@ -241,76 +261,125 @@ __device__ __forceinline__ void emit_run(void *out, unsigned long long off, uint
         }
         const uint32_t n2 = n >> 1;
         uint4 *o4 = reinterpret_cast<uint4 *>(out) + (off >> 1);
-        for (uint32_t i = lane; i < n2; i += 32) {
-            const uint32_t a0 = __ldg(sid + b + 2 * i), a1 = __ldg(sid + b + 2 * i + 1);
-            o4[i] = make_uint4(q, a0, q, a1);
+        const uint32_t *src = sid + b;
+        for (uint32_t i0 = 0; i0 < n2; i0 += 32u * kRunSteps) {
+            uint32_t a[2 * kRunSteps];
+#pragma unroll
+            for (int u = 0; u < kRunSteps; ++u) {
+                const uint32_t i = i0 + lane + 32u * u;
+                if (i < n2) {
+                    a[2 * u] = __ldg(src + 2 * i);
+                    a[2 * u + 1] = __ldg(src + 2 * i + 1);
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < kRunSteps; ++u) {
+                const uint32_t i = i0 + lane + 32u * u;
+                if (i < n2) o4[i] = make_uint4(q, a[2 * u], q, a[2 * u + 1]);
+            }
         }
         if ((n & 1u) && lane == 0) emit_one<KIND>(out, off + n - 1, q, __ldg(sid + b + n - 1), wpr);
     } else {
-        for (uint32_t i = lane; i < n; i += 32) emit_one<KIND>(out, off + i, q, __ldg(sid + b + i), wpr);
+        for (uint32_t i0 = 0; i0 < n; i0 += 32u * kRunSteps) {
+            uint32_t a[kRunSteps];
+#pragma unroll
+            for (int u = 0; u < kRunSteps; ++u) {
+                const uint32_t i = i0 + lane + 32u * u;
+                if (i < n) a[u] = __ldg(sid + b + i);
+            }
+#pragma unroll
+            for (int u = 0; u < kRunSteps; ++u) {
+                const uint32_t i = i0 + lane + 32u * u;
+                if (i < n) emit_rel<KIND>(out, off, i, q, a[u], wpr);
+            }
+        }
     }
+}
+
+// Decode NW consecutive bitmap words of one intersecting subquery (Alg. 4):
+// lane j holds word j (j < NW) and, for every word, the id of its object j;
+// a lane whose bit is set writes at run + popc(word & lanemask_lt), so the
+// i-th positive of a word goes to the i-th slot, coalesced.  The ids are
+// loaded before the first store so that their loads overlap.  nvalid =
+// objects covered by these words (bits past it are zero).  Returns run.
+template <int KIND, int NW>
+__device__ __forceinline__ uint32_t emit_words(void *out, unsigned long long off, uint32_t run, uint32_t q,
+                                               const uint32_t *__restrict__ ids, uint32_t nvalid,
+                                               uint32_t myw, int lane, uint32_t lt, uint32_t wpr) {
+    uint32_t id[NW];
+#pragma unroll
+    for (int wd = 0; wd < NW; ++wd) {
+        const uint32_t o = wd * 32u + lane;
+        id[wd] = o < nvalid ? __ldg(ids + o) : 0u;
+    }
+#pragma unroll
+    for (int wd = 0; wd < NW; ++wd) {
+        const uint32_t wv = __shfl_sync(0xffffffffu, myw, wd);
+        if ((wv >> lane) & 1u) emit_rel<KIND>(out, off, run + __popc(wv & lt), q, id[wd], wpr);
+        run += __popc(wv);
+    }
+    return run;
 }
 
 // One warp per batch of 32 consecutive subquery records (query-major order,
 // so the output is written front to back): lane j loads the metadata of
-// record j of the batch, then the warp handles the records one by one with
-// the metadata broadcast by shuffles.
+// record j into the warp's shared-memory slots, then the warp handles the
+// records one by one, reading each record's metadata with broadcast loads.
+// Intersecting records are decoded two words at a time.  The kernel is held
+// to 32 registers so that 64 warps per SM hide the load latency.
 template <int KIND>
-__global__ void __launch_bounds__(kEmitThreads)
+__global__ void __launch_bounds__(kEmitThreads, 8)
 emit_kernel(const uint32_t *__restrict__ sub_q, const uint32_t *__restrict__ sub_leaf,
             const uint32_t *__restrict__ sub_len, const uint32_t *__restrict__ sub_bm,
             const unsigned long long *__restrict__ out_off, const uint32_t *__restrict__ leaf_beg,
             const uint32_t *__restrict__ sid, const uint32_t *__restrict__ bitmap, void *out,
             uint32_t wpr, Caps caps, const Info *info) {
+    // per record: {q, bitmap row, first sorted object, objects | covering flag} and its output offset
+    __shared__ uint4 s_rec[kEmitWarps][32];
+    __shared__ unsigned long long s_off[kEmitWarps][32];
     if (!tick_buffers_ok(info, caps)) return;
     if (KIND != kEmitBitmap && info->n_results > caps.out) return;
     const uint32_t nsub = (uint32_t)info->n_sub;
     const int lane = threadIdx.x & 31;
+    const int wib = threadIdx.x >> 5;
     const uint32_t lt = lanemask_lt();
-    const uint32_t nwarps = gridDim.x * (kEmitThreads / 32);
+    const uint32_t nwarps = gridDim.x * kEmitWarps;
     const uint32_t nbatch = (nsub + 31u) >> 5;
     for (uint32_t batch = (blockIdx.x * kEmitThreads + threadIdx.x) >> 5; batch < nbatch; batch += nwarps) {
         const uint32_t k = batch * 32u + lane;
-        uint32_t q = 0, sl = 0, bm = 0, b = 0, e = 0;
-        unsigned long long off = 0;
         if (k < nsub) {
-            q = __ldg(sub_q + k);
-            sl = __ldg(sub_leaf + k);
-            off = __ldg(out_off + k);
+            const uint32_t sl = __ldg(sub_leaf + k);
             const uint32_t first = sl & 0x7fffffffu;
-            uint32_t len = 1;
-            if (sl & 0x80000000u) len = __ldg(sub_len + k);
-            else bm = __ldg(sub_bm + k);
-            b = __ldg(leaf_beg + first);
-            e = __ldg(leaf_beg + first + len);
+            const bool cov = (sl & 0x80000000u) != 0u;
+            const uint32_t len = cov ? __ldg(sub_len + k) : 1u;
+            const uint32_t b = __ldg(leaf_beg + first);
+            const uint32_t e = __ldg(leaf_beg + first + len);
+            const uint32_t row = cov ? 0u : __ldg(sub_bm + k);
+            s_rec[wib][lane] = make_uint4(__ldg(sub_q + k), row, b, (e - b) | (cov ? 0x80000000u : 0u));
+            s_off[wib][lane] = __ldg(out_off + k);
         }
+        __syncwarp();
         const uint32_t nrec = min(32u, nsub - batch * 32u);
         for (uint32_t j = 0; j < nrec; ++j) {
-            const uint32_t qj = __shfl_sync(0xffffffffu, q, j);
-            const uint32_t slj = __shfl_sync(0xffffffffu, sl, j);
-            const uint32_t bj = __shfl_sync(0xffffffffu, b, j);
-            const uint32_t ej = __shfl_sync(0xffffffffu, e, j);
-            const unsigned long long offj = __shfl_sync(0xffffffffu, off, j);
-            if (slj & 0x80000000u) {
-                emit_run<KIND>(out, offj, qj, sid, bj, ej - bj, wpr, lane);
-            } else {
-                const uint32_t row = __shfl_sync(0xffffffffu, bm, j);
-                const uint32_t nw = (ej - bj + 31u) >> 5;
-                unsigned long long run = offj;
-                for (uint32_t w0 = 0; w0 < nw; w0 += 32) {
-                    const uint32_t myw = (w0 + lane < nw) ? __ldg(bitmap + row + w0 + lane) : 0u;
-                    const uint32_t nj = min(32u, nw - w0);
-                    for (uint32_t jj = 0; jj < nj; ++jj) {
-                        const uint32_t word = __shfl_sync(0xffffffffu, myw, jj);
-                        if (word == 0u) continue;
-                        if ((word >> lane) & 1u)
-                            emit_one<KIND>(out, run + __popc(word & lt), qj,
-                                           __ldg(sid + bj + (w0 + jj) * 32u + lane), wpr);
-                        run += __popc(word);
-                    }
-                }
+            const uint4 r = s_rec[wib][j];
+            const unsigned long long offj = s_off[wib][j];
+            const uint32_t n = r.w & 0x7fffffffu;
+            if (r.w & 0x80000000u) {
+                emit_run<KIND>(out, offj, r.x, sid, r.z, n, wpr, lane);
+                continue;
+            }
+            const uint32_t nw = (n + 31u) >> 5;
+            uint32_t run = 0;
+            for (uint32_t w0 = 0; w0 < nw; w0 += 2) {
+                const uint32_t cnt = min(2u, nw - w0);
+                const uint32_t myw = (uint32_t)lane < cnt ? __ldg(bitmap + r.y + w0 + lane) : 0u;
+                const uint32_t *ids = sid + r.z + w0 * 32u;
+                const uint32_t nv = n - w0 * 32u;
+                if (cnt == 2) run = emit_words<KIND, 2>(out, offj, run, r.x, ids, nv, myw, lane, lt, wpr);
+                else run = emit_words<KIND, 1>(out, offj, run, r.x, ids, nv, myw, lane, lt, wpr);
             }
         }
+        __syncwarp();
     }
 }
 
@@ -341,29 +410,37 @@ void launch_emit(cudaStream_t st, int num_sms, int emit_kind, const uint32_t *su
 }
 
 // Per-query offsets: the first record of query q is the first record of its
-// first (query, block) pair (queries without pairs take the next pair's).
+// first (query, block) pair (queries without pairs take the next pair's);
+// pair_rec holds that record's padded candidate slot 32t + rank.
 __global__ void query_offsets_kernel(uint32_t Q, const uint32_t *__restrict__ qpair,
-                                     const uint32_t *__restrict__ pair_rec,
+                                     const uint32_t *__restrict__ pair_rec, const uint32_t *__restrict__ tile_off,
                                      const unsigned long long *__restrict__ out_off,
                                      unsigned long long *__restrict__ offsets, Caps caps,
                                      const Info *info) {
     if (!tick_buffers_ok(info, caps)) return;
-    const unsigned long long nsub = info->n_sub;
+    const uint32_t nsub = (uint32_t)info->n_sub;
+    const uint32_t npairs = (uint32_t)info->n_pairs;
     for (uint32_t q = blockIdx.x * blockDim.x + threadIdx.x; q <= Q; q += gridDim.x * blockDim.x) {
         if (Q == 0 || nsub == 0) {
             offsets[q] = 0;
             continue;
         }
-        offsets[q] = out_off[pair_rec[qpair[q]]];
+        const uint32_t p = qpair[q];
+        uint32_t rec = nsub;
+        if (p < npairs) {
+            const uint32_t slot = pair_rec[p];
+            rec = tile_off[slot >> 5] + (slot & 31u);
+        }
+        offsets[q] = out_off[rec];
     }
 }
 
 void launch_query_offsets(cudaStream_t st, uint32_t Q, const uint32_t *qpair, const uint32_t *pair_rec,
-                          const unsigned long long *out_off, unsigned long long *offsets,
-                          Caps caps, const Info *info) {
+                          const uint32_t *tile_off, const unsigned long long *out_off,
+                          unsigned long long *offsets, Caps caps, const Info *info) {
     uint32_t g = (Q + 1 + 255) / 256;
     if (g > 4096) g = 4096;
-    query_offsets_kernel<<<g, 256, 0, st>>>(Q, qpair, pair_rec, out_off, offsets, caps, info);
+    query_offsets_kernel<<<g, 256, 0, st>>>(Q, qpair, pair_rec, tile_off, out_off, offsets, caps, info);
 }
 
 // Sorted (qidx << 32 | id) keys to the requested layout.

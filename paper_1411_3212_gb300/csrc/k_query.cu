@@ -216,11 +216,14 @@ void launch_query_blocks(cudaStream_t st, const float4 *rects, uint32_t Q, float
 // gathered in one bit mask, and the pair of lane L is found by a popcount.
 // Consecutive covering leaves of one pair inside one tile form one covering
 // run (their objects are one contiguous range of the sorted objects).
-// Count pass -> scan of the per-tile record counts -> write pass.  Record k:
-// sub_q[k] = query, sub_leaf[k] = first leaf (bit 31 set for a covering run),
-// sub_len[k] = run length, sub_res[k] = result count (covering: the run's
-// objects; intersecting: 0, filled by the filter).  Records are in
-// query-major order.
+// One classification pass writes each tile's records into the tile's 32
+// padded slots (slot 32t + rank) and counts them; a scan of the per-tile
+// counts gives every tile its first record; a compaction pass moves the
+// records to their places.  Record k: sub_q[k] = query, sub_leaf[k] = first
+// leaf (bit 31 set for a covering run), sub_len[k] = run length, sub_res[k] =
+// result count (covering: the run's objects; intersecting: 0, filled by the
+// filter).  Records are in query-major order.  pair_rec[p] = padded slot of
+// pair p's first record (or of the record after it, if p has none).
 // ---------------------------------------------------------------------------
 struct CandLane {
     bool valid;
@@ -286,7 +289,8 @@ cand_count_kernel(int covering, const uint32_t *__restrict__ tile_p0, const uint
                   const unsigned long long *__restrict__ pair_off, const uint2 *__restrict__ qcells,
                   const uint2 *__restrict__ leaf_box,
                   const uint32_t *__restrict__ leaf_beg, uint32_t *__restrict__ tile_cnt,
-                  uint32_t *__restrict__ leaf_nsub, Caps caps, Info *info) {
+                  uint32_t *__restrict__ leaf_nsub, uint4 *__restrict__ pad, uint32_t *__restrict__ pair_rec,
+                  Caps caps, Info *info) {
     __shared__ unsigned long long s_red[3];
     if (threadIdx.x < 3) s_red[threadIdx.x] = 0;
     __syncthreads();
@@ -294,6 +298,7 @@ cand_count_kernel(int covering, const uint32_t *__restrict__ tile_p0, const uint
     const uint32_t npairs = (uint32_t)info->n_pairs;
     const unsigned long long ntiles = (ncand + 31) >> 5;
     const uint32_t lane = threadIdx.x & 31;
+    const uint32_t lt = lanemask_lt();
     unsigned long long n_i = 0, n_c = 0, tests = 0;
     if (ntiles <= caps.cand_tiles) {
         const unsigned long long nw = (unsigned long long)gridDim.x * (blockDim.x >> 5);
@@ -303,13 +308,25 @@ cand_count_kernel(int covering, const uint32_t *__restrict__ tile_p0, const uint
                                    qcells, leaf_box);
             const bool rec = r.code == 1 || (r.code == 2 && !r.cont);
             const uint32_t m = __ballot_sync(0xffffffffu, rec);
+            const uint32_t notcont = __ballot_sync(0xffffffffu, !(r.valid && r.cont));
+            const uint32_t slot0 = (uint32_t)(t << 5);
             if (lane == 0) tile_cnt[t] = __popc(m);
+            if (r.pj_starts) pair_rec[__ldg(tile_p0 + t) + lane] = slot0 + __popc(m & ((1u << r.po_j) - 1u));
             if (r.code == 1) {
                 ++n_i;
                 atomicAdd(leaf_nsub + r.leaf, 1u);
                 tests += __ldg(leaf_beg + r.leaf + 1) - __ldg(leaf_beg + r.leaf);
+                pad[slot0 + __popc(m & lt)] = make_uint4(r.q, r.leaf, 1u, 0u);
             } else if (r.code == 2) {
                 ++n_c;
+                if (!r.cont) {
+                    const uint32_t after = notcont & ~(lt | (1u << lane));   // later lanes that end the run
+                    const uint32_t end = after ? (uint32_t)(__ffs(after) - 1) : 32u;
+                    const uint32_t len = end - lane;
+                    pad[slot0 + __popc(m & lt)] =
+                        make_uint4(r.q, r.leaf | 0x80000000u, len,
+                                   __ldg(leaf_beg + r.leaf + len) - __ldg(leaf_beg + r.leaf));
+                }
             }
         }
     }
@@ -365,51 +382,26 @@ tile_scan_kernel(const uint32_t *__restrict__ tile_cnt, uint32_t *__restrict__ t
     if (tid == 0 && base + 2048 >= ntiles) info->n_sub = s_prefix + total;
 }
 
+// Padded slot 32t + rank (rank < the tile's count) -> record tile_off[t] + rank.
 __global__ void __launch_bounds__(256)
-cand_write_kernel(int covering, const uint32_t *__restrict__ tile_p0, const uint32_t *__restrict__ pair_q,
-                  const uint32_t *__restrict__ pair_first, const uint32_t *__restrict__ pair_blo,
-                  const unsigned long long *__restrict__ pair_off, const uint2 *__restrict__ qcells,
-                  const uint2 *__restrict__ leaf_box,
-                  const uint32_t *__restrict__ leaf_beg, const uint32_t *__restrict__ tile_off,
-                  uint32_t *__restrict__ sub_q, uint32_t *__restrict__ sub_leaf, uint32_t *__restrict__ sub_len,
-                  uint32_t *__restrict__ sub_res, uint32_t *__restrict__ pair_rec, Caps caps,
-                  const Info *info) {
-    const unsigned long long ncand = info->n_cand;
-    const uint32_t npairs = (uint32_t)info->n_pairs;
-    const unsigned long long ntiles = (ncand + 31) >> 5;
-    if (ntiles > caps.cand_tiles) return;
-    const uint32_t nsub = (uint32_t)info->n_sub;
-    if (blockIdx.x == 0 && threadIdx.x == 0) pair_rec[npairs] = nsub;
-    const uint32_t lane = threadIdx.x & 31;
-    const uint32_t lt = lanemask_lt();
-    const unsigned long long nw = (unsigned long long)gridDim.x * (blockDim.x >> 5);
-    for (unsigned long long t = (blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x) >> 5; t < ntiles;
-         t += nw) {
-        CandLane r = cand_lane(t, ncand, npairs, covering, tile_p0, pair_q, pair_first, pair_blo, pair_off,
-                               qcells, leaf_box);
-        const bool rec = r.code == 1 || (r.code == 2 && !r.cont);
-        const uint32_t m = __ballot_sync(0xffffffffu, rec);
-        const uint32_t notcont = __ballot_sync(0xffffffffu, !(r.valid && r.cont));
-        const uint32_t base = __ldg(tile_off + t);
-        // the first record of every pair that starts in this tile
-        if (r.pj_starts) pair_rec[__ldg(tile_p0 + t) + lane] = base + __popc(m & ((1u << r.po_j) - 1u));
-        if (!rec) continue;
-        const uint32_t k = base + __popc(m & lt);
-        if (k >= caps.sub) continue;
-        if (r.code == 1) {
-            sub_q[k] = r.q;
-            sub_leaf[k] = r.leaf;
-            sub_len[k] = 1;
-            sub_res[k] = 0;
-        } else {
-            const uint32_t after = notcont & ~(lt | (1u << lane));   // later lanes that end the run
-            const uint32_t end = after ? (uint32_t)(__ffs(after) - 1) : 32u;
-            const uint32_t len = end - lane;
-            sub_q[k] = r.q;
-            sub_leaf[k] = r.leaf | 0x80000000u;
-            sub_len[k] = len;
-            sub_res[k] = __ldg(leaf_beg + r.leaf + len) - __ldg(leaf_beg + r.leaf);
-        }
+cand_compact_kernel(const uint4 *__restrict__ pad, const uint32_t *__restrict__ tile_cnt,
+                    const uint32_t *__restrict__ tile_off, uint32_t *__restrict__ sub_q,
+                    uint32_t *__restrict__ sub_leaf, uint32_t *__restrict__ sub_len,
+                    uint32_t *__restrict__ sub_res, Caps caps, const Info *info) {
+    const unsigned long long ntiles = (info->n_cand + 31) >> 5;
+    if (ntiles > caps.cand_tiles || info->n_sub > caps.sub) return;
+    const unsigned long long nslots = ntiles << 5;
+    for (unsigned long long s = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; s < nslots;
+         s += (unsigned long long)gridDim.x * blockDim.x) {
+        const unsigned long long t = s >> 5;
+        const uint32_t rank = (uint32_t)s & 31u;
+        if (rank >= __ldg(tile_cnt + t)) continue;
+        const uint32_t k = __ldg(tile_off + t) + rank;
+        const uint4 r = __ldg(pad + s);
+        sub_q[k] = r.x;
+        sub_leaf[k] = r.y;
+        sub_len[k] = r.z;
+        sub_res[k] = r.w;
     }
 }
 
@@ -417,18 +409,17 @@ void launch_candidates(cudaStream_t st, int num_sms, int covering, const uint32_
                        const uint32_t *pair_q, const uint32_t *pair_first, const uint32_t *pair_blo,
                        const unsigned long long *pair_off, const uint2 *qcells, const uint2 *leaf_box,
                        const uint32_t *leaf_beg, uint32_t *tile_cnt,
-                       uint32_t *tile_off, uint32_t *leaf_nsub, uint32_t *sub_q, uint32_t *sub_leaf,
+                       uint32_t *tile_off, uint32_t *leaf_nsub, uint4 *pad, uint32_t *sub_q, uint32_t *sub_leaf,
                        uint32_t *sub_len, uint32_t *sub_res, uint32_t *pair_rec, uint32_t *status,
                        uint32_t *tile_counter, Caps caps, Info *info) {
     cand_count_kernel<<<num_sms * 8, 256, 0, st>>>(covering, tile_p0, pair_q, pair_first, pair_blo, pair_off,
-                                                   qcells, leaf_box, leaf_beg, tile_cnt, leaf_nsub,
-                                                   caps, info);
-    const unsigned long long scan_blocks = (caps.cand_tiles + 2047) / 2048;
+                                                   qcells, leaf_box, leaf_beg, tile_cnt, leaf_nsub, pad,
+                                                   pair_rec, caps, info);
+    const unsigned long long scan_blocks = (caps.cand_tiles + kCandScanTile - 1) / kCandScanTile;
     tile_scan_kernel<<<(unsigned)(scan_blocks ? scan_blocks : 1), 256, 0, st>>>(tile_cnt, tile_off, status,
                                                                               tile_counter, caps, info);
-    cand_write_kernel<<<num_sms * 8, 256, 0, st>>>(covering, tile_p0, pair_q, pair_first, pair_blo, pair_off,
-                                                   qcells, leaf_box, leaf_beg, tile_off, sub_q,
-                                                   sub_leaf, sub_len, sub_res, pair_rec, caps, info);
+    cand_compact_kernel<<<num_sms * 16, 256, 0, st>>>(pad, tile_cnt, tile_off, sub_q, sub_leaf, sub_len,
+                                                      sub_res, caps, info);
 }
 
 // ---------------------------------------------------------------------------

@@ -94,6 +94,7 @@ struct mqr_ctx {
     DevBuf<unsigned long long> out_off;
     // query splitting: coarse lookup table, per-query cells, (query, block) pairs
     DevBuf<uint32_t> zmap, pair_q, pair_first, pair_blo, pair_rec, qpair, tile_p0, tile_cnt, tile_off;
+    DevBuf<uint4> cand_pad;          // padded records, 32 slots per candidate tile
     DevBuf<uint2> qcells;
     DevBuf<unsigned long long> cand_off, pair_off;
     unsigned long long cand_tiles = 0;
@@ -296,7 +297,8 @@ mqr_status enqueue_tick(mqr_ctx *c, const float4 *rects, uint32_t Q, int emit_ki
     phase_begin(c, MQR_PHASE_CANDIDATES);
     launch_candidates(st, c->num_sms, cov, c->tile_p0.p, c->pair_q.p, c->pair_first.p, c->pair_blo.p,
                       c->pair_off.p, c->qcells.p, c->leaf_box.p, c->leaf_beg.p, c->tile_cnt.p,
-                      c->tile_off.p, c->leaf_nsub.p, c->sub_q.p, c->sub_leaf.p, c->sub_len.p, c->sub_res.p,
+                      c->tile_off.p, c->leaf_nsub.p, c->cand_pad.p, c->sub_q.p, c->sub_leaf.p, c->sub_len.p,
+                      c->sub_res.p,
                       c->pair_rec.p, at<uint32_t>(c, a.st_cand), ctr + 8, caps, info);
     phase_end(c, MQR_PHASE_CANDIDATES, 3);
     // a8: group intersecting subqueries by leaf
@@ -328,7 +330,7 @@ mqr_status enqueue_tick(mqr_ctx *c, const float4 *rects, uint32_t Q, int emit_ki
     }
     if (offsets != nullptr) {
         phase_begin(c, MQR_PHASE_OFFSETS);
-        launch_query_offsets(st, Q, c->qpair.p, c->pair_rec.p, c->out_off.p, offsets, caps, info);
+        launch_query_offsets(st, Q, c->qpair.p, c->pair_rec.p, c->tile_off.p, c->out_off.p, offsets, caps, info);
         phase_end(c, MQR_PHASE_OFFSETS, 1);
     }
     return check_launch("tick kernels");
@@ -347,10 +349,12 @@ mqr_status ensure_tick_buffers(mqr_ctx *c, uint32_t Q) {
     MQR_CUDA(c->pair_blo.ensure((size_t)Q * 9 + 1));
     MQR_CUDA(c->pair_off.ensure((size_t)Q * 9 + 1));
     MQR_CUDA(c->pair_rec.ensure((size_t)Q * 9 + 2));
-    c->cand_tiles = std::max<unsigned long long>(c->cand_tiles, std::max<unsigned long long>(1 << 16, 2ull * Q));
+    c->cand_tiles = std::min<unsigned long long>(
+        std::max<unsigned long long>(c->cand_tiles, std::max<unsigned long long>(1 << 16, 2ull * Q)), kMaxCandTiles);
     MQR_CUDA(c->tile_p0.ensure(c->cand_tiles));
     MQR_CUDA(c->tile_cnt.ensure(c->cand_tiles));
     MQR_CUDA(c->tile_off.ensure(c->cand_tiles));
+    MQR_CUDA(c->cand_pad.ensure(c->cand_tiles * 32));
     if (c->sub_q.n == 0) {
         MQR_CUDA(c->sub_q.ensure(sub0));
         MQR_CUDA(c->sub_leaf.ensure(sub0));
@@ -406,11 +410,14 @@ mqr_status run_tick(mqr_ctx *c, const float4 *rects, uint32_t Q, int emit_kind, 
         bool again = false;
         const unsigned long long need_tiles = (in.n_cand + 31) / 32;
         if (need_tiles > caps.cand_tiles) {
-            c->cand_tiles = grow_to(need_tiles);
-            c->tile_p0.release(); c->tile_cnt.release(); c->tile_off.release();
+            if (need_tiles > kMaxCandTiles)
+                return fail(MQR_ERR_INVALID_ARG, "too many candidate leaves in one tick (limit 2^32)");
+            c->cand_tiles = std::min<unsigned long long>(grow_to(need_tiles), kMaxCandTiles);
+            c->tile_p0.release(); c->tile_cnt.release(); c->tile_off.release(); c->cand_pad.release();
             MQR_CUDA(c->tile_p0.ensure(c->cand_tiles));
             MQR_CUDA(c->tile_cnt.ensure(c->cand_tiles));
             MQR_CUDA(c->tile_off.ensure(c->cand_tiles));
+            MQR_CUDA(c->cand_pad.ensure(c->cand_tiles * 32));
             again = true;
         } else if (in.n_sub > caps.sub) {
             s = grow_sub(c, in.n_sub);
@@ -602,6 +609,7 @@ void mqr_destroy(mqr_ctx *c) {
                                 &c->pair_first, &c->pair_blo, &c->pair_rec, &c->qpair, &c->tile_p0,
                                 &c->tile_cnt, &c->tile_off};
     for (auto *b : u32s) b->release();
+    c->cand_pad.release();
     c->qcells.release();
     c->leaf_box.release();
     c->cand_off.release();

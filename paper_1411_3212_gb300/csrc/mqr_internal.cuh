@@ -325,6 +325,7 @@ constexpr uint32_t kZCells = 1u << (2 * kZLevel);
 constexpr int kZShift = 2 * (kLevels - kZLevel);
 constexpr int kQBThreads = 256;                       // threads per block of query_blocks
 constexpr int kQBQueries = kQBThreads / 9;            // queries per block (9 block slots each)
+constexpr unsigned long long kMaxCandTiles = 1ull << 27;   // padded slots 32t + rank fit 32 bits
 constexpr int kCandScanTile = 2048;                   // warp tiles per block of the tile-count scan
 
 void launch_zmap(cudaStream_t st, const uint32_t *leaf_hi, const Info *info, uint32_t *zmap);
@@ -342,7 +343,7 @@ void launch_candidates(cudaStream_t st, int num_sms, int covering, const uint32_
                        const uint32_t *pair_q, const uint32_t *pair_first, const uint32_t *pair_blo,
                        const unsigned long long *pair_off, const uint2 *qcells, const uint2 *leaf_box,
                        const uint32_t *leaf_beg, uint32_t *tile_cnt,
-                       uint32_t *tile_off, uint32_t *leaf_nsub, uint32_t *sub_q, uint32_t *sub_leaf,
+                       uint32_t *tile_off, uint32_t *leaf_nsub, uint4 *pad, uint32_t *sub_q, uint32_t *sub_leaf,
                        uint32_t *sub_len, uint32_t *sub_res, uint32_t *pair_rec, uint32_t *status,
                        uint32_t *tile_counter, Caps caps, Info *info);
 
@@ -381,8 +382,8 @@ void launch_emit(cudaStream_t st, int num_sms, int emit_kind, const uint32_t *su
 
 // Per-query offsets: off[q] = out_off[pair_rec[qpair[q]]].
 void launch_query_offsets(cudaStream_t st, uint32_t Q, const uint32_t *qpair, const uint32_t *pair_rec,
-                          const unsigned long long *out_off, unsigned long long *offsets,
-                          Caps caps, const Info *info);
+                          const uint32_t *tile_off, const unsigned long long *out_off,
+                          unsigned long long *offsets, Caps caps, const Info *info);
 
 // (qidx << 32 | id) keys -> pairs (qidx, id) or ids.
 void launch_keys_to_output(cudaStream_t st, const unsigned long long *keys, uint64_t n,
