@@ -333,7 +333,7 @@ emit_kernel(const uint32_t *__restrict__ sub_q, const uint32_t *__restrict__ sub
             const uint32_t *__restrict__ sub_len, const uint32_t *__restrict__ sub_bm,
             const unsigned long long *__restrict__ out_off, const uint32_t *__restrict__ leaf_beg,
             const uint32_t *__restrict__ sid, const uint32_t *__restrict__ bitmap, void *out,
-            uint32_t wpr, Caps caps, const Info *info) {
+            uint32_t wpr, uint32_t *ticket, Caps caps, const Info *info) {
     // per record: {q, bitmap row, first sorted object, objects | covering flag} and its output offset
     __shared__ uint4 s_rec[kEmitWarps][32];
     __shared__ unsigned long long s_off[kEmitWarps][32];
@@ -343,9 +343,14 @@ emit_kernel(const uint32_t *__restrict__ sub_q, const uint32_t *__restrict__ sub
     const int lane = threadIdx.x & 31;
     const int wib = threadIdx.x >> 5;
     const uint32_t lt = lanemask_lt();
-    const uint32_t nwarps = gridDim.x * kEmitWarps;
     const uint32_t nbatch = (nsub + 31u) >> 5;
-    for (uint32_t batch = (blockIdx.x * kEmitThreads + threadIdx.x) >> 5; batch < nbatch; batch += nwarps) {
+    // batches are handed out by a ticket counter (their sizes vary widely);
+    // the next ticket is drawn while the current batch is processed
+    uint32_t batch = 0, next = 0;
+    if (lane == 0) batch = atomicAdd(ticket, 1u);
+    batch = __shfl_sync(0xffffffffu, batch, 0);
+    for (; batch < nbatch; batch = __shfl_sync(0xffffffffu, next, 0)) {
+        if (lane == 0) next = atomicAdd(ticket, 1u);
         const uint32_t k = batch * 32u + lane;
         if (k < nsub) {
             const uint32_t sl = __ldg(sub_leaf + k);
@@ -387,24 +392,24 @@ void launch_emit(cudaStream_t st, int num_sms, int emit_kind, const uint32_t *su
                  const uint32_t *sub_leaf, const uint32_t *sub_len, const uint32_t *sub_bm,
                  const unsigned long long *out_off, const uint32_t *leaf_beg,
                  const uint32_t *sid, const uint32_t *bitmap, void *out, uint32_t wpr,
-                 Caps caps, const Info *info) {
+                 uint32_t *ticket, Caps caps, const Info *info) {
     const int grid = num_sms * 8;
     switch (emit_kind) {
         case kEmitPairs:
             emit_kernel<kEmitPairs><<<grid, kEmitThreads, 0, st>>>(sub_q, sub_leaf, sub_len, sub_bm, out_off,
-                                                                   leaf_beg, sid, bitmap, out, wpr, caps, info);
+                                                                   leaf_beg, sid, bitmap, out, wpr, ticket, caps, info);
             break;
         case kEmitIds:
             emit_kernel<kEmitIds><<<grid, kEmitThreads, 0, st>>>(sub_q, sub_leaf, sub_len, sub_bm, out_off,
-                                                                 leaf_beg, sid, bitmap, out, wpr, caps, info);
+                                                                 leaf_beg, sid, bitmap, out, wpr, ticket, caps, info);
             break;
         case kEmitBitmap:
             emit_kernel<kEmitBitmap><<<grid, kEmitThreads, 0, st>>>(sub_q, sub_leaf, sub_len, sub_bm, out_off,
-                                                                    leaf_beg, sid, bitmap, out, wpr, caps, info);
+                                                                    leaf_beg, sid, bitmap, out, wpr, ticket, caps, info);
             break;
         default:
             emit_kernel<kEmitKeys64><<<grid, kEmitThreads, 0, st>>>(sub_q, sub_leaf, sub_len, sub_bm, out_off,
-                                                                    leaf_beg, sid, bitmap, out, wpr, caps, info);
+                                                                    leaf_beg, sid, bitmap, out, wpr, ticket, caps, info);
             break;
     }
 }

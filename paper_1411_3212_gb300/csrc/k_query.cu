@@ -314,9 +314,9 @@ cand_count_kernel(int covering, const uint32_t *__restrict__ tile_p0, const uint
             if (r.pj_starts) pair_rec[__ldg(tile_p0 + t) + lane] = slot0 + __popc(m & ((1u << r.po_j) - 1u));
             if (r.code == 1) {
                 ++n_i;
-                atomicAdd(leaf_nsub + r.leaf, 1u);
+                const uint32_t rank = atomicAdd(leaf_nsub + r.leaf, 1u);   // row in the leaf's list
                 tests += __ldg(leaf_beg + r.leaf + 1) - __ldg(leaf_beg + r.leaf);
-                pad[slot0 + __popc(m & lt)] = make_uint4(r.q, r.leaf, 1u, 0u);
+                pad[slot0 + __popc(m & lt)] = make_uint4(r.q, r.leaf, rank, 0u);
             } else if (r.code == 2) {
                 ++n_c;
                 if (!r.cont) {
@@ -382,44 +382,18 @@ tile_scan_kernel(const uint32_t *__restrict__ tile_cnt, uint32_t *__restrict__ t
     if (tid == 0 && base + 2048 >= ntiles) info->n_sub = s_prefix + total;
 }
 
-// Padded slot 32t + rank (rank < the tile's count) -> record tile_off[t] + rank.
-__global__ void __launch_bounds__(256)
-cand_compact_kernel(const uint4 *__restrict__ pad, const uint32_t *__restrict__ tile_cnt,
-                    const uint32_t *__restrict__ tile_off, uint32_t *__restrict__ sub_q,
-                    uint32_t *__restrict__ sub_leaf, uint32_t *__restrict__ sub_len,
-                    uint32_t *__restrict__ sub_res, Caps caps, const Info *info) {
-    const unsigned long long ntiles = (info->n_cand + 31) >> 5;
-    if (ntiles > caps.cand_tiles || info->n_sub > caps.sub) return;
-    const unsigned long long nslots = ntiles << 5;
-    for (unsigned long long s = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; s < nslots;
-         s += (unsigned long long)gridDim.x * blockDim.x) {
-        const unsigned long long t = s >> 5;
-        const uint32_t rank = (uint32_t)s & 31u;
-        if (rank >= __ldg(tile_cnt + t)) continue;
-        const uint32_t k = __ldg(tile_off + t) + rank;
-        const uint4 r = __ldg(pad + s);
-        sub_q[k] = r.x;
-        sub_leaf[k] = r.y;
-        sub_len[k] = r.z;
-        sub_res[k] = r.w;
-    }
-}
-
 void launch_candidates(cudaStream_t st, int num_sms, int covering, const uint32_t *tile_p0,
                        const uint32_t *pair_q, const uint32_t *pair_first, const uint32_t *pair_blo,
                        const unsigned long long *pair_off, const uint2 *qcells, const uint2 *leaf_box,
-                       const uint32_t *leaf_beg, uint32_t *tile_cnt,
-                       uint32_t *tile_off, uint32_t *leaf_nsub, uint4 *pad, uint32_t *sub_q, uint32_t *sub_leaf,
-                       uint32_t *sub_len, uint32_t *sub_res, uint32_t *pair_rec, uint32_t *status,
-                       uint32_t *tile_counter, Caps caps, Info *info) {
+                       const uint32_t *leaf_beg, uint32_t *tile_cnt, uint32_t *tile_off, uint32_t *leaf_nsub,
+                       uint4 *pad, uint32_t *pair_rec, uint32_t *status, uint32_t *tile_counter, Caps caps,
+                       Info *info) {
     cand_count_kernel<<<num_sms * 8, 256, 0, st>>>(covering, tile_p0, pair_q, pair_first, pair_blo, pair_off,
                                                    qcells, leaf_box, leaf_beg, tile_cnt, leaf_nsub, pad,
                                                    pair_rec, caps, info);
     const unsigned long long scan_blocks = (caps.cand_tiles + kCandScanTile - 1) / kCandScanTile;
     tile_scan_kernel<<<(unsigned)(scan_blocks ? scan_blocks : 1), 256, 0, st>>>(tile_cnt, tile_off, status,
                                                                               tile_counter, caps, info);
-    cand_compact_kernel<<<num_sms * 16, 256, 0, st>>>(pad, tile_cnt, tile_off, sub_q, sub_leaf, sub_len,
-                                                      sub_res, caps, info);
 }
 
 // ---------------------------------------------------------------------------
@@ -432,7 +406,7 @@ void launch_candidates(cudaStream_t st, int num_sms, int covering, const uint32_
 __global__ void __launch_bounds__(kLeafScanThreads)
 leaf_scan_kernel(const uint32_t *__restrict__ leaf_beg, const uint32_t *__restrict__ leaf_nsub,
                  uint32_t *__restrict__ leaf_sub_off, uint32_t *__restrict__ leaf_word_off,
-                 uint32_t *__restrict__ leaf_item_off, uint32_t *__restrict__ leaf_cursor,
+                 uint32_t *__restrict__ leaf_item_off,
                  uint32_t *__restrict__ item_leaf, uint32_t *status3, uint32_t num_tiles,
                  uint32_t *tile_counter, Caps caps, Info *info) {
     __shared__ uint32_t s_scan[kLeafScanThreads / 32 + 1];
@@ -482,7 +456,6 @@ leaf_scan_kernel(const uint32_t *__restrict__ leaf_beg, const uint32_t *__restri
         uint32_t l = lb + e;
         if (l < L) {
             leaf_sub_off[l] = o_s;
-            leaf_cursor[l] = o_s;
             leaf_word_off[l] = o_w;
             leaf_item_off[l] = o_i;
             for (uint32_t t = 0; t < ni[e]; ++t)
@@ -501,44 +474,86 @@ leaf_scan_kernel(const uint32_t *__restrict__ leaf_beg, const uint32_t *__restri
 
 void launch_leaf_scan(cudaStream_t st, uint32_t nmax, const uint32_t *leaf_beg,
                       const uint32_t *leaf_nsub, uint32_t *leaf_sub_off, uint32_t *leaf_word_off,
-                      uint32_t *leaf_item_off, uint32_t *leaf_cursor, uint32_t *item_leaf,
+                      uint32_t *leaf_item_off, uint32_t *item_leaf,
                       uint32_t *status3, uint32_t *tile_counter, Caps caps, Info *info) {
     if (nmax == 0) return;
     uint32_t tiles = (nmax + kLeafScanTile - 1) / kLeafScanTile;
     leaf_scan_kernel<<<tiles, kLeafScanThreads, 0, st>>>(leaf_beg, leaf_nsub, leaf_sub_off,
-                                                         leaf_word_off, leaf_item_off, leaf_cursor,
+                                                         leaf_word_off, leaf_item_off,
                                                          item_leaf, status3, tiles, tile_counter, caps,
                                                          info);
 }
 
 // ---------------------------------------------------------------------------
-// a8 (scatter): intersecting subqueries into their leaf's list, each with the
-// offset of its bitmap row (row = rank in the leaf's list).
+// a7/a8 compaction: padded slot 32t + r (r < the tile's count) -> record
+// k = tile_off[t] + r.  An intersecting record also takes its place in its
+// leaf's list (its rank there came from the count pass's per-leaf atomic
+// count) and its bitmap row: the grouping by leaf needs no second pass.
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(256)
-scatter_kernel(const uint32_t *__restrict__ sub_leaf, const uint32_t *__restrict__ leaf_beg,
-               const uint32_t *__restrict__ leaf_sub_off, const uint32_t *__restrict__ leaf_word_off,
-               uint32_t *__restrict__ leaf_cursor, uint32_t *__restrict__ sub_bm,
-               uint32_t *__restrict__ isub, Caps caps, const Info *info) {
-    if (info->n_sub > caps.sub || info->n_sub_i > caps.sub_i || info->n_words > caps.words ||
-        info->n_items > caps.items)
-        return;
-    const uint32_t nsub = (uint32_t)info->n_sub;
-    for (uint32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < nsub; k += gridDim.x * blockDim.x) {
-        const uint32_t sl = sub_leaf[k];
-        if (sl & 0x80000000u) continue;
-        const uint32_t pos = atomicAdd(leaf_cursor + sl, 1u);
-        const uint32_t n = __ldg(leaf_beg + sl + 1) - __ldg(leaf_beg + sl);
-        isub[pos] = k;
-        sub_bm[k] = __ldg(leaf_word_off + sl) + (pos - __ldg(leaf_sub_off + sl)) * ((n + 31u) >> 5);
+cand_compact_kernel(const uint4 *__restrict__ pad, const uint32_t *__restrict__ tile_cnt,
+                    const uint32_t *__restrict__ tile_off, const uint32_t *__restrict__ leaf_beg,
+                    const uint32_t *__restrict__ leaf_sub_off, const uint32_t *__restrict__ leaf_word_off,
+                    uint32_t *__restrict__ sub_q, uint32_t *__restrict__ sub_leaf, uint32_t *__restrict__ sub_len,
+                    uint32_t *__restrict__ sub_res, uint32_t *__restrict__ sub_bm, uint32_t *__restrict__ isub,
+                    Caps caps, const Info *info) {
+    constexpr int U = 4;   // independent slots per thread per step: their load chains overlap
+    const unsigned long long ntiles = (info->n_cand + 31) >> 5;
+    if (ntiles > caps.cand_tiles || info->n_sub > caps.sub || info->n_sub_i > caps.sub_i) return;
+    const unsigned long long nslots = ntiles << 5;
+    const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
+    for (unsigned long long s0 = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; s0 < nslots;
+         s0 += U * stride) {
+        bool ok[U];
+        uint4 v[U];
+        uint32_t k[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const unsigned long long s = s0 + u * stride;
+            ok[u] = s < nslots && ((uint32_t)s & 31u) < __ldg(tile_cnt + (s >> 5));
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const unsigned long long s = s0 + u * stride;
+            if (ok[u]) {
+                v[u] = __ldg(pad + s);
+                k[u] = __ldg(tile_off + (s >> 5)) + ((uint32_t)s & 31u);
+            }
+        }
+        uint32_t n[U], so[U], wo[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            if (ok[u] && !(v[u].y & 0x80000000u)) {
+                n[u] = __ldg(leaf_beg + v[u].y + 1) - __ldg(leaf_beg + v[u].y);
+                so[u] = __ldg(leaf_sub_off + v[u].y);
+                wo[u] = __ldg(leaf_word_off + v[u].y);
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            if (!ok[u]) continue;
+            sub_q[k[u]] = v[u].x;
+            sub_leaf[k[u]] = v[u].y;
+            if (v[u].y & 0x80000000u) {
+                sub_len[k[u]] = v[u].z;
+                sub_res[k[u]] = v[u].w;
+            } else {
+                sub_len[k[u]] = 1;
+                sub_res[k[u]] = 0;
+                isub[so[u] + v[u].z] = k[u];
+                sub_bm[k[u]] = wo[u] + v[u].z * ((n[u] + 31u) >> 5);
+            }
+        }
     }
 }
 
-void launch_scatter(cudaStream_t st, int num_sms, const uint32_t *sub_leaf, const uint32_t *leaf_beg,
-                    const uint32_t *leaf_sub_off, const uint32_t *leaf_word_off, uint32_t *leaf_cursor,
-                    uint32_t *sub_bm, uint32_t *isub, Caps caps, const Info *info) {
-    scatter_kernel<<<num_sms * 8, 256, 0, st>>>(sub_leaf, leaf_beg, leaf_sub_off, leaf_word_off, leaf_cursor,
-                                                sub_bm, isub, caps, info);
+void launch_compact(cudaStream_t st, int num_sms, const uint4 *pad, const uint32_t *tile_cnt,
+                    const uint32_t *tile_off, const uint32_t *leaf_beg, const uint32_t *leaf_sub_off,
+                    const uint32_t *leaf_word_off, uint32_t *sub_q, uint32_t *sub_leaf, uint32_t *sub_len,
+                    uint32_t *sub_res, uint32_t *sub_bm, uint32_t *isub, Caps caps, const Info *info) {
+    cand_compact_kernel<<<num_sms * 8, 256, 0, st>>>(pad, tile_cnt, tile_off, leaf_beg, leaf_sub_off,
+                                                      leaf_word_off, sub_q, sub_leaf, sub_len, sub_res, sub_bm,
+                                                      isub, caps, info);
 }
 
 }  // namespace mqr

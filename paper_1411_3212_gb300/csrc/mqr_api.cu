@@ -86,7 +86,7 @@ struct mqr_ctx {
     DevBuf<float2> sxy;
     // leaves
     DevBuf<uint32_t> leaf_lo, leaf_hi, leaf_beg, leaf_nsub, leaf_sub_off, leaf_word_off,
-        leaf_item_off, leaf_cursor;
+        leaf_item_off;
     DevBuf<uint8_t> mk_a, mk_b;
     DevBuf<uint2> leaf_box;
     // per query / subquery
@@ -240,6 +240,8 @@ mqr_status enqueue_tick(mqr_ctx *c, const float4 *rects, uint32_t Q, int emit_ki
     cudaStream_t st = c->stream;
     Info *info = at<Info>(c, a.info);
     uint32_t *hist = at<uint32_t>(c, a.hist);
+    // tile/ticket counters: 0-3 sort passes, 4 leaves, 5 query blocks, 6 leaf scan, 7 result scan,
+    // 8 candidate scan, 9 emit batches; 12-13 the output sort's error word
     uint32_t *ctr = at<uint32_t>(c, a.counters);
     unsigned long long *err = &info->err;
     const float x0 = c->bounds.xmin, y0 = c->bounds.ymin;
@@ -297,17 +299,16 @@ mqr_status enqueue_tick(mqr_ctx *c, const float4 *rects, uint32_t Q, int emit_ki
     phase_begin(c, MQR_PHASE_CANDIDATES);
     launch_candidates(st, c->num_sms, cov, c->tile_p0.p, c->pair_q.p, c->pair_first.p, c->pair_blo.p,
                       c->pair_off.p, c->qcells.p, c->leaf_box.p, c->leaf_beg.p, c->tile_cnt.p,
-                      c->tile_off.p, c->leaf_nsub.p, c->cand_pad.p, c->sub_q.p, c->sub_leaf.p, c->sub_len.p,
-                      c->sub_res.p,
-                      c->pair_rec.p, at<uint32_t>(c, a.st_cand), ctr + 8, caps, info);
-    phase_end(c, MQR_PHASE_CANDIDATES, 3);
-    // a8: group intersecting subqueries by leaf
+                      c->tile_off.p, c->leaf_nsub.p, c->cand_pad.p, c->pair_rec.p,
+                      at<uint32_t>(c, a.st_cand), ctr + 8, caps, info);
+    phase_end(c, MQR_PHASE_CANDIDATES, 2);
+    // a8: group intersecting subqueries by leaf; compact the records
     phase_begin(c, MQR_PHASE_GROUP);
     launch_leaf_scan(st, nmax, c->leaf_beg.p, c->leaf_nsub.p, c->leaf_sub_off.p, c->leaf_word_off.p,
-                     c->leaf_item_off.p, c->leaf_cursor.p, c->item_leaf.p, at<uint32_t>(c, a.st_lscan),
-                     ctr + 6, caps, info);
-    launch_scatter(st, c->num_sms, c->sub_leaf.p, c->leaf_beg.p, c->leaf_sub_off.p, c->leaf_word_off.p,
-                   c->leaf_cursor.p, c->sub_bm.p, c->isub.p, caps, info);
+                     c->leaf_item_off.p, c->item_leaf.p, at<uint32_t>(c, a.st_lscan), ctr + 6, caps, info);
+    launch_compact(st, c->num_sms, c->cand_pad.p, c->tile_cnt.p, c->tile_off.p, c->leaf_beg.p,
+                   c->leaf_sub_off.p, c->leaf_word_off.p, c->sub_q.p, c->sub_leaf.p, c->sub_len.p, c->sub_res.p,
+                   c->sub_bm.p, c->isub.p, caps, info);
     phase_end(c, MQR_PHASE_GROUP, nmax ? 2 : 1);
     // a10
     phase_begin(c, MQR_PHASE_FILTER);
@@ -325,7 +326,7 @@ mqr_status enqueue_tick(mqr_ctx *c, const float4 *rects, uint32_t Q, int emit_ki
         phase_begin(c, MQR_PHASE_EMIT);
         launch_emit(st, c->num_sms, emit_kind, c->sub_q.p, c->sub_leaf.p, c->sub_len.p, c->sub_bm.p,
                     c->out_off.p, c->leaf_beg.p, c->sid.p, c->bitmap.p, out,
-                    bitmap_words_per_row(nmax), caps, info);
+                    bitmap_words_per_row(nmax), ctr + 9, caps, info);
         phase_end(c, MQR_PHASE_EMIT, 1);
     }
     if (offsets != nullptr) {
@@ -542,8 +543,8 @@ mqr_status tick_device_impl(mqr_ctx *c, const float *rects_dev, uint32_t Q, int 
     Info *info = at<Info>(c, a.info);
     phase_begin(c, MQR_PHASE_OUTPUT_SORT);
     launch_emit(c->stream, c->num_sms, kEmitKeys64, c->sub_q.p, c->sub_leaf.p, c->sub_len.p,
-                c->sub_bm.p, c->out_off.p, c->leaf_beg.p, c->sid.p, c->bitmap.p, c->sortA.p, wpr, caps,
-                info);
+                c->sub_bm.p, c->out_off.p, c->leaf_beg.p, c->sid.p, c->bitmap.p, c->sortA.p, wpr,
+                at<uint32_t>(c, a.counters) + 9, caps, info);
     s = check_launch("emit keys");
     if (s != MQR_OK) return s;
     unsigned long long *sorted = nullptr;
@@ -603,7 +604,7 @@ void mqr_destroy(mqr_ctx *c) {
                                           &c->sortA, &c->sortB};
     for (auto *b : u64s) b->release();
     DevBuf<uint32_t> *u32s[] = {&c->skey, &c->sid, &c->sort_counts, &c->sort_offs, &c->leaf_lo, &c->leaf_hi, &c->leaf_beg, &c->leaf_nsub,
-                                &c->leaf_sub_off, &c->leaf_word_off, &c->leaf_item_off, &c->leaf_cursor,
+                                &c->leaf_sub_off, &c->leaf_word_off, &c->leaf_item_off,
                                 &c->sub_q, &c->sub_leaf, &c->sub_len, &c->sub_res,
                                 &c->sub_bm, &c->isub, &c->bitmap, &c->item_leaf, &c->up_ids, &c->zmap, &c->pair_q,
                                 &c->pair_first, &c->pair_blo, &c->pair_rec, &c->qpair, &c->tile_p0,
@@ -679,7 +680,7 @@ mqr_status mqr_create_ex(mqr_rect bounds, const mqr_config *cfg, void *cuda_stre
         (e = c->sxy.ensure(n)) || (e = c->leaf_lo.ensure(n)) || (e = c->leaf_hi.ensure(n)) ||
         (e = c->leaf_beg.ensure(n + 1)) || (e = c->leaf_nsub.ensure(n)) ||
         (e = c->leaf_sub_off.ensure(n + 1)) || (e = c->leaf_word_off.ensure(n + 1)) ||
-        (e = c->leaf_item_off.ensure(n + 1)) || (e = c->leaf_cursor.ensure(n)) ||
+        (e = c->leaf_item_off.ensure(n + 1)) ||
         (e = c->sort_counts.ensure((size_t)256 * ((n + kSortTile - 1) / kSortTile))) ||
         (e = c->sort_offs.ensure((size_t)256 * ((n + kSortTile - 1) / kSortTile))) ||
         (e = c->upd_err.ensure(1)) || (e = c->leaf_box.ensure(n)))

@@ -342,22 +342,22 @@ void launch_query_blocks(cudaStream_t st, const float4 *rects, uint32_t Q, float
 void launch_candidates(cudaStream_t st, int num_sms, int covering, const uint32_t *tile_p0,
                        const uint32_t *pair_q, const uint32_t *pair_first, const uint32_t *pair_blo,
                        const unsigned long long *pair_off, const uint2 *qcells, const uint2 *leaf_box,
-                       const uint32_t *leaf_beg, uint32_t *tile_cnt,
-                       uint32_t *tile_off, uint32_t *leaf_nsub, uint4 *pad, uint32_t *sub_q, uint32_t *sub_leaf,
-                       uint32_t *sub_len, uint32_t *sub_res, uint32_t *pair_rec, uint32_t *status,
-                       uint32_t *tile_counter, Caps caps, Info *info);
+                       const uint32_t *leaf_beg, uint32_t *tile_cnt, uint32_t *tile_off, uint32_t *leaf_nsub,
+                       uint4 *pad, uint32_t *pair_rec, uint32_t *status, uint32_t *tile_counter, Caps caps,
+                       Info *info);
 
-// a8: scans over leaves -> leaf_sub_off, leaf_word_off, leaf_item_off, cursor.
+// a8: scans over leaves -> leaf_sub_off, leaf_word_off, leaf_item_off, item_leaf.
 constexpr int kLeafScanThreads = 256, kLeafScanItems = 8, kLeafScanTile = kLeafScanThreads * kLeafScanItems;
 void launch_leaf_scan(cudaStream_t st, uint32_t nmax, const uint32_t *leaf_beg,
                       const uint32_t *leaf_nsub, uint32_t *leaf_sub_off, uint32_t *leaf_word_off,
-                      uint32_t *leaf_item_off, uint32_t *leaf_cursor, uint32_t *item_leaf,
+                      uint32_t *leaf_item_off, uint32_t *item_leaf,
                       uint32_t *status3, uint32_t *tile_counter, Caps caps, Info *info);
 
-// a8 scatter: intersecting subqueries into their leaf's list + bitmap rows.
-void launch_scatter(cudaStream_t st, int num_sms, const uint32_t *sub_leaf, const uint32_t *leaf_beg,
-                    const uint32_t *leaf_sub_off, const uint32_t *leaf_word_off, uint32_t *leaf_cursor,
-                    uint32_t *sub_bm, uint32_t *isub, Caps caps, const Info *info);
+// a7/a8 compaction of the padded records; intersecting ones into their leaf's list.
+void launch_compact(cudaStream_t st, int num_sms, const uint4 *pad, const uint32_t *tile_cnt,
+                    const uint32_t *tile_off, const uint32_t *leaf_beg, const uint32_t *leaf_sub_off,
+                    const uint32_t *leaf_word_off, uint32_t *sub_q, uint32_t *sub_leaf, uint32_t *sub_len,
+                    uint32_t *sub_res, uint32_t *sub_bm, uint32_t *isub, Caps caps, const Info *info);
 
 // a10: filtering into bitmap words + per-subquery counts.
 void launch_filter(cudaStream_t st, int num_sms, const float4 *rects, const float2 *sxy,
@@ -378,7 +378,7 @@ void launch_emit(cudaStream_t st, int num_sms, int emit_kind, const uint32_t *su
                  const uint32_t *sub_leaf, const uint32_t *sub_len, const uint32_t *sub_bm,
                  const unsigned long long *out_off, const uint32_t *leaf_beg,
                  const uint32_t *sid, const uint32_t *bitmap, void *out, uint32_t bitmap_words_per_row,
-                 Caps caps, const Info *info);
+                 uint32_t *ticket, Caps caps, const Info *info);
 
 // Per-query offsets: off[q] = out_off[pair_rec[qpair[q]]].
 void launch_query_offsets(cudaStream_t st, uint32_t Q, const uint32_t *qpair, const uint32_t *pair_rec,
