@@ -52,15 +52,19 @@ filter_kernel(const float4 *__restrict__ rects, const float2 *__restrict__ sxy,
               const uint32_t *__restrict__ leaf_word_off, const uint32_t *__restrict__ leaf_item_off,
               const uint32_t *__restrict__ item_leaf, const uint32_t *__restrict__ isub,
               const uint32_t *__restrict__ sub_q,
-              uint32_t *__restrict__ sub_res, uint32_t *__restrict__ bitmap, Caps caps,
+              uint32_t *__restrict__ sub_res, uint32_t *__restrict__ bitmap, uint32_t *ticket, Caps caps,
               const Info *info) {
     if (!tick_buffers_ok(info, caps)) return;
     const uint32_t items = (uint32_t)info->n_items;
     const int lane = threadIdx.x & 31;
-    const uint32_t nwarps = gridDim.x * (kFilterThreads / 32);
     const float qnan = __int_as_float(0x7fc00000);
-
-    for (uint32_t item = (blockIdx.x * kFilterThreads + threadIdx.x) >> 5; item < items; item += nwarps) {
+    // items are handed out by a ticket counter (their sizes vary: 1-32
+    // subqueries x 1-8 words); the next ticket is drawn during the current item
+    uint32_t item = 0, next = 0;
+    if (lane == 0) item = atomicAdd(ticket, 1u);
+    item = __shfl_sync(0xffffffffu, item, 0);
+    for (; item < items; item = __shfl_sync(0xffffffffu, next, 0)) {
+        if (lane == 0) next = atomicAdd(ticket, 1u);
         const uint32_t leaf = __ldg(item_leaf + item);
         const uint32_t r = item - __ldg(leaf_item_off + leaf);
         const uint32_t soff = __ldg(leaf_sub_off + leaf);
@@ -129,10 +133,10 @@ void launch_filter(cudaStream_t st, int num_sms, const float4 *rects, const floa
                    const uint32_t *leaf_beg, const uint32_t *leaf_sub_off,
                    const uint32_t *leaf_word_off, const uint32_t *leaf_item_off,
                    const uint32_t *item_leaf, const uint32_t *isub, const uint32_t *sub_q,
-                   uint32_t *sub_res, uint32_t *bitmap, Caps caps, const Info *info) {
+                   uint32_t *sub_res, uint32_t *bitmap, uint32_t *ticket, Caps caps, const Info *info) {
     filter_kernel<<<num_sms * 8, kFilterThreads, 0, st>>>(rects, sxy, leaf_beg, leaf_sub_off,
                                                           leaf_word_off, leaf_item_off, item_leaf, isub,
-                                                          sub_q, sub_res, bitmap, caps, info);
+                                                          sub_q, sub_res, bitmap, ticket, caps, info);
 }
 
 // ---------------------------------------------------------------------------

@@ -241,7 +241,7 @@ mqr_status enqueue_tick(mqr_ctx *c, const float4 *rects, uint32_t Q, int emit_ki
     Info *info = at<Info>(c, a.info);
     uint32_t *hist = at<uint32_t>(c, a.hist);
     // tile/ticket counters: 0-3 sort passes, 4 leaves, 5 query blocks, 6 leaf scan, 7 result scan,
-    // 8 candidate scan, 9 emit batches; 12-13 the output sort's error word
+    // 8 candidate scan, 9 emit batches, 10 filter items; 12-13 the output sort's error word
     uint32_t *ctr = at<uint32_t>(c, a.counters);
     unsigned long long *err = &info->err;
     const float x0 = c->bounds.xmin, y0 = c->bounds.ymin;
@@ -314,7 +314,7 @@ mqr_status enqueue_tick(mqr_ctx *c, const float4 *rects, uint32_t Q, int emit_ki
     phase_begin(c, MQR_PHASE_FILTER);
     launch_filter(st, c->num_sms, rects, c->sxy.p, c->leaf_beg.p, c->leaf_sub_off.p,
                   c->leaf_word_off.p, c->leaf_item_off.p, c->item_leaf.p, c->isub.p, c->sub_q.p, c->sub_res.p,
-                  c->bitmap.p, caps, info);
+                  c->bitmap.p, ctr + 10, caps, info);
     phase_end(c, MQR_PHASE_FILTER, 1);
     // a11
     phase_begin(c, MQR_PHASE_RESULT_SCAN);

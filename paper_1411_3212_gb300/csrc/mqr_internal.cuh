@@ -364,7 +364,7 @@ void launch_filter(cudaStream_t st, int num_sms, const float4 *rects, const floa
                    const uint32_t *leaf_beg, const uint32_t *leaf_sub_off,
                    const uint32_t *leaf_word_off, const uint32_t *leaf_item_off,
                    const uint32_t *item_leaf, const uint32_t *isub, const uint32_t *sub_q,
-                   uint32_t *sub_res, uint32_t *bitmap, Caps caps, const Info *info);
+                   uint32_t *sub_res, uint32_t *bitmap, uint32_t *ticket, Caps caps, const Info *info);
 
 // a11: result offsets out_off[k] (u64, exclusive) over subquery records.
 constexpr int kResThreads = 256, kResItems = 8, kResTile = kResThreads * kResItems;
