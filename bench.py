@@ -86,7 +86,7 @@ def gen_ticks(name, seed, count):
 
 
 # ----------------------------------------------------------------------------
-# algorithmic bytes per phase (the data the method must move; see DESIGN.md)
+# algorithmic bytes per phase (the data the method must move)
 # ----------------------------------------------------------------------------
 def phase_bytes(s, n_updates, nmax):
     N, Q = s["n_objects"], s["n_queries"]
@@ -373,9 +373,10 @@ def run_gpu(args, name):
     per_launch_bytes = bytes_acc[dom] / launches
     peak, peak_kind = read_peaks()
     achieved = per_launch_bytes / (per_launch_ms / 1000.0) / 1e9
-    kernel_names = {"emit": "emit_kernel", "filter": "filter_kernel", "sort": "onesweep_kernel",
-                    "query_blocks": "query_blocks_kernel", "candidates": "candidates_kernel",
-                    "group": "leaf_scan_kernel+scatter_kernel",
+    kernel_names = {"emit": "emit_kernel", "filter": "filter_kernel",
+                    "sort": "tile_hist_kernel+digit_scan_kernel+onesweep_kernel",
+                    "query_blocks": "zmap_kernel+query_blocks_kernel", "candidates": "cand_count_kernel+tile_scan_kernel",
+                    "group": "leaf_scan_kernel+cand_compact_kernel",
                     "leaves": "leaves_kernel", "keys": "morton_kernel", "updates": "stamp_kernel+write_winner_kernel",
                     "result_scan": "result_scan_kernel"}
     roofline = {"bound": "hbm", "kernel": kernel_names.get(dom, dom), "phase": dom,
@@ -470,7 +471,7 @@ def main():
     ap.add_argument("--flush-mb", type=int, default=256)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--cpu-sample", type=int, default=100000)
+    ap.add_argument("--cpu-sample", type=int, default=400000)
     ap.add_argument("--ref-sample", type=int, default=10000)
     args = ap.parse_args()
     if args.warmup < 3:
