@@ -317,7 +317,7 @@ def run_gpu(args, name):
 
     idx = mqr.Index(bounds=(0.0, 0.0, 1.0, 1.0), leaf_cap=w["cap"], max_objects=nmax)
     kind = mqr.KINDS[args.kind]
-    elem = 8 if kind in (mqr.MQR_OUT_PAIRS, mqr.MQR_OUT_PAIRS_SORTED) else 4
+    elem = 8 if kind in (mqr.MQR_OUT_PAIRS, mqr.MQR_OUT_PAIRS_SORTED, mqr.MQR_OUT_RUNS) else 4
     out = torch.empty(1, dtype=torch.int32, device=dev)
     offs = torch.empty(Q + 1, dtype=torch.int64, device=dev) if args.offsets else None
 
@@ -395,9 +395,12 @@ def run_gpu(args, name):
     gpu_launches = int(sum(timing["launches"].values()))
 
     # end to end through the host-buffer entry points
-    e2e = None
+    e2e = e2e_runs = None
     if not args.no_e2e:
         e2e = run_e2e(args, idx, ticks, kind, elem, Q, stats["n_results"], dev)
+        if kind == mqr.MQR_OUT_PAIRS:
+            # the same ticks with covering runs reported compressed (RUNS kind)
+            e2e_runs = run_e2e(args, idx, ticks, mqr.MQR_OUT_RUNS, 8, Q, stats["n_results"], dev)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -422,6 +425,7 @@ def run_gpu(args, name):
         "roofline": roofline,
         "cpu_baseline": cpu,
         "e2e": e2e,
+        "e2e_covering_compressed": e2e_runs,
         "gpu_launches": gpu_launches,
         "clocks": clk,
         "phases": phases,
@@ -432,9 +436,13 @@ def run_gpu(args, name):
 
 
 def run_e2e(args, idx, ticks, kind, elem, Q, r_hint, dev):
+    """End to end through the host-buffer entry points.  For the covering-
+    compressed kind the step also copies the tick's sorted ids (what a
+    consumer needs to expand the runs) with mqr_get_sorted."""
     import torch
     from paper_1411_3212_gb300 import mqr
     n = ticks[0].ids.shape[0]
+    sid_h = torch.empty(n, dtype=torch.int32).pin_memory().numpy().view(np.uint32)
     ids_h = torch.from_numpy(ticks[0].ids.view(np.int32)).pin_memory().numpy().view(np.uint32)
     xy_h = [torch.from_numpy(t.xy).pin_memory().numpy() for t in ticks]
     rect_h = [torch.from_numpy(t.rects).pin_memory().numpy() for t in ticks]
@@ -445,17 +453,23 @@ def run_e2e(args, idx, ticks, kind, elem, Q, r_hint, dev):
     mqr.mqr_apply_updates_host(idx.ctx, ids_h, xy_h[0])
     mqr.mqr_tick_host(idx.ctx, rect_h[0], Q, kind, out_h, out_h.nbytes)
     times, d2h = [], []
+    runs = kind == mqr.MQR_OUT_RUNS
+    lib = mqr.load()
+    nsorted = mqr.ctypes.c_uint64(0)
     for k in range(steps):
         t0 = time.perf_counter()
         mqr.mqr_apply_updates_host(idx.ctx, ids_h, xy_h[k])
         st, cnt = mqr.mqr_tick_host(idx.ctx, rect_h[k], Q, kind, out_h, out_h.nbytes)
+        if runs and st == mqr.MQR_OK:
+            mqr._check(lib.mqr_get_sorted(idx.ctx, None, sid_h.ctypes.data, n, mqr.ctypes.byref(nsorted)))
         times.append(time.perf_counter() - t0)
         mqr._check(st)
-        d2h.append(cnt * elem)
+        d2h.append(cnt * elem + (nsorted.value * 4 if runs else 0))
     return {"value": Q * steps / sum(times), "unit": "queries/s",
             "h2d_bytes_per_step": int(n * 12 + Q * 16), "d2h_bytes_per_step": int(sum(d2h) / steps),
             "ms_per_step": 1000.0 * sum(times) / steps, "steps": steps,
-            "api": "mqr_apply_updates_host + mqr_tick_host (pinned host buffers)"}
+            "api": "mqr_apply_updates_host + mqr_tick_host%s (pinned host buffers)"
+                   % (" + mqr_get_sorted" if runs else "")}
 
 
 def main():
@@ -466,7 +480,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="mine", choices=["mine", "reference"])
     ap.add_argument("--workload", default="hotspot4m", choices=sorted(WORKLOADS))
-    ap.add_argument("--kind", default="pairs", choices=["pairs", "csr", "count"])
+    ap.add_argument("--kind", default="pairs", choices=["pairs", "csr", "count", "runs"])
     ap.add_argument("--offsets", action="store_true", help="also write per-query offsets")
     ap.add_argument("--flush-mb", type=int, default=256)
     ap.add_argument("--no-e2e", action="store_true")

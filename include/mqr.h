@@ -75,6 +75,17 @@ typedef struct {
  *                in the result of query qidx.  Padding bits are 0.
  *  COUNT         no id output (out_dev may be NULL); only *out_count and, if
  *                given, offsets_dev.
+ *  RUNS          covering-compressed pairs (the paper reports a covering
+ *                subquery as (query, cell) and leaves its expansion to the
+ *                consumer, Sec. 1 and Sec. 5.6): out_dev holds 8-byte
+ *                elements grouped by query in ascending qidx, each either a
+ *                result pair (qidx, id) with qidx < 2^31, or a covering run
+ *                taking two elements (qidx | 2^31, first) (count, 0): every
+ *                object sorted_ids[first .. first + count) of the tick's
+ *                Morton-sorted order (mqr_get_sorted) is in the result of
+ *                qidx.  *out_count = number of elements (R_I + 2 * runs);
+ *                offsets_dev counts elements too.  Every result appears
+ *                exactly once, as a pair or inside one run.
  * offsets_dev, when non-NULL, receives the per-query offsets for every kind.
  * out_dev must be 16-byte aligned (cudaMalloc and torch allocations are).
  * The sorted kinds are limited to R < 2^30. */
@@ -84,7 +95,8 @@ typedef enum {
     MQR_OUT_CSR = 2,
     MQR_OUT_CSR_SORTED = 3,
     MQR_OUT_BITMAP = 4,
-    MQR_OUT_COUNT = 5
+    MQR_OUT_COUNT = 5,
+    MQR_OUT_RUNS = 6
 } mqr_out_kind;
 
 typedef enum {
@@ -183,8 +195,8 @@ mqr_status mqr_apply_updates_host(mqr_ctx *ctx, const uint32_t *ids_host, const 
  * rects_dev: float32[4Q] device, (xa, ya, xb, yb) per query; the query index
  * qidx is its position in rects_dev.  kind: an mqr_out_kind.  out_dev /
  * out_capacity_bytes: caller's device output buffer (see mqr_out_kind).
- * out_count (host, required): receives the number of results R (pairs or ids)
- * or, for BITMAP, the number of words Q*W.  offsets_dev: NULL or uint64[Q+1]
+ * out_count (host, required): receives the number of results R (pairs or ids),
+ * for BITMAP the number of words Q*W, for RUNS the number of 8-byte elements.  offsets_dev: NULL or uint64[Q+1]
  * device.  Blocks until the tick's work on the stream is complete.
  * Errors: INVALID_ARG, CAPACITY (buffer too small; *out_count holds the
  * size needed, nothing usable was written; call again with a larger buffer),

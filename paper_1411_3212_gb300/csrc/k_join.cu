@@ -140,19 +140,22 @@ void launch_filter(cudaStream_t st, int num_sms, const float4 *rects, const floa
 }
 
 // ---------------------------------------------------------------------------
-// a11: exclusive scan of the per-subquery result counts (query-major order)
-// into 64-bit output offsets; R = out_off[n_sub].
+// a11: exclusive scan of the per-record output sizes (query-major order) into
+// 64-bit output offsets.  A record's size is its result count, except that a
+// covering run takes run_elems elements when the output reports covering
+// runs compressed (run_elems = 2), else 0 = expanded.  n_out = out_off[n_sub];
+// R (n_results) is the sum of the result counts either way.
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(kResThreads)
 result_scan_kernel(const uint32_t *__restrict__ sub_res, const uint32_t *__restrict__ sub_leaf,
                    unsigned long long *__restrict__ out_off, unsigned long long *status,
-                   uint32_t *tile_counter, Caps caps, Info *info) {
+                   uint32_t *tile_counter, uint32_t run_elems, Caps caps, Info *info) {
     __shared__ unsigned long long s_scan[kResThreads / 32 + 1];
-    __shared__ unsigned long long s_cov;
+    __shared__ unsigned long long s_cov, s_res;
     __shared__ uint32_t s_tile;
     __shared__ unsigned long long s_prefix;
     const int tid = threadIdx.x;
-    if (tid == 0) { s_tile = atomicAdd(tile_counter, 1u); s_cov = 0; }
+    if (tid == 0) { s_tile = atomicAdd(tile_counter, 1u); s_cov = 0; s_res = 0; }
     __syncthreads();
     if (!tick_buffers_ok(info, caps)) return;
     const uint32_t tile = s_tile;
@@ -164,13 +167,16 @@ result_scan_kernel(const uint32_t *__restrict__ sub_res, const uint32_t *__restr
     }
     const uint32_t kb = base + tid * kResItems;
     uint32_t v[kResItems];
-    unsigned long long t = 0, cov = 0;
+    unsigned long long t = 0, cov = 0, res = 0;
 #pragma unroll
     for (int e = 0; e < kResItems; ++e) {
-        uint32_t k = kb + e;
-        v[e] = k < nsub ? sub_res[k] : 0u;
+        const uint32_t k = kb + e;
+        const uint32_t r = k < nsub ? sub_res[k] : 0u;
+        const bool c = k < nsub && (sub_leaf[k] & 0x80000000u);
+        v[e] = (c && run_elems) ? run_elems : r;
         t += v[e];
-        if (k < nsub && (sub_leaf[k] & 0x80000000u)) cov += v[e];
+        res += r;
+        if (c) cov += r;
     }
     unsigned long long total;
     unsigned long long off = block_excl_scan<kResThreads>(t, &total, s_scan);
@@ -179,7 +185,11 @@ result_scan_kernel(const uint32_t *__restrict__ sub_res, const uint32_t *__restr
         if (tid == 0) s_prefix = pre;
     }
     cov = warp_sum(cov);
-    if ((tid & 31) == 0 && cov) atomicAdd(&s_cov, cov);
+    res = warp_sum(res);
+    if ((tid & 31) == 0) {
+        if (cov) atomicAdd(&s_cov, cov);
+        if (res) atomicAdd(&s_res, res);
+    }
     __syncthreads();
     off += s_prefix;
 #pragma unroll
@@ -190,20 +200,22 @@ result_scan_kernel(const uint32_t *__restrict__ sub_res, const uint32_t *__restr
     }
     if (tid == 0) {
         if (s_cov) atomicAdd(&info->n_results_cov, s_cov);
+        if (s_res) atomicAdd(&info->n_results, s_res);
         if (base + kResTile >= nsub) {
             out_off[nsub] = s_prefix + total;
-            info->n_results = s_prefix + total;
+            info->n_out = s_prefix + total;
         }
     }
 }
 
 void launch_result_scan(cudaStream_t st, unsigned long long sub_cap, const uint32_t *sub_res,
                         const uint32_t *sub_leaf, unsigned long long *out_off,
-                        unsigned long long *status, uint32_t *tile_counter, Caps caps, Info *info) {
+                        unsigned long long *status, uint32_t *tile_counter, uint32_t run_elems, Caps caps,
+                        Info *info) {
     unsigned long long tiles = (sub_cap + kResTile - 1) / kResTile;
     if (tiles == 0) tiles = 1;
     result_scan_kernel<<<(unsigned)tiles, kResThreads, 0, st>>>(sub_res, sub_leaf, out_off, status,
-                                                               tile_counter, caps, info);
+                                                               tile_counter, run_elems, caps, info);
 }
 
 // ---------------------------------------------------------------------------
@@ -218,7 +230,7 @@ void launch_result_scan(cudaStream_t st, unsigned long long sub_cap, const uint3
 template <int KIND>
 __device__ __forceinline__ void emit_one(void *out, unsigned long long pos, uint32_t q, uint32_t id,
                                          uint32_t wpr) {
-    if (KIND == kEmitPairs) {
+    if (KIND == kEmitPairs || KIND == kEmitRuns) {
         reinterpret_cast<uint2 *>(out)[pos] = make_uint2(q, id);
     } else if (KIND == kEmitIds) {
         reinterpret_cast<uint32_t *>(out)[pos] = id;
@@ -234,7 +246,7 @@ __device__ __forceinline__ void emit_one(void *out, unsigned long long pos, uint
 template <int KIND>
 __device__ __forceinline__ void emit_rel(void *out, unsigned long long base, uint32_t rel, uint32_t q, uint32_t id,
                                          uint32_t wpr) {
-    if (KIND == kEmitPairs) {
+    if (KIND == kEmitPairs || KIND == kEmitRuns) {
         (reinterpret_cast<uint2 *>(out) + base)[rel] = make_uint2(q, id);
     } else if (KIND == kEmitIds) {
         (reinterpret_cast<uint32_t *>(out) + base)[rel] = id;
@@ -256,7 +268,13 @@ template <int KIND>
 __device__ __forceinline__ void emit_run(void *out, unsigned long long off, uint32_t q,
                                          const uint32_t *__restrict__ sid, uint32_t b, uint32_t n,
                                          uint32_t wpr, int lane) {
-    if (KIND == kEmitPairs) {
+    if (KIND == kEmitRuns) {
+        // compressed: the run itself, (q | 2^31, first sorted object), (objects, 0)
+        if (lane == 0) {
+            reinterpret_cast<uint2 *>(out)[off] = make_uint2(q | 0x80000000u, b);
+            reinterpret_cast<uint2 *>(out)[off + 1] = make_uint2(n, 0u);
+        }
+    } else if (KIND == kEmitPairs) {
         // 16-byte stores of two pairs once the output slot is even
         if (n == 0) return;
         if (off & 1ull) {
@@ -342,7 +360,7 @@ emit_kernel(const uint32_t *__restrict__ sub_q, const uint32_t *__restrict__ sub
     __shared__ uint4 s_rec[kEmitWarps][32];
     __shared__ unsigned long long s_off[kEmitWarps][32];
     if (!tick_buffers_ok(info, caps)) return;
-    if (KIND != kEmitBitmap && info->n_results > caps.out) return;
+    if (KIND != kEmitBitmap && info->n_out > caps.out) return;
     const uint32_t nsub = (uint32_t)info->n_sub;
     const int lane = threadIdx.x & 31;
     const int wib = threadIdx.x >> 5;
@@ -410,6 +428,10 @@ void launch_emit(cudaStream_t st, int num_sms, int emit_kind, const uint32_t *su
         case kEmitBitmap:
             emit_kernel<kEmitBitmap><<<grid, kEmitThreads, 0, st>>>(sub_q, sub_leaf, sub_len, sub_bm, out_off,
                                                                     leaf_beg, sid, bitmap, out, wpr, ticket, caps, info);
+            break;
+        case kEmitRuns:
+            emit_kernel<kEmitRuns><<<grid, kEmitThreads, 0, st>>>(sub_q, sub_leaf, sub_len, sub_bm, out_off,
+                                                                  leaf_beg, sid, bitmap, out, wpr, ticket, caps, info);
             break;
         default:
             emit_kernel<kEmitKeys64><<<grid, kEmitThreads, 0, st>>>(sub_q, sub_leaf, sub_len, sub_bm, out_off,

@@ -225,7 +225,8 @@ uint32_t bitmap_words_per_row(uint32_t nmax) { return (nmax + 31u) / 32u; }
 size_t out_elem_bytes(int kind) {
     switch (kind) {
         case MQR_OUT_PAIRS:
-        case MQR_OUT_PAIRS_SORTED: return 8;
+        case MQR_OUT_PAIRS_SORTED:
+        case MQR_OUT_RUNS: return 8;
         case MQR_OUT_CSR:
         case MQR_OUT_CSR_SORTED: return 4;
         default: return 4;
@@ -319,7 +320,8 @@ mqr_status enqueue_tick(mqr_ctx *c, const float4 *rects, uint32_t Q, int emit_ki
     // a11
     phase_begin(c, MQR_PHASE_RESULT_SCAN);
     launch_result_scan(st, caps.sub, c->sub_res.p, c->sub_leaf.p, c->out_off.p,
-                       at<unsigned long long>(c, a.st_res), ctr + 7, caps, info);
+                       at<unsigned long long>(c, a.st_res), ctr + 7, emit_kind == kEmitRuns ? 2u : 0u, caps,
+                       info);
     phase_end(c, MQR_PHASE_RESULT_SCAN, 1);
     // a12 + a13
     if (out != nullptr && emit_kind >= 0) {
@@ -512,16 +514,16 @@ mqr_status tick_device_impl(mqr_ctx *c, const float *rects_dev, uint32_t Q, int 
         *out_count = c->last.n_results;
         return s;
     }
-    if (kind == MQR_OUT_PAIRS || kind == MQR_OUT_CSR) {
+    if (kind == MQR_OUT_PAIRS || kind == MQR_OUT_CSR || kind == MQR_OUT_RUNS) {
         if (out_dev && (reinterpret_cast<uintptr_t>(out_dev) & 15u))
             return fail(MQR_ERR_INVALID_ARG, "out_dev must be 16-byte aligned");
         const size_t eb = out_elem_bytes(kind);
         unsigned long long cap_elems = cap_bytes / eb;
-        mqr_status s = run_tick(c, rects, Q, kind == MQR_OUT_PAIRS ? kEmitPairs : kEmitIds,
-                                out_dev, out_dev ? cap_elems : 0, offs);
-        *out_count = c->last.n_results;
+        const int ek = kind == MQR_OUT_PAIRS ? kEmitPairs : (kind == MQR_OUT_CSR ? kEmitIds : kEmitRuns);
+        mqr_status s = run_tick(c, rects, Q, ek, out_dev, out_dev ? cap_elems : 0, offs);
+        *out_count = c->last.n_out;
         if (s != MQR_OK) return s;
-        if (c->last.n_results > cap_elems || (c->last.n_results && out_dev == nullptr))
+        if (c->last.n_out > cap_elems || (c->last.n_out && out_dev == nullptr))
             return fail(MQR_ERR_CAPACITY, "output buffer too small for the tick's results");
         return MQR_OK;
     }
@@ -747,7 +749,7 @@ static mqr_status tick_args(mqr_ctx *c, const void *rects, uint32_t Q, int kind,
     if (!out_count) return fail(MQR_ERR_INVALID_ARG, "out_count is NULL");
     if (Q > 0 && !rects) return fail(MQR_ERR_INVALID_ARG, "rects is NULL");
     if (Q >= (1u << 30)) return fail(MQR_ERR_INVALID_ARG, "Q must be < 2^30");
-    if (kind < MQR_OUT_PAIRS || kind > MQR_OUT_COUNT) return fail(MQR_ERR_INVALID_ARG, "unknown output kind");
+    if (kind < MQR_OUT_PAIRS || kind > MQR_OUT_RUNS) return fail(MQR_ERR_INVALID_ARG, "unknown output kind");
     return MQR_OK;
 }
 

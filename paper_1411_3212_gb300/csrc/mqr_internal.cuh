@@ -51,6 +51,7 @@ struct Info {
     unsigned long long n_item_objs;  // objects loaded by the filter (sum over items)
     unsigned long long n_pairs;      // (query, block) pairs of query splitting
     unsigned long long n_cand;       // candidate (query, leaf) pairs
+    unsigned long long n_out;        // output elements (R, or R_I + 2 per covering run for the run kind)
 };
 
 // Capacities of the growable per-tick buffers (host-chosen, passed by value).
@@ -370,10 +371,10 @@ void launch_filter(cudaStream_t st, int num_sms, const float4 *rects, const floa
 constexpr int kResThreads = 256, kResItems = 8, kResTile = kResThreads * kResItems;
 void launch_result_scan(cudaStream_t st, unsigned long long sub_cap, const uint32_t *sub_res,
                         const uint32_t *sub_leaf, unsigned long long *out_off,
-                        unsigned long long *status, uint32_t *tile_counter, Caps caps, Info *info);
+                        unsigned long long *status, uint32_t *tile_counter, uint32_t run_elems, Caps caps, Info *info);
 
 // a12 + a13: emit results in query-major order.
-enum EmitKind { kEmitPairs = 0, kEmitIds = 1, kEmitBitmap = 2, kEmitKeys64 = 3 };
+enum EmitKind { kEmitPairs = 0, kEmitIds = 1, kEmitBitmap = 2, kEmitKeys64 = 3, kEmitRuns = 4 };
 void launch_emit(cudaStream_t st, int num_sms, int emit_kind, const uint32_t *sub_q,
                  const uint32_t *sub_leaf, const uint32_t *sub_len, const uint32_t *sub_bm,
                  const unsigned long long *out_off, const uint32_t *leaf_beg,

@@ -17,11 +17,12 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libmqr.so")
 
 MQR_OK, MQR_ERR_INVALID_ARG, MQR_ERR_OOM, MQR_ERR_CAPACITY, MQR_ERR_CUDA, MQR_ERR_TIMEOUT, MQR_ERR_INTERNAL = range(7)
-MQR_OUT_PAIRS, MQR_OUT_PAIRS_SORTED, MQR_OUT_CSR, MQR_OUT_CSR_SORTED, MQR_OUT_BITMAP, MQR_OUT_COUNT = range(6)
+MQR_OUT_PAIRS, MQR_OUT_PAIRS_SORTED, MQR_OUT_CSR, MQR_OUT_CSR_SORTED, MQR_OUT_BITMAP, MQR_OUT_COUNT, MQR_OUT_RUNS = range(7)
 MQR_INDEX_QUADTREE, MQR_INDEX_UNIFORM_GRID = 0, 1
 
 KINDS = {"pairs": MQR_OUT_PAIRS, "pairs_sorted": MQR_OUT_PAIRS_SORTED, "csr": MQR_OUT_CSR,
-         "csr_sorted": MQR_OUT_CSR_SORTED, "bitmap": MQR_OUT_BITMAP, "count": MQR_OUT_COUNT}
+         "csr_sorted": MQR_OUT_CSR_SORTED, "bitmap": MQR_OUT_BITMAP, "count": MQR_OUT_COUNT,
+         "runs": MQR_OUT_RUNS}
 
 # Every symbol include/mqr.h declares.
 EXPORTS = ["mqr_config_default", "mqr_create", "mqr_create_ex", "mqr_apply_updates",
@@ -275,8 +276,9 @@ class Index:
     def tick(self, rects, kind="pairs"):
         """Answer the queries; returns (result, offsets) as CUDA tensors.
         pairs/pairs_sorted -> int32[R, 2] (qidx, id); csr/csr_sorted -> int32[R];
-        bitmap -> int32[Q, ceil(max_objects/32)]; count -> None.  Values are
-        uint32 reinterpreted as int32."""
+        bitmap -> int32[Q, ceil(max_objects/32)]; count -> None; runs ->
+        int32[E, 2] covering-compressed elements (MQR_OUT_RUNS).  Values
+        are uint32 reinterpreted as int32."""
         torch = self._torch
         k = KINDS[kind]
         Q = int(rects.shape[0])
@@ -289,7 +291,7 @@ class Index:
         if k == MQR_OUT_COUNT:
             mqr_tick(self.ctx, rects, Q, k, None, 0, offs)
             return None, offs
-        elem = 8 if k in (MQR_OUT_PAIRS, MQR_OUT_PAIRS_SORTED) else 4
+        elem = 8 if k in (MQR_OUT_PAIRS, MQR_OUT_PAIRS_SORTED, MQR_OUT_RUNS) else 4
         if self._out is None:
             self._out = torch.empty(max(1 << 16, 8 * Q) * 2, dtype=torch.int32, device=rects.device)
         st, cnt = mqr_tick(self.ctx, rects, Q, k, self._out, self._out.numel() * 4, offs)

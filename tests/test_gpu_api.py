@@ -7,7 +7,7 @@ import pytest
 
 import oracle
 from paper_1411_3212_gb300 import workloads
-from tests.gpu_util import assert_same_csr, oracle_state, to_dev, torch_dev
+from tests.gpu_util import assert_same_csr, expand_runs, oracle_state, to_dev, torch_dev
 
 pytestmark = pytest.mark.gpu
 
@@ -76,6 +76,36 @@ def test_host_entry_points(case):
         st, cnt = mqr.mqr_tick_host(ctx, np.ascontiguousarray(t.rects), Q, mqr.MQR_OUT_BITMAP, bm, bm.nbytes)
         assert st == mqr.MQR_OK
         np.testing.assert_array_equal(bm, oracle.bitmap(*want, 30000))
+    finally:
+        mqr.mqr_destroy(ctx)
+
+
+def test_runs_kind_through_host_entry_point(case):
+    """Covering-compressed output through mqr_tick_host: every result exactly
+    once, as a pair or inside a covering run of the tick's sorted ids."""
+    torch, dev = torch_dev()
+    t, want = case
+    from paper_1411_3212_gb300 import mqr
+    ctx = mqr.mqr_create((0.0, 0.0, 1.0, 1.0), 32, 30000)
+    try:
+        mqr.mqr_apply_updates_host(ctx, np.ascontiguousarray(t.ids), np.ascontiguousarray(t.xy))
+        Q = t.rects.shape[0]
+        offs = np.zeros(Q + 1, np.uint64)
+        out = np.zeros((want[1].shape[0] + 16, 2), np.uint32)
+        st, cnt = mqr.mqr_tick_host(ctx, np.ascontiguousarray(t.rects), Q, mqr.MQR_OUT_RUNS, out, out.nbytes,
+                                    offs)
+        assert st == mqr.MQR_OK and offs[-1] == cnt
+        s = mqr.mqr_get_stats(ctx)
+        assert s["n_covering_runs"] > 0
+        assert cnt == s["n_results"] - s["n_results_covering"] + 2 * s["n_covering_runs"]
+        _, sid = mqr.mqr_get_sorted(ctx)
+        pairs, counts = expand_runs(out[:cnt], sid)
+        per_q = np.array([counts[int(offs[q]):int(offs[q + 1])].sum() for q in range(Q)], np.int64)
+        off = np.concatenate([[0], np.cumsum(per_q)]).astype(np.uint64)
+        ids = pairs[:, 1].copy()
+        for q in range(Q):
+            ids[int(off[q]):int(off[q + 1])] = np.sort(ids[int(off[q]):int(off[q + 1])])
+        assert_same_csr((off, ids), want)
     finally:
         mqr.mqr_destroy(ctx)
 

@@ -1,7 +1,8 @@
 """Full-size parity: the 4M-object hotspot workload with 400,000 queries per
 tick, in the launch configuration bench.py times (leaf_cap 128, quadtree,
 pair-list output).  Every query's result count is compared with the oracle's,
-and the complete id lists of a random sample of queries are compared exactly.
+and the complete id lists of a random sample of queries are compared exactly;
+the covering-compressed output of the same ticks must give the same counts.
 """
 import numpy as np
 import pytest
@@ -46,4 +47,17 @@ def test_hotspot_4m_full_size_counts_and_sampled_lists():
         s = idx.stats()
         assert s["n_results"] == R and s["n_objects"] == w.n
         assert s["n_results_covering"] <= R
+        # covering-compressed output of the same tick: per-query counts
+        elems, eoffs = idx.tick(rects_d, kind="runs")
+        e = elems.cpu().numpy().view(np.uint32)
+        eoff = eoffs.cpu().numpy().view(np.uint64).astype(np.int64)
+        assert eoff[-1] == e.shape[0] == R - s["n_results_covering"] + 2 * s["n_covering_runs"]
+        run = (e[:, 0] & 0x80000000) != 0
+        heads = np.nonzero(run)[0]
+        counts = np.ones(e.shape[0], np.int64)
+        counts[heads] = e[heads + 1, 0]
+        counts[heads + 1] = 0
+        csum = np.concatenate([[0], np.cumsum(counts)])
+        np.testing.assert_array_equal(csum[eoff[1:]] - csum[eoff[:-1]], want_cnt)
+        del elems, e, counts, csum
     idx.close()
