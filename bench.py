@@ -472,6 +472,72 @@ def run_e2e(args, idx, ticks, kind, elem, Q, r_hint, dev):
                    % (" + mqr_get_sorted" if runs else "")}
 
 
+def run_served(args):
+    """--served: the served stream (10M objects, 95% in 16 hotspots of sigma
+    0.005; Poisson query arrivals at --rate per second, batched into ticks of
+    --dt-ms; covering-compressed output with admission by --budget-mb of
+    output memory per tick, copied to pinned host memory on a second stream).
+    Prints one JSON line with Def. 3 tick latency and Def. 2 query latency
+    percentiles and beta (answered queries per second of processing)."""
+    import torch
+    from paper_1411_3212_gb300 import mqr, workloads
+    from paper_1411_3212_gb300.serve import GpuBackend, TickServer
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    dt = args.dt_ms / 1000.0
+    n_pos = 10                                          # distinct position sets, cycled over the ticks
+    t_gen = time.perf_counter()
+    world = workloads.ServedWorld(n=args.served_objects, rate=args.rate, dt=dt, seed=0)
+    ticks = [world.next_tick() for _ in range(n_pos)]
+    rng = np.random.default_rng(12345)                  # arrivals of the ticks after the first n_pos
+    arr, rects = [], []
+    for k in range(args.served_ticks):
+        if k < n_pos:
+            a, r = ticks[k].arrivals, ticks[k].rects
+        else:
+            xy = ticks[k % n_pos].xy
+            q = int(rng.poisson(args.rate * dt))
+            a = np.sort(rng.random(q)) * dt
+            iss = rng.integers(0, world.n, size=q)
+            r = workloads.squares_around(xy[iss], np.exp(rng.uniform(np.log(world.side_lo),
+                                                                      np.log(world.side_hi), q)))
+        arr.append(k * dt + a)
+        rects.append(r)
+    arrivals = np.concatenate(arr)
+    rects = np.concatenate(rects)
+    log("served: %d queries over %d ticks generated in %.1f s" % (rects.shape[0], args.served_ticks,
+                                                                  time.perf_counter() - t_gen))
+    ids_d = torch.from_numpy(ticks[0].ids.view(np.int32)).to(dev)
+    updates = [(ids_d, torch.from_numpy(t.xy).to(dev)) for t in ticks]
+    rects_d = torch.from_numpy(rects).to(dev)
+    idx = mqr.Index(bounds=(0.0, 0.0, 1.0, 1.0), leaf_cap=128, max_objects=world.n)
+    be = GpuBackend(idx, updates, rects_d, kind="runs", budget_bytes=args.budget_mb << 20,
+                    copy_out=not args.no_copy_out)
+    max_batch = int(args.max_batch_factor * args.rate * dt) if args.max_batch_factor > 0 else None
+    warm = TickServer(be, dt, max_batch=max_batch).run(arrivals[arrivals < 3 * dt], n_ticks=3)   # warm-up
+    clocks = Clocks(0)
+    clocks.start()
+    rep = TickServer(be, dt, max_batch=max_batch).run(arrivals, n_ticks=args.served_ticks,
+                                                      drain_ticks=args.served_ticks)
+    clk = clocks.stop()
+    idx.close()
+    per = rep.pop("per_tick")
+    line = {"metric": "served queries/s (beta, Lemma 2)", "value": rep["beta_queries_per_s"],
+            "unit": "queries/s", "n_gpus": 1, "higher_is_better": True, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "served-10M: %d objects (95%% in 16 Gaussian hotspots, sigma 0.005; 5%% "
+                                   "uniform), Poisson arrivals %.3g queries/s, square sides log-uniform "
+                                   "0.0005-0.004, ticks of %.1f ms, leaf_cap 128, covering-compressed output, "
+                                   "admission by %d MB of output per tick, %s"
+                                   % (world.n, args.rate, args.dt_ms, args.budget_mb,
+                                      "output kept on the device" if args.no_copy_out
+                                      else "output copied to pinned host memory"),
+                       "ticks": args.served_ticks, "max_batch": max_batch},
+            "served": rep, "warmup_ticks": warm["ticks"],
+            "max_out_elems_per_tick": max((t.get("out_elems", 0) for t in per), default=0),
+            "clocks": clk}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -487,11 +553,22 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample", type=int, default=400000)
     ap.add_argument("--ref-sample", type=int, default=10000)
+    ap.add_argument("--served", action="store_true", help="run the served stream instead")
+    ap.add_argument("--rate", type=float, default=5.0e6, help="served: query arrivals per second")
+    ap.add_argument("--dt-ms", type=float, default=10.0, help="served: tick duration")
+    ap.add_argument("--served-ticks", type=int, default=100)
+    ap.add_argument("--served-objects", type=int, default=10_000_000)
+    ap.add_argument("--budget-mb", type=int, default=1024, help="served: output memory per tick")
+    ap.add_argument("--max-batch-factor", type=float, default=1.5,
+                    help="served: queries offered per tick, x the mean arrivals per tick (0: whole queue)")
+    ap.add_argument("--no-copy-out", action="store_true", help="served: keep each tick's output on the device")
     args = ap.parse_args()
     if args.warmup < 3:
         log("warm-up raised to 3 steps")
         args.warmup = 3
-    if args.impl == "reference":
+    if args.served:
+        run_served(args)
+    elif args.impl == "reference":
         run_reference(args, args.workload)
     else:
         run_gpu(args, args.workload)

@@ -211,6 +211,23 @@ mqr_status mqr_tick_host(mqr_ctx *ctx, const float *rects_host, uint32_t Q, int 
                          void *out_host, uint64_t out_capacity_bytes, uint64_t *out_count,
                          uint64_t *offsets_host);
 
+/* A tick with admission by output memory, for served streams (the tick and
+ * latency model of Sec. 2.4, Def. 2-3 and Lemma 2: a tick must finish within
+ * the latency budget, so its output is bounded).  As mqr_tick, but instead of
+ * failing with CAPACITY it answers the longest prefix rects[0 .. *admitted)
+ * of the queries whose output fits out_capacity_bytes (the exact counts of
+ * the two-pass scheme, Sec. 5.3, decide it before anything is written); the
+ * queries from *admitted on are not answered, and the caller submits them
+ * again in a later tick.  kind: PAIRS, CSR or RUNS.  *out_count: elements
+ * written (results for PAIRS/CSR, 8-byte elements for RUNS).  offsets_dev:
+ * NULL or uint64[Q+1] device; entries 0 .. *admitted are the answered
+ * queries' offsets (later entries describe the unanswered queries and are to
+ * be ignored).  Blocks until the output is written.  Errors as mqr_tick,
+ * except that CAPACITY is not returned for the output buffer. */
+mqr_status mqr_tick_admit(mqr_ctx *ctx, const float *rects_dev, uint32_t Q, int kind, void *out_dev,
+                          uint64_t out_capacity_bytes, uint32_t *admitted, uint64_t *out_count,
+                          uint64_t *offsets_dev);
+
 /* Counters of the last completed tick. */
 mqr_status mqr_get_stats(const mqr_ctx *ctx, mqr_stats *out);
 

@@ -360,8 +360,9 @@ emit_kernel(const uint32_t *__restrict__ sub_q, const uint32_t *__restrict__ sub
     __shared__ uint4 s_rec[kEmitWarps][32];
     __shared__ unsigned long long s_off[kEmitWarps][32];
     if (!tick_buffers_ok(info, caps)) return;
-    if (KIND != kEmitBitmap && info->n_out > caps.out) return;
-    const uint32_t nsub = (uint32_t)info->n_sub;
+    uint32_t nsub = (uint32_t)info->n_sub;
+    if (info->emit_end) nsub = min(nsub, (uint32_t)info->emit_end);     // admitted prefix only
+    if (KIND != kEmitBitmap && out_off[nsub] > caps.out) return;
     const int lane = threadIdx.x & 31;
     const int wib = threadIdx.x >> 5;
     const uint32_t lt = lanemask_lt();
@@ -472,6 +473,40 @@ void launch_query_offsets(cudaStream_t st, uint32_t Q, const uint32_t *qpair, co
     uint32_t g = (Q + 1 + 255) / 256;
     if (g > 4096) g = 4096;
     query_offsets_kernel<<<g, 256, 0, st>>>(Q, qpair, pair_rec, tile_off, out_off, offsets, caps, info);
+}
+
+// Admission by output memory (served streams): with offsets the per-query
+// output offsets of the whole batch and cap < offsets[Q], the answered prefix
+// is [0, A) for the one A with offsets[A] <= cap < offsets[A + 1]; the emit
+// then stops before A's first record.
+__global__ void admit_kernel(uint32_t Q, const unsigned long long *__restrict__ offsets, unsigned long long cap,
+                             const uint32_t *__restrict__ qpair, const uint32_t *__restrict__ pair_rec,
+                             const uint32_t *__restrict__ tile_off, Caps caps, Info *info) {
+    if (!tick_buffers_ok(info, caps)) return;
+    const uint32_t nsub = (uint32_t)info->n_sub;
+    const uint32_t npairs = (uint32_t)info->n_pairs;
+    for (uint32_t q = blockIdx.x * blockDim.x + threadIdx.x; q < Q; q += gridDim.x * blockDim.x) {
+        if (offsets[q] <= cap && offsets[q + 1] > cap) {
+            const uint32_t p = qpair[q];
+            uint32_t rec = nsub;
+            if (p < npairs) {
+                const uint32_t slot = pair_rec[p];
+                rec = tile_off[slot >> 5] + (slot & 31u);
+            }
+            info->admitted = q;
+            info->admitted_out = offsets[q];
+            info->emit_end = rec;
+        }
+    }
+}
+
+void launch_admit(cudaStream_t st, uint32_t Q, const unsigned long long *offsets, unsigned long long cap,
+                  const uint32_t *qpair, const uint32_t *pair_rec, const uint32_t *tile_off, Caps caps,
+                  Info *info) {
+    uint32_t g = (Q + 255) / 256;
+    if (g > 4096) g = 4096;
+    if (g == 0) g = 1;
+    admit_kernel<<<g, 256, 0, st>>>(Q, offsets, cap, qpair, pair_rec, tile_off, caps, info);
 }
 
 // Sorted (qidx << 32 | id) keys to the requested layout.

@@ -807,6 +807,61 @@ mqr_status mqr_tick_host(mqr_ctx *c, const float *rects_host, uint32_t Q, int ki
     return MQR_OK;
 }
 
+mqr_status mqr_tick_admit(mqr_ctx *c, const float *rects_dev, uint32_t Q, int kind, void *out_dev,
+                          uint64_t out_capacity_bytes, uint32_t *admitted, uint64_t *out_count,
+                          uint64_t *offsets_dev) {
+    mqr_status s = tick_args(c, rects_dev, Q, kind, out_count);
+    if (s != MQR_OK) return s;
+    if (!admitted) return fail(MQR_ERR_INVALID_ARG, "admitted is NULL");
+    if (kind != MQR_OUT_PAIRS && kind != MQR_OUT_CSR && kind != MQR_OUT_RUNS)
+        return fail(MQR_ERR_INVALID_ARG, "admission supports the PAIRS, CSR and RUNS kinds");
+    if (out_dev && (reinterpret_cast<uintptr_t>(out_dev) & 15u))
+        return fail(MQR_ERR_INVALID_ARG, "out_dev must be 16-byte aligned");
+    *out_count = 0;
+    *admitted = 0;
+    MQR_CUDA(cudaSetDevice(c->device));
+    const float4 *rects = reinterpret_cast<const float4 *>(rects_dev);
+    unsigned long long *offs = reinterpret_cast<unsigned long long *>(offsets_dev);
+    if (!offs) {
+        MQR_CUDA(c->off_stage.ensure((size_t)Q + 1));
+        offs = c->off_stage.p;
+    }
+    const int ek = kind == MQR_OUT_PAIRS ? kEmitPairs : (kind == MQR_OUT_CSR ? kEmitIds : kEmitRuns);
+    // exact counts and per-query offsets first (no output written) ...
+    s = run_tick(c, rects, Q, ek, nullptr, 0, offs);
+    if (s != MQR_OK) return s;
+    const unsigned long long cap_elems = out_dev ? out_capacity_bytes / out_elem_bytes(kind) : 0;
+    Arena a = arena_layout(c->nmax, Q, c->sub_q.n, c->cand_tiles);
+    Caps caps{c->sub_q.n, c->isub.n, std::min<size_t>(c->bitmap.n, 0xffffffffull), cap_elems, c->cand_tiles,
+              c->item_leaf.n};
+    Info *info = at<Info>(c, a.info);
+    uint32_t A = Q;
+    unsigned long long n = c->last.n_out;
+    // ... then the longest prefix of queries whose output fits
+    if (n > cap_elems) {
+        launch_admit(c->stream, Q, offs, cap_elems, c->qpair.p, c->pair_rec.p, c->tile_off.p, caps, info);
+        MQR_CUDA(cudaGetLastError());
+        MQR_CUDA(cudaMemcpyAsync(c->info_host, info, sizeof(Info), cudaMemcpyDeviceToHost, c->stream));
+        MQR_CUDA(cudaStreamSynchronize(c->stream));
+        A = (uint32_t)c->info_host->admitted;
+        n = c->info_host->admitted_out;
+    }
+    if (n > 0) {
+        phase_begin(c, MQR_PHASE_EMIT);
+        launch_emit(c->stream, c->num_sms, ek, c->sub_q.p, c->sub_leaf.p, c->sub_len.p, c->sub_bm.p,
+                    c->out_off.p, c->leaf_beg.p, c->sid.p, c->bitmap.p, out_dev,
+                    bitmap_words_per_row(c->nmax), at<uint32_t>(c, a.counters) + 9, caps, info);
+        phase_end(c, MQR_PHASE_EMIT, 1);
+        s = check_launch("emit");
+        if (s != MQR_OK) return s;
+        MQR_CUDA(cudaStreamSynchronize(c->stream));
+        phases_collect(c, false);
+    }
+    *admitted = A;
+    *out_count = n;
+    return MQR_OK;
+}
+
 mqr_status mqr_get_stats(const mqr_ctx *c, mqr_stats *o) {
     if (!c || !o) return fail(MQR_ERR_INVALID_ARG, "NULL argument");
     const Info &in = c->last;

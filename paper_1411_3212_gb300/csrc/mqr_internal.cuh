@@ -52,6 +52,9 @@ struct Info {
     unsigned long long n_pairs;      // (query, block) pairs of query splitting
     unsigned long long n_cand;       // candidate (query, leaf) pairs
     unsigned long long n_out;        // output elements (R, or R_I + 2 per covering run for the run kind)
+    unsigned long long emit_end;     // admission: emit records [0, emit_end) only (0 = all)
+    unsigned long long admitted;     // admission: queries [0, admitted) answered
+    unsigned long long admitted_out; // admission: their output elements
 };
 
 // Capacities of the growable per-tick buffers (host-chosen, passed by value).
@@ -380,6 +383,11 @@ void launch_emit(cudaStream_t st, int num_sms, int emit_kind, const uint32_t *su
                  const unsigned long long *out_off, const uint32_t *leaf_beg,
                  const uint32_t *sid, const uint32_t *bitmap, void *out, uint32_t bitmap_words_per_row,
                  uint32_t *ticket, Caps caps, const Info *info);
+
+// Admission by output memory: queries [0, A) whose output fits cap elements.
+void launch_admit(cudaStream_t st, uint32_t Q, const unsigned long long *offsets, unsigned long long cap,
+                  const uint32_t *qpair, const uint32_t *pair_rec, const uint32_t *tile_off, Caps caps,
+                  Info *info);
 
 // Per-query offsets: off[q] = out_off[pair_rec[qpair[q]]].
 void launch_query_offsets(cudaStream_t st, uint32_t Q, const uint32_t *qpair, const uint32_t *pair_rec,

@@ -26,7 +26,8 @@ KINDS = {"pairs": MQR_OUT_PAIRS, "pairs_sorted": MQR_OUT_PAIRS_SORTED, "csr": MQ
 
 # Every symbol include/mqr.h declares.
 EXPORTS = ["mqr_config_default", "mqr_create", "mqr_create_ex", "mqr_apply_updates",
-           "mqr_apply_updates_host", "mqr_tick", "mqr_tick_host", "mqr_get_stats", "mqr_get_leaves",
+           "mqr_apply_updates_host", "mqr_tick", "mqr_tick_host", "mqr_tick_admit", "mqr_get_stats",
+           "mqr_get_leaves",
            "mqr_get_sorted", "mqr_set_timing", "mqr_get_timing", "mqr_sort_objects_noalloc",
            "mqr_last_error", "mqr_destroy"]
 
@@ -94,6 +95,7 @@ def load(path: str = LIB_PATH):
         "mqr_apply_updates_host": ([P, P, P, u32], i32),
         "mqr_tick": ([P, P, u32, i32, P, u64, ctypes.POINTER(u64), P], i32),
         "mqr_tick_host": ([P, P, u32, i32, P, u64, ctypes.POINTER(u64), P], i32),
+        "mqr_tick_admit": ([P, P, u32, i32, P, u64, ctypes.POINTER(u32), ctypes.POINTER(u64), P], i32),
         "mqr_get_stats": ([P, ctypes.POINTER(mqr_stats)], i32),
         "mqr_get_leaves": ([P, P, u64, ctypes.POINTER(u64)], i32),
         "mqr_get_sorted": ([P, P, P, u64, ctypes.POINTER(u64)], i32),
@@ -185,6 +187,15 @@ def mqr_tick_host(ctx, rects_host, Q, kind, out_host, out_capacity_bytes, offset
     if check and st not in (MQR_OK, MQR_ERR_CAPACITY):
         _check(st)
     return st, int(cnt.value)
+
+
+def mqr_tick_admit(ctx, rects_dev, Q, kind, out_dev, out_capacity_bytes, offsets_dev=None):
+    """Returns (admitted, out_count)."""
+    adm = ctypes.c_uint32(0)
+    cnt = ctypes.c_uint64(0)
+    _check(load().mqr_tick_admit(ctx, _ptr(rects_dev), Q, kind, _ptr(out_dev), out_capacity_bytes,
+                                 ctypes.byref(adm), ctypes.byref(cnt), _ptr(offsets_dev)))
+    return int(adm.value), int(cnt.value)
 
 
 def mqr_get_stats(ctx):

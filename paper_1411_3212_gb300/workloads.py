@@ -54,6 +54,7 @@ class Tick:
     xy: np.ndarray           # f32[n, 2]
     rects: np.ndarray        # f32[Q, 4]  (xa, ya, xb, yb)
     issuers: np.ndarray      # u32[Q]     object that issued each query
+    arrivals: np.ndarray = None   # f64[Q]  served streams: arrival time inside the tick, s (ascending)
 
 
 # ----------------------------------------------------------------------------
@@ -160,6 +161,43 @@ class HotspotWalk:
         sides = np.exp(self._r_q.uniform(np.log(self.side_lo), np.log(self.side_hi), self.q))
         rects = squares_around(xy[iss], sides)
         return Tick(np.arange(self.n, dtype=np.uint32), xy, rects, iss)
+
+
+# ----------------------------------------------------------------------------
+# Served stream: a denser hotspot world (95% of the objects in 16 hotspots of
+# sigma 0.005) whose queries arrive as a Poisson process of the given rate;
+# the queries arriving during a tick of duration dt form that tick's batch
+# (Sec. 2.2), each with its arrival time inside the tick (for the latency of
+# Def. 2-3).  Issuers are drawn with replacement (several queries of one
+# object may share a tick).
+# ----------------------------------------------------------------------------
+@dataclass
+class ServedWorld(HotspotWalk):
+    n: int = 10_000_000
+    hotspots: int = 16
+    frac_hot: float = 0.95
+    sigma_lo: float = 0.005
+    sigma_hi: float = 0.005
+    side_lo: float = 0.0005
+    side_hi: float = 0.004
+    rate: float = 5.0e6          # query arrivals per second
+    dt: float = 0.010            # tick duration, s
+
+    def next_tick(self) -> Tick:
+        if self._t > 0:
+            delta = self._advance_hotspots()
+            hot = self.member >= 0
+            move = self._r_move.normal(0.0, self.step, (self.n, 2))
+            move[hot] += delta[self.member[hot]]
+            self._xy = np.clip(self._xy + move, 0.0, float(TOP))
+        self._t += 1
+        xy = self._xy.astype(np.float32)
+        q = int(self._r_q.poisson(self.rate * self.dt))
+        arrivals = np.sort(self._r_q.random(q)) * self.dt
+        iss = self._r_q.integers(0, self.n, size=q).astype(np.uint32)
+        sides = np.exp(self._r_q.uniform(np.log(self.side_lo), np.log(self.side_hi), q))
+        rects = squares_around(xy[iss], sides)
+        return Tick(np.arange(self.n, dtype=np.uint32), xy, rects, iss, arrivals)
 
 
 def hotspot_small(seed: int = 0, n: int = 200_000, q: int = 20_000) -> HotspotWalk:
