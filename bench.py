@@ -317,7 +317,7 @@ def run_gpu(args, name):
 
     idx = mqr.Index(bounds=(0.0, 0.0, 1.0, 1.0), leaf_cap=w["cap"], max_objects=nmax)
     kind = mqr.KINDS[args.kind]
-    elem = 8 if kind in (mqr.MQR_OUT_PAIRS, mqr.MQR_OUT_PAIRS_SORTED, mqr.MQR_OUT_RUNS) else 4
+    elem = 8 if kind in (mqr.MQR_OUT_PAIRS, mqr.MQR_OUT_PAIRS_SORTED, mqr.MQR_OUT_RUNS, mqr.MQR_OUT_PAIRS_ATOMIC) else 4
     out = torch.empty(1, dtype=torch.int32, device=dev)
     offs = torch.empty(Q + 1, dtype=torch.int64, device=dev) if args.offsets else None
 
@@ -546,7 +546,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="mine", choices=["mine", "reference"])
     ap.add_argument("--workload", default="hotspot4m", choices=sorted(WORKLOADS))
-    ap.add_argument("--kind", default="pairs", choices=["pairs", "csr", "count", "runs"])
+    ap.add_argument("--kind", default="pairs", choices=["pairs", "csr", "count", "runs", "pairs_atomic"])
     ap.add_argument("--offsets", action="store_true", help="also write per-query offsets")
     ap.add_argument("--flush-mb", type=int, default=256)
     ap.add_argument("--no-e2e", action="store_true")

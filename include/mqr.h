@@ -86,7 +86,13 @@ typedef struct {
  *                qidx.  *out_count = number of elements (R_I + 2 * runs);
  *                offsets_dev counts elements too.  Every result appears
  *                exactly once, as a pair or inside one run.
- * offsets_dev, when non-NULL, receives the per-query offsets for every kind.
+ *  PAIRS_ATOMIC  as PAIRS but in no particular order, produced by the
+ *                paper's baseline filtering (Alg. 3: results appended through
+ *                shared-memory buffers and an atomic global counter, with no
+ *                bitmaps and no decoding phase; the ablation of the paper's
+ *                study S1).  offsets_dev must be NULL.
+ * offsets_dev, when non-NULL, receives the per-query offsets for every kind
+ * except PAIRS_ATOMIC.
  * out_dev must be 16-byte aligned (cudaMalloc and torch allocations are).
  * The sorted kinds are limited to R < 2^30. */
 typedef enum {
@@ -96,7 +102,8 @@ typedef enum {
     MQR_OUT_CSR_SORTED = 3,
     MQR_OUT_BITMAP = 4,
     MQR_OUT_COUNT = 5,
-    MQR_OUT_RUNS = 6
+    MQR_OUT_RUNS = 6,
+    MQR_OUT_PAIRS_ATOMIC = 7
 } mqr_out_kind;
 
 typedef enum {

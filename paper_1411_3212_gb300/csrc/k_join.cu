@@ -509,6 +509,158 @@ void launch_admit(cudaStream_t st, uint32_t Q, const unsigned long long *offsets
     admit_kernel<<<g, 256, 0, st>>>(Q, offsets, cap, qpair, pair_rec, tile_off, caps, info);
 }
 
+// ---------------------------------------------------------------------------
+// Ablation: the paper's baseline filtering (Alg. 3, the method that appends
+// results with atomic operations instead of building bitmaps; compared in the
+// paper's study S1).  No bitmap, no result scan and no decoding: a warp tests
+// a work item like filter_kernel, and the positives of every ballot word are
+// appended as (query, id) pairs to the warp's buffer in shared memory (one
+// warp-aggregated slot count per word); a full buffer is flushed to global
+// memory at a slot range reserved with one atomic add on the global result
+// counter.  Covering runs reserve their range the same way.  Pairs come out
+// in no particular order; slots past `cap` are counted but not written.
+// ---------------------------------------------------------------------------
+constexpr int kAtomBuf = 512;     // pairs per warp buffer
+
+__device__ __forceinline__ void atomic_flush(uint2 *buf, uint32_t n, uint2 *out, unsigned long long cap,
+                                             unsigned long long *counter, int lane) {
+    __syncwarp();
+    unsigned long long base = 0;
+    if (lane == 0) base = atomicAdd(counter, (unsigned long long)n);
+    base = __shfl_sync(0xffffffffu, base, 0);
+    for (uint32_t i = lane; i < n; i += 32)
+        if (base + i < cap) out[base + i] = buf[i];
+    __syncwarp();
+}
+
+__global__ void __launch_bounds__(kFilterThreads)
+filter_atomic_kernel(const float4 *__restrict__ rects, const float2 *__restrict__ sxy,
+                     const uint32_t *__restrict__ sid, const uint32_t *__restrict__ leaf_beg,
+                     const uint32_t *__restrict__ leaf_sub_off, const uint32_t *__restrict__ leaf_item_off,
+                     const uint32_t *__restrict__ item_leaf, const uint32_t *__restrict__ isub,
+                     const uint32_t *__restrict__ sub_q, uint2 *__restrict__ out, unsigned long long cap,
+                     uint32_t *ticket, Caps caps, Info *info) {
+    __shared__ uint2 s_buf[kFilterThreads / 32][kAtomBuf];
+    if (!tick_buffers_ok(info, caps)) return;
+    const uint32_t items = (uint32_t)info->n_items;
+    const int lane = threadIdx.x & 31;
+    uint2 *buf = s_buf[threadIdx.x >> 5];
+    const uint32_t lt = lanemask_lt();
+    const float qnan = __int_as_float(0x7fc00000);
+    uint32_t nbuf = 0;
+    uint32_t item = 0, next = 0;
+    if (lane == 0) item = atomicAdd(ticket, 1u);
+    item = __shfl_sync(0xffffffffu, item, 0);
+    for (; item < items; item = __shfl_sync(0xffffffffu, next, 0)) {
+        if (lane == 0) next = atomicAdd(ticket, 1u);
+        const uint32_t leaf = __ldg(item_leaf + item);
+        const uint32_t r = item - __ldg(leaf_item_off + leaf);
+        const uint32_t soff = __ldg(leaf_sub_off + leaf);
+        const uint32_t nsub = __ldg(leaf_sub_off + leaf + 1) - soff;
+        const uint32_t beg = __ldg(leaf_beg + leaf);
+        const uint32_t nobj = __ldg(leaf_beg + leaf + 1) - beg;
+        const uint32_t ngroups = (nsub + 31u) >> 5;
+        const uint32_t c = r / ngroups, g = r - c * ngroups;
+        const uint32_t obase = beg + c * 256u;
+        const uint32_t ocnt = min(256u, nobj - c * 256u);
+        const uint32_t nwc = (ocnt + 31u) >> 5;
+        float x[8], y[8];
+        uint32_t id[8];
+#pragma unroll
+        for (int wd = 0; wd < 8; ++wd) {
+            const uint32_t o = wd * 32 + lane;
+            x[wd] = y[wd] = qnan;
+            id[wd] = 0;
+            if (o < ocnt) {
+                const float2 p = __ldg(sxy + obase + o);
+                x[wd] = p.x;
+                y[wd] = p.y;
+                id[wd] = __ldg(sid + obase + o);
+            }
+        }
+        const uint32_t s0 = g * 32u;
+        const uint32_t ns = min(32u, nsub - s0);
+        uint32_t myq = 0;
+        float4 myr = make_float4(qnan, qnan, qnan, qnan);
+        if ((uint32_t)lane < ns) {
+            myq = __ldg(sub_q + __ldg(isub + soff + s0 + lane));
+            myr = __ldg(rects + myq);
+        }
+        for (uint32_t s = 0; s < ns; ++s) {
+            const float xa = __shfl_sync(0xffffffffu, myr.x, s), ya = __shfl_sync(0xffffffffu, myr.y, s);
+            const float xb = __shfl_sync(0xffffffffu, myr.z, s), yb = __shfl_sync(0xffffffffu, myr.w, s);
+            const uint32_t q = __shfl_sync(0xffffffffu, myq, s);
+#pragma unroll
+            for (int wd = 0; wd < 8; ++wd) {
+                if ((uint32_t)wd >= nwc) break;
+                const bool in = (xa <= x[wd]) & (x[wd] <= xb) & (ya <= y[wd]) & (y[wd] <= yb);
+                const uint32_t word = __ballot_sync(0xffffffffu, in);
+                const uint32_t k = __popc(word);
+                if (k == 0) continue;
+                if (nbuf + k > (uint32_t)kAtomBuf) {
+                    atomic_flush(buf, nbuf, out, cap, &info->n_out, lane);
+                    nbuf = 0;
+                }
+                if (in) buf[nbuf + __popc(word & lt)] = make_uint2(q, id[wd]);
+                nbuf += k;
+            }
+        }
+    }
+    if (nbuf) atomic_flush(buf, nbuf, out, cap, &info->n_out, lane);
+}
+
+// Covering runs of the atomic baseline: each run reserves its slot range.
+__global__ void __launch_bounds__(256)
+runs_atomic_kernel(const uint32_t *__restrict__ sub_q, const uint32_t *__restrict__ sub_leaf,
+                   const uint32_t *__restrict__ sub_len, const uint32_t *__restrict__ leaf_beg,
+                   const uint32_t *__restrict__ sid, uint2 *__restrict__ out, unsigned long long cap,
+                   Caps caps, Info *info) {
+    if (!tick_buffers_ok(info, caps)) return;
+    const uint32_t nsub = (uint32_t)info->n_sub;
+    const int lane = threadIdx.x & 31;
+    const uint32_t nwarps = gridDim.x * (blockDim.x >> 5);
+    for (uint32_t batch = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; batch * 32u < nsub; batch += nwarps) {
+        const uint32_t k = batch * 32u + lane;
+        bool cov = false;
+        uint32_t q = 0, b = 0, n = 0;
+        if (k < nsub) {
+            const uint32_t sl = __ldg(sub_leaf + k);
+            cov = (sl & 0x80000000u) != 0u;
+            if (cov) {
+                const uint32_t first = sl & 0x7fffffffu;
+                q = __ldg(sub_q + k);
+                b = __ldg(leaf_beg + first);
+                n = __ldg(leaf_beg + first + __ldg(sub_len + k)) - b;
+            }
+        }
+        unsigned long long base = 0;
+        if (cov) base = atomicAdd(&info->n_out, (unsigned long long)n);
+        uint32_t m = __ballot_sync(0xffffffffu, cov);
+        while (m) {
+            const int j = __ffs(m) - 1;
+            m &= m - 1u;
+            const unsigned long long bj = __shfl_sync(0xffffffffu, base, j);
+            const uint32_t qj = __shfl_sync(0xffffffffu, q, j), sj = __shfl_sync(0xffffffffu, b, j);
+            const uint32_t nj = __shfl_sync(0xffffffffu, n, j);
+            for (uint32_t i = lane; i < nj; i += 32)
+                if (bj + i < cap) out[bj + i] = make_uint2(qj, __ldg(sid + sj + i));
+        }
+    }
+}
+
+void launch_atomic_baseline(cudaStream_t st, int num_sms, const float4 *rects, const float2 *sxy,
+                            const uint32_t *sid, const uint32_t *leaf_beg, const uint32_t *leaf_sub_off,
+                            const uint32_t *leaf_item_off, const uint32_t *item_leaf, const uint32_t *isub,
+                            const uint32_t *sub_q, const uint32_t *sub_leaf, const uint32_t *sub_len, void *out,
+                            unsigned long long cap, uint32_t *ticket, Caps caps, Info *info) {
+    filter_atomic_kernel<<<num_sms * 4, kFilterThreads, 0, st>>>(rects, sxy, sid, leaf_beg, leaf_sub_off,
+                                                                 leaf_item_off, item_leaf, isub, sub_q,
+                                                                 reinterpret_cast<uint2 *>(out), cap, ticket,
+                                                                 caps, info);
+    runs_atomic_kernel<<<num_sms * 8, 256, 0, st>>>(sub_q, sub_leaf, sub_len, leaf_beg, sid,
+                                                    reinterpret_cast<uint2 *>(out), cap, caps, info);
+}
+
 // Sorted (qidx << 32 | id) keys to the requested layout.
 __global__ void keys_to_output_kernel(const unsigned long long *__restrict__ keys, uint64_t n,
                                       int as_pairs, void *out) {

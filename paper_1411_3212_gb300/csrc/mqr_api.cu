@@ -226,7 +226,8 @@ size_t out_elem_bytes(int kind) {
     switch (kind) {
         case MQR_OUT_PAIRS:
         case MQR_OUT_PAIRS_SORTED:
-        case MQR_OUT_RUNS: return 8;
+        case MQR_OUT_RUNS:
+        case MQR_OUT_PAIRS_ATOMIC: return 8;
         case MQR_OUT_CSR:
         case MQR_OUT_CSR_SORTED: return 4;
         default: return 4;
@@ -312,6 +313,15 @@ mqr_status enqueue_tick(mqr_ctx *c, const float4 *rects, uint32_t Q, int emit_ki
                    c->sub_bm.p, c->isub.p, caps, info);
     phase_end(c, MQR_PHASE_GROUP, nmax ? 2 : 1);
     // a10
+    if (emit_kind == kEmitAtomic) {
+        // the atomic-append baseline: no bitmaps, no result scan, no decoding
+        phase_begin(c, MQR_PHASE_FILTER);
+        launch_atomic_baseline(st, c->num_sms, rects, c->sxy.p, c->sid.p, c->leaf_beg.p, c->leaf_sub_off.p,
+                               c->leaf_item_off.p, c->item_leaf.p, c->isub.p, c->sub_q.p, c->sub_leaf.p,
+                               c->sub_len.p, out, out ? out_cap_elems : 0, ctr + 10, caps, info);
+        phase_end(c, MQR_PHASE_FILTER, 2);
+        return check_launch("tick kernels");
+    }
     phase_begin(c, MQR_PHASE_FILTER);
     launch_filter(st, c->num_sms, rects, c->sxy.p, c->leaf_beg.p, c->leaf_sub_off.p,
                   c->leaf_word_off.p, c->leaf_item_off.p, c->item_leaf.p, c->isub.p, c->sub_q.p, c->sub_res.p,
@@ -513,6 +523,19 @@ mqr_status tick_device_impl(mqr_ctx *c, const float *rects_dev, uint32_t Q, int 
         mqr_status s = run_tick(c, rects, Q, -1, nullptr, 0, offs);
         *out_count = c->last.n_results;
         return s;
+    }
+    if (kind == MQR_OUT_PAIRS_ATOMIC) {
+        if (offs) return fail(MQR_ERR_INVALID_ARG, "the unordered PAIRS_ATOMIC kind has no per-query offsets");
+        if (out_dev && (reinterpret_cast<uintptr_t>(out_dev) & 15u))
+            return fail(MQR_ERR_INVALID_ARG, "out_dev must be 16-byte aligned");
+        const unsigned long long cap_elems = cap_bytes / 8;
+        mqr_status s = run_tick(c, rects, Q, kEmitAtomic, out_dev, out_dev ? cap_elems : 0, nullptr);
+        c->last.n_results = c->last.n_out;
+        *out_count = c->last.n_out;
+        if (s != MQR_OK) return s;
+        if (c->last.n_out > cap_elems || (c->last.n_out && out_dev == nullptr))
+            return fail(MQR_ERR_CAPACITY, "output buffer too small for the tick's results");
+        return MQR_OK;
     }
     if (kind == MQR_OUT_PAIRS || kind == MQR_OUT_CSR || kind == MQR_OUT_RUNS) {
         if (out_dev && (reinterpret_cast<uintptr_t>(out_dev) & 15u))
@@ -749,7 +772,7 @@ static mqr_status tick_args(mqr_ctx *c, const void *rects, uint32_t Q, int kind,
     if (!out_count) return fail(MQR_ERR_INVALID_ARG, "out_count is NULL");
     if (Q > 0 && !rects) return fail(MQR_ERR_INVALID_ARG, "rects is NULL");
     if (Q >= (1u << 30)) return fail(MQR_ERR_INVALID_ARG, "Q must be < 2^30");
-    if (kind < MQR_OUT_PAIRS || kind > MQR_OUT_RUNS) return fail(MQR_ERR_INVALID_ARG, "unknown output kind");
+    if (kind < MQR_OUT_PAIRS || kind > MQR_OUT_PAIRS_ATOMIC) return fail(MQR_ERR_INVALID_ARG, "unknown output kind");
     return MQR_OK;
 }
 

@@ -377,12 +377,20 @@ void launch_result_scan(cudaStream_t st, unsigned long long sub_cap, const uint3
                         unsigned long long *status, uint32_t *tile_counter, uint32_t run_elems, Caps caps, Info *info);
 
 // a12 + a13: emit results in query-major order.
-enum EmitKind { kEmitPairs = 0, kEmitIds = 1, kEmitBitmap = 2, kEmitKeys64 = 3, kEmitRuns = 4 };
+enum EmitKind { kEmitPairs = 0, kEmitIds = 1, kEmitBitmap = 2, kEmitKeys64 = 3, kEmitRuns = 4,
+                kEmitAtomic = 5 /* the atomic-append baseline (no bitmaps, unordered pairs) */ };
 void launch_emit(cudaStream_t st, int num_sms, int emit_kind, const uint32_t *sub_q,
                  const uint32_t *sub_leaf, const uint32_t *sub_len, const uint32_t *sub_bm,
                  const unsigned long long *out_off, const uint32_t *leaf_beg,
                  const uint32_t *sid, const uint32_t *bitmap, void *out, uint32_t bitmap_words_per_row,
                  uint32_t *ticket, Caps caps, const Info *info);
+
+// The atomic-append baseline filtering (Alg. 3) and its covering runs.
+void launch_atomic_baseline(cudaStream_t st, int num_sms, const float4 *rects, const float2 *sxy,
+                            const uint32_t *sid, const uint32_t *leaf_beg, const uint32_t *leaf_sub_off,
+                            const uint32_t *leaf_item_off, const uint32_t *item_leaf, const uint32_t *isub,
+                            const uint32_t *sub_q, const uint32_t *sub_leaf, const uint32_t *sub_len, void *out,
+                            unsigned long long cap, uint32_t *ticket, Caps caps, Info *info);
 
 // Admission by output memory: queries [0, A) whose output fits cap elements.
 void launch_admit(cudaStream_t st, uint32_t Q, const unsigned long long *offsets, unsigned long long cap,

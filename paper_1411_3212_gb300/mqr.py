@@ -17,12 +17,13 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libmqr.so")
 
 MQR_OK, MQR_ERR_INVALID_ARG, MQR_ERR_OOM, MQR_ERR_CAPACITY, MQR_ERR_CUDA, MQR_ERR_TIMEOUT, MQR_ERR_INTERNAL = range(7)
-MQR_OUT_PAIRS, MQR_OUT_PAIRS_SORTED, MQR_OUT_CSR, MQR_OUT_CSR_SORTED, MQR_OUT_BITMAP, MQR_OUT_COUNT, MQR_OUT_RUNS = range(7)
+(MQR_OUT_PAIRS, MQR_OUT_PAIRS_SORTED, MQR_OUT_CSR, MQR_OUT_CSR_SORTED, MQR_OUT_BITMAP, MQR_OUT_COUNT, MQR_OUT_RUNS,
+ MQR_OUT_PAIRS_ATOMIC) = range(8)
 MQR_INDEX_QUADTREE, MQR_INDEX_UNIFORM_GRID = 0, 1
 
 KINDS = {"pairs": MQR_OUT_PAIRS, "pairs_sorted": MQR_OUT_PAIRS_SORTED, "csr": MQR_OUT_CSR,
          "csr_sorted": MQR_OUT_CSR_SORTED, "bitmap": MQR_OUT_BITMAP, "count": MQR_OUT_COUNT,
-         "runs": MQR_OUT_RUNS}
+         "runs": MQR_OUT_RUNS, "pairs_atomic": MQR_OUT_PAIRS_ATOMIC}
 
 # Every symbol include/mqr.h declares.
 EXPORTS = ["mqr_config_default", "mqr_create", "mqr_create_ex", "mqr_apply_updates",
@@ -293,7 +294,7 @@ class Index:
         torch = self._torch
         k = KINDS[kind]
         Q = int(rects.shape[0])
-        offs = torch.empty(Q + 1, dtype=torch.int64, device=rects.device)
+        offs = torch.empty(Q + 1, dtype=torch.int64, device=rects.device) if k != MQR_OUT_PAIRS_ATOMIC else None
         if k == MQR_OUT_BITMAP:
             W = (self.max_objects + 31) // 32
             out = torch.empty((Q, W), dtype=torch.int32, device=rects.device)
@@ -302,7 +303,7 @@ class Index:
         if k == MQR_OUT_COUNT:
             mqr_tick(self.ctx, rects, Q, k, None, 0, offs)
             return None, offs
-        elem = 8 if k in (MQR_OUT_PAIRS, MQR_OUT_PAIRS_SORTED, MQR_OUT_RUNS) else 4
+        elem = 8 if k in (MQR_OUT_PAIRS, MQR_OUT_PAIRS_SORTED, MQR_OUT_RUNS, MQR_OUT_PAIRS_ATOMIC) else 4
         if self._out is None:
             self._out = torch.empty(max(1 << 16, 8 * Q) * 2, dtype=torch.int32, device=rects.device)
         st, cnt = mqr_tick(self.ctx, rects, Q, k, self._out, self._out.numel() * 4, offs)

@@ -106,3 +106,16 @@ def gpu_runs_as_csr(idx, rects, dev):
         a, b = int(off[q]), int(off[q + 1])
         ids[a:b] = np.sort(ids[a:b])
     return off, ids, e
+
+
+def gpu_atomic_as_csr(idx, rects, dev):
+    """PAIRS_ATOMIC output (unordered pairs) -> sorted CSR on the host."""
+    res, _ = idx.tick(to_dev(rects, dev), kind="pairs_atomic")
+    p = res.cpu().numpy().view(np.uint32)
+    Q = rects.shape[0]
+    order = np.lexsort((p[:, 1], p[:, 0]))
+    p = p[order]
+    counts = np.bincount(p[:, 0], minlength=Q) if p.shape[0] else np.zeros(Q, np.int64)
+    assert counts.shape[0] == Q
+    off = np.concatenate([[0], np.cumsum(counts)]).astype(np.uint64)
+    return off, p[:, 1].copy()

@@ -110,6 +110,35 @@ def test_runs_kind_through_host_entry_point(case):
         mqr.mqr_destroy(ctx)
 
 
+def test_atomic_baseline_capacity_then_retry(case):
+    """The unordered atomic-append kind: a too-small buffer gives CAPACITY with
+    the exact count (nothing past the buffer is written), then the full set."""
+    torch, dev = torch_dev()
+    t, (woff, wids) = case
+    from paper_1411_3212_gb300 import mqr
+    mqr_, idx = mk(30000)
+    idx.apply_updates(to_dev(t.ids, dev), to_dev(t.xy, dev))
+    Q = t.rects.shape[0]
+    rd = to_dev(t.rects, dev)
+    guard = torch.full((4096,), -7, dtype=torch.int32, device=dev)
+    small = guard[:1024]
+    st, cnt = mqr.mqr_tick(idx.ctx, rd, Q, mqr.MQR_OUT_PAIRS_ATOMIC, small, small.numel() * 4)
+    assert st == mqr.MQR_ERR_CAPACITY and cnt == wids.shape[0]
+    assert bool((guard[1024:] == -7).all().item())
+    with pytest.raises(mqr.MqrError, match="offsets"):
+        mqr.mqr_tick(idx.ctx, rd, Q, mqr.MQR_OUT_PAIRS_ATOMIC, small, small.numel() * 4,
+                     torch.empty(Q + 1, dtype=torch.int64, device=dev))
+    big = torch.empty(2 * cnt + 16, dtype=torch.int32, device=dev)
+    st, cnt2 = mqr.mqr_tick(idx.ctx, rd, Q, mqr.MQR_OUT_PAIRS_ATOMIC, big, big.numel() * 4)
+    assert st == mqr.MQR_OK and cnt2 == cnt
+    p = big[: 2 * cnt].cpu().numpy().view(np.uint32).reshape(-1, 2)
+    p = p[np.lexsort((p[:, 1], p[:, 0]))]
+    want_q = np.repeat(np.arange(Q, dtype=np.uint32), np.diff(woff.astype(np.int64)))
+    np.testing.assert_array_equal(p[:, 0], want_q)
+    np.testing.assert_array_equal(p[:, 1], wids)
+    idx.close()
+
+
 def test_device_capacity_error_then_retry(case):
     torch, dev = torch_dev()
     t, want = case

@@ -8,7 +8,7 @@ import pytest
 
 import oracle
 from paper_1411_3212_gb300 import workloads
-from tests.gpu_util import (assert_same_csr, gpu_csr_sorted, gpu_pairs_as_csr, gpu_runs_as_csr, oracle_state,
+from tests.gpu_util import (assert_same_csr, gpu_atomic_as_csr, gpu_csr_sorted, gpu_pairs_as_csr, gpu_runs_as_csr, oracle_state,
                             to_dev, torch_dev)
 
 pytestmark = pytest.mark.gpu
@@ -149,6 +149,7 @@ def test_index_independence(mqr, hotspot_case, cfg):
     assert_same_csr((go, gi), want, "runs " + str(cfg))
     s = idx.stats()
     assert e.shape[0] == s["n_results"] - s["n_results_covering"] + 2 * s["n_covering_runs"]
+    assert_same_csr(gpu_atomic_as_csr(idx, t.rects, dev), want, "atomic " + str(cfg))
     idx.close()
 
 
@@ -195,6 +196,7 @@ def test_adversarial(mqr, seed, n, q, cap):
     assert_same_csr(gpu_pairs_as_csr(idx, rects, dev), want)
     go, gi, _ = gpu_runs_as_csr(idx, rects, dev)
     assert_same_csr((go, gi), want, "runs")
+    assert_same_csr(gpu_atomic_as_csr(idx, rects, dev), want, "atomic")
     idx.close()
 
 
