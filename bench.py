@@ -52,6 +52,11 @@ WORKLOADS = {
                            "of side 0.002 centred on objects, leaf_cap 128, pair-list output"),
     "uniform16k": dict(kind="small", n=16384, q=1024, cap=64,
                        desc="uniform-16K: 16,384 uniform objects, 1,024 queries of side 0.01, leaf_cap 64"),
+    "batched256": dict(kind="batched", n=0, q=0, cap=128,
+                       desc="batched-256: 256 independent worlds in one index, sizes log-uniform 1,000-262,144 "
+                            "objects (12.3M in all), half uniform and half 8-hotspot (sigma 0.01) random walks, "
+                            "each issuing sizes/10 queries of side 0.003 per tick (1.23M in all), leaf_cap 128, "
+                            "pair-list output"),
 }
 
 
@@ -69,6 +74,8 @@ def make_world(name, seed):
         return workloads.HotspotWalk(n=w["n"], q=w["q"], seed=seed)
     if w["kind"] == "uniform":
         return workloads.UniformWalk(n=w["n"], q=w["q"], seed=seed)
+    if w["kind"] == "batched":
+        return workloads.BatchedWorlds(n_worlds=256, seed=seed)
 
     class Small:
         def __init__(self):
@@ -310,12 +317,18 @@ def run_gpu(args, name):
     ticks = gen_ticks(name, 1000 * rank, args.warmup + uniq)
     log("rank %d: generated %d ticks in %.1f s" % (rank, len(ticks), time.perf_counter() - t_gen))
 
+    batched = w["kind"] == "batched"
+    if batched:                                          # sizes come from the generated worlds
+        nmax, Q = int(ticks[0].ids.shape[0]), int(ticks[0].rects.shape[0])
     ids_d = torch.from_numpy(ticks[0].ids.view(np.int32)).to(dev)
     xy_d = [torch.from_numpy(t.xy).to(dev) for t in ticks]
     rect_d = [torch.from_numpy(t.rects).to(dev) for t in ticks]
     flush = torch.empty(args.flush_mb * (1 << 20) // 4, dtype=torch.int32, device=dev)
 
     idx = mqr.Index(bounds=(0.0, 0.0, 1.0, 1.0), leaf_cap=w["cap"], max_objects=nmax)
+    if batched:
+        idx.set_worlds(ticks[0].obj_base)
+        idx.set_query_worlds(ticks[0].q_base)
     kind = mqr.KINDS[args.kind]
     elem = 8 if kind in (mqr.MQR_OUT_PAIRS, mqr.MQR_OUT_PAIRS_SORTED, mqr.MQR_OUT_RUNS, mqr.MQR_OUT_PAIRS_ATOMIC) else 4
     out = torch.empty(1, dtype=torch.int32, device=dev)
@@ -403,7 +416,7 @@ def run_gpu(args, name):
             e2e_runs = run_e2e(args, idx, ticks, mqr.MQR_OUT_RUNS, 8, Q, stats["n_results"], dev)
 
     cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and not batched:
         cpu = cpu_baseline(ticks, name, nmax, args.cpu_sample)
 
     idx.close()
@@ -507,6 +520,9 @@ def run_served(args):
     rects = np.concatenate(rects)
     log("served: %d queries over %d ticks generated in %.1f s" % (rects.shape[0], args.served_ticks,
                                                                   time.perf_counter() - t_gen))
+    batched = w["kind"] == "batched"
+    if batched:                                          # sizes come from the generated worlds
+        nmax, Q = int(ticks[0].ids.shape[0]), int(ticks[0].rects.shape[0])
     ids_d = torch.from_numpy(ticks[0].ids.view(np.int32)).to(dev)
     updates = [(ids_d, torch.from_numpy(t.xy).to(dev)) for t in ticks]
     rects_d = torch.from_numpy(rects).to(dev)

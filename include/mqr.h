@@ -235,6 +235,28 @@ mqr_status mqr_tick_admit(mqr_ctx *ctx, const float *rects_dev, uint32_t Q, int 
                           uint64_t out_capacity_bytes, uint32_t *admitted, uint64_t *out_count,
                           uint64_t *offsets_dev);
 
+/* Batched independent worlds in one index (many small instances of the
+ * problem of Sec. 2.5 answered by one tick; the paper has no batched mode,
+ * this keeps each world's result exact and its own).  World w owns the
+ * object ids [obj_base_host[w], obj_base_host[w+1]) (obj_base_host: uint32
+ * host array of n_worlds+1 entries, 0 first, max_objects last, not
+ * decreasing); its objects and queries are in the context's bounds, in its
+ * own coordinates.  Internally the quadtree (Alg. 1) gets ceil(log4
+ * n_worlds) levels above the worlds' roots, so each world is one node, keys
+ * keep their 30 bits (a world's cells are its l_max cells shifted right by
+ * those levels) and no leaf spans two worlds; containment tests use the
+ * objects' own coordinates, so results are exact.  n_worlds = 1 returns to
+ * the plain index.  1 <= n_worlds <= 16384.  Call between ticks; the query
+ * ranges must then be set with mqr_set_query_worlds. */
+mqr_status mqr_set_worlds(mqr_ctx *ctx, uint32_t n_worlds, const uint32_t *obj_base_host);
+
+/* Query ranges of the batched worlds for the following ticks: the queries
+ * [q_base_host[w], q_base_host[w+1]) of a tick's rects belong to world w
+ * (uint32 host array of n_worlds+1 entries, 0 first, not decreasing); the
+ * ticks must pass Q = q_base_host[n_worlds].  Result pairs carry the global
+ * query index and object id. */
+mqr_status mqr_set_query_worlds(mqr_ctx *ctx, const uint32_t *q_base_host);
+
 /* Counters of the last completed tick. */
 mqr_status mqr_get_stats(const mqr_ctx *ctx, mqr_stats *out);
 

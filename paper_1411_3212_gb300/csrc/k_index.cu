@@ -57,7 +57,7 @@ constexpr int kMortonThreads = 256, kMortonItems = 16;
 
 __global__ void __launch_bounds__(kMortonThreads)
 morton_kernel(const float2 *__restrict__ pos, const unsigned long long *__restrict__ stamp,
-              uint32_t nmax, float x0, float y0, float sx, float sy,
+              uint32_t nmax, float x0, float y0, float sx, float sy, Worlds worlds,
               unsigned long long *__restrict__ keys, uint32_t *__restrict__ hist, Info *info) {
     __shared__ uint32_t s_hist[4 * 256];
     __shared__ uint32_t s_cnt;
@@ -73,7 +73,13 @@ morton_kernel(const float2 *__restrict__ pos, const unsigned long long *__restri
         uint32_t k;
         if (stamp[i] != 0ull) {
             float2 p = pos[i];
-            k = morton2(cell_of(p.x, x0, sx), cell_of(p.y, y0, sy));
+            uint32_t ci = cell_of(p.x, x0, sx), cj = cell_of(p.y, y0, sy);
+            if (worlds.n) {
+                const uint32_t w = world_of(i, worlds.obj_base, worlds.n);
+                ci = world_cell(ci, w, worlds.bits, 0);
+                cj = world_cell(cj, w, worlds.bits, 1);
+            }
+            k = morton2(ci, cj);
             ++present;
         } else {
             k = kAbsentKey;
@@ -93,12 +99,12 @@ morton_kernel(const float2 *__restrict__ pos, const unsigned long long *__restri
 }
 
 void launch_morton_keys(cudaStream_t st, const float2 *pos, const unsigned long long *stamp,
-                        uint32_t nmax, float x0, float y0, float sx, float sy,
+                        uint32_t nmax, float x0, float y0, float sx, float sy, Worlds worlds,
                         unsigned long long *keys, uint32_t *hist4x256, Info *info) {
     if (nmax == 0) return;
     uint32_t per = kMortonThreads * kMortonItems;
     morton_kernel<<<(nmax + per - 1) / per, kMortonThreads, 0, st>>>(pos, stamp, nmax, x0, y0, sx, sy,
-                                                                      keys, hist4x256, info);
+                                                                      worlds, keys, hist4x256, info);
 }
 
 // ---------------------------------------------------------------------------
@@ -368,7 +374,7 @@ __global__ void window_double_kernel(const uint8_t *__restrict__ a, uint8_t *__r
 
 __global__ void __launch_bounds__(kLeafThreads)
 leaves_kernel(const uint32_t *__restrict__ K, uint32_t cap, int uniform_grid, uint32_t grid_level,
-              int kexp, const uint8_t *__restrict__ Mk_global, uint32_t *status,
+              uint32_t min_level, int kexp, const uint8_t *__restrict__ Mk_global, uint32_t *status,
               uint32_t *tile_counter, uint32_t *__restrict__ leaf_lo, uint32_t *__restrict__ leaf_hi,
               uint32_t *__restrict__ leaf_beg, uint32_t *__restrict__ leaf_nsub, uint2 *__restrict__ leaf_box,
               Info *info) {
@@ -424,6 +430,10 @@ leaves_kernel(const uint32_t *__restrict__ K, uint32_t cap, int uniform_grid, ui
         }
     }
     __syncthreads();
+    if (min_level) {           // batched worlds: no leaf above the worlds' roots
+        for (int i = tid; i <= kLeafTile; i += kLeafThreads) s_L[i] = max(s_L[i], (uint8_t)min_level);
+        __syncthreads();
+    }
 
     // Leaf starts: thread handles positions t0 + tid*8 .. +8 (blocked).
     constexpr int PER = kLeafTile / kLeafThreads;
@@ -478,7 +488,7 @@ leaves_kernel(const uint32_t *__restrict__ K, uint32_t cap, int uniform_grid, ui
 }
 
 void launch_build_leaves(cudaStream_t st, const uint32_t *skey, uint32_t nmax, uint32_t cap,
-                         int uniform_grid, uint32_t grid_level, uint8_t *mk_a, uint8_t *mk_b,
+                         int uniform_grid, uint32_t grid_level, uint32_t min_level, uint8_t *mk_a, uint8_t *mk_b,
                          uint32_t *status, uint32_t *tile_counter, uint32_t *leaf_lo,
                          uint32_t *leaf_hi, uint32_t *leaf_beg, uint32_t *leaf_nsub, uint2 *leaf_box,
                          Info *info) {
@@ -502,7 +512,7 @@ void launch_build_leaves(cudaStream_t st, const uint32_t *skey, uint32_t nmax, u
             mk = a;
         }
     }
-    leaves_kernel<<<tiles, kLeafThreads, dyn, st>>>(skey, cap, uniform_grid, grid_level, kexp, mk,
+    leaves_kernel<<<tiles, kLeafThreads, dyn, st>>>(skey, cap, uniform_grid, grid_level, min_level, kexp, mk,
                                                     status, tile_counter, leaf_lo, leaf_hi, leaf_beg,
                                                     leaf_nsub, leaf_box, info);
 }

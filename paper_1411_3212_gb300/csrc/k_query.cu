@@ -111,7 +111,7 @@ __device__ __forceinline__ int classify(uint32_t i0, uint32_t i1, uint32_t j0, u
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(kQBThreads)
 query_blocks_kernel(const float4 *__restrict__ rects, uint32_t Q, float x0, float y0, float sx, float sy,
-                    const uint32_t *__restrict__ leaf_lo, const uint32_t *__restrict__ leaf_hi,
+                    Worlds worlds, const uint32_t *__restrict__ leaf_lo, const uint32_t *__restrict__ leaf_hi,
                     const uint32_t *__restrict__ zmap, uint2 *__restrict__ qcells,
                     unsigned long long *__restrict__ cand_off, uint32_t *__restrict__ pair_q,
                     uint32_t *__restrict__ pair_first, uint32_t *__restrict__ pair_blo,
@@ -135,6 +135,13 @@ query_blocks_kernel(const float4 *__restrict__ rects, uint32_t Q, float x0, floa
     uint32_t f = 0, cnt = 0, blk = 0;
     QCells c;
     const bool qok = qvalid && L > 0 && query_cells(rects[q], x0, y0, sx, sy, c);
+    if (qok && worlds.n) {      // the query's cells inside its world's node
+        const uint32_t w = world_of(q, worlds.q_base, worlds.n);
+        c.i0 = world_cell(c.i0, w, worlds.bits, 0);
+        c.i1 = world_cell(c.i1, w, worlds.bits, 0);
+        c.j0 = world_cell(c.j0, w, worlds.bits, 1);
+        c.j1 = world_cell(c.j1, w, worlds.bits, 1);
+    }
     if (qok) {
         const uint32_t k = block_log2(c.i0, c.i1, c.j0, c.j1);
         const uint32_t bi = (c.i0 >> k) + slot % 3u, bj = (c.j0 >> k) + slot / 3u;
@@ -194,7 +201,7 @@ void launch_zmap(cudaStream_t st, const uint32_t *leaf_hi, const Info *info, uin
 }
 
 void launch_query_blocks(cudaStream_t st, const float4 *rects, uint32_t Q, float x0, float y0, float sx,
-                         float sy, const uint32_t *leaf_lo, const uint32_t *leaf_hi, const uint32_t *zmap,
+                         float sy, Worlds worlds, const uint32_t *leaf_lo, const uint32_t *leaf_hi, const uint32_t *zmap,
                          uint2 *qcells, unsigned long long *cand_off, uint32_t *pair_q,
                          uint32_t *pair_first, uint32_t *pair_blo, unsigned long long *pair_off,
                          uint32_t *qpair, uint32_t *tile_p0, unsigned long long tile_cap,
@@ -202,7 +209,7 @@ void launch_query_blocks(cudaStream_t st, const float4 *rects, uint32_t Q, float
                          Info *info) {
     if (Q == 0) return;
     uint32_t tiles = (Q + kQBQueries - 1) / kQBQueries;
-    query_blocks_kernel<<<tiles, kQBThreads, 0, st>>>(rects, Q, x0, y0, sx, sy, leaf_lo, leaf_hi, zmap,
+    query_blocks_kernel<<<tiles, kQBThreads, 0, st>>>(rects, Q, x0, y0, sx, sy, worlds, leaf_lo, leaf_hi, zmap,
                                                       qcells, cand_off, pair_q, pair_first, pair_blo,
                                                       pair_off, qpair, tile_p0, tile_cap, status_p,
                                                       status_c, tile_counter, info);

@@ -108,6 +108,11 @@ struct mqr_ctx {
     DevBuf<unsigned long long> off_stage, sortA, sortB;
     DevBuf<unsigned char> sort_arena;
     DevBuf<unsigned long long> upd_err;  // sticky error word of the update kernels
+    // batched independent worlds (mqr_set_worlds): id and query ranges per world
+    uint32_t n_worlds = 0, world_bits = 0;
+    DevBuf<uint32_t> world_obj, world_q;
+    unsigned long long world_q_total = 0;
+    bool world_q_set = false;
 
     Info *info_host = nullptr;  // pinned
     Info last{};
@@ -258,7 +263,8 @@ mqr_status enqueue_tick(mqr_ctx *c, const float4 *rects, uint32_t Q, int emit_ki
 
     // a2 + a3: keys and the 4-pass onesweep sort of (key << 32 | id).
     phase_begin(c, MQR_PHASE_KEYS);
-    launch_morton_keys(st, c->pos.p, c->stamp.p, nmax, x0, y0, c->sx, c->sy, c->keysA.p, hist, info);
+    const Worlds worlds{c->world_obj.p, c->world_q.p, c->n_worlds, c->world_bits};
+    launch_morton_keys(st, c->pos.p, c->stamp.p, nmax, x0, y0, c->sx, c->sy, worlds, c->keysA.p, hist, info);
     phase_end(c, MQR_PHASE_KEYS, nmax ? 1 : 0);
     unsigned long long *src = c->keysA.p, *dst = c->keysB.p;
     phase_begin(c, MQR_PHASE_SORT);
@@ -273,7 +279,7 @@ mqr_status enqueue_tick(mqr_ctx *c, const float4 *rects, uint32_t Q, int emit_ki
     phase_begin(c, MQR_PHASE_LEAVES);
     const uint32_t cap = c->cfg.leaf_cap;
     const bool ug = c->cfg.index_kind == MQR_INDEX_UNIFORM_GRID;
-    launch_build_leaves(st, c->skey.p, nmax, cap, ug, c->cfg.grid_level, c->mk_a.p, c->mk_b.p,
+    launch_build_leaves(st, c->skey.p, nmax, cap, ug, c->cfg.grid_level, c->world_bits, c->mk_a.p, c->mk_b.p,
                         at<uint32_t>(c, a.st_leaf), ctr + 4, c->leaf_lo.p, c->leaf_hi.p, c->leaf_beg.p,
                         c->leaf_nsub.p, c->leaf_box.p, info);
     uint64_t leaf_launches = nmax ? 1 : 0;
@@ -292,7 +298,7 @@ mqr_status enqueue_tick(mqr_ctx *c, const float4 *rects, uint32_t Q, int emit_ki
     caps.items = c->item_leaf.n;
     phase_begin(c, MQR_PHASE_QUERY_BLOCKS);
     launch_zmap(st, c->leaf_hi.p, info, c->zmap.p);
-    launch_query_blocks(st, rects, Q, x0, y0, c->sx, c->sy, c->leaf_lo.p, c->leaf_hi.p, c->zmap.p,
+    launch_query_blocks(st, rects, Q, x0, y0, c->sx, c->sy, worlds, c->leaf_lo.p, c->leaf_hi.p, c->zmap.p,
                         c->qcells.p, c->cand_off.p, c->pair_q.p, c->pair_first.p, c->pair_blo.p,
                         c->pair_off.p, c->qpair.p, c->tile_p0.p, a.cand_tiles,
                         at<uint32_t>(c, a.st_qb_p), at<unsigned long long>(c, a.st_qb_c), ctr + 5, info);
@@ -625,6 +631,8 @@ void mqr_destroy(mqr_ctx *c) {
     if (c->stream) cudaStreamSynchronize(c->stream);
     DevBuf<float2> *f2[] = {&c->pos, &c->sxy, &c->up_xy};
     for (auto *b : f2) b->release();
+    c->world_obj.release();
+    c->world_q.release();
     DevBuf<unsigned long long> *u64s[] = {&c->stamp, &c->keysA, &c->keysB, &c->out_off, &c->off_stage,
                                           &c->sortA, &c->sortB};
     for (auto *b : u64s) b->release();
@@ -773,6 +781,50 @@ static mqr_status tick_args(mqr_ctx *c, const void *rects, uint32_t Q, int kind,
     if (Q > 0 && !rects) return fail(MQR_ERR_INVALID_ARG, "rects is NULL");
     if (Q >= (1u << 30)) return fail(MQR_ERR_INVALID_ARG, "Q must be < 2^30");
     if (kind < MQR_OUT_PAIRS || kind > MQR_OUT_PAIRS_ATOMIC) return fail(MQR_ERR_INVALID_ARG, "unknown output kind");
+    if (c->n_worlds && (!c->world_q_set || Q != c->world_q_total))
+        return fail(MQR_ERR_INVALID_ARG, "batched worlds: Q must equal the total of mqr_set_query_worlds");
+    return MQR_OK;
+}
+
+mqr_status mqr_set_worlds(mqr_ctx *c, uint32_t n_worlds, const uint32_t *obj_base_host) {
+    if (!c) return fail(MQR_ERR_INVALID_ARG, "ctx is NULL");
+    if (n_worlds == 0 || n_worlds > kMaxWorlds) return fail(MQR_ERR_INVALID_ARG, "n_worlds must be 1..16384");
+    if (n_worlds > 1 && !obj_base_host) return fail(MQR_ERR_INVALID_ARG, "obj_base_host is NULL");
+    MQR_CUDA(cudaSetDevice(c->device));
+    MQR_CUDA(cudaStreamSynchronize(c->stream));
+    c->world_q_set = false;
+    if (n_worlds == 1) {                        // one world: the plain index
+        c->n_worlds = c->world_bits = 0;
+        return MQR_OK;
+    }
+    if (obj_base_host[0] != 0 || obj_base_host[n_worlds] != c->nmax)
+        return fail(MQR_ERR_INVALID_ARG, "obj_base must start at 0 and end at max_objects");
+    for (uint32_t w = 0; w < n_worlds; ++w)
+        if (obj_base_host[w + 1] < obj_base_host[w]) return fail(MQR_ERR_INVALID_ARG, "obj_base must not decrease");
+    uint32_t bits = 0;
+    while ((1u << (2 * bits)) < n_worlds) ++bits;
+    if (c->cfg.index_kind == MQR_INDEX_UNIFORM_GRID && c->cfg.grid_level < bits)
+        return fail(MQR_ERR_INVALID_ARG, "uniform grid: grid_level must be >= log4(n_worlds)");
+    MQR_CUDA(c->world_obj.ensure((size_t)n_worlds + 1));
+    MQR_CUDA(c->world_q.ensure((size_t)n_worlds + 1));
+    MQR_CUDA(cudaMemcpy(c->world_obj.p, obj_base_host, ((size_t)n_worlds + 1) * 4, cudaMemcpyHostToDevice));
+    c->n_worlds = n_worlds;
+    c->world_bits = bits;
+    return MQR_OK;
+}
+
+mqr_status mqr_set_query_worlds(mqr_ctx *c, const uint32_t *q_base_host) {
+    if (!c) return fail(MQR_ERR_INVALID_ARG, "ctx is NULL");
+    if (!c->n_worlds) return fail(MQR_ERR_INVALID_ARG, "no batched worlds (mqr_set_worlds)");
+    if (!q_base_host) return fail(MQR_ERR_INVALID_ARG, "q_base_host is NULL");
+    if (q_base_host[0] != 0) return fail(MQR_ERR_INVALID_ARG, "q_base must start at 0");
+    for (uint32_t w = 0; w < c->n_worlds; ++w)
+        if (q_base_host[w + 1] < q_base_host[w]) return fail(MQR_ERR_INVALID_ARG, "q_base must not decrease");
+    MQR_CUDA(cudaSetDevice(c->device));
+    MQR_CUDA(cudaStreamSynchronize(c->stream));
+    MQR_CUDA(cudaMemcpy(c->world_q.p, q_base_host, ((size_t)c->n_worlds + 1) * 4, cudaMemcpyHostToDevice));
+    c->world_q_total = q_base_host[c->n_worlds];
+    c->world_q_set = true;
     return MQR_OK;
 }
 

@@ -97,6 +97,36 @@ __host__ __device__ __forceinline__ uint32_t compact15(uint32_t v) {
     v = (v | (v >> 8)) & 0x0000ffffu;
     return v;
 }
+
+// Independent worlds sharing one index: world w (0 <= w < 4^bits) owns the
+// object ids [obj_base[w], obj_base[w+1]) and the queries [q_base[w],
+// q_base[w+1]).  Its quadtree is the node of depth `bits` whose Morton prefix
+// is w, so a world's cells are its own l_max cells shifted right by `bits`
+// and placed in that node; leaves never lie above depth `bits`.  n == 0: one
+// world, the whole grid.
+constexpr uint32_t kMaxWorlds = 16384;     // 4^7: at least 8 levels left per world
+struct Worlds {
+    const uint32_t *obj_base;
+    const uint32_t *q_base;
+    uint32_t n;       // number of worlds (0: not batched)
+    uint32_t bits;    // levels above the worlds' roots (4^bits >= n)
+};
+
+// The world of item i: the largest w with base[w] <= i.
+__device__ __forceinline__ uint32_t world_of(uint32_t i, const uint32_t *__restrict__ base, uint32_t n) {
+    uint32_t lo = 0, hi = n;
+    while (hi - lo > 1u) {
+        const uint32_t m = (lo + hi) >> 1;
+        if (__ldg(base + m) <= i) lo = m; else hi = m;
+    }
+    return lo;
+}
+
+// An l_max cell of world w on one axis (odd = y) -> its cell in the batched grid.
+__device__ __forceinline__ uint32_t world_cell(uint32_t c, uint32_t w, uint32_t bits, int odd) {
+    const uint32_t wc = compact15(odd ? (w >> 1) : w);
+    return (wc << (kLevels - bits)) | (c >> bits);
+}
 // x index in the even bits, y index in the odd bits.
 __host__ __device__ __forceinline__ uint32_t morton2(uint32_t i, uint32_t j) {
     return spread15(i) | (spread15(j) << 1);
@@ -293,7 +323,7 @@ void launch_apply_updates(cudaStream_t st, const uint32_t *ids, const float2 *xy
 
 // a2: Morton keys of every slot + digit histograms of the 4 sort passes.
 void launch_morton_keys(cudaStream_t st, const float2 *pos, const unsigned long long *stamp,
-                        uint32_t nmax, float x0, float y0, float sx, float sy,
+                        uint32_t nmax, float x0, float y0, float sx, float sy, Worlds worlds,
                         unsigned long long *keys, uint32_t *hist4x256, Info *info);
 
 // a3: one onesweep pass over n u64 keys, 8-bit digit at `shift`.  The final
@@ -315,10 +345,11 @@ void launch_key_histograms(cudaStream_t st, const unsigned long long *keys, uint
                            const int *shifts_host, int nd, uint32_t *hist);
 
 // a4: leaves.  level_mode: 0 = quadtree (capacity rule), 1 = uniform grid at
-// `grid_level`.  Writes leaf_lo/leaf_hi/leaf_beg and Info::n_leaves/max_level.
+// `grid_level`; no leaf above depth min_level (the batched worlds' roots).
+// Writes leaf_lo/leaf_hi/leaf_beg and Info::n_leaves/max_level.
 constexpr int kLeafThreads = 256, kLeafTile = 2048, kLeafCapSmem = 16384;
 void launch_build_leaves(cudaStream_t st, const uint32_t *skey, uint32_t nmax, uint32_t cap,
-                         int uniform_grid, uint32_t grid_level, uint8_t *mk_a, uint8_t *mk_b,
+                         int uniform_grid, uint32_t grid_level, uint32_t min_level, uint8_t *mk_a, uint8_t *mk_b,
                          uint32_t *status, uint32_t *tile_counter, uint32_t *leaf_lo,
                          uint32_t *leaf_hi, uint32_t *leaf_beg, uint32_t *leaf_nsub, uint2 *leaf_box,
                          Info *info);
@@ -335,7 +366,7 @@ constexpr int kCandScanTile = 2048;                   // warp tiles per block of
 void launch_zmap(cudaStream_t st, const uint32_t *leaf_hi, const Info *info, uint32_t *zmap);
 // a5 + a6: blocks, leaf ranges and candidate counts per query, scanned.
 void launch_query_blocks(cudaStream_t st, const float4 *rects, uint32_t Q, float x0, float y0, float sx,
-                         float sy, const uint32_t *leaf_lo, const uint32_t *leaf_hi, const uint32_t *zmap,
+                         float sy, Worlds worlds, const uint32_t *leaf_lo, const uint32_t *leaf_hi, const uint32_t *zmap,
                          uint2 *qcells, unsigned long long *cand_off, uint32_t *pair_q,
                          uint32_t *pair_first, uint32_t *pair_blo, unsigned long long *pair_off,
                          uint32_t *qpair, uint32_t *tile_p0, unsigned long long tile_cap,

@@ -27,7 +27,8 @@ KINDS = {"pairs": MQR_OUT_PAIRS, "pairs_sorted": MQR_OUT_PAIRS_SORTED, "csr": MQ
 
 # Every symbol include/mqr.h declares.
 EXPORTS = ["mqr_config_default", "mqr_create", "mqr_create_ex", "mqr_apply_updates",
-           "mqr_apply_updates_host", "mqr_tick", "mqr_tick_host", "mqr_tick_admit", "mqr_get_stats",
+           "mqr_apply_updates_host", "mqr_tick", "mqr_tick_host", "mqr_tick_admit", "mqr_set_worlds",
+           "mqr_set_query_worlds", "mqr_get_stats",
            "mqr_get_leaves",
            "mqr_get_sorted", "mqr_set_timing", "mqr_get_timing", "mqr_sort_objects_noalloc",
            "mqr_last_error", "mqr_destroy"]
@@ -97,6 +98,8 @@ def load(path: str = LIB_PATH):
         "mqr_tick": ([P, P, u32, i32, P, u64, ctypes.POINTER(u64), P], i32),
         "mqr_tick_host": ([P, P, u32, i32, P, u64, ctypes.POINTER(u64), P], i32),
         "mqr_tick_admit": ([P, P, u32, i32, P, u64, ctypes.POINTER(u32), ctypes.POINTER(u64), P], i32),
+        "mqr_set_worlds": ([P, u32, P], i32),
+        "mqr_set_query_worlds": ([P, P], i32),
         "mqr_get_stats": ([P, ctypes.POINTER(mqr_stats)], i32),
         "mqr_get_leaves": ([P, P, u64, ctypes.POINTER(u64)], i32),
         "mqr_get_sorted": ([P, P, P, u64, ctypes.POINTER(u64)], i32),
@@ -197,6 +200,16 @@ def mqr_tick_admit(ctx, rects_dev, Q, kind, out_dev, out_capacity_bytes, offsets
     _check(load().mqr_tick_admit(ctx, _ptr(rects_dev), Q, kind, _ptr(out_dev), out_capacity_bytes,
                                  ctypes.byref(adm), ctypes.byref(cnt), _ptr(offsets_dev)))
     return int(adm.value), int(cnt.value)
+
+
+def mqr_set_worlds(ctx, obj_base):
+    b = np.ascontiguousarray(obj_base, dtype=np.uint32)
+    _check(load().mqr_set_worlds(ctx, int(b.shape[0]) - 1, b.ctypes.data))
+
+
+def mqr_set_query_worlds(ctx, q_base):
+    b = np.ascontiguousarray(q_base, dtype=np.uint32)
+    _check(load().mqr_set_query_worlds(ctx, b.ctypes.data))
 
 
 def mqr_get_stats(ctx):
@@ -313,6 +326,12 @@ class Index:
             _check(st)
         res = self._out[: cnt * elem // 4]
         return (res.view(cnt, 2) if elem == 8 else res), offs
+
+    def set_worlds(self, obj_base):
+        mqr_set_worlds(self.ctx, obj_base)
+
+    def set_query_worlds(self, q_base):
+        mqr_set_query_worlds(self.ctx, q_base)
 
     def stats(self):
         return mqr_get_stats(self.ctx)

@@ -200,6 +200,48 @@ class ServedWorld(HotspotWalk):
         return Tick(np.arange(self.n, dtype=np.uint32), xy, rects, iss, arrivals)
 
 
+# ----------------------------------------------------------------------------
+# Batched independent worlds: world sizes log-uniform in [n_lo, n_hi], half of
+# the worlds uniform random walks, half hotspot walks (8 hotspots of sigma
+# 0.01); each world issues n_w * q_frac fixed-side queries per tick.  A tick
+# concatenates the worlds in order: object ids and queries are global, world
+# w owning ids [obj_base[w], obj_base[w+1]) and queries [q_base[w],
+# q_base[w+1]).
+# ----------------------------------------------------------------------------
+@dataclass
+class BatchedTick:
+    ids: np.ndarray
+    xy: np.ndarray
+    rects: np.ndarray
+    obj_base: np.ndarray     # u32[W+1]
+    q_base: np.ndarray       # u32[W+1]
+
+
+class BatchedWorlds:
+    def __init__(self, n_worlds: int = 256, n_lo: int = 1000, n_hi: int = 262_144, q_frac: float = 0.1,
+                 side: float = 0.003, step: float = 0.0005, seed: int = 0):
+        r_size, r_seed = _rngs(seed, 2)
+        sizes = np.exp(r_size.uniform(np.log(n_lo), np.log(n_hi), n_worlds)).astype(np.int64)
+        seeds = r_seed.integers(0, 2 ** 31, size=n_worlds)
+        self.worlds = []
+        for w in range(n_worlds):
+            n = int(sizes[w])
+            q = max(1, int(n * q_frac))
+            if w % 2 == 0:
+                self.worlds.append(UniformWalk(n=n, q=q, side=side, step=step, seed=int(seeds[w])))
+            else:
+                self.worlds.append(HotspotWalk(n=n, q=q, hotspots=8, sigma_lo=0.01, sigma_hi=0.01, side_lo=side,
+                                               side_hi=side, step=step, seed=int(seeds[w])))
+        self.obj_base = np.concatenate([[0], np.cumsum(sizes)]).astype(np.uint32)
+        self.n = int(self.obj_base[-1])
+
+    def next_tick(self) -> BatchedTick:
+        ticks = [w.next_tick() for w in self.worlds]
+        q_base = np.concatenate([[0], np.cumsum([t.rects.shape[0] for t in ticks])]).astype(np.uint32)
+        return BatchedTick(np.arange(self.n, dtype=np.uint32), np.concatenate([t.xy for t in ticks]),
+                           np.concatenate([t.rects for t in ticks]), self.obj_base.copy(), q_base)
+
+
 def hotspot_small(seed: int = 0, n: int = 200_000, q: int = 20_000) -> HotspotWalk:
     """A reduced hotspot world with the same recipe (for parity tests)."""
     return HotspotWalk(n=n, q=q, seed=seed)
