@@ -1,0 +1,43 @@
+"""Leaf-capacity autotuning.
+
+The quadtree's split threshold (th_quad, Alg. 1; the paper fixes it per
+experiment) trades fewer, larger leaves (more containment tests, Eq. of the
+filtering complexity) against more subqueries and candidates.  Every
+capacity gives the same results (the index never changes an answer), so the
+choice only moves time: this tunes it on the caller's own ticks by timing a
+few ticks per candidate capacity with CUDA events and keeping the fastest.
+Scheduling only: the ticks themselves run in the kernels behind the C ABI.
+"""
+from __future__ import annotations
+
+
+def tune_leaf_cap(make_index, ticks, caps=(32, 64, 128, 256, 512), kind="pairs", reps=2):
+    """make_index(cap) -> mqr.Index; ticks: list of (ids_dev, xy_dev,
+    rects_dev) in the caller's order.  Each capacity answers every tick once
+    untimed, then `reps` more times timed.  Returns (best_cap, table) with
+    table[cap] = {"ms_per_tick", "results"}; results must agree across caps."""
+    import torch
+    table = {}
+    for cap in caps:
+        idx = make_index(cap)
+        try:
+            for ids, xy, rects in ticks:                   # warm-up: buffer growth
+                idx.apply_updates(ids, xy)
+                idx.tick(rects, kind=kind)
+            torch.cuda.synchronize()
+            start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            results = 0
+            start.record()
+            for _ in range(reps):
+                for ids, xy, rects in ticks:
+                    idx.apply_updates(ids, xy)
+                    idx.tick(rects, kind=kind)
+                    results += idx.stats()["n_results"]
+            end.record()
+            end.synchronize()
+            table[cap] = {"ms_per_tick": start.elapsed_time(end) / (reps * len(ticks)),
+                          "results": results // reps}
+        finally:
+            idx.close()
+    best = min(table, key=lambda c: table[c]["ms_per_tick"])
+    return best, table

@@ -224,3 +224,16 @@ def test_uniform_grid_subquery_counts_match_oracle(case):
     s = idx.stats()
     assert s["n_sub_intersecting"] == n_i and s["n_sub_covering"] == n_c
     idx.close()
+
+
+def test_leaf_cap_autotune_picks_a_capacity_with_identical_results(case):
+    torch, dev = torch_dev()
+    t, want = case
+    from paper_1411_3212_gb300 import mqr
+    from paper_1411_3212_gb300.autotune import tune_leaf_cap
+    ticks = [(to_dev(t.ids, dev), to_dev(t.xy, dev), to_dev(t.rects, dev))]
+    best, table = tune_leaf_cap(lambda cap: mqr.Index(bounds=(0.0, 0.0, 1.0, 1.0), leaf_cap=cap, max_objects=30000),
+                                ticks, caps=(8, 32, 128), reps=2)
+    assert best in (8, 32, 128) and set(table) == {8, 32, 128}
+    assert {v["results"] for v in table.values()} == {int(want[1].shape[0])}
+    assert all(v["ms_per_tick"] > 0 for v in table.values())
