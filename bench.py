@@ -326,7 +326,11 @@ def run_gpu(args, name):
     flush = torch.empty(args.flush_mb * (1 << 20) // 4, dtype=torch.int32, device=dev)
 
     cap = args.leaf_cap or w["cap"]
-    idx = mqr.Index(bounds=(0.0, 0.0, 1.0, 1.0), leaf_cap=cap, max_objects=nmax)
+    if args.index == "ug":                               # uniform grid of 2^grid_level cells per axis
+        idx = mqr.Index(bounds=(0.0, 0.0, 1.0, 1.0), leaf_cap=1, max_objects=nmax, index_kind=1,
+                        grid_level=args.grid_level)
+    else:
+        idx = mqr.Index(bounds=(0.0, 0.0, 1.0, 1.0), leaf_cap=cap, max_objects=nmax)
     if batched:
         idx.set_worlds(ticks[0].obj_base)
         idx.set_query_worlds(ticks[0].q_base)
@@ -429,7 +433,9 @@ def run_gpu(args, name):
         "value": value, "unit": "queries/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": mean_ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32", "data": "synthetic",
-        "config": {"workload": w["desc"], "objects": nmax, "queries_per_tick": Q, "leaf_cap": cap,
+        "config": {"workload": w["desc"], "objects": nmax, "queries_per_tick": Q,
+                   "index": "quadtree" if args.index == "quad" else "uniform grid level %d" % args.grid_level,
+                   "leaf_cap": cap,
                    "output": args.kind, "parallelism": "replicas" if world > 1 else "single-gpu",
                    "l2": "flushed (%d MB write) between timed steps" % args.flush_mb,
                    "ticks": "%d distinct generated ticks, cycled over the %d timed steps" % (uniq, args.steps)},
@@ -571,6 +577,8 @@ def main():
     ap.add_argument("--cpu-sample", type=int, default=400000)
     ap.add_argument("--ref-sample", type=int, default=10000)
     ap.add_argument("--leaf-cap", type=int, default=0, help="override the workload's leaf capacity")
+    ap.add_argument("--index", default="quad", choices=["quad", "ug"], help="quadtree or uniform grid")
+    ap.add_argument("--grid-level", type=int, default=8, help="uniform grid: 2^level cells per axis")
     ap.add_argument("--served", action="store_true", help="run the served stream instead")
     ap.add_argument("--rate", type=float, default=5.0e6, help="served: query arrivals per second")
     ap.add_argument("--dt-ms", type=float, default=10.0, help="served: tick duration")
