@@ -147,7 +147,7 @@ void launch_key_histograms(cudaStream_t st, const unsigned long long *keys, uint
 // Status layout: status[digit * num_tiles + tile].
 // ---------------------------------------------------------------------------
 template <bool FINAL, bool PRE>
-__global__ void __launch_bounds__(kSortThreads)
+__global__ void __launch_bounds__(kSortThreads, 3)     // 40 registers: 3 tiles in flight per SM
 onesweep_kernel(const unsigned long long *__restrict__ in, unsigned long long *__restrict__ out,
                 uint32_t n, int shift, const uint32_t *__restrict__ hist256, uint32_t *status,
                 uint32_t *tile_counter, unsigned long long *err, const float2 *__restrict__ pos,
