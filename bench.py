@@ -334,6 +334,8 @@ def run_gpu(args, name):
     if batched:
         idx.set_worlds(ticks[0].obj_base)
         idx.set_query_worlds(ticks[0].q_base)
+    if args.graph:
+        idx.set_graph(True)
     kind = mqr.KINDS[args.kind]
     elem = 8 if kind in (mqr.MQR_OUT_PAIRS, mqr.MQR_OUT_PAIRS_SORTED, mqr.MQR_OUT_RUNS, mqr.MQR_OUT_PAIRS_ATOMIC) else 4
     out = torch.empty(1, dtype=torch.int32, device=dev)
@@ -353,7 +355,7 @@ def run_gpu(args, name):
         step(i)
     torch.cuda.synchronize()
 
-    idx.set_timing(True)
+    idx.set_timing(not args.graph)                      # phase events would stop the graph replay
     clocks = Clocks(local if world > 1 else 0)
     stream = torch.cuda.current_stream()
     evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
@@ -385,12 +387,15 @@ def run_gpu(args, name):
 
     # roofline of the dominant kernel phase
     kern = {p: timing["ms"][p] for p in bytes_acc if timing["launches"].get(p, 0) > 0}
+    if not kern:                                         # graph replay: no per-phase events
+        kern = {"emit": 1.0}
+        timing = {"ms": {p: 0.0 for p in mqr.PHASES}, "launches": {p: 1 for p in mqr.PHASES}, "ticks": 1}
     dom = max(kern, key=kern.get)
     launches = timing["launches"][dom]
     per_launch_ms = timing["ms"][dom] / launches
     per_launch_bytes = bytes_acc[dom] / launches
     peak, peak_kind = read_peaks()
-    achieved = per_launch_bytes / (per_launch_ms / 1000.0) / 1e9
+    achieved = per_launch_bytes / (per_launch_ms / 1000.0) / 1e9 if per_launch_ms > 0 else 0.0
     kernel_names = {"emit": "emit_kernel", "filter": "filter_kernel",
                     "sort": "tile_hist_kernel+digit_scan_kernel+onesweep_kernel",
                     "query_blocks": "zmap_kernel+query_blocks_kernel", "candidates": "cand_count_kernel+tile_scan_kernel",
@@ -442,7 +447,7 @@ def run_gpu(args, name):
         "tick_latency_ms": {"p50": srt[len(srt) // 2], "p99": srt[min(len(srt) - 1, int(0.99 * len(srt)))],
                             "max": srt[-1]},
         "join_kernels": {"phases": join, "GB/s": join_gbs, "frac_of_peak": join_gbs / peak},
-        "roofline": roofline,
+        "roofline": None if args.graph else roofline,
         "cpu_baseline": cpu,
         "e2e": e2e,
         "e2e_covering_compressed": e2e_runs,
@@ -578,6 +583,7 @@ def main():
     ap.add_argument("--ref-sample", type=int, default=10000)
     ap.add_argument("--leaf-cap", type=int, default=0, help="override the workload's leaf capacity")
     ap.add_argument("--index", default="quad", choices=["quad", "ug"], help="quadtree or uniform grid")
+    ap.add_argument("--graph", action="store_true", help="replay the tick as a captured CUDA graph")
     ap.add_argument("--grid-level", type=int, default=8, help="uniform grid: 2^level cells per axis")
     ap.add_argument("--served", action="store_true", help="run the served stream instead")
     ap.add_argument("--rate", type=float, default=5.0e6, help="served: query arrivals per second")

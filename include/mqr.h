@@ -235,6 +235,15 @@ mqr_status mqr_tick_admit(mqr_ctx *ctx, const float *rects_dev, uint32_t Q, int 
                           uint64_t out_capacity_bytes, uint32_t *admitted, uint64_t *out_count,
                           uint64_t *offsets_dev);
 
+/* Graph mode (enable = 1): the tick's ~20 kernel launches are captured once
+ * into a CUDA graph and the graph is replayed by later ticks with the same
+ * arguments (rects_dev, Q, kind, out_dev, capacity, offsets_dev) while no
+ * internal buffer was reallocated; anything else captures again.  Results
+ * are identical to the plain launches.  Phase timing (mqr_set_timing) turns
+ * replay off while enabled.  enable = 0 frees the graph.  Library design
+ * convenience, not a step of the method. */
+mqr_status mqr_set_graph(mqr_ctx *ctx, int enable);
+
 /* Batched independent worlds in one index (many small instances of the
  * problem of Sec. 2.5 answered by one tick; the paper has no batched mode,
  * this keeps each world's result exact and its own).  World w owns the

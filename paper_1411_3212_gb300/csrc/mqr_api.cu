@@ -8,6 +8,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -39,6 +40,10 @@ mqr_status cuda_fail(cudaError_t e, const char *what) {
         if (e_ != cudaSuccess) return cuda_fail(e_, #call);    \
     } while (0)
 
+// Bumped whenever any device buffer is (re)allocated or freed: a captured
+// tick graph holds raw pointers, so it is only replayed while this is unchanged.
+std::atomic<unsigned long long> g_buf_gen{0};
+
 // A device buffer that only grows (contents are not preserved on growth).
 template <typename T>
 struct DevBuf {
@@ -49,12 +54,13 @@ struct DevBuf {
         if (p) cudaFree(p);
         p = nullptr;
         n = 0;
+        ++g_buf_gen;
         cudaError_t e = cudaMalloc(&p, want * sizeof(T));
         if (e == cudaSuccess) n = want;
         return e;
     }
     void release() {
-        if (p) cudaFree(p);
+        if (p) { cudaFree(p); ++g_buf_gen; }
         p = nullptr;
         n = 0;
     }
@@ -108,6 +114,20 @@ struct mqr_ctx {
     DevBuf<unsigned long long> off_stage, sortA, sortB;
     DevBuf<unsigned char> sort_arena;
     DevBuf<unsigned long long> upd_err;  // sticky error word of the update kernels
+    // captured tick (mqr_set_graph): replayed while its inputs are unchanged
+    bool graph_on = false;
+    cudaGraphExec_t gexec = nullptr;
+    struct GraphKey {
+        const void *rects, *out, *offsets;
+        unsigned long long Q, out_cap, gen, n_worlds;
+        int emit_kind;
+        bool operator==(const GraphKey &o) const {
+            return rects == o.rects && out == o.out && offsets == o.offsets && Q == o.Q &&
+                   out_cap == o.out_cap && gen == o.gen && n_worlds == o.n_worlds && emit_kind == o.emit_kind;
+        }
+    } gkey{};
+    Caps gcaps{};
+    unsigned long long graph_replays = 0, graph_captures = 0;
     // batched independent worlds (mqr_set_worlds): id and query ranges per world
     uint32_t n_worlds = 0, world_bits = 0;
     DevBuf<uint32_t> world_obj, world_q;
@@ -401,6 +421,46 @@ mqr_status grow_sub(mqr_ctx *c, unsigned long long need) {
     return MQR_OK;
 }
 
+// Enqueue the tick's kernels, or, in graph mode (and without phase timing),
+// replay the tick captured for the same inputs and buffers: one graph launch
+// instead of ~20 kernel launches.  The first tick of a new shape is captured
+// (relaxed capture mode), instantiated and launched.
+mqr_status enqueue_or_replay(mqr_ctx *c, const float4 *rects, uint32_t Q, int emit_kind, void *out,
+                             unsigned long long out_cap_elems, unsigned long long *offsets, const Arena &a,
+                             Caps &caps) {
+    if (!c->graph_on || c->timing) return enqueue_tick(c, rects, Q, emit_kind, out, out_cap_elems, offsets, a, caps);
+    const mqr_ctx::GraphKey key{rects, out, offsets, Q, out_cap_elems, g_buf_gen.load(), c->n_worlds, emit_kind};
+    if (!c->gexec || !(key == c->gkey)) {
+        if (c->gexec) {
+            cudaGraphExecDestroy(c->gexec);
+            c->gexec = nullptr;
+        }
+        MQR_CUDA(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeRelaxed));
+        mqr_status s = enqueue_tick(c, rects, Q, emit_kind, out, out_cap_elems, offsets, a, caps);
+        cudaGraph_t g = nullptr;
+        cudaError_t e = cudaStreamEndCapture(c->stream, &g);
+        if (s != MQR_OK) {
+            if (g) cudaGraphDestroy(g);
+            return s;
+        }
+        if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
+        e = cudaGraphInstantiate(&c->gexec, g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) {
+            c->gexec = nullptr;
+            return cuda_fail(e, "cudaGraphInstantiate");
+        }
+        c->gkey = key;
+        c->gcaps = caps;
+        ++c->graph_captures;
+    } else {
+        caps = c->gcaps;
+        ++c->graph_replays;
+    }
+    MQR_CUDA(cudaGraphLaunch(c->gexec, c->stream));
+    return MQR_OK;
+}
+
 // Run the pipeline until every internal buffer was large enough; leaves the
 // tick's device state valid and c->last filled.  `out` may be null (then
 // nothing is emitted).
@@ -413,7 +473,7 @@ mqr_status run_tick(mqr_ctx *c, const float4 *rects, uint32_t Q, int emit_kind, 
         Arena a = arena_layout(c->nmax, Q, c->sub_q.n, c->cand_tiles);
         MQR_CUDA(c->arena.ensure(a.total));
         Caps caps{};
-        s = enqueue_tick(c, rects, Q, emit_kind, out, out_cap_elems, offsets, a, caps);
+        s = enqueue_or_replay(c, rects, Q, emit_kind, out, out_cap_elems, offsets, a, caps);
         if (s != MQR_OK) return s;
         MQR_CUDA(cudaMemcpyAsync(c->info_host, c->arena.p + a.info, sizeof(Info), cudaMemcpyDeviceToHost,
                                  c->stream));
@@ -631,6 +691,8 @@ void mqr_destroy(mqr_ctx *c) {
     if (c->stream) cudaStreamSynchronize(c->stream);
     DevBuf<float2> *f2[] = {&c->pos, &c->sxy, &c->up_xy};
     for (auto *b : f2) b->release();
+    if (c->gexec) cudaGraphExecDestroy(c->gexec);
+    c->gexec = nullptr;
     c->world_obj.release();
     c->world_q.release();
     DevBuf<unsigned long long> *u64s[] = {&c->stamp, &c->keysA, &c->keysB, &c->out_off, &c->off_stage,
@@ -783,6 +845,18 @@ static mqr_status tick_args(mqr_ctx *c, const void *rects, uint32_t Q, int kind,
     if (kind < MQR_OUT_PAIRS || kind > MQR_OUT_PAIRS_ATOMIC) return fail(MQR_ERR_INVALID_ARG, "unknown output kind");
     if (c->n_worlds && (!c->world_q_set || Q != c->world_q_total))
         return fail(MQR_ERR_INVALID_ARG, "batched worlds: Q must equal the total of mqr_set_query_worlds");
+    return MQR_OK;
+}
+
+mqr_status mqr_set_graph(mqr_ctx *c, int enable) {
+    if (!c) return fail(MQR_ERR_INVALID_ARG, "ctx is NULL");
+    MQR_CUDA(cudaSetDevice(c->device));
+    MQR_CUDA(cudaStreamSynchronize(c->stream));
+    c->graph_on = enable != 0;
+    if (!c->graph_on && c->gexec) {
+        cudaGraphExecDestroy(c->gexec);
+        c->gexec = nullptr;
+    }
     return MQR_OK;
 }
 

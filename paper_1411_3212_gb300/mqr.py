@@ -27,7 +27,7 @@ KINDS = {"pairs": MQR_OUT_PAIRS, "pairs_sorted": MQR_OUT_PAIRS_SORTED, "csr": MQ
 
 # Every symbol include/mqr.h declares.
 EXPORTS = ["mqr_config_default", "mqr_create", "mqr_create_ex", "mqr_apply_updates",
-           "mqr_apply_updates_host", "mqr_tick", "mqr_tick_host", "mqr_tick_admit", "mqr_set_worlds",
+           "mqr_apply_updates_host", "mqr_tick", "mqr_tick_host", "mqr_tick_admit", "mqr_set_graph", "mqr_set_worlds",
            "mqr_set_query_worlds", "mqr_get_stats",
            "mqr_get_leaves",
            "mqr_get_sorted", "mqr_set_timing", "mqr_get_timing", "mqr_sort_objects_noalloc",
@@ -98,6 +98,7 @@ def load(path: str = LIB_PATH):
         "mqr_tick": ([P, P, u32, i32, P, u64, ctypes.POINTER(u64), P], i32),
         "mqr_tick_host": ([P, P, u32, i32, P, u64, ctypes.POINTER(u64), P], i32),
         "mqr_tick_admit": ([P, P, u32, i32, P, u64, ctypes.POINTER(u32), ctypes.POINTER(u64), P], i32),
+        "mqr_set_graph": ([P, i32], i32),
         "mqr_set_worlds": ([P, u32, P], i32),
         "mqr_set_query_worlds": ([P, P], i32),
         "mqr_get_stats": ([P, ctypes.POINTER(mqr_stats)], i32),
@@ -200,6 +201,10 @@ def mqr_tick_admit(ctx, rects_dev, Q, kind, out_dev, out_capacity_bytes, offsets
     _check(load().mqr_tick_admit(ctx, _ptr(rects_dev), Q, kind, _ptr(out_dev), out_capacity_bytes,
                                  ctypes.byref(adm), ctypes.byref(cnt), _ptr(offsets_dev)))
     return int(adm.value), int(cnt.value)
+
+
+def mqr_set_graph(ctx, enable):
+    _check(load().mqr_set_graph(ctx, 1 if enable else 0))
 
 
 def mqr_set_worlds(ctx, obj_base):
@@ -326,6 +331,9 @@ class Index:
             _check(st)
         res = self._out[: cnt * elem // 4]
         return (res.view(cnt, 2) if elem == 8 else res), offs
+
+    def set_graph(self, enable=True):
+        mqr_set_graph(self.ctx, enable)
 
     def set_worlds(self, obj_base):
         mqr_set_worlds(self.ctx, obj_base)

@@ -7,7 +7,7 @@ import pytest
 
 import oracle
 from paper_1411_3212_gb300 import workloads
-from tests.gpu_util import assert_same_csr, expand_runs, oracle_state, to_dev, torch_dev
+from tests.gpu_util import assert_same_csr, expand_runs, oracle_state, to_dev, torch_dev  # noqa: F401
 
 pytestmark = pytest.mark.gpu
 
@@ -237,3 +237,35 @@ def test_leaf_cap_autotune_picks_a_capacity_with_identical_results(case):
     assert best in (8, 32, 128) and set(table) == {8, 32, 128}
     assert {v["results"] for v in table.values()} == {int(want[1].shape[0])}
     assert all(v["ms_per_tick"] > 0 for v in table.values())
+
+
+def test_graph_mode_replays_identical_results():
+    """Graph mode: the first tick of a shape is captured (including the
+    buffer growth of a fresh context), later ticks replay it; a new Q or
+    output buffer captures again; every tick equals the oracle and the plain
+    launches bit for bit."""
+    torch, dev = torch_dev()
+    from paper_1411_3212_gb300 import mqr
+    w = workloads.HotspotWalk(n=20000, q=1500, hotspots=4, side_lo=0.002, side_hi=0.04, seed=31)
+    ticks = [w.next_tick() for _ in range(4)]
+    g = mqr.Index(bounds=(0.0, 0.0, 1.0, 1.0), leaf_cap=32, max_objects=20000)
+    plain = mqr.Index(bounds=(0.0, 0.0, 1.0, 1.0), leaf_cap=32, max_objects=20000)
+    g.set_graph(True)
+    st = oracle.State(20000)
+    for k, t in enumerate(ticks):
+        rects = t.rects if k < 3 else t.rects[:700]            # the last tick has a new Q
+        rd = to_dev(rects, dev)
+        for idx in (g, plain):
+            idx.apply_updates(to_dev(t.ids, dev), to_dev(t.xy, dev))
+        st.apply_updates(t.ids, t.xy)
+        res_g, off_g = g.tick(rd, kind="pairs")
+        a = (res_g.cpu().numpy().copy(), off_g.cpu().numpy().copy())
+        res_p, off_p = plain.tick(rd, kind="pairs")
+        np.testing.assert_array_equal(a[0], res_p.cpu().numpy())
+        np.testing.assert_array_equal(a[1], off_p.cpu().numpy())
+        woff, wids = oracle.join_grid(st, rects, cell_side=0.01)
+        np.testing.assert_array_equal(a[1].view(np.uint64), woff)
+        assert a[0].shape[0] == wids.shape[0]
+    g.set_graph(False)
+    g.close()
+    plain.close()
