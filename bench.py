@@ -566,6 +566,73 @@ def run_served(args):
     print(json.dumps(line), flush=True)
 
 
+def run_costmodel(args):
+    """--costmodel: the index configuration chosen per tick by the learned
+    cost model (leaf capacities 64..512 and the uniform grid at levels 8 and
+    9) against the fixed workload configuration, on the same ticks."""
+    import torch
+    from paper_1411_3212_gb300 import mqr
+    from paper_1411_3212_gb300.costmodel import GRID, QUAD, IndexChooser, mean_log2_side
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    name = args.workload
+    w = WORKLOADS[name]
+    nmax, Q = w["n"], w["q"]
+    uniq = min(args.steps, args.unique_ticks)
+    ticks = gen_ticks(name, 0, args.warmup + uniq)
+    ids_d = torch.from_numpy(ticks[0].ids.view(np.int32)).to(dev)
+    xy_d = [torch.from_numpy(t.xy).to(dev) for t in ticks]
+    rect_d = [torch.from_numpy(t.rects).to(dev) for t in ticks]
+    sides = [mean_log2_side(t.rects) for t in ticks]
+    idx = mqr.Index(bounds=(0.0, 0.0, 1.0, 1.0), leaf_cap=w["cap"], max_objects=nmax)
+    out = torch.empty(1, dtype=torch.int32, device=dev)
+
+    def tick(i):
+        nonlocal out
+        idx.apply_updates(ids_d, xy_d[i])
+        st, cnt = mqr.mqr_tick(idx.ctx, rect_d[i], Q, mqr.MQR_OUT_PAIRS, out, out.numel() * 4)
+        if st == mqr.MQR_ERR_CAPACITY:
+            out = torch.empty(int(cnt * 2 * 1.3) + 1024, dtype=torch.int32, device=dev)
+            st, cnt = mqr.mqr_tick(idx.ctx, rect_d[i], Q, mqr.MQR_OUT_PAIRS, out, out.numel() * 4)
+        mqr._check(st)
+
+    def timed(i):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        tick(i)
+        b.record()
+        b.synchronize()
+        return a.elapsed_time(b)
+
+    for i in range(args.warmup):
+        tick(i)
+    fixed = [timed(args.warmup + (k % uniq)) for k in range(args.steps)]
+    cands = [(QUAD, 64), (QUAD, 128), (QUAD, 256), (QUAD, 512), (GRID, 8), (GRID, 9)]
+    ch = IndexChooser(candidates=cands, fallback=(QUAD, w["cap"]), seed=0)
+    chosen, times = [], []
+    for k in range(args.steps):
+        i = args.warmup + (k % uniq)
+        c = ch.choose(nmax, Q, sides[i])
+        ch.apply(idx, c)
+        ms = timed(i)
+        ch.record(c, nmax, Q, sides[i], ms)
+        chosen.append(c)
+        times.append(ms)
+    idx.close()
+    ch.close()
+    tail = max(1, args.steps // 2)
+    counts = {}
+    for c in chosen[-tail:]:
+        key = ("leaf_cap %d" % c[1]) if c[0] == QUAD else ("grid level %d" % c[1])
+        counts[key] = counts.get(key, 0) + 1
+    line = {"metric": "ms per tick, learned per-tick index choice vs fixed", "unit": "ms",
+            "config": {"workload": w["desc"], "candidates": [list(c) for c in cands], "steps": args.steps},
+            "fixed_ms_mean": float(np.mean(fixed[-tail:])), "chosen_ms_mean": float(np.mean(times[-tail:])),
+            "explore_ms_mean": float(np.mean(times[:2 * len(cands)])), "chosen_last_half": counts,
+            "model_loss": getattr(ch, "loss", None)}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -586,6 +653,7 @@ def main():
     ap.add_argument("--graph", action="store_true", help="replay the tick as a captured CUDA graph")
     ap.add_argument("--grid-level", type=int, default=8, help="uniform grid: 2^level cells per axis")
     ap.add_argument("--served", action="store_true", help="run the served stream instead")
+    ap.add_argument("--costmodel", action="store_true", help="learned per-tick index choice vs fixed")
     ap.add_argument("--rate", type=float, default=5.0e6, help="served: query arrivals per second")
     ap.add_argument("--dt-ms", type=float, default=10.0, help="served: tick duration")
     ap.add_argument("--served-ticks", type=int, default=100)
@@ -600,6 +668,8 @@ def main():
         args.warmup = 3
     if args.served:
         run_served(args)
+    elif args.costmodel:
+        run_costmodel(args)
     elif args.impl == "reference":
         run_reference(args, args.workload)
     else:

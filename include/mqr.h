@@ -266,6 +266,44 @@ mqr_status mqr_set_worlds(mqr_ctx *ctx, uint32_t n_worlds, const uint32_t *obj_b
  * query index and object id. */
 mqr_status mqr_set_query_worlds(mqr_ctx *ctx, const uint32_t *q_base_host);
 
+/* Change the index between ticks (leaves are rebuilt every tick, Alg. 1):
+ * index_kind MQR_INDEX_QUADTREE with leaf_cap >= 1 (th_quad), or
+ * MQR_INDEX_UNIFORM_GRID with 1 <= grid_level <= 15 (and >= the batched
+ * worlds' levels).  Results never depend on the choice; time does.  Errors:
+ * INVALID_ARG. */
+mqr_status mqr_set_index(mqr_ctx *ctx, int index_kind, uint32_t leaf_cap, uint32_t grid_level);
+
+/* Learned tick-cost model: a multilayer perceptron 5 -> 64 -> 64 -> 1 with
+ * ReLU hidden layers, trained on the device (hand-written forward, backward
+ * and Adam kernels, one block) to map tick features to the logarithm of the
+ * tick's time, so that a caller can pick the index configuration of the next
+ * tick (mqr_set_index).  The paper models its phases' costs analytically
+ * (the filtering complexity of Sec. 5.4); this learns the cost from
+ * measurements instead.  Parameters (mqr_cost_param_count() floats):
+ * W1[64][5], b1[64], W2[64][64], b2[64], W3[64], b3, row-major, host
+ * arrays.  The model lives on the current device with its own stream. */
+typedef struct mqr_cost mqr_cost;
+uint32_t mqr_cost_param_count(void);
+/* Parameters start at zero: set an initialisation with mqr_cost_set_params. */
+mqr_status mqr_cost_create(mqr_cost **out);
+/* Replace the parameters (host array) and reset the optimiser state. */
+mqr_status mqr_cost_set_params(mqr_cost *m, const float *params_host, uint32_t n_params);
+mqr_status mqr_cost_get_params(mqr_cost *m, float *params_host, uint32_t n_params);
+/* `epochs` full-batch Adam steps (beta 0.9 / 0.999, eps 1e-8, bias-corrected)
+ * of the mean squared error over the n samples X_host[n][5] -> y_host[n];
+ * *loss_out (may be NULL) = the loss before the last step.  Blocks. */
+mqr_status mqr_cost_train(mqr_cost *m, const float *X_host, const float *y_host, uint32_t n, uint32_t epochs,
+                          float lr, float *loss_out);
+/* The gradient of the mean squared error over the n samples with respect to
+ * the parameters (grad_host: mqr_cost_param_count() floats), computed by the
+ * training kernel's backward pass without updating anything; *loss_out (may
+ * be NULL) = the loss.  n >= 1.  Blocks. */
+mqr_status mqr_cost_gradient(mqr_cost *m, const float *X_host, const float *y_host, uint32_t n, float *grad_host,
+                             float *loss_out);
+/* out_host[i] = model(X_host[i]) for n samples.  Blocks. */
+mqr_status mqr_cost_predict(mqr_cost *m, const float *X_host, uint32_t n, float *out_host);
+void mqr_cost_destroy(mqr_cost *m);
+
 /* Counters of the last completed tick. */
 mqr_status mqr_get_stats(const mqr_ctx *ctx, mqr_stats *out);
 

@@ -1,0 +1,96 @@
+"""Per-tick choice of the index configuration by a learned cost model.
+
+Every index configuration answers every tick exactly (the index only decides
+how much work the filter does, never a result), so the configuration of the
+next tick can be chosen for speed alone.  The paper reasons about that cost
+analytically (the filtering complexity of Sec. 5.4; the estimated number of
+intersecting subqueries of Sec. 6) and fixes the quadtree threshold per
+experiment; here an MLP (5 -> 64 -> 64 -> 1, trained on the device by the
+library's own kernels, `mqr_cost_*`) learns log(tick time) from the ticks
+already run, and the chooser takes the configuration with the smallest
+prediction -- after a round-robin exploration of the candidates, with a
+small exploration rate afterwards, and the fixed configuration as fallback
+while there is too little data.
+
+Features of a (tick, configuration): log2 objects, log2 queries, the mean
+log2 of the query sides, log2 of the objects per leaf the configuration aims
+for (leaf capacity, or objects per grid cell for the uniform grid), and
+whether it is the uniform grid.  Scheduling and marshalling only: the ticks
+and the model's arithmetic run in the library's kernels.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+from . import mqr
+
+QUAD, GRID = 0, 1
+
+
+def he_uniform_params(seed: int) -> np.ndarray:
+    """Initial parameters in the C ABI layout (W1, b1, W2, b2, W3, b3)."""
+    rng = np.random.default_rng(seed)
+    w1 = rng.uniform(-1, 1, (64, 5)) * math.sqrt(6.0 / 5)
+    w2 = rng.uniform(-1, 1, (64, 64)) * math.sqrt(6.0 / 64)
+    w3 = rng.uniform(-1, 1, 64) * math.sqrt(6.0 / 64)
+    return np.concatenate([w1.ravel(), np.zeros(64), w2.ravel(), np.zeros(64), w3, [0.0]]).astype(np.float32)
+
+
+class IndexChooser:
+    def __init__(self, candidates=((QUAD, 64), (QUAD, 128), (QUAD, 256), (QUAD, 512)),
+                 fallback=(QUAD, 128), explore_rounds=2, epsilon=0.1, retrain_every=4, epochs=400, lr=3e-3,
+                 seed=0):
+        self.cands = [tuple(c) for c in candidates]
+        self.fallback = tuple(fallback)
+        self.explore_rounds = explore_rounds
+        self.epsilon = epsilon
+        self.retrain_every = retrain_every
+        self.epochs, self.lr = epochs, lr
+        self.rng = np.random.default_rng(seed)
+        self.model = mqr.CostModel(he_uniform_params(seed))
+        self.X, self.y = [], []
+        self.trained = False
+        self.n_choices = 0
+
+    @staticmethod
+    def features(cand, n_objects, n_queries, mean_log2_side):
+        kind, v = cand
+        per_leaf = v if kind == QUAD else max(n_objects / float(4 ** v), 1e-3)
+        return np.array([math.log2(max(n_objects, 1)) / 32.0, math.log2(max(n_queries, 1)) / 32.0,
+                         mean_log2_side / 16.0, math.log2(per_leaf) / 16.0, float(kind == GRID)], np.float32)
+
+    def choose(self, n_objects, n_queries, mean_log2_side):
+        k = self.n_choices
+        self.n_choices += 1
+        if k < self.explore_rounds * len(self.cands):                 # round-robin exploration
+            return self.cands[k % len(self.cands)]
+        if not self.trained:
+            return self.fallback
+        if self.rng.random() < self.epsilon:
+            return self.cands[int(self.rng.integers(len(self.cands)))]
+        X = np.stack([self.features(c, n_objects, n_queries, mean_log2_side) for c in self.cands])
+        return self.cands[int(np.argmin(self.model.predict(X)))]
+
+    def record(self, cand, n_objects, n_queries, mean_log2_side, ms):
+        self.X.append(self.features(cand, n_objects, n_queries, mean_log2_side))
+        self.y.append(math.log(max(ms, 1e-6)))
+        if len(self.y) >= len(self.cands) and len(self.y) % self.retrain_every == 0:
+            self.loss = self.model.train(np.stack(self.X), np.array(self.y, np.float32), self.epochs, self.lr)
+            self.trained = True
+
+    def apply(self, idx, cand):
+        kind, v = cand
+        if kind == QUAD:
+            idx.set_index(QUAD, leaf_cap=v)
+        else:
+            idx.set_index(GRID, grid_level=v)
+
+    def close(self):
+        self.model.close()
+
+
+def mean_log2_side(rects: np.ndarray) -> float:
+    s = np.maximum(np.maximum(rects[:, 2] - rects[:, 0], rects[:, 3] - rects[:, 1]), 1e-9)
+    return float(np.mean(np.log2(s)))

@@ -672,6 +672,138 @@ extern "C" {
 
 const char *mqr_last_error(void) { return g_err.c_str(); }
 
+struct mqr_cost {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    DevBuf<float> params, m, v, X, y, out, loss;
+    uint32_t steps = 0;
+};
+
+uint32_t mqr_cost_param_count(void) { return (uint32_t)cost_param_count(); }
+
+mqr_status mqr_cost_create(mqr_cost **out) {
+    if (!out) return fail(MQR_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    mqr_cost *m = new (std::nothrow) mqr_cost();
+    if (!m) return fail(MQR_ERR_OOM, "host allocation failed");
+    const size_t P = cost_param_count();
+    cudaError_t e = cudaGetDevice(&m->device);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&m->stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = m->params.ensure(P);
+    if (e == cudaSuccess) e = m->m.ensure(P);
+    if (e == cudaSuccess) e = m->v.ensure(P);
+    if (e == cudaSuccess) e = m->loss.ensure(1);
+    if (e == cudaSuccess) e = cudaMemset(m->params.p, 0, P * 4);
+    if (e == cudaSuccess) e = cudaMemset(m->m.p, 0, P * 4);
+    if (e == cudaSuccess) e = cudaMemset(m->v.p, 0, P * 4);
+    if (e != cudaSuccess) {
+        mqr_cost_destroy(m);
+        return cuda_fail(e, "mqr_cost_create");
+    }
+    *out = m;
+    return MQR_OK;
+}
+
+mqr_status mqr_cost_set_params(mqr_cost *m, const float *params_host, uint32_t n_params) {
+    if (!m || !params_host) return fail(MQR_ERR_INVALID_ARG, "NULL argument");
+    if (n_params != cost_param_count()) return fail(MQR_ERR_INVALID_ARG, "wrong parameter count");
+    MQR_CUDA(cudaSetDevice(m->device));
+    MQR_CUDA(cudaMemcpy(m->params.p, params_host, (size_t)n_params * 4, cudaMemcpyHostToDevice));
+    MQR_CUDA(cudaMemset(m->m.p, 0, (size_t)n_params * 4));
+    MQR_CUDA(cudaMemset(m->v.p, 0, (size_t)n_params * 4));
+    m->steps = 0;
+    return MQR_OK;
+}
+
+mqr_status mqr_cost_get_params(mqr_cost *m, float *params_host, uint32_t n_params) {
+    if (!m || !params_host) return fail(MQR_ERR_INVALID_ARG, "NULL argument");
+    if (n_params != cost_param_count()) return fail(MQR_ERR_INVALID_ARG, "wrong parameter count");
+    MQR_CUDA(cudaSetDevice(m->device));
+    MQR_CUDA(cudaStreamSynchronize(m->stream));
+    MQR_CUDA(cudaMemcpy(params_host, m->params.p, (size_t)n_params * 4, cudaMemcpyDeviceToHost));
+    return MQR_OK;
+}
+
+mqr_status mqr_cost_train(mqr_cost *m, const float *X_host, const float *y_host, uint32_t n, uint32_t epochs,
+                          float lr, float *loss_out) {
+    if (!m || (n && (!X_host || !y_host))) return fail(MQR_ERR_INVALID_ARG, "NULL argument");
+    if (n == 0 || epochs == 0) return MQR_OK;
+    if (!(lr > 0.f)) return fail(MQR_ERR_INVALID_ARG, "lr must be > 0");
+    MQR_CUDA(cudaSetDevice(m->device));
+    MQR_CUDA(m->X.ensure((size_t)n * 5));
+    MQR_CUDA(m->y.ensure(n));
+    MQR_CUDA(cudaMemcpyAsync(m->X.p, X_host, (size_t)n * 5 * 4, cudaMemcpyHostToDevice, m->stream));
+    MQR_CUDA(cudaMemcpyAsync(m->y.p, y_host, (size_t)n * 4, cudaMemcpyHostToDevice, m->stream));
+    MQR_CUDA(launch_cost_train(m->stream, m->params.p, m->m.p, m->v.p, m->steps, m->X.p, m->y.p, n, epochs, lr,
+                               m->loss.p, nullptr));
+    m->steps += epochs;
+    float l = 0.f;
+    MQR_CUDA(cudaMemcpyAsync(&l, m->loss.p, 4, cudaMemcpyDeviceToHost, m->stream));
+    MQR_CUDA(cudaStreamSynchronize(m->stream));
+    if (loss_out) *loss_out = l;
+    return MQR_OK;
+}
+
+mqr_status mqr_cost_gradient(mqr_cost *m, const float *X_host, const float *y_host, uint32_t n, float *grad_host,
+                             float *loss_out) {
+    if (!m || !grad_host || (n && (!X_host || !y_host))) return fail(MQR_ERR_INVALID_ARG, "NULL argument");
+    if (n == 0) return fail(MQR_ERR_INVALID_ARG, "n must be >= 1");
+    const size_t P = cost_param_count();
+    MQR_CUDA(cudaSetDevice(m->device));
+    MQR_CUDA(m->X.ensure((size_t)n * 5));
+    MQR_CUDA(m->y.ensure(n));
+    MQR_CUDA(m->out.ensure(std::max<size_t>(P, n)));
+    MQR_CUDA(cudaMemcpyAsync(m->X.p, X_host, (size_t)n * 5 * 4, cudaMemcpyHostToDevice, m->stream));
+    MQR_CUDA(cudaMemcpyAsync(m->y.p, y_host, (size_t)n * 4, cudaMemcpyHostToDevice, m->stream));
+    MQR_CUDA(launch_cost_train(m->stream, m->params.p, m->m.p, m->v.p, m->steps, m->X.p, m->y.p, n, 1, 1.f,
+                               m->loss.p, m->out.p));
+    float l = 0.f;
+    MQR_CUDA(cudaMemcpyAsync(grad_host, m->out.p, P * 4, cudaMemcpyDeviceToHost, m->stream));
+    MQR_CUDA(cudaMemcpyAsync(&l, m->loss.p, 4, cudaMemcpyDeviceToHost, m->stream));
+    MQR_CUDA(cudaStreamSynchronize(m->stream));
+    if (loss_out) *loss_out = l;
+    return MQR_OK;
+}
+
+mqr_status mqr_cost_predict(mqr_cost *m, const float *X_host, uint32_t n, float *out_host) {
+    if (!m || (n && (!X_host || !out_host))) return fail(MQR_ERR_INVALID_ARG, "NULL argument");
+    if (n == 0) return MQR_OK;
+    MQR_CUDA(cudaSetDevice(m->device));
+    MQR_CUDA(m->X.ensure((size_t)n * 5));
+    MQR_CUDA(m->out.ensure(n));
+    MQR_CUDA(cudaMemcpyAsync(m->X.p, X_host, (size_t)n * 5 * 4, cudaMemcpyHostToDevice, m->stream));
+    MQR_CUDA(launch_cost_predict(m->stream, m->params.p, m->X.p, n, m->out.p));
+    MQR_CUDA(cudaMemcpyAsync(out_host, m->out.p, (size_t)n * 4, cudaMemcpyDeviceToHost, m->stream));
+    MQR_CUDA(cudaStreamSynchronize(m->stream));
+    return MQR_OK;
+}
+
+void mqr_cost_destroy(mqr_cost *m) {
+    if (!m) return;
+    cudaSetDevice(m->device);
+    if (m->stream) cudaStreamSynchronize(m->stream);
+    m->params.release(); m->m.release(); m->v.release(); m->X.release(); m->y.release();
+    m->out.release(); m->loss.release();
+    if (m->stream) cudaStreamDestroy(m->stream);
+    delete m;
+}
+
+mqr_status mqr_set_index(mqr_ctx *c, int index_kind, uint32_t leaf_cap, uint32_t grid_level) {
+    if (!c) return fail(MQR_ERR_INVALID_ARG, "ctx is NULL");
+    if (index_kind != MQR_INDEX_QUADTREE && index_kind != MQR_INDEX_UNIFORM_GRID)
+        return fail(MQR_ERR_INVALID_ARG, "unknown index kind");
+    if (index_kind == MQR_INDEX_QUADTREE && leaf_cap == 0) return fail(MQR_ERR_INVALID_ARG, "leaf_cap must be >= 1");
+    if (index_kind == MQR_INDEX_UNIFORM_GRID && (grid_level < 1 || grid_level > 15 || grid_level < c->world_bits))
+        return fail(MQR_ERR_INVALID_ARG, "grid_level must be in 1..15 (and >= the worlds' levels)");
+    MQR_CUDA(cudaSetDevice(c->device));
+    MQR_CUDA(cudaStreamSynchronize(c->stream));
+    c->cfg.index_kind = index_kind;
+    if (index_kind == MQR_INDEX_QUADTREE) c->cfg.leaf_cap = leaf_cap;
+    else c->cfg.grid_level = grid_level;
+    ++g_buf_gen;                                   // a captured tick holds the old configuration
+    return MQR_OK;
+}
+
 mqr_status mqr_config_default(mqr_config *cfg) {
     if (!cfg) return fail(MQR_ERR_INVALID_ARG, "cfg is NULL");
     std::memset(cfg, 0, sizeof(*cfg));

@@ -423,6 +423,12 @@ void launch_atomic_baseline(cudaStream_t st, int num_sms, const float4 *rects, c
                             const uint32_t *sub_q, const uint32_t *sub_leaf, const uint32_t *sub_len, void *out,
                             unsigned long long cap, uint32_t *ticket, Caps caps, Info *info);
 
+// Learned tick-cost model (k_cost.cu): MLP 5 -> 64 -> 64 -> 1.
+size_t cost_param_count();
+cudaError_t launch_cost_train(cudaStream_t st, float *params, float *m, float *v, uint32_t step0, const float *X,
+                              const float *y, uint32_t n, uint32_t epochs, float lr, float *loss, float *grad);
+cudaError_t launch_cost_predict(cudaStream_t st, const float *params, const float *X, uint32_t n, float *out);
+
 // Admission by output memory: queries [0, A) whose output fits cap elements.
 void launch_admit(cudaStream_t st, uint32_t Q, const unsigned long long *offsets, unsigned long long cap,
                   const uint32_t *qpair, const uint32_t *pair_rec, const uint32_t *tile_off, Caps caps,

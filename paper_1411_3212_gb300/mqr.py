@@ -28,7 +28,9 @@ KINDS = {"pairs": MQR_OUT_PAIRS, "pairs_sorted": MQR_OUT_PAIRS_SORTED, "csr": MQ
 # Every symbol include/mqr.h declares.
 EXPORTS = ["mqr_config_default", "mqr_create", "mqr_create_ex", "mqr_apply_updates",
            "mqr_apply_updates_host", "mqr_tick", "mqr_tick_host", "mqr_tick_admit", "mqr_set_graph", "mqr_set_worlds",
-           "mqr_set_query_worlds", "mqr_get_stats",
+           "mqr_set_query_worlds", "mqr_set_index", "mqr_cost_param_count", "mqr_cost_create",
+           "mqr_cost_set_params", "mqr_cost_get_params", "mqr_cost_train", "mqr_cost_gradient", "mqr_cost_predict",
+           "mqr_cost_destroy", "mqr_get_stats",
            "mqr_get_leaves",
            "mqr_get_sorted", "mqr_set_timing", "mqr_get_timing", "mqr_sort_objects_noalloc",
            "mqr_last_error", "mqr_destroy"]
@@ -101,6 +103,15 @@ def load(path: str = LIB_PATH):
         "mqr_set_graph": ([P, i32], i32),
         "mqr_set_worlds": ([P, u32, P], i32),
         "mqr_set_query_worlds": ([P, P], i32),
+        "mqr_set_index": ([P, i32, u32, u32], i32),
+        "mqr_cost_param_count": ([], u32),
+        "mqr_cost_create": ([pctx], i32),
+        "mqr_cost_set_params": ([P, P, u32], i32),
+        "mqr_cost_get_params": ([P, P, u32], i32),
+        "mqr_cost_train": ([P, P, P, u32, u32, ctypes.c_float, ctypes.POINTER(ctypes.c_float)], i32),
+        "mqr_cost_gradient": ([P, P, P, u32, P, ctypes.POINTER(ctypes.c_float)], i32),
+        "mqr_cost_predict": ([P, P, u32, P], i32),
+        "mqr_cost_destroy": ([P], None),
         "mqr_get_stats": ([P, ctypes.POINTER(mqr_stats)], i32),
         "mqr_get_leaves": ([P, P, u64, ctypes.POINTER(u64)], i32),
         "mqr_get_sorted": ([P, P, P, u64, ctypes.POINTER(u64)], i32),
@@ -205,6 +216,61 @@ def mqr_tick_admit(ctx, rects_dev, Q, kind, out_dev, out_capacity_bytes, offsets
 
 def mqr_set_graph(ctx, enable):
     _check(load().mqr_set_graph(ctx, 1 if enable else 0))
+
+
+def mqr_set_index(ctx, index_kind, leaf_cap=0, grid_level=0):
+    _check(load().mqr_set_index(ctx, int(index_kind), int(leaf_cap), int(grid_level)))
+
+
+class CostModel:
+    """The learned tick-cost model (MLP 5 -> 64 -> 64 -> 1 trained on the
+    device); marshalling only."""
+
+    def __init__(self, params=None):
+        lib = load()
+        self.P = int(lib.mqr_cost_param_count())
+        h = ctypes.c_void_p()
+        _check(lib.mqr_cost_create(ctypes.byref(h)))
+        self.h = h
+        if params is not None:
+            self.set_params(params)
+
+    def set_params(self, params):
+        a = np.ascontiguousarray(params, dtype=np.float32)
+        _check(load().mqr_cost_set_params(self.h, a.ctypes.data, int(a.shape[0])))
+
+    def params(self):
+        a = np.zeros(self.P, np.float32)
+        _check(load().mqr_cost_get_params(self.h, a.ctypes.data, self.P))
+        return a
+
+    def train(self, X, y, epochs=1, lr=1e-3):
+        X = np.ascontiguousarray(X, dtype=np.float32).reshape(-1, 5)
+        y = np.ascontiguousarray(y, dtype=np.float32).reshape(-1)
+        loss = ctypes.c_float(0.0)
+        _check(load().mqr_cost_train(self.h, X.ctypes.data, y.ctypes.data, int(X.shape[0]), int(epochs),
+                                     float(lr), ctypes.byref(loss)))
+        return float(loss.value)
+
+    def gradient(self, X, y):
+        X = np.ascontiguousarray(X, dtype=np.float32).reshape(-1, 5)
+        y = np.ascontiguousarray(y, dtype=np.float32).reshape(-1)
+        g = np.zeros(self.P, np.float32)
+        loss = ctypes.c_float(0.0)
+        _check(load().mqr_cost_gradient(self.h, X.ctypes.data, y.ctypes.data, int(X.shape[0]), g.ctypes.data,
+                                        ctypes.byref(loss)))
+        return g, float(loss.value)
+
+    def predict(self, X):
+        X = np.ascontiguousarray(X, dtype=np.float32).reshape(-1, 5)
+        out = np.zeros(X.shape[0], np.float32)
+        _check(load().mqr_cost_predict(self.h, X.ctypes.data, int(X.shape[0]), out.ctypes.data))
+        return out
+
+    def close(self):
+        if self.h:
+            load().mqr_cost_destroy(self.h)
+            self.h = None
 
 
 def mqr_set_worlds(ctx, obj_base):
@@ -331,6 +397,9 @@ class Index:
             _check(st)
         res = self._out[: cnt * elem // 4]
         return (res.view(cnt, 2) if elem == 8 else res), offs
+
+    def set_index(self, index_kind=0, leaf_cap=0, grid_level=0):
+        mqr_set_index(self.ctx, index_kind, leaf_cap, grid_level)
 
     def set_graph(self, enable=True):
         mqr_set_graph(self.ctx, enable)
