@@ -352,7 +352,7 @@ __device__ __forceinline__ uint32_t emit_words(void *out, unsigned long long off
 template <int KIND>
 __global__ void __launch_bounds__(kEmitThreads, 8)
 emit_kernel(const uint32_t *__restrict__ sub_q, const uint32_t *__restrict__ sub_leaf,
-            const uint32_t *__restrict__ sub_len, const uint32_t *__restrict__ sub_bm,
+            const uint32_t *__restrict__ sub_len, const uint32_t *__restrict__ leaf_word_off,
             const unsigned long long *__restrict__ out_off, const uint32_t *__restrict__ leaf_beg,
             const uint32_t *__restrict__ sid, const uint32_t *__restrict__ bitmap, void *out,
             uint32_t wpr, uint32_t *ticket, Caps caps, const Info *info) {
@@ -379,10 +379,11 @@ emit_kernel(const uint32_t *__restrict__ sub_q, const uint32_t *__restrict__ sub
             const uint32_t sl = __ldg(sub_leaf + k);
             const uint32_t first = sl & 0x7fffffffu;
             const bool cov = (sl & 0x80000000u) != 0u;
-            const uint32_t len = cov ? __ldg(sub_len + k) : 1u;
+            const uint32_t lr = __ldg(sub_len + k);          // run length, or rank in the leaf's list
+            const uint32_t len = cov ? lr : 1u;
             const uint32_t b = __ldg(leaf_beg + first);
             const uint32_t e = __ldg(leaf_beg + first + len);
-            const uint32_t row = cov ? 0u : __ldg(sub_bm + k);
+            const uint32_t row = cov ? 0u : __ldg(leaf_word_off + first) + lr * ((e - b + 31u) >> 5);
             s_rec[wib][lane] = make_uint4(__ldg(sub_q + k), row, b, (e - b) | (cov ? 0x80000000u : 0u));
             s_off[wib][lane] = __ldg(out_off + k);
         }
@@ -412,30 +413,30 @@ emit_kernel(const uint32_t *__restrict__ sub_q, const uint32_t *__restrict__ sub
 }
 
 void launch_emit(cudaStream_t st, int num_sms, int emit_kind, const uint32_t *sub_q,
-                 const uint32_t *sub_leaf, const uint32_t *sub_len, const uint32_t *sub_bm,
+                 const uint32_t *sub_leaf, const uint32_t *sub_len, const uint32_t *leaf_word_off,
                  const unsigned long long *out_off, const uint32_t *leaf_beg,
                  const uint32_t *sid, const uint32_t *bitmap, void *out, uint32_t wpr,
                  uint32_t *ticket, Caps caps, const Info *info) {
     const int grid = num_sms * 8;
     switch (emit_kind) {
         case kEmitPairs:
-            emit_kernel<kEmitPairs><<<grid, kEmitThreads, 0, st>>>(sub_q, sub_leaf, sub_len, sub_bm, out_off,
+            emit_kernel<kEmitPairs><<<grid, kEmitThreads, 0, st>>>(sub_q, sub_leaf, sub_len, leaf_word_off, out_off,
                                                                    leaf_beg, sid, bitmap, out, wpr, ticket, caps, info);
             break;
         case kEmitIds:
-            emit_kernel<kEmitIds><<<grid, kEmitThreads, 0, st>>>(sub_q, sub_leaf, sub_len, sub_bm, out_off,
+            emit_kernel<kEmitIds><<<grid, kEmitThreads, 0, st>>>(sub_q, sub_leaf, sub_len, leaf_word_off, out_off,
                                                                  leaf_beg, sid, bitmap, out, wpr, ticket, caps, info);
             break;
         case kEmitBitmap:
-            emit_kernel<kEmitBitmap><<<grid, kEmitThreads, 0, st>>>(sub_q, sub_leaf, sub_len, sub_bm, out_off,
+            emit_kernel<kEmitBitmap><<<grid, kEmitThreads, 0, st>>>(sub_q, sub_leaf, sub_len, leaf_word_off, out_off,
                                                                     leaf_beg, sid, bitmap, out, wpr, ticket, caps, info);
             break;
         case kEmitRuns:
-            emit_kernel<kEmitRuns><<<grid, kEmitThreads, 0, st>>>(sub_q, sub_leaf, sub_len, sub_bm, out_off,
+            emit_kernel<kEmitRuns><<<grid, kEmitThreads, 0, st>>>(sub_q, sub_leaf, sub_len, leaf_word_off, out_off,
                                                                   leaf_beg, sid, bitmap, out, wpr, ticket, caps, info);
             break;
         default:
-            emit_kernel<kEmitKeys64><<<grid, kEmitThreads, 0, st>>>(sub_q, sub_leaf, sub_len, sub_bm, out_off,
+            emit_kernel<kEmitKeys64><<<grid, kEmitThreads, 0, st>>>(sub_q, sub_leaf, sub_len, leaf_word_off, out_off,
                                                                     leaf_beg, sid, bitmap, out, wpr, ticket, caps, info);
             break;
     }

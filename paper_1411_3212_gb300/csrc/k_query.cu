@@ -249,36 +249,37 @@ __device__ __forceinline__ CandLane cand_lane(unsigned long long t, unsigned lon
                                               const unsigned long long *__restrict__ pair_off,
                                               const uint2 *__restrict__ qcells,
                                               const uint2 *__restrict__ leaf_box) {
+    // candidate indices fit 32 bits (at most kMaxCandTiles tiles of 32)
     const uint32_t lane = threadIdx.x & 31;
-    const unsigned long long c0 = t << 5;
+    const uint32_t c0 = (uint32_t)t << 5;
     const uint32_t p0 = __ldg(tile_p0 + t);
     const uint32_t pj = p0 + lane;
     uint32_t q_j = 0, f_j = 0, b_j = 0;
-    unsigned long long po = ~0ull;
+    uint32_t po = 0xffffffffu;
     if (pj < npairs) {
-        po = __ldg(pair_off + pj);
+        po = (uint32_t)__ldg(pair_off + pj);
         q_j = __ldg(pair_q + pj);
         f_j = __ldg(pair_first + pj);
         b_j = __ldg(pair_blo + pj);
     }
     CandLane r;
-    r.pj_starts = pj < npairs && po >= c0 && po < c0 + 32;
-    r.po_j = r.pj_starts ? (uint32_t)(po - c0) : 0u;
+    r.pj_starts = pj < npairs && po >= c0 && po < c0 + 32u;
+    r.po_j = r.pj_starts ? po - c0 : 0u;
     const uint32_t bit = (r.pj_starts && lane > 0) ? (1u << r.po_j) : 0u;
     const uint32_t start_mask = __reduce_or_sync(0xffffffffu, bit);
     uint32_t le;
     asm("mov.u32 %0, %%lanemask_le;" : "=r"(le));
     r.p_rel = __popc(start_mask & le);
-    const unsigned long long c = c0 + lane;
+    const uint32_t c = c0 + lane;
     r.valid = c < ncand;
     r.q = __shfl_sync(0xffffffffu, q_j, r.p_rel);
     const uint32_t first = __shfl_sync(0xffffffffu, f_j, r.p_rel);
     const uint32_t blo = __shfl_sync(0xffffffffu, b_j, r.p_rel);   // block corner
-    const unsigned long long pstart = __shfl_sync(0xffffffffu, po, r.p_rel);
+    const uint32_t pstart = __shfl_sync(0xffffffffu, po, r.p_rel);
     r.code = 0;
     r.leaf = 0;
     if (r.valid) {
-        r.leaf = first + (uint32_t)(c - pstart);
+        r.leaf = first + (c - pstart);
         uint32_t i0, i1, j0, j1;
         unpack_cells(__ldg(qcells + r.q), i0, i1, j0, j1);
         r.code = classify(i0, i1, j0, j1, block_log2(i0, i1, j0, j1), blo, __ldg(leaf_box + r.leaf));
@@ -298,15 +299,15 @@ cand_count_kernel(int covering, const uint32_t *__restrict__ tile_p0, const uint
                   const uint32_t *__restrict__ leaf_beg, uint32_t *__restrict__ tile_cnt,
                   uint32_t *__restrict__ leaf_nsub, uint4 *__restrict__ pad, uint32_t *__restrict__ pair_rec,
                   Caps caps, Info *info) {
-    __shared__ unsigned long long s_red[3];
-    if (threadIdx.x < 3) s_red[threadIdx.x] = 0;
+    __shared__ unsigned long long s_red[2];
+    if (threadIdx.x < 2) s_red[threadIdx.x] = 0;
     __syncthreads();
     const unsigned long long ncand = info->n_cand;
     const uint32_t npairs = (uint32_t)info->n_pairs;
     const unsigned long long ntiles = (ncand + 31) >> 5;
     const uint32_t lane = threadIdx.x & 31;
     const uint32_t lt = lanemask_lt();
-    unsigned long long n_i = 0, n_c = 0, tests = 0;
+    unsigned long long n_i = 0, n_c = 0;
     if (ntiles <= caps.cand_tiles) {
         const unsigned long long nw = (unsigned long long)gridDim.x * (blockDim.x >> 5);
         for (unsigned long long t = (blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x) >> 5; t < ntiles;
@@ -322,7 +323,6 @@ cand_count_kernel(int covering, const uint32_t *__restrict__ tile_p0, const uint
             if (r.code == 1) {
                 ++n_i;
                 const uint32_t rank = atomicAdd(leaf_nsub + r.leaf, 1u);   // row in the leaf's list
-                tests += __ldg(leaf_beg + r.leaf + 1) - __ldg(leaf_beg + r.leaf);
                 pad[slot0 + __popc(m & lt)] = make_uint4(r.q, r.leaf, rank, 0u);
             } else if (r.code == 2) {
                 ++n_c;
@@ -337,17 +337,15 @@ cand_count_kernel(int covering, const uint32_t *__restrict__ tile_p0, const uint
             }
         }
     }
-    n_i = warp_sum(n_i); n_c = warp_sum(n_c); tests = warp_sum(tests);
+    n_i = warp_sum(n_i); n_c = warp_sum(n_c);
     if (lane == 0) {
         if (n_i) atomicAdd(&s_red[0], n_i);
         if (n_c) atomicAdd(&s_red[1], n_c);
-        if (tests) atomicAdd(&s_red[2], tests);
     }
     __syncthreads();
     if (threadIdx.x == 0) {
         if (s_red[0]) atomicAdd(&info->n_sub_i, s_red[0]);
         if (s_red[1]) atomicAdd(&info->n_sub_c, s_red[1]);
-        if (s_red[2]) atomicAdd(&info->n_tests, s_red[2]);
     }
 }
 
@@ -429,7 +427,7 @@ leaf_scan_kernel(const uint32_t *__restrict__ leaf_beg, const uint32_t *__restri
 
     uint32_t ns[kLeafScanItems], nw[kLeafScanItems], ni[kLeafScanItems];
     uint32_t t_s = 0, t_w = 0, t_i = 0;
-    unsigned long long objs = 0;
+    unsigned long long objs = 0, tests = 0;
 #pragma unroll
     for (int e = 0; e < kLeafScanItems; ++e) {
         uint32_t l = lb + e;
@@ -441,6 +439,7 @@ leaf_scan_kernel(const uint32_t *__restrict__ leaf_beg, const uint32_t *__restri
             nw[e] = s * ((n + 31u) >> 5);
             ni[e] = s ? ((n + 255u) >> 8) * ((s + 31u) >> 5) : 0u;
             if (s) objs += (unsigned long long)n * ((s + 31u) >> 5);
+            tests += (unsigned long long)n * s;                 // containment tests of the leaf
         }
         t_s += ns[e]; t_w += nw[e]; t_i += ni[e];
     }
@@ -449,7 +448,9 @@ leaf_scan_kernel(const uint32_t *__restrict__ leaf_beg, const uint32_t *__restri
     uint32_t o_w = block_excl_scan<kLeafScanThreads>(t_w, &tot_w, s_scan);
     uint32_t o_i = block_excl_scan<kLeafScanThreads>(t_i, &tot_i, s_scan);
     objs = warp_sum(objs);
+    tests = warp_sum(tests);
     if ((tid & 31) == 0 && objs) atomicAdd(&info->n_item_objs, objs);
+    if ((tid & 31) == 0 && tests) atomicAdd(&info->n_tests, tests);
     if (tid < 96) {
         const int w = tid >> 5;
         const uint32_t agg = w == 0 ? tot_s : (w == 1 ? tot_w : tot_i);
@@ -495,15 +496,14 @@ void launch_leaf_scan(cudaStream_t st, uint32_t nmax, const uint32_t *leaf_beg,
 // a7/a8 compaction: padded slot 32t + r (r < the tile's count) -> record
 // k = tile_off[t] + r.  An intersecting record also takes its place in its
 // leaf's list (its rank there came from the count pass's per-leaf atomic
-// count) and its bitmap row: the grouping by leaf needs no second pass.
+// count, and is kept in sub_len: it is the record's bitmap row in the leaf),
+// so the grouping by leaf needs no second pass.
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(256)
 cand_compact_kernel(const uint4 *__restrict__ pad, const uint32_t *__restrict__ tile_cnt,
-                    const uint32_t *__restrict__ tile_off, const uint32_t *__restrict__ leaf_beg,
-                    const uint32_t *__restrict__ leaf_sub_off, const uint32_t *__restrict__ leaf_word_off,
+                    const uint32_t *__restrict__ tile_off, const uint32_t *__restrict__ leaf_sub_off,
                     uint32_t *__restrict__ sub_q, uint32_t *__restrict__ sub_leaf, uint32_t *__restrict__ sub_len,
-                    uint32_t *__restrict__ sub_res, uint32_t *__restrict__ sub_bm, uint32_t *__restrict__ isub,
-                    Caps caps, const Info *info) {
+                    uint32_t *__restrict__ sub_res, uint32_t *__restrict__ isub, Caps caps, const Info *info) {
     constexpr int U = 4;   // independent slots per thread per step: their load chains overlap
     const unsigned long long ntiles = (info->n_cand + 31) >> 5;
     if (ntiles > caps.cand_tiles || info->n_sub > caps.sub || info->n_sub_i > caps.sub_i) return;
@@ -513,7 +513,7 @@ cand_compact_kernel(const uint4 *__restrict__ pad, const uint32_t *__restrict__ 
          s0 += U * stride) {
         bool ok[U];
         uint4 v[U];
-        uint32_t k[U];
+        uint32_t k[U], so[U];
 #pragma unroll
         for (int u = 0; u < U; ++u) {
             const unsigned long long s = s0 + u * stride;
@@ -527,40 +527,30 @@ cand_compact_kernel(const uint4 *__restrict__ pad, const uint32_t *__restrict__ 
                 k[u] = __ldg(tile_off + (s >> 5)) + ((uint32_t)s & 31u);
             }
         }
-        uint32_t n[U], so[U], wo[U];
 #pragma unroll
-        for (int u = 0; u < U; ++u) {
-            if (ok[u] && !(v[u].y & 0x80000000u)) {
-                n[u] = __ldg(leaf_beg + v[u].y + 1) - __ldg(leaf_beg + v[u].y);
-                so[u] = __ldg(leaf_sub_off + v[u].y);
-                wo[u] = __ldg(leaf_word_off + v[u].y);
-            }
-        }
+        for (int u = 0; u < U; ++u)
+            if (ok[u] && !(v[u].y & 0x80000000u)) so[u] = __ldg(leaf_sub_off + v[u].y);
 #pragma unroll
         for (int u = 0; u < U; ++u) {
             if (!ok[u]) continue;
             sub_q[k[u]] = v[u].x;
             sub_leaf[k[u]] = v[u].y;
+            sub_len[k[u]] = v[u].z;           // run length, or rank in the leaf's list (its bitmap row)
             if (v[u].y & 0x80000000u) {
-                sub_len[k[u]] = v[u].z;
                 sub_res[k[u]] = v[u].w;
             } else {
-                sub_len[k[u]] = 1;
                 sub_res[k[u]] = 0;
                 isub[so[u] + v[u].z] = k[u];
-                sub_bm[k[u]] = wo[u] + v[u].z * ((n[u] + 31u) >> 5);
             }
         }
     }
 }
 
 void launch_compact(cudaStream_t st, int num_sms, const uint4 *pad, const uint32_t *tile_cnt,
-                    const uint32_t *tile_off, const uint32_t *leaf_beg, const uint32_t *leaf_sub_off,
-                    const uint32_t *leaf_word_off, uint32_t *sub_q, uint32_t *sub_leaf, uint32_t *sub_len,
-                    uint32_t *sub_res, uint32_t *sub_bm, uint32_t *isub, Caps caps, const Info *info) {
-    cand_compact_kernel<<<num_sms * 8, 256, 0, st>>>(pad, tile_cnt, tile_off, leaf_beg, leaf_sub_off,
-                                                      leaf_word_off, sub_q, sub_leaf, sub_len, sub_res, sub_bm,
-                                                      isub, caps, info);
+                    const uint32_t *tile_off, const uint32_t *leaf_sub_off, uint32_t *sub_q, uint32_t *sub_leaf,
+                    uint32_t *sub_len, uint32_t *sub_res, uint32_t *isub, Caps caps, const Info *info) {
+    cand_compact_kernel<<<num_sms * 8, 256, 0, st>>>(pad, tile_cnt, tile_off, leaf_sub_off, sub_q, sub_leaf,
+                                                     sub_len, sub_res, isub, caps, info);
 }
 
 }  // namespace mqr

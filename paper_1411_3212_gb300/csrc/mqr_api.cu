@@ -96,7 +96,7 @@ struct mqr_ctx {
     DevBuf<uint8_t> mk_a, mk_b;
     DevBuf<uint2> leaf_box;
     // per query / subquery
-    DevBuf<uint32_t> sub_q, sub_leaf, sub_len, sub_res, sub_bm, isub, bitmap, item_leaf;
+    DevBuf<uint32_t> sub_q, sub_leaf, sub_len, sub_res, isub, bitmap, item_leaf;
     DevBuf<unsigned long long> out_off;
     // query splitting: coarse lookup table, per-query cells, (query, block) pairs
     DevBuf<uint32_t> zmap, pair_q, pair_first, pair_blo, pair_rec, qpair, tile_p0, tile_cnt, tile_off;
@@ -334,9 +334,8 @@ mqr_status enqueue_tick(mqr_ctx *c, const float4 *rects, uint32_t Q, int emit_ki
     phase_begin(c, MQR_PHASE_GROUP);
     launch_leaf_scan(st, nmax, c->leaf_beg.p, c->leaf_nsub.p, c->leaf_sub_off.p, c->leaf_word_off.p,
                      c->leaf_item_off.p, c->item_leaf.p, at<uint32_t>(c, a.st_lscan), ctr + 6, caps, info);
-    launch_compact(st, c->num_sms, c->cand_pad.p, c->tile_cnt.p, c->tile_off.p, c->leaf_beg.p,
-                   c->leaf_sub_off.p, c->leaf_word_off.p, c->sub_q.p, c->sub_leaf.p, c->sub_len.p, c->sub_res.p,
-                   c->sub_bm.p, c->isub.p, caps, info);
+    launch_compact(st, c->num_sms, c->cand_pad.p, c->tile_cnt.p, c->tile_off.p, c->leaf_sub_off.p, c->sub_q.p,
+                   c->sub_leaf.p, c->sub_len.p, c->sub_res.p, c->isub.p, caps, info);
     phase_end(c, MQR_PHASE_GROUP, nmax ? 2 : 1);
     // a10
     if (emit_kind == kEmitAtomic) {
@@ -362,7 +361,7 @@ mqr_status enqueue_tick(mqr_ctx *c, const float4 *rects, uint32_t Q, int emit_ki
     // a12 + a13
     if (out != nullptr && emit_kind >= 0) {
         phase_begin(c, MQR_PHASE_EMIT);
-        launch_emit(st, c->num_sms, emit_kind, c->sub_q.p, c->sub_leaf.p, c->sub_len.p, c->sub_bm.p,
+        launch_emit(st, c->num_sms, emit_kind, c->sub_q.p, c->sub_leaf.p, c->sub_len.p, c->leaf_word_off.p,
                     c->out_off.p, c->leaf_beg.p, c->sid.p, c->bitmap.p, out,
                     bitmap_words_per_row(nmax), ctr + 9, caps, info);
         phase_end(c, MQR_PHASE_EMIT, 1);
@@ -399,7 +398,6 @@ mqr_status ensure_tick_buffers(mqr_ctx *c, uint32_t Q) {
         MQR_CUDA(c->sub_leaf.ensure(sub0));
         MQR_CUDA(c->sub_len.ensure(sub0));
         MQR_CUDA(c->sub_res.ensure(sub0));
-        MQR_CUDA(c->sub_bm.ensure(sub0));
         MQR_CUDA(c->out_off.ensure(sub0 + 1));
         MQR_CUDA(c->isub.ensure(sub0));
         MQR_CUDA(c->bitmap.ensure(std::max<size_t>(1 << 16, (size_t)Q * 16)));
@@ -411,12 +409,11 @@ mqr_status ensure_tick_buffers(mqr_ctx *c, uint32_t Q) {
 mqr_status grow_sub(mqr_ctx *c, unsigned long long need) {
     size_t n = grow_to(need);
     c->sub_q.release(); c->sub_leaf.release(); c->sub_len.release(); c->sub_res.release();
-    c->sub_bm.release(); c->out_off.release();
+    c->out_off.release();
     MQR_CUDA(c->sub_q.ensure(n));
     MQR_CUDA(c->sub_leaf.ensure(n));
     MQR_CUDA(c->sub_len.ensure(n));
     MQR_CUDA(c->sub_res.ensure(n));
-    MQR_CUDA(c->sub_bm.ensure(n));
     MQR_CUDA(c->out_off.ensure(n + 1));
     return MQR_OK;
 }
@@ -634,7 +631,7 @@ mqr_status tick_device_impl(mqr_ctx *c, const float *rects_dev, uint32_t Q, int 
     Info *info = at<Info>(c, a.info);
     phase_begin(c, MQR_PHASE_OUTPUT_SORT);
     launch_emit(c->stream, c->num_sms, kEmitKeys64, c->sub_q.p, c->sub_leaf.p, c->sub_len.p,
-                c->sub_bm.p, c->out_off.p, c->leaf_beg.p, c->sid.p, c->bitmap.p, c->sortA.p, wpr,
+                c->leaf_word_off.p, c->out_off.p, c->leaf_beg.p, c->sid.p, c->bitmap.p, c->sortA.p, wpr,
                 at<uint32_t>(c, a.counters) + 9, caps, info);
     s = check_launch("emit keys");
     if (s != MQR_OK) return s;
@@ -833,7 +830,7 @@ void mqr_destroy(mqr_ctx *c) {
     DevBuf<uint32_t> *u32s[] = {&c->skey, &c->sid, &c->sort_counts, &c->sort_offs, &c->leaf_lo, &c->leaf_hi, &c->leaf_beg, &c->leaf_nsub,
                                 &c->leaf_sub_off, &c->leaf_word_off, &c->leaf_item_off,
                                 &c->sub_q, &c->sub_leaf, &c->sub_len, &c->sub_res,
-                                &c->sub_bm, &c->isub, &c->bitmap, &c->item_leaf, &c->up_ids, &c->zmap, &c->pair_q,
+                                &c->isub, &c->bitmap, &c->item_leaf, &c->up_ids, &c->zmap, &c->pair_q,
                                 &c->pair_first, &c->pair_blo, &c->pair_rec, &c->qpair, &c->tile_p0,
                                 &c->tile_cnt, &c->tile_off};
     for (auto *b : u32s) b->release();
@@ -1129,7 +1126,7 @@ mqr_status mqr_tick_admit(mqr_ctx *c, const float *rects_dev, uint32_t Q, int ki
     }
     if (n > 0) {
         phase_begin(c, MQR_PHASE_EMIT);
-        launch_emit(c->stream, c->num_sms, ek, c->sub_q.p, c->sub_leaf.p, c->sub_len.p, c->sub_bm.p,
+        launch_emit(c->stream, c->num_sms, ek, c->sub_q.p, c->sub_leaf.p, c->sub_len.p, c->leaf_word_off.p,
                     c->out_off.p, c->leaf_beg.p, c->sid.p, c->bitmap.p, out_dev,
                     bitmap_words_per_row(c->nmax), at<uint32_t>(c, a.counters) + 9, caps, info);
         phase_end(c, MQR_PHASE_EMIT, 1);

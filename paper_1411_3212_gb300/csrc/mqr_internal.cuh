@@ -360,7 +360,7 @@ constexpr uint32_t kZCells = 1u << (2 * kZLevel);
 constexpr int kZShift = 2 * (kLevels - kZLevel);
 constexpr int kQBThreads = 256;                       // threads per block of query_blocks
 constexpr int kQBQueries = kQBThreads / 9;            // queries per block (9 block slots each)
-constexpr unsigned long long kMaxCandTiles = 1ull << 27;   // padded slots 32t + rank fit 32 bits
+constexpr unsigned long long kMaxCandTiles = (1ull << 27) - 1;   // candidates and slots 32t + rank fit 32 bits
 constexpr int kCandScanTile = 2048;                   // warp tiles per block of the tile-count scan
 
 void launch_zmap(cudaStream_t st, const uint32_t *leaf_hi, const Info *info, uint32_t *zmap);
@@ -390,9 +390,8 @@ void launch_leaf_scan(cudaStream_t st, uint32_t nmax, const uint32_t *leaf_beg,
 
 // a7/a8 compaction of the padded records; intersecting ones into their leaf's list.
 void launch_compact(cudaStream_t st, int num_sms, const uint4 *pad, const uint32_t *tile_cnt,
-                    const uint32_t *tile_off, const uint32_t *leaf_beg, const uint32_t *leaf_sub_off,
-                    const uint32_t *leaf_word_off, uint32_t *sub_q, uint32_t *sub_leaf, uint32_t *sub_len,
-                    uint32_t *sub_res, uint32_t *sub_bm, uint32_t *isub, Caps caps, const Info *info);
+                    const uint32_t *tile_off, const uint32_t *leaf_sub_off, uint32_t *sub_q, uint32_t *sub_leaf,
+                    uint32_t *sub_len, uint32_t *sub_res, uint32_t *isub, Caps caps, const Info *info);
 
 // a10: filtering into bitmap words + per-subquery counts.
 void launch_filter(cudaStream_t st, int num_sms, const float4 *rects, const float2 *sxy,
@@ -411,7 +410,7 @@ void launch_result_scan(cudaStream_t st, unsigned long long sub_cap, const uint3
 enum EmitKind { kEmitPairs = 0, kEmitIds = 1, kEmitBitmap = 2, kEmitKeys64 = 3, kEmitRuns = 4,
                 kEmitAtomic = 5 /* the atomic-append baseline (no bitmaps, unordered pairs) */ };
 void launch_emit(cudaStream_t st, int num_sms, int emit_kind, const uint32_t *sub_q,
-                 const uint32_t *sub_leaf, const uint32_t *sub_len, const uint32_t *sub_bm,
+                 const uint32_t *sub_leaf, const uint32_t *sub_len, const uint32_t *leaf_word_off,
                  const unsigned long long *out_off, const uint32_t *leaf_beg,
                  const uint32_t *sid, const uint32_t *bitmap, void *out, uint32_t bitmap_words_per_row,
                  uint32_t *ticket, Caps caps, const Info *info);
