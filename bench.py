@@ -34,6 +34,7 @@ sys.path.insert(0, ROOT)
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "emit_kernel_traffic.txt")
 FALLBACK_HBM_GBS = 6800.0
+NOMINAL_HBM_GBS = 7900.0
 
 WORKLOADS = {
     "hotspot4m": dict(kind="hotspot", n=4_000_000, q=400_000, cap=128,
@@ -404,6 +405,7 @@ def run_gpu(args, name):
                     "result_scan": "result_scan_kernel"}
     roofline = {"bound": "hbm", "kernel": kernel_names.get(dom, dom), "phase": dom,
                 "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "peak_nominal": NOMINAL_HBM_GBS, "frac_nominal": achieved / NOMINAL_HBM_GBS,
                 "peak_source": "%s (MEASURED_PEAKS.json hbm_gbs)" % peak_kind if peak_kind == "measured" else "fallback 6.8 TB/s",
                 "traffic": read_traffic(kernel_names.get(dom, dom), results / max(args.steps, 1)),
                 "algorithmic_bytes_per_launch": per_launch_bytes, "launch_ms": per_launch_ms}
@@ -566,6 +568,63 @@ def run_served(args):
     print(json.dumps(line), flush=True)
 
 
+def run_per_world(args):
+    """--per-world: the batched-worlds workload answered the plain way, one
+    context per world and one tick per world in turn, for comparison with the
+    single batched index (`--workload batched256`)."""
+    import torch
+    from paper_1411_3212_gb300 import mqr
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    w = WORKLOADS["batched256"]
+    uniq = min(args.steps, args.unique_ticks)
+    ticks = gen_ticks("batched256", 0, args.warmup + uniq)
+    ob, qb = ticks[0].obj_base.astype(np.int64), ticks[0].q_base.astype(np.int64)
+    W = ob.shape[0] - 1
+    xy_d = [torch.from_numpy(t.xy).to(dev) for t in ticks]
+    rect_d = [torch.from_numpy(t.rects).to(dev) for t in ticks]
+    ids_w = [torch.arange(ob[k + 1] - ob[k], dtype=torch.int32, device=dev) for k in range(W)]
+    idxs = [mqr.Index(bounds=(0.0, 0.0, 1.0, 1.0), leaf_cap=w["cap"], max_objects=int(ob[k + 1] - ob[k]))
+            for k in range(W)]
+    outs = [torch.empty(1, dtype=torch.int32, device=dev) for _ in range(W)]
+
+    def step(i):
+        res = 0
+        for k in range(W):
+            idx = idxs[k]
+            idx.apply_updates(ids_w[k], xy_d[i][ob[k]:ob[k + 1]])
+            q = int(qb[k + 1] - qb[k])
+            st, cnt = mqr.mqr_tick(idx.ctx, rect_d[i][qb[k]:qb[k + 1]], q, mqr.MQR_OUT_PAIRS, outs[k],
+                                   outs[k].numel() * 4)
+            if st == mqr.MQR_ERR_CAPACITY:
+                outs[k] = torch.empty(int(cnt * 2 * 1.3) + 1024, dtype=torch.int32, device=dev)
+                st, cnt = mqr.mqr_tick(idx.ctx, rect_d[i][qb[k]:qb[k + 1]], q, mqr.MQR_OUT_PAIRS, outs[k],
+                                       outs[k].numel() * 4)
+            mqr._check(st)
+            res += cnt
+        return res
+
+    for i in range(args.warmup):
+        step(i)
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    results = 0
+    for k in range(args.steps):
+        results += step(args.warmup + (k % uniq))
+    b.record()
+    b.synchronize()
+    ms = a.elapsed_time(b) / args.steps
+    for idx in idxs:
+        idx.close()
+    Q = int(qb[-1])
+    print(json.dumps({"metric": "queries/s", "value": Q / (ms / 1000.0), "unit": "queries/s", "ms_per_step": ms,
+                      "steps": args.steps, "warmup": args.warmup,
+                      "config": {"workload": w["desc"] + "; answered per world, one context and one tick each",
+                                 "worlds": W, "objects": int(ob[-1]), "queries_per_tick": Q},
+                      "results_per_tick": results / args.steps}), flush=True)
+
+
 def run_costmodel(args):
     """--costmodel: the index configuration chosen per tick by the learned
     cost model (leaf capacities 64..512 and the uniform grid at levels 8 and
@@ -654,6 +713,7 @@ def main():
     ap.add_argument("--grid-level", type=int, default=8, help="uniform grid: 2^level cells per axis")
     ap.add_argument("--served", action="store_true", help="run the served stream instead")
     ap.add_argument("--costmodel", action="store_true", help="learned per-tick index choice vs fixed")
+    ap.add_argument("--per-world", action="store_true", help="batched-256 worlds answered one context each")
     ap.add_argument("--rate", type=float, default=5.0e6, help="served: query arrivals per second")
     ap.add_argument("--dt-ms", type=float, default=10.0, help="served: tick duration")
     ap.add_argument("--served-ticks", type=int, default=100)
@@ -670,6 +730,8 @@ def main():
         run_served(args)
     elif args.costmodel:
         run_costmodel(args)
+    elif args.per_world:
+        run_per_world(args)
     elif args.impl == "reference":
         run_reference(args, args.workload)
     else:
