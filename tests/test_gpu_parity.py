@@ -251,3 +251,35 @@ def test_uniform_walk_multi_tick(mqr):
         want = oracle.join_grid(st, t.rects, cell_side=0.002)
         assert_same_csr(gpu_pairs_as_csr(idx, t.rects, dev), want)
     idx.close()
+
+
+def test_overfull_leaf_of_identical_points(mqr):
+    """120,000 objects on one point (a level-15 leaf of 120K objects: 469 filter
+    chunks, multi-chunk counts, thousands of bitmap words per subquery) beside
+    80,000 uniform ones; queries that cover the point, touch it on their
+    boundary, and miss it; every output kind against the oracle."""
+    torch, dev = torch_dev()
+    rng = np.random.default_rng(17)
+    n = 200_000
+    xy = rng.random((n, 2)).astype(np.float32)
+    xy[:120_000] = np.float32(0.3125)                  # exactly representable
+    ids = rng.permutation(n).astype(np.uint32)          # the cluster's ids are scattered
+    c = rng.random((300, 2)).astype(np.float32)
+    rects = workloads.squares_around(c, rng.choice([0.001, 0.01, 0.1], 300))
+    rects[:40] = workloads.squares_around(np.full((40, 2), 0.3125, np.float32), rng.choice([0.0, 0.001, 0.2], 40))
+    rects[40:50] = [[0.3125, 0.3125, 0.5, 0.5]] * 10    # the point on the lower-left corner
+    rects[50:60] = [[0.1, 0.1, 0.3125, 0.3125]] * 10    # ... and on the upper-right corner
+    rects[60:70] = [[0.1, 0.1, 0.3124, 0.3124]] * 10    # just missing it
+    idx = make_index(mqr, n, cap=64)
+    idx.apply_updates(to_dev(ids, dev), to_dev(xy, dev))
+    st = oracle_state(n, [(ids, xy)])
+    want = oracle.join_grid(st, rects, cell_side=0.01)
+    assert int(np.diff(want[0].astype(np.int64))[:60].min()) >= 120_000
+    assert_same_csr(gpu_csr_sorted(idx, rects, dev), want)
+    assert_same_csr(gpu_pairs_as_csr(idx, rects, dev), want)
+    go, gi, _ = gpu_runs_as_csr(idx, rects, dev)
+    assert_same_csr((go, gi), want, "runs")
+    assert_same_csr(gpu_atomic_as_csr(idx, rects, dev), want, "atomic")
+    lv = idx.leaves()
+    assert (lv[:, 3] - lv[:, 2]).max() >= 120_000 and lv[:, 0].max() == 15
+    idx.close()
