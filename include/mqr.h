@@ -218,6 +218,31 @@ mqr_status mqr_tick_host(mqr_ctx *ctx, const float *rects_host, uint32_t Q, int 
                          void *out_host, uint64_t out_capacity_bytes, uint64_t *out_count,
                          uint64_t *offsets_host);
 
+/* As mqr_tick_host, but returns as soon as the tick's result is complete in
+ * device staging memory and its copy to out_host (and offsets_host) has been
+ * started on a second stream, so that the copy of one tick overlaps the
+ * updates and kernels of the next (the host link, not the GPU, bounds a
+ * pair-list output on this hardware).  *out_count is set on return.  The host
+ * buffers must not be read or reused until mqr_host_wait returns; page-locked
+ * buffers are needed for the overlap.  Two ticks' copies may be in flight (two
+ * staging buffers alternate); a third call first waits for the oldest.
+ * mqr_tick_host waits for every pending copy first.  Library design
+ * convenience, not a step of the method. */
+mqr_status mqr_tick_host_async(mqr_ctx *ctx, const float *rects_host, uint32_t Q, int kind,
+                               void *out_host, uint64_t out_capacity_bytes, uint64_t *out_count,
+                               uint64_t *offsets_host);
+
+/* Wait until every copy started by mqr_tick_host_async has landed. */
+mqr_status mqr_host_wait(mqr_ctx *ctx);
+
+/* After mqr_tick_host_async: start copying that tick's Morton-sorted object
+ * ids (what a consumer of the RUNS kind needs to expand covering runs; the
+ * same array as mqr_get_sorted's ids) to ids_host on the same second stream,
+ * behind the tick's output.  *n receives their number; they land by
+ * mqr_host_wait.  A snapshot is taken on the device first, so the next tick
+ * may start at once.  cap (in ids) too small: CAPACITY. */
+mqr_status mqr_get_sorted_async(mqr_ctx *ctx, uint32_t *ids_host, uint64_t cap, uint64_t *n);
+
 /* A tick with admission by output memory, for served streams (the tick and
  * latency model of Sec. 2.4, Def. 2-3 and Lemma 2: a tick must finish within
  * the latency budget, so its output is bounded).  As mqr_tick, but instead of

@@ -110,8 +110,14 @@ struct mqr_ctx {
     DevBuf<uint32_t> up_ids;
     DevBuf<float2> up_xy;
     DevBuf<float4> q_rects;
-    DevBuf<unsigned char> out_stage;
-    DevBuf<unsigned long long> off_stage, sortA, sortB;
+    DevBuf<unsigned char> out_stage, out_stage2;     // host-output staging (two for the async path)
+    DevBuf<unsigned long long> off_stage, off_stage2, sortA, sortB;
+    cudaStream_t copy_stream = nullptr;              // device-to-host copies of mqr_tick_host_async
+    DevBuf<uint32_t> sid_stage, sid_stage2;          // sorted-id snapshots copied by mqr_get_sorted_async
+    cudaEvent_t snap_done = nullptr;
+    cudaEvent_t copy_done[2] = {nullptr, nullptr};
+    bool copy_pending[2] = {false, false};
+    int next_stage = 0;
     DevBuf<unsigned char> sort_arena;
     DevBuf<unsigned long long> upd_err;  // sticky error word of the update kernels
     // captured tick (mqr_set_graph): replayed while its inputs are unchanged
@@ -845,7 +851,15 @@ void mqr_destroy(mqr_ctx *c) {
     c->sort_arena.release();
     c->upd_err.release();
     c->q_rects.release();
+    for (int b = 0; b < 2; ++b)
+        if (c->copy_done[b]) { cudaEventSynchronize(c->copy_done[b]); cudaEventDestroy(c->copy_done[b]); }
+    if (c->copy_stream) cudaStreamDestroy(c->copy_stream);
+    if (c->snap_done) cudaEventDestroy(c->snap_done);
+    c->sid_stage.release();
+    c->sid_stage2.release();
     c->out_stage.release();
+    c->out_stage2.release();
+    c->off_stage2.release();
     for (int p = 0; p < MQR_NUM_PHASES; ++p)
         for (int k = 0; k < 2; ++k)
             if (c->ev[p][k]) cudaEventDestroy(c->ev[p][k]);
@@ -1042,20 +1056,51 @@ mqr_status mqr_tick(mqr_ctx *c, const float *rects_dev, uint32_t Q, int kind, vo
     return tick_device(c, rects_dev, Q, kind, out_dev, out_capacity_bytes, out_count, offsets_dev);
 }
 
-mqr_status mqr_tick_host(mqr_ctx *c, const float *rects_host, uint32_t Q, int kind, void *out_host,
-                         uint64_t out_capacity_bytes, uint64_t *out_count, uint64_t *offsets_host) {
+// Wait for the host copies started by mqr_tick_host_async.
+static mqr_status host_copies_wait(mqr_ctx *c) {
+    for (int b = 0; b < 2; ++b)
+        if (c->copy_pending[b]) {
+            MQR_CUDA(cudaEventSynchronize(c->copy_done[b]));
+            c->copy_pending[b] = false;
+        }
+    return MQR_OK;
+}
+
+// The host-buffer tick: inputs staged to the device, the tick into a device
+// staging buffer, the result copied back -- on the context's stream (sync) or
+// on a second stream left running (async, staging buffers alternating).
+static mqr_status tick_host_impl(mqr_ctx *c, const float *rects_host, uint32_t Q, int kind, void *out_host,
+                                 uint64_t out_capacity_bytes, uint64_t *out_count, uint64_t *offsets_host,
+                                 bool async) {
     mqr_status s = tick_args(c, rects_host, Q, kind, out_count);
     if (s != MQR_OK) return s;
     if ((kind == MQR_OUT_CSR || kind == MQR_OUT_CSR_SORTED) && !offsets_host)
         return fail(MQR_ERR_INVALID_ARG, "CSR output needs offsets_host");
     *out_count = 0;
     MQR_CUDA(cudaSetDevice(c->device));
+    int b = 0;
+    if (async) {
+        if (!c->copy_stream) {
+            MQR_CUDA(cudaStreamCreateWithFlags(&c->copy_stream, cudaStreamNonBlocking));
+            for (int k = 0; k < 2; ++k) MQR_CUDA(cudaEventCreateWithFlags(&c->copy_done[k], cudaEventDisableTiming));
+        }
+        b = c->next_stage;
+        if (c->copy_pending[b]) {                          // the copy that last read this staging buffer
+            MQR_CUDA(cudaEventSynchronize(c->copy_done[b]));
+            c->copy_pending[b] = false;
+        }
+    } else {
+        s = host_copies_wait(c);
+        if (s != MQR_OK) return s;
+    }
+    DevBuf<unsigned char> &stage = b ? c->out_stage2 : c->out_stage;
+    DevBuf<unsigned long long> &ostage = b ? c->off_stage2 : c->off_stage;
     MQR_CUDA(c->q_rects.ensure(std::max<size_t>(Q, 1)));
     if (Q) MQR_CUDA(cudaMemcpyAsync(c->q_rects.p, rects_host, (size_t)Q * 16, cudaMemcpyHostToDevice, c->stream));
     uint64_t *offs_dev = nullptr;
     if (offsets_host) {
-        MQR_CUDA(c->off_stage.ensure((size_t)Q + 1));
-        offs_dev = reinterpret_cast<uint64_t *>(c->off_stage.p);
+        MQR_CUDA(ostage.ensure((size_t)Q + 1));
+        offs_dev = reinterpret_cast<uint64_t *>(ostage.p);
     }
     const float *rd = reinterpret_cast<const float *>(c->q_rects.p);
     // Device staging buffer: as large as the caller's buffer allows, grown on
@@ -1064,25 +1109,46 @@ mqr_status mqr_tick_host(mqr_ctx *c, const float *rects_host, uint32_t Q, int ki
     size_t want = out_capacity_bytes;
     if (kind == MQR_OUT_BITMAP) want = std::min<uint64_t>(want, (uint64_t)Q * bitmap_words_per_row(c->nmax) * 4);
     if (kind == MQR_OUT_COUNT) want = 0;
-    size_t have = std::min(c->out_stage.n, want);
-    s = tick_device(c, rd, Q, kind, have ? c->out_stage.p : nullptr, have, out_count, offs_dev);
+    size_t have = std::min(stage.n, want);
+    s = tick_device(c, rd, Q, kind, have ? stage.p : nullptr, have, out_count, offs_dev);
     if (s == MQR_ERR_CAPACITY && kind != MQR_OUT_COUNT) {
         uint64_t need = kind == MQR_OUT_BITMAP ? *out_count * 4 : *out_count * out_elem_bytes(kind);
         if (need > out_capacity_bytes) return s;
-        MQR_CUDA(c->out_stage.ensure(std::max<size_t>(need, 1)));
-        s = tick_device(c, rd, Q, kind, c->out_stage.p, need, out_count, offs_dev);
+        MQR_CUDA(stage.ensure(std::max<size_t>(need, 1)));
+        s = tick_device(c, rd, Q, kind, stage.p, need, out_count, offs_dev);
     }
     if (s != MQR_OK) return s;
     uint64_t bytes = kind == MQR_OUT_BITMAP ? *out_count * 4
                      : (kind == MQR_OUT_COUNT ? 0 : *out_count * out_elem_bytes(kind));
-    if (bytes) {
-        if (!out_host) return fail(MQR_ERR_INVALID_ARG, "out_host is NULL");
-        MQR_CUDA(cudaMemcpyAsync(out_host, c->out_stage.p, bytes, cudaMemcpyDeviceToHost, c->stream));
-    }
+    if (bytes && !out_host) return fail(MQR_ERR_INVALID_ARG, "out_host is NULL");
+    cudaStream_t cs = async ? c->copy_stream : c->stream;   // the tick's kernels have completed
+    if (bytes) MQR_CUDA(cudaMemcpyAsync(out_host, stage.p, bytes, cudaMemcpyDeviceToHost, cs));
     if (offsets_host)
-        MQR_CUDA(cudaMemcpyAsync(offsets_host, offs_dev, ((size_t)Q + 1) * 8, cudaMemcpyDeviceToHost, c->stream));
-    MQR_CUDA(cudaStreamSynchronize(c->stream));
+        MQR_CUDA(cudaMemcpyAsync(offsets_host, offs_dev, ((size_t)Q + 1) * 8, cudaMemcpyDeviceToHost, cs));
+    if (async) {
+        MQR_CUDA(cudaEventRecord(c->copy_done[b], cs));
+        c->copy_pending[b] = true;
+        c->next_stage = b ^ 1;
+    } else {
+        MQR_CUDA(cudaStreamSynchronize(c->stream));
+    }
     return MQR_OK;
+}
+
+mqr_status mqr_tick_host(mqr_ctx *c, const float *rects_host, uint32_t Q, int kind, void *out_host,
+                         uint64_t out_capacity_bytes, uint64_t *out_count, uint64_t *offsets_host) {
+    return tick_host_impl(c, rects_host, Q, kind, out_host, out_capacity_bytes, out_count, offsets_host, false);
+}
+
+mqr_status mqr_tick_host_async(mqr_ctx *c, const float *rects_host, uint32_t Q, int kind, void *out_host,
+                               uint64_t out_capacity_bytes, uint64_t *out_count, uint64_t *offsets_host) {
+    return tick_host_impl(c, rects_host, Q, kind, out_host, out_capacity_bytes, out_count, offsets_host, true);
+}
+
+mqr_status mqr_host_wait(mqr_ctx *c) {
+    if (!c) return fail(MQR_ERR_INVALID_ARG, "ctx is NULL");
+    MQR_CUDA(cudaSetDevice(c->device));
+    return host_copies_wait(c);
 }
 
 mqr_status mqr_tick_admit(mqr_ctx *c, const float *rects_dev, uint32_t Q, int kind, void *out_dev,
@@ -1206,6 +1272,30 @@ mqr_status mqr_get_sorted(mqr_ctx *c, uint32_t *keys_host, uint32_t *ids_host, u
     if (keys_host) MQR_CUDA(cudaMemcpyAsync(keys_host, c->skey.p, N * 4, cudaMemcpyDeviceToHost, c->stream));
     if (ids_host) MQR_CUDA(cudaMemcpyAsync(ids_host, c->sid.p, N * 4, cudaMemcpyDeviceToHost, c->stream));
     MQR_CUDA(cudaStreamSynchronize(c->stream));
+    return MQR_OK;
+}
+
+mqr_status mqr_get_sorted_async(mqr_ctx *c, uint32_t *ids_host, uint64_t cap, uint64_t *n) {
+    if (!c || !n || !ids_host) return fail(MQR_ERR_INVALID_ARG, "NULL argument");
+    if (!c->have_tick) return fail(MQR_ERR_INVALID_ARG, "no tick has completed yet");
+    if (!c->copy_stream) return fail(MQR_ERR_INVALID_ARG, "no mqr_tick_host_async before");
+    const uint64_t N = c->last.n_present;
+    *n = N;
+    if (N == 0) return MQR_OK;
+    if (cap < N) return fail(MQR_ERR_CAPACITY, "buffer too small");
+    MQR_CUDA(cudaSetDevice(c->device));
+    const int b = c->next_stage ^ 1;                 // the staging set of the last asynchronous tick
+    DevBuf<uint32_t> &snap = b ? c->sid_stage2 : c->sid_stage;
+    if (!c->snap_done) MQR_CUDA(cudaEventCreateWithFlags(&c->snap_done, cudaEventDisableTiming));
+    // the previous copy out of this snapshot buffer is ordered before the last tick's output copy,
+    // which the last asynchronous tick already waited for
+    MQR_CUDA(snap.ensure(c->nmax));
+    MQR_CUDA(cudaMemcpyAsync(snap.p, c->sid.p, N * 4, cudaMemcpyDeviceToDevice, c->stream));
+    MQR_CUDA(cudaEventRecord(c->snap_done, c->stream));
+    MQR_CUDA(cudaStreamWaitEvent(c->copy_stream, c->snap_done, 0));
+    MQR_CUDA(cudaMemcpyAsync(ids_host, snap.p, N * 4, cudaMemcpyDeviceToHost, c->copy_stream));
+    MQR_CUDA(cudaEventRecord(c->copy_done[b], c->copy_stream));
+    c->copy_pending[b] = true;
     return MQR_OK;
 }
 

@@ -27,7 +27,9 @@ KINDS = {"pairs": MQR_OUT_PAIRS, "pairs_sorted": MQR_OUT_PAIRS_SORTED, "csr": MQ
 
 # Every symbol include/mqr.h declares.
 EXPORTS = ["mqr_config_default", "mqr_create", "mqr_create_ex", "mqr_apply_updates",
-           "mqr_apply_updates_host", "mqr_tick", "mqr_tick_host", "mqr_tick_admit", "mqr_set_graph", "mqr_set_worlds",
+           "mqr_apply_updates_host", "mqr_tick", "mqr_tick_host", "mqr_tick_host_async", "mqr_host_wait",
+           "mqr_get_sorted_async",
+           "mqr_tick_admit", "mqr_set_graph", "mqr_set_worlds",
            "mqr_set_query_worlds", "mqr_set_index", "mqr_cost_param_count", "mqr_cost_create",
            "mqr_cost_set_params", "mqr_cost_get_params", "mqr_cost_train", "mqr_cost_gradient", "mqr_cost_predict",
            "mqr_cost_destroy", "mqr_get_stats",
@@ -99,6 +101,9 @@ def load(path: str = LIB_PATH):
         "mqr_apply_updates_host": ([P, P, P, u32], i32),
         "mqr_tick": ([P, P, u32, i32, P, u64, ctypes.POINTER(u64), P], i32),
         "mqr_tick_host": ([P, P, u32, i32, P, u64, ctypes.POINTER(u64), P], i32),
+        "mqr_tick_host_async": ([P, P, u32, i32, P, u64, ctypes.POINTER(u64), P], i32),
+        "mqr_host_wait": ([P], i32),
+        "mqr_get_sorted_async": ([P, P, u64, ctypes.POINTER(u64)], i32),
         "mqr_tick_admit": ([P, P, u32, i32, P, u64, ctypes.POINTER(u32), ctypes.POINTER(u64), P], i32),
         "mqr_set_graph": ([P, i32], i32),
         "mqr_set_worlds": ([P, u32, P], i32),
@@ -281,6 +286,25 @@ def mqr_set_worlds(ctx, obj_base):
 def mqr_set_query_worlds(ctx, q_base):
     b = np.ascontiguousarray(q_base, dtype=np.uint32)
     _check(load().mqr_set_query_worlds(ctx, b.ctypes.data))
+
+
+def mqr_tick_host_async(ctx, rects_host, Q, kind, out_host, out_capacity_bytes, offsets_host=None, check=True):
+    cnt = ctypes.c_uint64(0)
+    st = load().mqr_tick_host_async(ctx, _hptr(rects_host), Q, kind, _hptr(out_host), out_capacity_bytes,
+                                    ctypes.byref(cnt), _hptr(offsets_host))
+    if check and st not in (MQR_OK, MQR_ERR_CAPACITY):
+        _check(st)
+    return st, int(cnt.value)
+
+
+def mqr_host_wait(ctx):
+    _check(load().mqr_host_wait(ctx))
+
+
+def mqr_get_sorted_async(ctx, ids_host):
+    n = ctypes.c_uint64(0)
+    _check(load().mqr_get_sorted_async(ctx, _hptr(ids_host), int(ids_host.shape[0]), ctypes.byref(n)))
+    return int(n.value)
 
 
 def mqr_get_stats(ctx):

@@ -269,3 +269,79 @@ def test_graph_mode_replays_identical_results():
     g.set_graph(False)
     g.close()
     plain.close()
+
+
+def test_async_host_ticks_overlap_and_match_the_oracle():
+    """mqr_tick_host_async: four ticks in a row, each copying into its own
+    page-locked host buffer while the next runs; after mqr_host_wait every
+    buffer holds its tick's results (offsets and sorted lists = oracle)."""
+    torch, dev = torch_dev()
+    from paper_1411_3212_gb300 import mqr
+    w = workloads.HotspotWalk(n=30000, q=2000, hotspots=6, side_lo=0.001, side_hi=0.03, seed=44)
+    ticks = [w.next_tick() for _ in range(4)]
+    ctx = mqr.mqr_create((0.0, 0.0, 1.0, 1.0), 32, 30000)
+    st = oracle.State(30000)
+    wants, outs, offs, cnts = [], [], [], []
+    try:
+        for t in ticks:
+            st.apply_updates(t.ids, t.xy)
+            wants.append(oracle.join_grid(st, t.rects, cell_side=0.005))
+            out = torch.zeros(2 * (wants[-1][1].shape[0] + 64), dtype=torch.int32).pin_memory()
+            off = torch.zeros(t.rects.shape[0] + 1, dtype=torch.int64).pin_memory()
+            mqr.mqr_apply_updates_host(ctx, np.ascontiguousarray(t.ids), np.ascontiguousarray(t.xy))
+            s, cnt = mqr.mqr_tick_host_async(ctx, np.ascontiguousarray(t.rects), t.rects.shape[0], mqr.MQR_OUT_PAIRS,
+                                             out.numpy(), out.numel() * 4, off.numpy())
+            assert s == mqr.MQR_OK and cnt == wants[-1][1].shape[0]
+            outs.append(out)
+            offs.append(off)
+            cnts.append(cnt)
+        mqr.mqr_host_wait(ctx)
+        for (woff, wids), out, off, cnt, t in zip(wants, outs, offs, cnts, ticks):
+            p = out.numpy().view(np.uint32)[: 2 * cnt].reshape(-1, 2)
+            o = off.numpy().view(np.uint64)
+            np.testing.assert_array_equal(o, woff)
+            ids = p[:, 1].copy()
+            for q in range(t.rects.shape[0]):
+                ids[int(o[q]):int(o[q + 1])] = np.sort(ids[int(o[q]):int(o[q + 1])])
+            np.testing.assert_array_equal(ids, wids)
+    finally:
+        mqr.mqr_destroy(ctx)
+
+
+def test_async_runs_with_async_sorted_ids():
+    """RUNS output through mqr_tick_host_async + mqr_get_sorted_async on three
+    ticks in a row: each tick's runs expand, with that tick's sorted ids, to
+    the oracle's sets."""
+    torch, dev = torch_dev()
+    from paper_1411_3212_gb300 import mqr
+    w = workloads.HotspotWalk(n=30000, q=1500, hotspots=6, side_lo=0.002, side_hi=0.04, seed=45)
+    ticks = [w.next_tick() for _ in range(3)]
+    ctx = mqr.mqr_create((0.0, 0.0, 1.0, 1.0), 32, 30000)
+    st = oracle.State(30000)
+    keep = []
+    try:
+        for t in ticks:
+            st.apply_updates(t.ids, t.xy)
+            want = oracle.join_grid(st, t.rects, cell_side=0.005)
+            out = torch.zeros(2 * (want[1].shape[0] + 64), dtype=torch.int32).pin_memory()
+            off = torch.zeros(t.rects.shape[0] + 1, dtype=torch.int64).pin_memory()
+            sid = torch.zeros(30000, dtype=torch.int32).pin_memory()
+            mqr.mqr_apply_updates_host(ctx, np.ascontiguousarray(t.ids), np.ascontiguousarray(t.xy))
+            s, cnt = mqr.mqr_tick_host_async(ctx, np.ascontiguousarray(t.rects), t.rects.shape[0], mqr.MQR_OUT_RUNS,
+                                             out.numpy(), out.numel() * 4, off.numpy())
+            assert s == mqr.MQR_OK
+            assert mqr.mqr_get_sorted_async(ctx, sid.numpy().view(np.uint32)) == 30000
+            keep.append((want, out, off, sid, cnt, t.rects.shape[0]))
+        mqr.mqr_host_wait(ctx)
+        for (woff, wids), out, off, sid, cnt, Q in keep:
+            e = out.numpy().view(np.uint32)[: 2 * cnt].reshape(-1, 2)
+            pairs, counts = expand_runs(e, sid.numpy().view(np.uint32))
+            eo = off.numpy().view(np.uint64).astype(np.int64)
+            per_q = np.array([counts[eo[q]:eo[q + 1]].sum() for q in range(Q)], np.int64)
+            o = np.concatenate([[0], np.cumsum(per_q)]).astype(np.uint64)
+            ids = pairs[:, 1].copy()
+            for q in range(Q):
+                ids[int(o[q]):int(o[q + 1])] = np.sort(ids[int(o[q]):int(o[q + 1])])
+            assert_same_csr((o, ids), (woff, wids))
+    finally:
+        mqr.mqr_destroy(ctx)
