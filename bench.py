@@ -115,10 +115,14 @@ def phase_bytes(s, n_updates, nmax):
 
 
 def source_hash():
+    """Hash of the kernels' sources (k_*.cu and their shared header; the host
+    code of mqr_api.cu does not change what a kernel moves)."""
     h = hashlib.sha256()
-    for f in sorted(os.listdir(os.path.join(ROOT, "paper_1411_3212_gb300", "csrc"))):
-        with open(os.path.join(ROOT, "paper_1411_3212_gb300", "csrc", f), "rb") as fh:
-            h.update(fh.read())
+    d = os.path.join(ROOT, "paper_1411_3212_gb300", "csrc")
+    for f in sorted(os.listdir(d)):
+        if f.startswith("k_") or f == "mqr_internal.cuh":
+            with open(os.path.join(d, f), "rb") as fh:
+                h.update(fh.read())
     return h.hexdigest()[:16]
 
 
