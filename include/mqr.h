@@ -298,6 +298,20 @@ mqr_status mqr_set_query_worlds(mqr_ctx *ctx, const uint32_t *q_base_host);
  * INVALID_ARG. */
 mqr_status mqr_set_index(mqr_ctx *ctx, int index_kind, uint32_t leaf_cap, uint32_t grid_level);
 
+/* Per-region split thresholds of the quadtree (Alg. 1's th_quad chosen per
+ * region instead of once): the quadrants of level region_bits (1..4) are the
+ * regions, numbered in Morton order (region r holds the keys whose top
+ * 2*region_bits bits are r); a quadrant at or below that level splits iff it
+ * holds more objects than caps_host[r] of its region (and is above l_max);
+ * non-empty quadrants above that level always split.  caps_host: uint32 host
+ * array of 4^region_bits thresholds, each in 1..16384 (copied).  leaf_cap is
+ * then unused; region_bits = 0 returns to the single leaf_cap (caps_host may
+ * be NULL).  Applies to MQR_INDEX_QUADTREE ticks (a uniform grid ignores it);
+ * combines with batched worlds (no leaf above either level).  Results never
+ * depend on the thresholds; time does.  Call between ticks.  Errors:
+ * INVALID_ARG. */
+mqr_status mqr_set_region_caps(mqr_ctx *ctx, uint32_t region_bits, const uint32_t *caps_host);
+
 /* Learned tick-cost model: a multilayer perceptron 5 -> 64 -> 64 -> 1 with
  * ReLU hidden layers, trained on the device (hand-written forward, backward
  * and Adam kernels, one block) to map tick features to the logarithm of the

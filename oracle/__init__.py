@@ -14,7 +14,8 @@ Functions (each citing the paper passage its C routine follows):
   bitmap         -- query x object bitmap of a result (bitmap layout of the
                     filtering phase, Sec. 5.4, taken over the whole Q x N).
   cell / scale / morton / keys -- Morton codes at l_max = 15 (Alg. 1).
-  quadtree       -- Alg. 1 PR-quadtree leaves, level by level.
+  quadtree       -- Alg. 1 PR-quadtree leaves, level by level (one split
+                    threshold, or one per region of a chosen level).
   subqueries     -- Def. "Mapping functions" g(q), intersecting/covering.
 """
 from __future__ import annotations
@@ -77,6 +78,8 @@ def _load():
     lib.orc_keys.restype = None
     lib.orc_quadtree.argtypes = [P, u32, u32, u32, P, u64]
     lib.orc_quadtree.restype = i64
+    lib.orc_quadtree_regions.argtypes = [P, u32, u32, P, u32, P, u64]
+    lib.orc_quadtree_regions.restype = i64
     lib.orc_subqueries.argtypes = [P, u64, ctypes.c_int, P, f32, f32, f32, f32, P, P, u64]
     lib.orc_subqueries.restype = i64
     lib.orc_free.argtypes = [P]
@@ -194,14 +197,26 @@ def keys(state: State, bounds=(0.0, 0.0, 1.0, 1.0)):
     return out
 
 
-def quadtree(sorted_keys, th_quad: int, lmax: int = 15):
-    """Alg. 1 leaves -> structured array (level, z, begin, end) in Morton order."""
+def quadtree(sorted_keys, th_quad: int, lmax: int = 15, region_bits: int = 0, region_caps=None):
+    """Alg. 1 leaves -> structured array (level, z, begin, end) in Morton order.
+
+    region_bits > 0: the split threshold of a quadrant at level >= region_bits
+    is region_caps[its ancestor at level region_bits] (4^region_bits entries,
+    Morton order) and th_quad is unused; non-empty quadrants above that level
+    are split."""
     k = np.ascontiguousarray(sorted_keys, dtype=np.uint32)
     n = k.shape[0]
-    cap = 4 * max(n, 1) * (lmax + 1) + 4
+    cap = 4 * max(n, 1) * (lmax + 1) + 4 ** region_bits + 4
     out = (Leaf * cap)()
-    r = _load().orc_quadtree(_ptr(k), n, int(min(th_quad, 0xFFFFFFFF)), lmax,
-                             ctypes.cast(out, ctypes.c_void_p), cap)
+    if region_bits:
+        caps = np.ascontiguousarray(region_caps, dtype=np.uint32)
+        if caps.shape != (4 ** region_bits,):
+            raise ValueError("region_caps must hold 4^region_bits thresholds")
+        r = _load().orc_quadtree_regions(_ptr(k), n, region_bits, _ptr(caps), lmax,
+                                         ctypes.cast(out, ctypes.c_void_p), cap)
+    else:
+        r = _load().orc_quadtree(_ptr(k), n, int(min(th_quad, 0xFFFFFFFF)), lmax,
+                                 ctypes.cast(out, ctypes.c_void_p), cap)
     if r < 0:
         raise RuntimeError("oracle quadtree failed")
     dt = np.dtype([("level", np.uint32), ("z", np.uint32), ("begin", np.uint32), ("end", np.uint32)])

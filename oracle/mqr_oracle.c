@@ -30,6 +30,10 @@
  *                         child quadrant intervals of every quadrant to split,
  *                         keep a quadrant as a leaf when it holds at most
  *                         th_quad objects or sits at l_max.
+ *   - orc_quadtree_regions : the same with a split threshold per region (the
+ *                         quadrants of one chosen level): quadrants above that
+ *                         level split when non-empty, the others compare their
+ *                         count with their region's threshold.
  *   - orc_subqueries    : Def. "Mapping functions" (function g, query
  *                         splitting, intersecting vs covering subqueries),
  *                         by testing the query against every leaf.
@@ -348,12 +352,24 @@ static int orc_leaf_cmp(const void *a, const void *b)
     return (kx > ky) - (kx < ky);
 }
 
-int64_t orc_quadtree(const uint32_t *keys, uint32_t n, uint32_t th_quad,
-                     uint32_t lmax, orc_leaf *out, uint64_t out_cap)
+/* Split threshold of the quadrant z at level l.  With one global th_quad  */
+/* (region_bits = 0, caps = {th_quad}) this is Alg. 1's test.  With          */
+/* per-region thresholds the quadrants of level region_bits are regions:     */
+/* a quadrant at or below that level takes the threshold of the region that  */
+/* contains it, caps[z / 4^(l - region_bits)]; every non-empty quadrant      */
+/* above that level is split.                                                */
+static uint32_t orc_threshold(uint32_t l, uint32_t z, uint32_t region_bits, const uint32_t *caps)
+{
+    if (l < region_bits) return 0;
+    return caps[z >> (2 * (l - region_bits))];
+}
+
+int64_t orc_quadtree_regions(const uint32_t *keys, uint32_t n, uint32_t region_bits, const uint32_t *caps,
+                             uint32_t lmax, orc_leaf *out, uint64_t out_cap)
 {
     uint64_t nleaf = 0;
-    if (lmax > 15) return -1;
-    if (n <= th_quad || lmax == 0) {
+    if (lmax > 15 || region_bits > lmax) return -1;
+    if (n <= orc_threshold(0, 0, region_bits, caps) || lmax == 0) {
         if (out_cap < 1) return -1;
         out[0].level = 0; out[0].z = 0; out[0].begin = 0; out[0].end = n;
         return 1;
@@ -378,7 +394,7 @@ int64_t orc_quadtree(const uint32_t *keys, uint32_t n, uint32_t th_quad,
                 while (pos < IA[a].end && (keys[pos] >> shift) == zc) ++pos;
                 uint32_t cnt = pos - b;
                 /* CPUcheckQuadrants: split or keep as leaf. */
-                if (cnt > th_quad && l < lmax) {
+                if (cnt > orc_threshold(l, zc, region_bits, caps) && l < lmax) {
                     next[nn].level = l; next[nn].z = zc; next[nn].begin = b; next[nn].end = pos;
                     ++nn;
                 } else {
@@ -396,6 +412,12 @@ int64_t orc_quadtree(const uint32_t *keys, uint32_t n, uint32_t th_quad,
     free(IA);
     qsort(out, (size_t)nleaf, sizeof(orc_leaf), orc_leaf_cmp);
     return (int64_t)nleaf;
+}
+
+int64_t orc_quadtree(const uint32_t *keys, uint32_t n, uint32_t th_quad,
+                     uint32_t lmax, orc_leaf *out, uint64_t out_cap)
+{
+    return orc_quadtree_regions(keys, n, 0, &th_quad, lmax, out, out_cap);
 }
 
 /* ------------------------------------------------------------------------ */

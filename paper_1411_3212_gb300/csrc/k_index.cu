@@ -374,7 +374,8 @@ __global__ void window_double_kernel(const uint8_t *__restrict__ a, uint8_t *__r
 
 __global__ void __launch_bounds__(kLeafThreads)
 leaves_kernel(const uint32_t *__restrict__ K, uint32_t cap, int uniform_grid, uint32_t grid_level,
-              uint32_t min_level, int kexp, const uint8_t *__restrict__ Mk_global, uint32_t *status,
+              uint32_t min_level, uint32_t region_bits, const uint32_t *__restrict__ region_cap, int kexp,
+              const uint8_t *__restrict__ Mk_global, uint32_t *status,
               uint32_t *tile_counter, uint32_t *__restrict__ leaf_lo, uint32_t *__restrict__ leaf_hi,
               uint32_t *__restrict__ leaf_beg, uint32_t *__restrict__ leaf_nsub, uint2 *__restrict__ leaf_box,
               Info *info) {
@@ -392,8 +393,56 @@ leaves_kernel(const uint32_t *__restrict__ K, uint32_t cap, int uniform_grid, ui
     if (t0 >= (long)N) return;
     const long tend = min((long)N, t0 + kLeafTile);
 
-    const bool root_only = !uniform_grid && cap >= N;
-    if (uniform_grid || root_only) {
+    const bool root_only = !uniform_grid && !region_bits && cap >= N;
+    if (region_bits) {
+        // Per-region capacities: the nodes of depth region_bits are regions,
+        // region r (Morton prefix r) splitting its nodes at region_cap[r].
+        // The positions of one region are contiguous; for each region the
+        // tile meets, the window rule runs with that region's capacity.
+        // Windows that leave the region share fewer than region_bits levels
+        // and never raise a level above region_bits, the minimum level.
+        __shared__ long s_ab[2];
+        const uint32_t sh = 2u * (kLevels - region_bits);
+        const long pa = t0 > 0 ? t0 - 1 : 0, pb = tend;
+        const uint32_t r_lo = K[pa] >> sh, r_hi = K[pb - 1] >> sh;
+        for (uint32_t r = r_lo; r <= r_hi; ++r) {
+            if (tid == 0) {
+                long a = pa, b = pb;                  // first position with key >= r << sh
+                while (a < b) { long m = (a + b) >> 1; if ((K[m] >> sh) < r) a = m + 1; else b = m; }
+                long c = a, d = pb;                   // first position of a later region
+                while (c < d) { long m = (c + d) >> 1; if ((K[m] >> sh) <= r) c = m + 1; else d = m; }
+                s_ab[0] = a;
+                s_ab[1] = c;
+            }
+            __syncthreads();
+            const long a = s_ab[0], b = s_ab[1];
+            if (a < b) {
+                const uint32_t rc = region_cap[r];
+                int rk = 0;
+                while ((2ull << rk) <= (unsigned long long)rc + 1) ++rk;   // floor(log2(rc+1))
+                const long rs = a - (long)rc;         // the window of position a starts here
+                const int S = (int)(b - rs);
+                uint8_t *A = dsm, *B = dsm + (kLeafTile + kLeafCapSmem + 1);
+                for (int j = tid; j < S; j += kLeafThreads) A[j] = window_enc(K, rs + j, rc, N);
+                __syncthreads();
+                for (int st = 0; st < rk; ++st) {
+                    const int step = 1 << st;
+                    for (int j = tid; j < S; j += kLeafThreads) {
+                        uint8_t v = A[j];
+                        if (j + step < S) v = max(v, A[j + step]);
+                        B[j] = v;
+                    }
+                    __syncthreads();
+                    uint8_t *t = A; A = B; B = t;
+                }
+                for (long p = a + tid; p < b; p += kLeafThreads) {
+                    uint8_t m = max(A[p - (long)rc - rs], A[p - (1l << rk) + 1 - rs]);
+                    s_L[p - (t0 - 1)] = m > 15 ? 15 : m;
+                }
+            }
+            __syncthreads();
+        }
+    } else if (uniform_grid || root_only) {
         uint8_t lv = uniform_grid ? (uint8_t)grid_level : (uint8_t)0;
         for (int i = tid; i <= kLeafTile; i += kLeafThreads) s_L[i] = lv;
     } else if (Mk_global == nullptr) {
@@ -488,7 +537,8 @@ leaves_kernel(const uint32_t *__restrict__ K, uint32_t cap, int uniform_grid, ui
 }
 
 void launch_build_leaves(cudaStream_t st, const uint32_t *skey, uint32_t nmax, uint32_t cap,
-                         int uniform_grid, uint32_t grid_level, uint32_t min_level, uint8_t *mk_a, uint8_t *mk_b,
+                         int uniform_grid, uint32_t grid_level, uint32_t min_level, uint32_t region_bits,
+                         const uint32_t *region_cap, uint8_t *mk_a, uint8_t *mk_b,
                          uint32_t *status, uint32_t *tile_counter, uint32_t *leaf_lo,
                          uint32_t *leaf_hi, uint32_t *leaf_beg, uint32_t *leaf_nsub, uint2 *leaf_box,
                          Info *info) {
@@ -498,7 +548,9 @@ void launch_build_leaves(cudaStream_t st, const uint32_t *skey, uint32_t nmax, u
     while ((2ull << kexp) <= (unsigned long long)cap + 1) ++kexp;   // floor(log2(cap+1))
     const uint8_t *mk = nullptr;
     size_t dyn = 0;
-    if (!uniform_grid && cap < nmax) {
+    if (region_bits) {
+        dyn = 2 * (size_t)(kLeafTile + kLeafCapSmem + 1);        // every region capacity <= kLeafCapSmem
+    } else if (!uniform_grid && cap < nmax) {
         if (cap <= (uint32_t)kLeafCapSmem) {
             dyn = 2 * (size_t)(kLeafTile + kLeafCapSmem + 1);
         } else {
@@ -512,7 +564,8 @@ void launch_build_leaves(cudaStream_t st, const uint32_t *skey, uint32_t nmax, u
             mk = a;
         }
     }
-    leaves_kernel<<<tiles, kLeafThreads, dyn, st>>>(skey, cap, uniform_grid, grid_level, min_level, kexp, mk,
+    leaves_kernel<<<tiles, kLeafThreads, dyn, st>>>(skey, cap, uniform_grid, grid_level, min_level, region_bits,
+                                                    region_cap, kexp, mk,
                                                     status, tile_counter, leaf_lo, leaf_hi, leaf_beg,
                                                     leaf_nsub, leaf_box, info);
 }

@@ -137,6 +137,9 @@ struct mqr_ctx {
     // batched independent worlds (mqr_set_worlds): id and query ranges per world
     uint32_t n_worlds = 0, world_bits = 0;
     DevBuf<uint32_t> world_obj, world_q;
+    // per-region leaf capacities (mqr_set_region_caps): 4^region_bits entries
+    uint32_t region_bits = 0;
+    DevBuf<uint32_t> region_cap;
     unsigned long long world_q_total = 0;
     bool world_q_set = false;
 
@@ -305,11 +308,13 @@ mqr_status enqueue_tick(mqr_ctx *c, const float4 *rects, uint32_t Q, int emit_ki
     phase_begin(c, MQR_PHASE_LEAVES);
     const uint32_t cap = c->cfg.leaf_cap;
     const bool ug = c->cfg.index_kind == MQR_INDEX_UNIFORM_GRID;
-    launch_build_leaves(st, c->skey.p, nmax, cap, ug, c->cfg.grid_level, c->world_bits, c->mk_a.p, c->mk_b.p,
+    const uint32_t rbits = ug ? 0 : c->region_bits;          // region capacities refine the quadtree only
+    launch_build_leaves(st, c->skey.p, nmax, cap, ug, c->cfg.grid_level, std::max(c->world_bits, rbits), rbits,
+                        c->region_cap.p, c->mk_a.p, c->mk_b.p,
                         at<uint32_t>(c, a.st_leaf), ctr + 4, c->leaf_lo.p, c->leaf_hi.p, c->leaf_beg.p,
                         c->leaf_nsub.p, c->leaf_box.p, info);
     uint64_t leaf_launches = nmax ? 1 : 0;
-    if (nmax && !ug && cap > (uint32_t)kLeafCapSmem && cap < nmax) {
+    if (nmax && !ug && !rbits && cap > (uint32_t)kLeafCapSmem && cap < nmax) {
         int kexp = 0;
         while ((2ull << kexp) <= (unsigned long long)cap + 1) ++kexp;
         leaf_launches += 1 + kexp;
@@ -800,9 +805,35 @@ mqr_status mqr_set_index(mqr_ctx *c, int index_kind, uint32_t leaf_cap, uint32_t
         return fail(MQR_ERR_INVALID_ARG, "grid_level must be in 1..15 (and >= the worlds' levels)");
     MQR_CUDA(cudaSetDevice(c->device));
     MQR_CUDA(cudaStreamSynchronize(c->stream));
+    if (index_kind == MQR_INDEX_QUADTREE && leaf_cap > (uint32_t)kLeafCapSmem && leaf_cap < c->nmax) {
+        const size_t n = c->nmax;                  // the global window tables of large capacities
+        MQR_CUDA(c->mk_a.ensure(2 * n + 2));
+        MQR_CUDA(c->mk_b.ensure(2 * n + 2));
+    }
     c->cfg.index_kind = index_kind;
     if (index_kind == MQR_INDEX_QUADTREE) c->cfg.leaf_cap = leaf_cap;
     else c->cfg.grid_level = grid_level;
+    ++g_buf_gen;                                   // a captured tick holds the old configuration
+    return MQR_OK;
+}
+
+mqr_status mqr_set_region_caps(mqr_ctx *c, uint32_t region_bits, const uint32_t *caps_host) {
+    if (!c) return fail(MQR_ERR_INVALID_ARG, "ctx is NULL");
+    if (region_bits > kMaxRegionBits) return fail(MQR_ERR_INVALID_ARG, "region_bits must be 0..4");
+    const size_t n = (size_t)1 << (2 * region_bits);
+    if (region_bits) {
+        if (!caps_host) return fail(MQR_ERR_INVALID_ARG, "caps_host is NULL");
+        for (size_t r = 0; r < n; ++r)
+            if (caps_host[r] < 1 || caps_host[r] > (uint32_t)kLeafCapSmem)
+                return fail(MQR_ERR_INVALID_ARG, "region capacities must be in 1..16384");
+    }
+    MQR_CUDA(cudaSetDevice(c->device));
+    MQR_CUDA(cudaStreamSynchronize(c->stream));
+    if (region_bits) {
+        MQR_CUDA(c->region_cap.ensure(n));
+        MQR_CUDA(cudaMemcpy(c->region_cap.p, caps_host, n * sizeof(uint32_t), cudaMemcpyHostToDevice));
+    }
+    c->region_bits = region_bits;
     ++g_buf_gen;                                   // a captured tick holds the old configuration
     return MQR_OK;
 }
@@ -830,6 +861,7 @@ void mqr_destroy(mqr_ctx *c) {
     c->gexec = nullptr;
     c->world_obj.release();
     c->world_q.release();
+    c->region_cap.release();
     DevBuf<unsigned long long> *u64s[] = {&c->stamp, &c->keysA, &c->keysB, &c->out_off, &c->off_stage,
                                           &c->sortA, &c->sortB};
     for (auto *b : u64s) b->release();

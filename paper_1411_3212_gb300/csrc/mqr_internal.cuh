@@ -105,6 +105,9 @@ __host__ __device__ __forceinline__ uint32_t compact15(uint32_t v) {
 // and placed in that node; leaves never lie above depth `bits`.  n == 0: one
 // world, the whole grid.
 constexpr uint32_t kMaxWorlds = 16384;     // 4^7: at least 8 levels left per world
+// Per-region leaf capacities: the nodes of depth region_bits <= 4 (at most
+// 256 regions), each capacity at most kLeafCapSmem (shared-memory window table).
+constexpr uint32_t kMaxRegionBits = 4;
 struct Worlds {
     const uint32_t *obj_base;
     const uint32_t *q_base;
@@ -345,11 +348,14 @@ void launch_key_histograms(cudaStream_t st, const unsigned long long *keys, uint
                            const int *shifts_host, int nd, uint32_t *hist);
 
 // a4: leaves.  level_mode: 0 = quadtree (capacity rule), 1 = uniform grid at
-// `grid_level`; no leaf above depth min_level (the batched worlds' roots).
+// `grid_level`; no leaf above depth min_level (the batched worlds' roots);
+// region_bits > 0: per-region capacities region_cap[4^region_bits] (no leaf
+// above depth region_bits).
 // Writes leaf_lo/leaf_hi/leaf_beg and Info::n_leaves/max_level.
 constexpr int kLeafThreads = 256, kLeafTile = 2048, kLeafCapSmem = 16384;
 void launch_build_leaves(cudaStream_t st, const uint32_t *skey, uint32_t nmax, uint32_t cap,
-                         int uniform_grid, uint32_t grid_level, uint32_t min_level, uint8_t *mk_a, uint8_t *mk_b,
+                         int uniform_grid, uint32_t grid_level, uint32_t min_level, uint32_t region_bits,
+                         const uint32_t *region_cap, uint8_t *mk_a, uint8_t *mk_b,
                          uint32_t *status, uint32_t *tile_counter, uint32_t *leaf_lo,
                          uint32_t *leaf_hi, uint32_t *leaf_beg, uint32_t *leaf_nsub, uint2 *leaf_box,
                          Info *info);

@@ -30,7 +30,7 @@ EXPORTS = ["mqr_config_default", "mqr_create", "mqr_create_ex", "mqr_apply_updat
            "mqr_apply_updates_host", "mqr_tick", "mqr_tick_host", "mqr_tick_host_async", "mqr_host_wait",
            "mqr_get_sorted_async",
            "mqr_tick_admit", "mqr_set_graph", "mqr_set_worlds",
-           "mqr_set_query_worlds", "mqr_set_index", "mqr_cost_param_count", "mqr_cost_create",
+           "mqr_set_query_worlds", "mqr_set_index", "mqr_set_region_caps", "mqr_cost_param_count", "mqr_cost_create",
            "mqr_cost_set_params", "mqr_cost_get_params", "mqr_cost_train", "mqr_cost_gradient", "mqr_cost_predict",
            "mqr_cost_destroy", "mqr_get_stats",
            "mqr_get_leaves",
@@ -109,6 +109,7 @@ def load(path: str = LIB_PATH):
         "mqr_set_worlds": ([P, u32, P], i32),
         "mqr_set_query_worlds": ([P, P], i32),
         "mqr_set_index": ([P, i32, u32, u32], i32),
+        "mqr_set_region_caps": ([P, u32, P], i32),
         "mqr_cost_param_count": ([], u32),
         "mqr_cost_create": ([pctx], i32),
         "mqr_cost_set_params": ([P, P, u32], i32),
@@ -225,6 +226,17 @@ def mqr_set_graph(ctx, enable):
 
 def mqr_set_index(ctx, index_kind, leaf_cap=0, grid_level=0):
     _check(load().mqr_set_index(ctx, int(index_kind), int(leaf_cap), int(grid_level)))
+
+
+def mqr_set_region_caps(ctx, region_bits, caps=None):
+    """caps: 4^region_bits split thresholds in Morton order of the regions."""
+    if region_bits:
+        arr = np.ascontiguousarray(caps, dtype=np.uint32)
+        if arr.shape != (4 ** int(region_bits),):
+            raise ValueError("caps must hold 4^region_bits thresholds")
+        _check(load().mqr_set_region_caps(ctx, int(region_bits), arr.ctypes.data_as(ctypes.c_void_p)))
+    else:
+        _check(load().mqr_set_region_caps(ctx, 0, None))
 
 
 class CostModel:
@@ -424,6 +436,9 @@ class Index:
 
     def set_index(self, index_kind=0, leaf_cap=0, grid_level=0):
         mqr_set_index(self.ctx, index_kind, leaf_cap, grid_level)
+
+    def set_region_caps(self, region_bits, caps=None):
+        mqr_set_region_caps(self.ctx, region_bits, caps)
 
     def set_graph(self, enable=True):
         mqr_set_graph(self.ctx, enable)

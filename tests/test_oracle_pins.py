@@ -301,6 +301,70 @@ def test_quadtree_matches_geometric_definition(seed, cap, lmax):
     assert got == want
 
 
+def geometric_quadtree_regions(cells, region_bits, caps, lmax):
+    """Per-region split thresholds by the geometric definition: a quadrant at
+    level >= region_bits splits iff it holds more points than the threshold
+    of the level-region_bits quadrant containing it (and level < lmax); a
+    quadrant above that level splits iff it holds any point."""
+    out = []
+
+    def rec(l, bi, bj):
+        side = 1 << (lmax - l)
+        m = (cells[:, 0] >= bi) & (cells[:, 0] < bi + side) & (cells[:, 1] >= bj) & (cells[:, 1] < bj + side)
+        cnt = int(m.sum())
+        if l < region_bits:
+            th = 0
+        else:
+            rs = lmax - region_bits                  # region cell side: 2^rs finest cells
+            th = int(caps[py_interleave(bi >> rs, bj >> rs, region_bits)])
+        if cnt > th and l < lmax:
+            h = side // 2
+            for c in range(4):
+                rec(l + 1, bi + (c & 1) * h, bj + (c >> 1) * h)
+        else:
+            out.append((l, py_interleave(bi >> (lmax - l), bj >> (lmax - l), l), cnt))
+
+    rec(0, 0, 0)
+    return out
+
+
+@pytest.mark.parametrize("seed", range(4))
+@pytest.mark.parametrize("region_bits", [1, 2, 3])
+@pytest.mark.parametrize("lmax", [3, 6])
+def test_quadtree_regions_match_geometric_definition(seed, region_bits, lmax):
+    rng = np.random.default_rng(seed * 10 + region_bits)
+    n = int(rng.integers(0, 150))
+    side = 1 << lmax
+    if seed % 2:
+        cells = np.clip(rng.normal(side * 0.6, side * 0.08, (n, 2)), 0, side - 1).astype(np.int64)
+    else:
+        cells = rng.integers(0, side, (n, 2))
+    caps = rng.integers(1, 12, 4 ** region_bits)
+    keys = np.sort(np.array([py_interleave(int(i), int(j), lmax) for i, j in cells], np.uint32))
+    lv = oracle.quadtree(keys, 0, lmax, region_bits=region_bits, region_caps=caps)
+    want = geometric_quadtree_regions(cells, region_bits, caps, lmax)
+    got = [(int(l), int(z), int(e - b)) for l, z, b, e in zip(lv["level"], lv["z"], lv["begin"], lv["end"])]
+    assert got == want
+    # every non-empty leaf lies at or below the region level
+    assert all(l >= region_bits for l, _, c in got if c)
+
+
+def test_quadtree_regions_special_cases():
+    """Equal thresholds reduce to the single-threshold tree wherever that
+    tree's leaves already lie at or below the region level; region level 0
+    is the single-threshold tree itself."""
+    rng = np.random.default_rng(3)
+    cells = rng.integers(0, 64, (400, 2))
+    keys = np.sort(np.array([py_interleave(int(i), int(j), 6) for i, j in cells], np.uint32))
+    plain = oracle.quadtree(keys, 5, 6)
+    assert int(plain["level"][plain["begin"] != plain["end"]].min()) >= 2
+    for rb in (1, 2):
+        reg = oracle.quadtree(keys, 0, 6, region_bits=rb, region_caps=np.full(4 ** rb, 5))
+        np.testing.assert_array_equal(reg, plain)
+    with pytest.raises(ValueError):
+        oracle.quadtree(keys, 0, 6, region_bits=1, region_caps=[1, 2, 3])
+
+
 @pytest.mark.parametrize("cap", [1, 4, 64, 128, 5000, 2 ** 31])
 def test_quadtree_invariants_lmax15(cap):
     """Leaves partition [0, 4^15) in Morton order, own contiguous runs of the
