@@ -51,6 +51,11 @@ WORKLOADS = {
     "uniform1m": dict(kind="uniform", n=1_000_000, q=100_000, cap=128,
                       desc="uniform-1M: 1,000,000 uniform objects, random walk sigma 0.0005, 100,000 queries/tick "
                            "of side 0.002 centred on objects, leaf_cap 128, pair-list output"),
+    "mixed4m": dict(kind="mixed", n=4_000_000, q=310_000, cap=128,
+                    desc="mixed-4M: 4,000,000 objects, 75% in 32 Gaussian hotspots (sigma 0.01) in the left "
+                         "half queried by 300,000 squares of side log-uniform 0.0003-0.001, 25% uniform in the "
+                         "right half queried by 10,000 squares of side log-uniform 0.01-0.04; random walk "
+                         "sigma 0.0005 inside each half; leaf_cap 128, pair-list output"),
     "uniform16k": dict(kind="small", n=16384, q=1024, cap=64,
                        desc="uniform-16K: 16,384 uniform objects, 1,024 queries of side 0.01, leaf_cap 64"),
     "batched256": dict(kind="batched", n=0, q=0, cap=128,
@@ -77,6 +82,8 @@ def make_world(name, seed):
         return workloads.UniformWalk(n=w["n"], q=w["q"], seed=seed)
     if w["kind"] == "batched":
         return workloads.BatchedWorlds(n_worlds=256, seed=seed)
+    if w["kind"] == "mixed":
+        return workloads.MixedDensity(n=w["n"], seed=seed)
 
     class Small:
         def __init__(self):
@@ -639,7 +646,7 @@ def run_costmodel(args):
     9) against the fixed workload configuration, on the same ticks."""
     import torch
     from paper_1411_3212_gb300 import mqr
-    from paper_1411_3212_gb300.costmodel import GRID, QUAD, IndexChooser, mean_log2_side
+    from paper_1411_3212_gb300.costmodel import GRID, QUAD, REGIONS, IndexChooser, mean_log2_side
     dev = torch.device("cuda", 0)
     torch.cuda.set_device(dev)
     name = args.workload
@@ -674,7 +681,8 @@ def run_costmodel(args):
     for i in range(args.warmup):
         tick(i)
     fixed = [timed(args.warmup + (k % uniq)) for k in range(args.steps)]
-    cands = [(QUAD, 64), (QUAD, 128), (QUAD, 256), (QUAD, 512), (GRID, 8), (GRID, 9)]
+    cands = [(QUAD, 64), (QUAD, 128), (QUAD, 256), (QUAD, 512), (GRID, 8), (GRID, 9),
+             (REGIONS, 3, 8, -0.25), (REGIONS, 3, 8, 0.25), (REGIONS, 3, 7, 0.5)]
     ch = IndexChooser(candidates=cands, fallback=(QUAD, w["cap"]), seed=0)
     chosen, times = [], []
     for k in range(args.steps):
@@ -688,14 +696,24 @@ def run_costmodel(args):
     idx.close()
     ch.close()
     tail = max(1, args.steps // 2)
+
+    def label(c):
+        if c[0] == QUAD:
+            return "leaf_cap %d" % c[1]
+        if c[0] == GRID:
+            return "grid level %d" % c[1]
+        return "regions %d: cap 2^(%g %+g log2 density)" % (c[1], c[2], c[3])
     counts = {}
     for c in chosen[-tail:]:
-        key = ("leaf_cap %d" % c[1]) if c[0] == QUAD else ("grid level %d" % c[1])
-        counts[key] = counts.get(key, 0) + 1
+        counts[label(c)] = counts.get(label(c), 0) + 1
+    explored = {}
+    for c, ms in zip(chosen[:2 * len(cands)], times[:2 * len(cands)]):   # the round-robin exploration
+        explored.setdefault(label(c), []).append(ms)
     line = {"metric": "ms per tick, learned per-tick index choice vs fixed", "unit": "ms",
             "config": {"workload": w["desc"], "candidates": [list(c) for c in cands], "steps": args.steps},
             "fixed_ms_mean": float(np.mean(fixed[-tail:])), "chosen_ms_mean": float(np.mean(times[-tail:])),
             "explore_ms_mean": float(np.mean(times[:2 * len(cands)])), "chosen_last_half": counts,
+            "explored_ms": {k: float(np.mean(v)) for k, v in explored.items()},
             "model_loss": getattr(ch, "loss", None)}
     print(json.dumps(line), flush=True)
 

@@ -312,6 +312,16 @@ mqr_status mqr_set_index(mqr_ctx *ctx, int index_kind, uint32_t leaf_cap, uint32
  * INVALID_ARG. */
 mqr_status mqr_set_region_caps(mqr_ctx *ctx, uint32_t region_bits, const uint32_t *caps_host);
 
+/* Objects per region in the last completed tick: counts_host[r] = the number
+ * of present objects whose key has the Morton prefix r of length
+ * 2*region_bits (uint32 host array of 4^region_bits entries; regions as in
+ * mqr_set_region_caps, in the batched worlds' key space when worlds are
+ * set).  Computed on the device from the tick's sorted keys (Alg. 1), so a
+ * caller can choose the next tick's per-region thresholds from the local
+ * density.  1 <= region_bits <= 4.  Blocks.  Errors: INVALID_ARG (also
+ * before the first tick). */
+mqr_status mqr_region_counts(mqr_ctx *ctx, uint32_t region_bits, uint32_t *counts_host);
+
 /* Learned tick-cost model: a multilayer perceptron 5 -> 64 -> 64 -> 1 with
  * ReLU hidden layers, trained on the device (hand-written forward, backward
  * and Adam kernels, one block) to map tick features to the logarithm of the

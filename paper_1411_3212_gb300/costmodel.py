@@ -12,11 +12,19 @@ prediction -- after a round-robin exploration of the candidates, with a
 small exploration rate afterwards, and the fixed configuration as fallback
 while there is too little data.
 
+Configurations: the quadtree with one leaf capacity (QUAD, cap), the uniform
+grid (GRID, level), and the quadtree with per-region capacities (REGIONS,
+region_bits, a, b): region r of density d_r (objects per unit area over the
+mean, counted on the device from the previous tick) splits at
+2^(a + b log2 d_r).  b = 0 is one capacity everywhere; b = 1 keeps leaves of
+one size, like a grid.
+
 Features of a (tick, configuration): log2 objects, log2 queries, the mean
 log2 of the query sides, log2 of the objects per leaf the configuration aims
-for (leaf capacity, or objects per grid cell for the uniform grid), and
-whether it is the uniform grid.  Scheduling and marshalling only: the ticks
-and the model's arithmetic run in the library's kernels.
+for at the mean density (leaf capacity, objects per grid cell, or 2^a), and
+how that target scales with the local density (0 for one capacity, 1 for the
+grid, b for per-region capacities).  Scheduling and marshalling only: the
+ticks and the model's arithmetic run in the library's kernels.
 """
 from __future__ import annotations
 
@@ -26,7 +34,20 @@ import numpy as np
 
 from . import mqr
 
-QUAD, GRID = 0, 1
+QUAD, GRID, REGIONS = 0, 1, 2
+MAX_REGION_CAP = 16384
+
+
+def region_caps(counts, region_bits, a, b):
+    """Per-region capacities 2^(a + b log2 d_r), d_r = the region's objects per
+    unit area over the mean (empty regions: 2^a), rounded, within 1..16384."""
+    c = np.asarray(counts, np.float64)
+    if c.shape != (4 ** region_bits,):
+        raise ValueError("counts must hold 4^region_bits entries")
+    total = c.sum()
+    d = c * (4 ** region_bits) / total if total > 0 else np.ones_like(c)
+    ld = np.where(c > 0, np.log2(np.maximum(d, 1e-30)), 0.0)
+    return np.clip(np.rint(np.exp2(a + b * ld)), 1, MAX_REGION_CAP).astype(np.uint32)
 
 
 def he_uniform_params(seed: int) -> np.ndarray:
@@ -56,10 +77,15 @@ class IndexChooser:
 
     @staticmethod
     def features(cand, n_objects, n_queries, mean_log2_side):
-        kind, v = cand
-        per_leaf = v if kind == QUAD else max(n_objects / float(4 ** v), 1e-3)
+        kind = cand[0]
+        if kind == QUAD:
+            per_leaf, slope = cand[1], 0.0
+        elif kind == GRID:
+            per_leaf, slope = max(n_objects / float(4 ** cand[1]), 1e-3), 1.0
+        else:
+            per_leaf, slope = 2.0 ** cand[2], float(cand[3])
         return np.array([math.log2(max(n_objects, 1)) / 32.0, math.log2(max(n_queries, 1)) / 32.0,
-                         mean_log2_side / 16.0, math.log2(per_leaf) / 16.0, float(kind == GRID)], np.float32)
+                         mean_log2_side / 16.0, math.log2(per_leaf) / 16.0, slope], np.float32)
 
     def choose(self, n_objects, n_queries, mean_log2_side):
         k = self.n_choices
@@ -81,11 +107,23 @@ class IndexChooser:
             self.trained = True
 
     def apply(self, idx, cand):
-        kind, v = cand
+        """Configure the index for the next tick (between ticks: leaves are
+        rebuilt every tick, results never change)."""
+        kind = cand[0]
+        if kind == REGIONS:
+            _, rb, a, b = cand
+            try:
+                counts = idx.region_counts(rb)          # densities of the previous tick
+            except mqr.MqrError:                        # no tick yet: one capacity
+                counts = np.ones(4 ** rb, np.uint32)
+            idx.set_index(QUAD, leaf_cap=int(min(2 ** a, MAX_REGION_CAP)))
+            idx.set_region_caps(rb, region_caps(counts, rb, a, b))
+            return
+        idx.set_region_caps(0)
         if kind == QUAD:
-            idx.set_index(QUAD, leaf_cap=v)
+            idx.set_index(QUAD, leaf_cap=cand[1])
         else:
-            idx.set_index(GRID, grid_level=v)
+            idx.set_index(GRID, grid_level=cand[1])
 
     def close(self):
         self.model.close()

@@ -401,21 +401,22 @@ leaves_kernel(const uint32_t *__restrict__ K, uint32_t cap, int uniform_grid, ui
         // tile meets, the window rule runs with that region's capacity.
         // Windows that leave the region share fewer than region_bits levels
         // and never raise a level above region_bits, the minimum level.
-        __shared__ long s_ab[2];
+        // s_first[r - r_lo] = first position of region r (r_lo < r <= r_hi),
+        // found in parallel at the positions where the region changes.
+        __shared__ int s_first[(1 << (2 * kMaxRegionBits)) + 1];
         const uint32_t sh = 2u * (kLevels - region_bits);
         const long pa = t0 > 0 ? t0 - 1 : 0, pb = tend;
         const uint32_t r_lo = K[pa] >> sh, r_hi = K[pb - 1] >> sh;
-        for (uint32_t r = r_lo; r <= r_hi; ++r) {
-            if (tid == 0) {
-                long a = pa, b = pb;                  // first position with key >= r << sh
-                while (a < b) { long m = (a + b) >> 1; if ((K[m] >> sh) < r) a = m + 1; else b = m; }
-                long c = a, d = pb;                   // first position of a later region
-                while (c < d) { long m = (c + d) >> 1; if ((K[m] >> sh) <= r) c = m + 1; else d = m; }
-                s_ab[0] = a;
-                s_ab[1] = c;
+        if (r_hi > r_lo) {
+            for (long p = pa + 1 + tid; p < pb; p += kLeafThreads) {
+                const uint32_t r0 = K[p - 1] >> sh, r1 = K[p] >> sh;
+                for (uint32_t r = r0 + 1; r <= r1; ++r) s_first[r - r_lo] = (int)(p - pa);
             }
             __syncthreads();
-            const long a = s_ab[0], b = s_ab[1];
+        }
+        for (uint32_t r = r_lo; r <= r_hi; ++r) {
+            const long a = r == r_lo ? pa : pa + s_first[r - r_lo];
+            const long b = r == r_hi ? pb : pa + s_first[r + 1 - r_lo];
             if (a < b) {
                 const uint32_t rc = region_cap[r];
                 int rk = 0;
@@ -534,6 +535,33 @@ leaves_kernel(const uint32_t *__restrict__ K, uint32_t cap, int uniform_grid, ui
         leaf_beg[s_prefix + total] = N;
         info->n_leaves = s_prefix + total;
     }
+}
+
+// Objects per region (the Morton prefixes of length 2*region_bits) of the
+// sorted keys: thread r finds the first key of regions r and r+1.
+__global__ void region_counts_kernel(const uint32_t *__restrict__ K, uint32_t N, uint32_t region_bits,
+                                     uint32_t *__restrict__ counts) {
+    const uint32_t R = 1u << (2 * region_bits), sh = 2u * (kLevels - region_bits);
+    const uint32_t r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= R) return;
+    uint32_t bound[2];
+    for (int e = 0; e < 2; ++e) {
+        const uint32_t v = r + e;
+        uint32_t a = 0, b = N;
+        while (a < b) {
+            const uint32_t m = a + (b - a) / 2;
+            if ((K[m] >> sh) < v) a = m + 1; else b = m;
+        }
+        bound[e] = a;
+    }
+    counts[r] = bound[1] - bound[0];
+}
+
+cudaError_t launch_region_counts(cudaStream_t st, const uint32_t *skey, uint32_t n, uint32_t region_bits,
+                                 uint32_t *counts) {
+    const uint32_t R = 1u << (2 * region_bits);
+    region_counts_kernel<<<(R + 127) / 128, 128, 0, st>>>(skey, n, region_bits, counts);
+    return cudaGetLastError();
 }
 
 void launch_build_leaves(cudaStream_t st, const uint32_t *skey, uint32_t nmax, uint32_t cap,

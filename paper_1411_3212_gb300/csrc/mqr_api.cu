@@ -139,7 +139,7 @@ struct mqr_ctx {
     DevBuf<uint32_t> world_obj, world_q;
     // per-region leaf capacities (mqr_set_region_caps): 4^region_bits entries
     uint32_t region_bits = 0;
-    DevBuf<uint32_t> region_cap;
+    DevBuf<uint32_t> region_cap, region_cnt;
     unsigned long long world_q_total = 0;
     bool world_q_set = false;
 
@@ -827,6 +827,7 @@ mqr_status mqr_set_region_caps(mqr_ctx *c, uint32_t region_bits, const uint32_t 
             if (caps_host[r] < 1 || caps_host[r] > (uint32_t)kLeafCapSmem)
                 return fail(MQR_ERR_INVALID_ARG, "region capacities must be in 1..16384");
     }
+    if (!region_bits && !c->region_bits) return MQR_OK;     // nothing changes
     MQR_CUDA(cudaSetDevice(c->device));
     MQR_CUDA(cudaStreamSynchronize(c->stream));
     if (region_bits) {
@@ -862,6 +863,7 @@ void mqr_destroy(mqr_ctx *c) {
     c->world_obj.release();
     c->world_q.release();
     c->region_cap.release();
+    c->region_cnt.release();
     DevBuf<unsigned long long> *u64s[] = {&c->stamp, &c->keysA, &c->keysB, &c->out_off, &c->off_stage,
                                           &c->sortA, &c->sortB};
     for (auto *b : u64s) b->release();
@@ -1258,6 +1260,20 @@ mqr_status mqr_get_stats(const mqr_ctx *c, mqr_stats *o) {
     o->n_filter_loads = in.n_item_objs;
     o->n_pairs = in.n_pairs;
     o->n_candidates = in.n_cand;
+    return MQR_OK;
+}
+
+mqr_status mqr_region_counts(mqr_ctx *c, uint32_t region_bits, uint32_t *counts_host) {
+    if (!c || !counts_host) return fail(MQR_ERR_INVALID_ARG, "NULL argument");
+    if (region_bits < 1 || region_bits > kMaxRegionBits) return fail(MQR_ERR_INVALID_ARG, "region_bits must be 1..4");
+    if (!c->have_tick) return fail(MQR_ERR_INVALID_ARG, "no tick has completed yet");
+    const size_t R = (size_t)1 << (2 * region_bits);
+    MQR_CUDA(cudaSetDevice(c->device));
+    MQR_CUDA(c->region_cnt.ensure(R));
+    MQR_CUDA(launch_region_counts(c->stream, c->skey.p, (uint32_t)c->last.n_present, region_bits,
+                                  c->region_cnt.p));
+    MQR_CUDA(cudaMemcpyAsync(counts_host, c->region_cnt.p, R * 4, cudaMemcpyDeviceToHost, c->stream));
+    MQR_CUDA(cudaStreamSynchronize(c->stream));
     return MQR_OK;
 }
 

@@ -353,6 +353,8 @@ void launch_key_histograms(cudaStream_t st, const unsigned long long *keys, uint
 // above depth region_bits).
 // Writes leaf_lo/leaf_hi/leaf_beg and Info::n_leaves/max_level.
 constexpr int kLeafThreads = 256, kLeafTile = 2048, kLeafCapSmem = 16384;
+cudaError_t launch_region_counts(cudaStream_t st, const uint32_t *skey, uint32_t n, uint32_t region_bits,
+                                 uint32_t *counts);
 void launch_build_leaves(cudaStream_t st, const uint32_t *skey, uint32_t nmax, uint32_t cap,
                          int uniform_grid, uint32_t grid_level, uint32_t min_level, uint32_t region_bits,
                          const uint32_t *region_cap, uint8_t *mk_a, uint8_t *mk_b,

@@ -164,6 +164,63 @@ class HotspotWalk:
 
 
 # ----------------------------------------------------------------------------
+# Mixed density: the left half of the square holds Gaussian hotspots (a
+# fraction frac_dense of the objects) queried by many small squares, the right
+# half a uniform sparse population queried by few large squares; objects
+# random-walk inside their half.  A workload whose regions prefer different
+# leaf capacities.
+# ----------------------------------------------------------------------------
+@dataclass
+class MixedDensity:
+    n: int = 4_000_000
+    q_small: int = 300_000
+    q_large: int = 10_000
+    frac_dense: float = 0.75
+    hotspots: int = 32
+    sigma: float = 0.01
+    small_lo: float = 0.0003
+    small_hi: float = 0.001
+    large_lo: float = 0.01
+    large_hi: float = 0.04
+    step: float = 0.0005
+    seed: int = 0
+
+    def __post_init__(self):
+        r_init, self._r_move, self._r_q = _rngs(self.seed, 3)
+        self.n_dense = int(round(self.n * self.frac_dense))
+        cent = np.column_stack([r_init.uniform(0.05, 0.45, self.hotspots), r_init.uniform(0.05, 0.95, self.hotspots)])
+        k = r_init.integers(0, self.hotspots, self.n_dense)
+        dense = cent[k] + r_init.normal(0.0, self.sigma, (self.n_dense, 2))
+        sparse = np.column_stack([r_init.uniform(0.5, 1.0, self.n - self.n_dense),
+                                  r_init.uniform(0.0, 1.0, self.n - self.n_dense)])
+        self._xy = self._clamp(np.concatenate([dense, sparse]))
+        self._t = 0
+
+    def _clamp(self, xy):
+        xy[: self.n_dense, 0] = np.clip(xy[: self.n_dense, 0], 0.0, 0.4999)
+        xy[self.n_dense:, 0] = np.clip(xy[self.n_dense:, 0], 0.5, float(TOP))
+        xy[:, 1] = np.clip(xy[:, 1], 0.0, float(TOP))
+        return xy
+
+    @property
+    def q(self):
+        return self.q_small + self.q_large
+
+    def next_tick(self) -> Tick:
+        if self._t > 0:
+            self._xy = self._clamp(self._xy + self._r_move.normal(0.0, self.step, (self.n, 2)))
+        self._t += 1
+        xy = self._xy.astype(np.float32)
+        iss_s = self._r_q.choice(self.n_dense, size=self.q_small, replace=False)
+        iss_l = self.n_dense + self._r_q.choice(self.n - self.n_dense, size=self.q_large, replace=False)
+        iss = np.concatenate([np.sort(iss_s), np.sort(iss_l)]).astype(np.uint32)
+        sides = np.concatenate([np.exp(self._r_q.uniform(np.log(self.small_lo), np.log(self.small_hi), self.q_small)),
+                                np.exp(self._r_q.uniform(np.log(self.large_lo), np.log(self.large_hi), self.q_large))])
+        rects = squares_around(xy[iss], sides)
+        return Tick(np.arange(self.n, dtype=np.uint32), xy, rects, iss)
+
+
+# ----------------------------------------------------------------------------
 # Served stream: a denser hotspot world (95% of the objects in 16 hotspots of
 # sigma 0.005) whose queries arrive as a Poisson process of the given rate;
 # the queries arriving during a tick of duration dt form that tick's batch

@@ -100,3 +100,22 @@ def test_chooser_learns_the_cheapest_configuration():
     assert all(c[0] == QUAD for c in picks)
     assert picks[-10:] == [(QUAD, 256)] * 10
     ch.close()
+
+
+def test_chooser_learns_a_region_candidate():
+    """With per-region candidates among the configurations, the chooser
+    settles on the cheapest one of a known cost function."""
+    torch_dev()
+    from paper_1411_3212_gb300.costmodel import GRID, QUAD, REGIONS, IndexChooser
+    cost = {(QUAD, 128): 1.9, (QUAD, 256): 1.8, (GRID, 8): 2.4, (REGIONS, 3, 8, 0.25): 1.6,
+            (REGIONS, 3, 8, -0.25): 2.0, (REGIONS, 3, 7, 0.5): 1.75}
+    ch = IndexChooser(candidates=list(cost), seed=2, epsilon=0.0)
+    rng = np.random.default_rng(1)
+    picks = []
+    for k in range(48):
+        side = -9.0 + 0.05 * rng.normal()
+        c = ch.choose(4_000_000, 400_000, side)
+        ch.record(c, 4_000_000, 400_000, side, cost[c] * (1 + 0.01 * rng.normal()))
+        picks.append(c)
+    assert picks[-10:] == [(REGIONS, 3, 8, 0.25)] * 10
+    ch.close()

@@ -147,3 +147,54 @@ def test_region_caps_arguments_and_uniform_grid():
     assert_same_csr(gpu_csr_sorted(idx, rects, dev), want, "regions")
     check_leaves(idx, st, n, 2, np.full(16, 3, np.uint32))
     idx.close()
+
+
+@pytest.mark.parametrize("region_bits", [1, 2, 3, 4])
+def test_region_counts_match_sorted_keys(region_bits):
+    torch, dev = torch_dev()
+    from paper_1411_3212_gb300 import mqr
+    n = 40_000
+    w = workloads.HotspotWalk(n=n, q=100, hotspots=3, seed=region_bits)
+    t = w.next_tick()
+    idx = mqr.Index(bounds=(0.0, 0.0, 1.0, 1.0), leaf_cap=32, max_objects=n + 5)
+    with pytest.raises(mqr.MqrError):
+        idx.region_counts(region_bits)                                # no tick yet
+    idx.apply_updates(to_dev(t.ids, dev), to_dev(t.xy, dev))
+    idx.tick(to_dev(t.rects, dev), kind="count")
+    st = oracle_state(n + 5, [(t.ids, t.xy)])
+    k = oracle.keys(st)
+    k = k[k != 0xFFFFFFFF]
+    want = np.bincount(k >> (2 * (15 - region_bits)), minlength=4 ** region_bits)
+    np.testing.assert_array_equal(idx.region_counts(region_bits), want)
+    with pytest.raises(mqr.MqrError):
+        idx.region_counts(0)
+    with pytest.raises(mqr.MqrError):
+        idx.region_counts(5)
+    idx.close()
+
+
+def test_chooser_applies_region_candidates_exactly():
+    """A per-region candidate of the cost-model chooser configures the
+    thresholds from the previous tick's densities; results stay the
+    oracle's and the leaves are Alg. 1 with those thresholds."""
+    torch, dev = torch_dev()
+    from paper_1411_3212_gb300 import mqr
+    from paper_1411_3212_gb300.costmodel import QUAD, REGIONS, IndexChooser, region_caps
+    n = 80_000
+    w = workloads.HotspotWalk(n=n, q=2000, hotspots=6, side_lo=0.001, side_hi=0.03, seed=13)
+    idx = mqr.Index(bounds=(0.0, 0.0, 1.0, 1.0), leaf_cap=128, max_objects=n)
+    ch = IndexChooser(candidates=[(QUAD, 128), (REGIONS, 3, 7, 0.5)], seed=1)
+    st = oracle.State(n)
+    for k, cand in enumerate([(REGIONS, 3, 7, 0.5), (REGIONS, 3, 7, 0.5), (QUAD, 128), (REGIONS, 2, 6, -0.25)]):
+        t = w.next_tick()
+        st.apply_updates(t.ids, t.xy)
+        caps = region_caps(idx.region_counts(cand[1]), cand[1], cand[2], cand[3]) \
+            if cand[0] == REGIONS and k > 0 else None
+        ch.apply(idx, cand)
+        idx.apply_updates(to_dev(t.ids, dev), to_dev(t.xy, dev))
+        assert_same_csr(gpu_csr_sorted(idx, t.rects, dev), oracle.join_grid(st, t.rects, cell_side=0.005),
+                        str(cand))
+        if caps is not None:
+            check_leaves(idx, st, n, cand[1], caps)
+    ch.close()
+    idx.close()
