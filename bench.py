@@ -642,11 +642,14 @@ def run_per_world(args):
 
 def run_costmodel(args):
     """--costmodel: the index configuration chosen per tick by the learned
-    cost model (leaf capacities 64..512 and the uniform grid at levels 8 and
-    9) against the fixed workload configuration, on the same ticks."""
+    cost model (leaf capacities 64..512, the uniform grid at levels 8 and 9,
+    density rules for per-region capacities), and per-region capacities chosen
+    by the node-level model, against the fixed workload configuration, on the
+    same ticks."""
     import torch
     from paper_1411_3212_gb300 import mqr
-    from paper_1411_3212_gb300.costmodel import GRID, QUAD, REGIONS, IndexChooser, mean_log2_side
+    from paper_1411_3212_gb300.costmodel import (GRID, QUAD, REGIONS, WORK_KINDS, IndexChooser, RegionChooser,
+                                                 mean_log2_side)
     dev = torch.device("cuda", 0)
     torch.cuda.set_device(dev)
     name = args.workload
@@ -670,7 +673,10 @@ def run_costmodel(args):
             st, cnt = mqr.mqr_tick(idx.ctx, rect_d[i], Q, mqr.MQR_OUT_PAIRS, out, out.numel() * 4)
         mqr._check(st)
 
+    flush = torch.empty(args.flush_mb * (1 << 20) // 4, dtype=torch.int32, device=dev)
+
     def timed(i):
+        flush.zero_()                 # every arm starts its tick from a flushed L2
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a.record()
         tick(i)
@@ -693,8 +699,20 @@ def run_costmodel(args):
         ch.record(c, nmax, Q, sides[i], ms)
         chosen.append(c)
         times.append(ms)
+    # node level: per-region capacities from the MLP over region features
+    rch = RegionChooser(region_bits=args.region_bits, fallback=w["cap"], seed=0)
+    rtimes = []
+    for k in range(args.steps):
+        i = args.warmup + (k % uniq)
+        rch.apply(idx)
+        rtimes.append(timed(i))
+        rch.record(idx, rect_d[i])
+    final_caps = rch.current.copy()
+    rch.finish(idx)
+    idx.set_region_caps(0)
     idx.close()
     ch.close()
+    rch.close()
     tail = max(1, args.steps // 2)
 
     def label(c):
@@ -710,11 +728,19 @@ def run_costmodel(args):
     for c, ms in zip(chosen[:2 * len(cands)], times[:2 * len(cands)]):   # the round-robin exploration
         explored.setdefault(label(c), []).append(ms)
     line = {"metric": "ms per tick, learned per-tick index choice vs fixed", "unit": "ms",
-            "config": {"workload": w["desc"], "candidates": [list(c) for c in cands], "steps": args.steps},
+            "config": {"workload": w["desc"], "candidates": [list(c) for c in cands], "steps": args.steps,
+                       "l2": "flushed (%d MB write) before every timed tick" % args.flush_mb},
             "fixed_ms_mean": float(np.mean(fixed[-tail:])), "chosen_ms_mean": float(np.mean(times[-tail:])),
             "explore_ms_mean": float(np.mean(times[:2 * len(cands)])), "chosen_last_half": counts,
             "explored_ms": {k: float(np.mean(v)) for k, v in explored.items()},
-            "model_loss": getattr(ch, "loss", None)}
+            "model_loss": getattr(ch, "loss", None),
+            "regions": {"region_bits": args.region_bits, "ms_mean": float(np.mean(rtimes[-tail:])),
+                        "explore_ms_mean": float(np.mean(rtimes[:rch.explore_ticks])),
+                        "capacities_last_tick": {str(int(c)): int((final_caps == c).sum())
+                                                 for c in np.unique(final_caps)},
+                        "model_loss": getattr(rch, "loss", None), "samples": len(rch.X),
+                        "unit_cost_ms": None if rch.unit_cost is None else
+                        {k: float(v) for k, v in zip(WORK_KINDS, rch.unit_cost)}}}
     print(json.dumps(line), flush=True)
 
 
@@ -739,6 +765,7 @@ def main():
     ap.add_argument("--grid-level", type=int, default=8, help="uniform grid: 2^level cells per axis")
     ap.add_argument("--served", action="store_true", help="run the served stream instead")
     ap.add_argument("--costmodel", action="store_true", help="learned per-tick index choice vs fixed")
+    ap.add_argument("--region-bits", type=int, default=3, help="--costmodel: depth of the node-level regions")
     ap.add_argument("--per-world", action="store_true", help="batched-256 worlds answered one context each")
     ap.add_argument("--rate", type=float, default=5.0e6, help="served: query arrivals per second")
     ap.add_argument("--dt-ms", type=float, default=10.0, help="served: tick duration")

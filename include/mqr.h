@@ -322,6 +322,24 @@ mqr_status mqr_set_region_caps(mqr_ctx *ctx, uint32_t region_bits, const uint32_
  * before the first tick). */
 mqr_status mqr_region_counts(mqr_ctx *ctx, uint32_t region_bits, uint32_t *counts_host);
 
+/* Per-region work of the last completed tick, the node-level data a cost
+ * model of the split thresholds learns from: out_host (double host array of
+ * 9 x 4^region_bits, statistic-major: out_host[s * 4^region_bits + r]) gets
+ * for every region r (as in mqr_region_counts)
+ *   s = 0 objects, 1 leaves (Alg. 1), 2 queries whose centre lies in r
+ *   (inverted, NaN or infinite rectangles skipped), 3 the sum of log2 of
+ *   those queries' longer sides, 4 intersecting subqueries on leaves of r,
+ *   5 covering subqueries on leaves of r (Def. mapping functions), 6 the
+ *   containment tests of the filter (Alg. 2: the leaf's objects for every
+ *   intersecting subquery), 7 results of intersecting subqueries, 8 results
+ *   of covering subqueries.
+ * rects_dev / Q: the last tick's queries (device, as passed to it).  Computed
+ * on the device from the tick's leaf table and subquery records; valid until
+ * the next tick.  1 <= region_bits <= 4.  Blocks.  Errors: INVALID_ARG (no
+ * tick yet, a different Q, the atomic-baseline kind, batched worlds). */
+mqr_status mqr_region_work(mqr_ctx *ctx, const float *rects_dev, uint32_t Q, uint32_t region_bits,
+                           double *out_host);
+
 /* Learned tick-cost model: a multilayer perceptron 5 -> 64 -> 64 -> 1 with
  * ReLU hidden layers, trained on the device (hand-written forward, backward
  * and Adam kernels, one block) to map tick features to the logarithm of the

@@ -16,7 +16,7 @@ CSRC = os.path.join(HERE, "csrc")
 ROOT = os.path.dirname(HERE)
 LIB = os.path.join(HERE, "libmqr.so")
 BUILD_DIR = os.path.join(ROOT, "_build", platform.machine())   # objects never cross machines
-SOURCES = ["k_index.cu", "k_query.cu", "k_join.cu", "k_cost.cu", "mqr_api.cu", "mqr_noalloc.cu"]
+SOURCES = ["k_index.cu", "k_query.cu", "k_join.cu", "k_cost.cu", "k_region.cu", "mqr_api.cu", "mqr_noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-ffp-contract=off",
          "-I" + os.path.join(ROOT, "include")]

@@ -140,6 +140,8 @@ struct mqr_ctx {
     // per-region leaf capacities (mqr_set_region_caps): 4^region_bits entries
     uint32_t region_bits = 0;
     DevBuf<uint32_t> region_cap, region_cnt;
+    DevBuf<double> region_stats;
+    int last_emit_kind = -1;
     unsigned long long world_q_total = 0;
     bool world_q_set = false;
 
@@ -489,6 +491,7 @@ mqr_status run_tick(mqr_ctx *c, const float4 *rects, uint32_t Q, int emit_kind, 
         Info in = *c->info_host;
         c->last = in;
         c->last_q = Q;
+        c->last_emit_kind = emit_kind;
         c->have_tick = true;
         if (in.err & kErrTimeout)
             return fail(MQR_ERR_TIMEOUT, "a device-side wait exceeded its deadline");
@@ -864,6 +867,7 @@ void mqr_destroy(mqr_ctx *c) {
     c->world_q.release();
     c->region_cap.release();
     c->region_cnt.release();
+    c->region_stats.release();
     DevBuf<unsigned long long> *u64s[] = {&c->stamp, &c->keysA, &c->keysB, &c->out_off, &c->off_stage,
                                           &c->sortA, &c->sortB};
     for (auto *b : u64s) b->release();
@@ -1273,6 +1277,28 @@ mqr_status mqr_region_counts(mqr_ctx *c, uint32_t region_bits, uint32_t *counts_
     MQR_CUDA(launch_region_counts(c->stream, c->skey.p, (uint32_t)c->last.n_present, region_bits,
                                   c->region_cnt.p));
     MQR_CUDA(cudaMemcpyAsync(counts_host, c->region_cnt.p, R * 4, cudaMemcpyDeviceToHost, c->stream));
+    MQR_CUDA(cudaStreamSynchronize(c->stream));
+    return MQR_OK;
+}
+
+mqr_status mqr_region_work(mqr_ctx *c, const float *rects_dev, uint32_t Q, uint32_t region_bits, double *out_host) {
+    if (!c || !out_host) return fail(MQR_ERR_INVALID_ARG, "NULL argument");
+    if (region_bits < 1 || region_bits > kMaxRegionBits) return fail(MQR_ERR_INVALID_ARG, "region_bits must be 1..4");
+    if (!c->have_tick) return fail(MQR_ERR_INVALID_ARG, "no tick has completed yet");
+    if (c->last_emit_kind == kEmitAtomic)
+        return fail(MQR_ERR_INVALID_ARG, "the last tick used the atomic baseline (no per-subquery counts)");
+    if (c->n_worlds) return fail(MQR_ERR_INVALID_ARG, "not available with batched worlds");
+    if (Q != c->last_q) return fail(MQR_ERR_INVALID_ARG, "Q must be the last tick's query count");
+    if (Q && !rects_dev) return fail(MQR_ERR_INVALID_ARG, "rects_dev is NULL");
+    const size_t R = (size_t)1 << (2 * region_bits);
+    MQR_CUDA(cudaSetDevice(c->device));
+    MQR_CUDA(c->region_stats.ensure(kRegionStats * R));
+    MQR_CUDA(launch_region_work(c->stream, c->num_sms, c->leaf_lo.p, c->leaf_beg.p, (uint32_t)c->last.n_leaves,
+                                c->sub_leaf.p, c->sub_len.p, c->sub_res.p, c->last.n_sub,
+                                reinterpret_cast<const float4 *>(rects_dev), Q, c->bounds.xmin, c->bounds.ymin,
+                                c->sx, c->sy, region_bits, c->region_stats.p));
+    MQR_CUDA(cudaMemcpyAsync(out_host, c->region_stats.p, kRegionStats * R * sizeof(double),
+                             cudaMemcpyDeviceToHost, c->stream));
     MQR_CUDA(cudaStreamSynchronize(c->stream));
     return MQR_OK;
 }

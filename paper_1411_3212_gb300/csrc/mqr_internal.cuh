@@ -108,6 +108,9 @@ constexpr uint32_t kMaxWorlds = 16384;     // 4^7: at least 8 levels left per wo
 // Per-region leaf capacities: the nodes of depth region_bits <= 4 (at most
 // 256 regions), each capacity at most kLeafCapSmem (shared-memory window table).
 constexpr uint32_t kMaxRegionBits = 4;
+// Per-region work statistics of a tick (mqr_region_work), in this order.
+enum RegionStat { kRsObjects, kRsLeaves, kRsQueries, kRsSideLog2, kRsSubI, kRsSubC, kRsTests, kRsResI, kRsResC,
+                  kRegionStats };
 struct Worlds {
     const uint32_t *obj_base;
     const uint32_t *q_base;
@@ -353,6 +356,10 @@ void launch_key_histograms(cudaStream_t st, const unsigned long long *keys, uint
 // above depth region_bits).
 // Writes leaf_lo/leaf_hi/leaf_beg and Info::n_leaves/max_level.
 constexpr int kLeafThreads = 256, kLeafTile = 2048, kLeafCapSmem = 16384;
+cudaError_t launch_region_work(cudaStream_t st, int num_sms, const uint32_t *leaf_lo, const uint32_t *leaf_beg,
+                               uint32_t n_leaves, const uint32_t *sub_leaf, const uint32_t *sub_len,
+                               const uint32_t *sub_res, unsigned long long n_sub, const float4 *rects, uint32_t Q,
+                               float x0, float y0, float sx, float sy, uint32_t region_bits, double *out);
 cudaError_t launch_region_counts(cudaStream_t st, const uint32_t *skey, uint32_t n, uint32_t region_bits,
                                  uint32_t *counts);
 void launch_build_leaves(cudaStream_t st, const uint32_t *skey, uint32_t nmax, uint32_t cap,

@@ -30,7 +30,7 @@ EXPORTS = ["mqr_config_default", "mqr_create", "mqr_create_ex", "mqr_apply_updat
            "mqr_apply_updates_host", "mqr_tick", "mqr_tick_host", "mqr_tick_host_async", "mqr_host_wait",
            "mqr_get_sorted_async",
            "mqr_tick_admit", "mqr_set_graph", "mqr_set_worlds",
-           "mqr_set_query_worlds", "mqr_set_index", "mqr_set_region_caps", "mqr_region_counts", "mqr_cost_param_count", "mqr_cost_create",
+           "mqr_set_query_worlds", "mqr_set_index", "mqr_set_region_caps", "mqr_region_counts", "mqr_region_work", "mqr_cost_param_count", "mqr_cost_create",
            "mqr_cost_set_params", "mqr_cost_get_params", "mqr_cost_train", "mqr_cost_gradient", "mqr_cost_predict",
            "mqr_cost_destroy", "mqr_get_stats",
            "mqr_get_leaves",
@@ -111,6 +111,7 @@ def load(path: str = LIB_PATH):
         "mqr_set_index": ([P, i32, u32, u32], i32),
         "mqr_set_region_caps": ([P, u32, P], i32),
         "mqr_region_counts": ([P, u32, P], i32),
+        "mqr_region_work": ([P, P, u32, u32, P], i32),
         "mqr_cost_param_count": ([], u32),
         "mqr_cost_create": ([pctx], i32),
         "mqr_cost_set_params": ([P, P, u32], i32),
@@ -244,6 +245,18 @@ def mqr_region_counts(ctx, region_bits):
     out = np.zeros(4 ** int(region_bits), np.uint32)
     _check(load().mqr_region_counts(ctx, int(region_bits), out.ctypes.data_as(ctypes.c_void_p)))
     return out
+
+
+REGION_STATS = ("objects", "leaves", "queries", "side_log2_sum", "sub_intersecting", "sub_covering", "tests",
+                "results_intersecting", "results_covering")
+
+
+def mqr_region_work(ctx, rects_dev, Q, region_bits):
+    """Per-region work of the last tick: dict statistic -> float64[4^region_bits]."""
+    out = np.zeros((len(REGION_STATS), 4 ** int(region_bits)), np.float64)
+    _check(load().mqr_region_work(ctx, _ptr(rects_dev), int(Q), int(region_bits),
+                                  out.ctypes.data_as(ctypes.c_void_p)))
+    return dict(zip(REGION_STATS, out))
 
 
 class CostModel:
@@ -449,6 +462,9 @@ class Index:
 
     def region_counts(self, region_bits):
         return mqr_region_counts(self.ctx, region_bits)
+
+    def region_work(self, rects, region_bits):
+        return mqr_region_work(self.ctx, rects, rects.shape[0], region_bits)
 
     def set_graph(self, enable=True):
         mqr_set_graph(self.ctx, enable)

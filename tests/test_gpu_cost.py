@@ -119,3 +119,42 @@ def test_chooser_learns_a_region_candidate():
         picks.append(c)
     assert picks[-10:] == [(REGIONS, 3, 8, 0.25)] * 10
     ch.close()
+
+
+def test_region_chooser_learns_per_region_optimum():
+    """Synthetic per-region costs whose best capacity grows with the region's
+    density: after exploration the node-level model gives most regions their
+    own best capacity (neighbouring candidates cost within a few percent)."""
+    torch_dev()
+    from paper_1411_3212_gb300.costmodel import RegionChooser
+    rb = 2
+    R = 16
+    rng = np.random.default_rng(3)
+    objects = np.exp2(rng.uniform(8, 18, R)).round()
+    queries = (objects / 10).round()
+    caps = np.array([32, 64, 128, 256, 512, 1024], np.float64)
+    best = np.clip(np.round(4 + (np.log2(objects) - 8) * 0.5), 5, 10)      # log2 of the best capacity
+
+    def work_for(cap_r):
+        # region cost 1 ms x (1 + 0.3 (log2 cap - best)^2) x objects / 2^16, as filter tests at 1 ms each
+        cost = (1 + 0.3 * (np.log2(cap_r) - best) ** 2) * objects / 65536.0
+        w = {k: np.zeros(R) for k in ("objects", "leaves", "queries", "side_log2_sum", "sub_intersecting",
+                                      "sub_covering", "tests", "results_intersecting", "results_covering")}
+        w["objects"] = objects.copy()
+        w["queries"] = queries.copy()
+        w["side_log2_sum"] = queries * -9.0
+        w["tests"] = cost
+        return w, {"filter": float(cost.sum())}
+
+    ch = RegionChooser(region_bits=rb, caps=caps, explore_rounds=5, epsilon=0.0, retrain_every=10, first_epochs=600,
+                       seed=5)
+    w, ph = work_for(np.full(R, 128.0))
+    ch.observe(w, ph)                                  # a first tick at the fallback capacity
+    for k in range(60):
+        c = ch.choose().astype(np.float64)
+        w, ph = work_for(c)
+        ch.observe(w, ph)
+    got = np.log2(ch.choose().astype(np.float64))
+    assert np.mean(np.abs(got - best) <= 1) >= 0.9, (got, best)
+    assert np.mean(got == best) >= 0.6, (got, best)
+    ch.close()

@@ -198,3 +198,110 @@ def test_chooser_applies_region_candidates_exactly():
             check_leaves(idx, st, n, cand[1], caps)
     ch.close()
     idx.close()
+
+
+def oracle_region_work(st, rects, cap, region_bits):
+    """The per-region statistics of mqr_region_work from the oracle: Alg. 1
+    leaves, g(q) subqueries (Def. mapping functions), Def. 1 results."""
+    R = 4 ** region_bits
+    keys_slot = oracle.keys(st)
+    order = np.argsort(keys_slot, kind="stable")
+    n = int(st.present.sum())
+    order = order[:n]
+    keys = keys_slot[order]
+    lv = oracle.quadtree(keys, cap, 15)
+    lv = lv[lv["begin"] != lv["end"]]
+    reg = (lv["z"].astype(np.int64) << (2 * (15 - lv["level"].astype(np.int64)))) >> (2 * (15 - region_bits))
+    size = (lv["end"] - lv["begin"]).astype(np.int64)
+    out = {k: np.zeros(R) for k in ("objects", "leaves", "queries", "side_log2_sum", "sub_intersecting",
+                                    "sub_covering", "tests", "results_intersecting", "results_covering")}
+    np.add.at(out["objects"], reg, size)
+    np.add.at(out["leaves"], reg, 1)
+    pos = st.pos[order]
+    sc = oracle.scale(0.0, 1.0)
+    for r in rects:
+        li, cov = oracle.subqueries(lv, r)
+        for l, c in zip(li, cov):
+            g = reg[l]
+            if c:
+                out["sub_covering"][g] += 1
+                out["results_covering"][g] += size[l]
+            else:
+                p = pos[lv["begin"][l]:lv["end"][l]]
+                hit = (p[:, 0] >= r[0]) & (p[:, 0] <= r[2]) & (p[:, 1] >= r[1]) & (p[:, 1] <= r[3])
+                out["sub_intersecting"][g] += 1
+                out["tests"][g] += size[l]
+                out["results_intersecting"][g] += int(hit.sum())
+        if not (r[0] <= r[2] and r[1] <= r[3]) or not np.all(np.isfinite(r)):
+            continue
+        cx = np.float32(np.float32(0.5) * r[0] + np.float32(0.5) * r[2])
+        cy = np.float32(np.float32(0.5) * r[1] + np.float32(0.5) * r[3])
+        z = oracle.morton(oracle.cell(float(cx), 0.0, sc), oracle.cell(float(cy), 0.0, sc))
+        g = z >> (2 * (15 - region_bits))
+        out["queries"][g] += 1
+        out["side_log2_sum"][g] += np.log2(max(float(max(r[2] - r[0], r[3] - r[1])), 1e-9))
+    return out
+
+
+@pytest.mark.parametrize("region_bits,cap", [(1, 16), (2, 32), (4, 8)])
+def test_region_work_matches_oracle(region_bits, cap):
+    torch, dev = torch_dev()
+    from paper_1411_3212_gb300 import mqr
+    n = 20_000
+    w = workloads.HotspotWalk(n=n, q=400, hotspots=4, side_lo=0.002, side_hi=0.08, seed=region_bits)
+    t = w.next_tick()
+    rects = t.rects.copy()
+    rects[3] = [0.7, 0.7, 0.2, 0.9]                     # inverted: no subqueries, not counted
+    rects[5, 1] = np.nan
+    nmax = n + 11
+    idx = mqr.Index(bounds=(0.0, 0.0, 1.0, 1.0), leaf_cap=cap, max_objects=nmax)
+    idx.apply_updates(to_dev(t.ids, dev), to_dev(t.xy, dev))
+    r_d = to_dev(rects, dev)
+    idx.tick(r_d, kind="pairs")
+    got = idx.region_work(r_d, region_bits)
+    st = oracle_state(nmax, [(t.ids, t.xy)])
+    want = oracle_region_work(st, rects, cap, region_bits)
+    for k in want:
+        if k == "side_log2_sum":
+            np.testing.assert_allclose(got[k], want[k], rtol=1e-5, atol=1e-3, err_msg=k)
+        else:
+            np.testing.assert_array_equal(got[k], want[k], err_msg=k)
+    s = idx.stats()
+    assert got["tests"].sum() == s["n_tests"] and got["results_covering"].sum() == s["n_results_covering"]
+    with pytest.raises(mqr.MqrError):
+        mqr.mqr_region_work(idx.ctx, r_d, 399, region_bits)          # not the last tick's Q
+    idx.tick(r_d, kind="pairs_atomic")
+    with pytest.raises(mqr.MqrError):
+        idx.region_work(r_d, region_bits)                            # no per-subquery counts
+    idx.close()
+
+
+def test_region_chooser_on_real_ticks_stays_exact():
+    """The node-level chooser logs each tick's region work and phase times,
+    sets per-region capacities for the next tick, and every tick's result
+    stays the oracle's; the leaves are Alg. 1 with the capacities chosen."""
+    torch, dev = torch_dev()
+    from paper_1411_3212_gb300 import mqr
+    from paper_1411_3212_gb300.costmodel import RegionChooser
+    n = 60_000
+    w = workloads.HotspotWalk(n=n, q=3000, hotspots=6, side_lo=0.001, side_hi=0.03, seed=17)
+    idx = mqr.Index(bounds=(0.0, 0.0, 1.0, 1.0), leaf_cap=128, max_objects=n)
+    ch = RegionChooser(region_bits=2, caps=(16, 64, 256, 1024), explore_rounds=1, retrain_every=1, epochs=100)
+    st = oracle.State(n)
+    for k in range(6):
+        t = w.next_tick()
+        st.apply_updates(t.ids, t.xy)
+        ch.apply(idx)
+        caps = ch.current.copy()
+        idx.apply_updates(to_dev(t.ids, dev), to_dev(t.xy, dev))
+        r_d = to_dev(t.rects, dev)
+        res, offs = idx.tick(r_d, kind="csr_sorted")
+        got = (offs.cpu().numpy().view(np.uint64), res.cpu().numpy().view(np.uint32).copy())
+        assert_same_csr(got, oracle.join_grid(st, t.rects, cell_side=0.005), "tick %d" % k)
+        ch.record(idx, r_d)
+        check_leaves(idx, st, n, 2, caps)
+    assert ch.trained and len(ch.X) > 0
+    cost = ch.region_costs(ch.last_work)
+    assert cost.shape == (16,) and np.all(cost >= 0) and cost.sum() > 0
+    ch.close()
+    idx.close()
