@@ -121,15 +121,17 @@ def phase_bytes(s, n_updates, nmax):
     }
 
 
-def source_hash():
-    """Hash of the kernels' sources (k_*.cu and their shared header; the host
-    code of mqr_api.cu does not change what a kernel moves)."""
+KERNEL_SOURCES = {"emit_kernel": "k_join.cu"}
+
+
+def source_hash(kernel="emit_kernel"):
+    """Hash of a kernel's source file and the shared header (the host code
+    and the other kernels' files do not change what the kernel moves)."""
     h = hashlib.sha256()
     d = os.path.join(ROOT, "paper_1411_3212_gb300", "csrc")
-    for f in sorted(os.listdir(d)):
-        if f.startswith("k_") or f == "mqr_internal.cuh":
-            with open(os.path.join(d, f), "rb") as fh:
-                h.update(fh.read())
+    for f in (KERNEL_SOURCES[kernel], "mqr_internal.cuh"):
+        with open(os.path.join(d, f), "rb") as fh:
+            h.update(fh.read())
     return h.hexdigest()[:16]
 
 
@@ -155,7 +157,8 @@ def read_traffic(kernel, results_per_launch):
                 if line and not line.startswith("#") and "=" in line:
                     k, v = line.split("=", 1)
                     kv[k.strip()] = v.strip()
-        if kv.get("kernel") == kernel and kv.get("source_hash") == source_hash() and kv.get("workload") == "hotspot4m":
+        if (kv.get("kernel") == kernel and kernel in KERNEL_SOURCES and kv.get("source_hash") == source_hash(kernel)
+                and kv.get("workload") == "hotspot4m"):
             return float(kv["dram_bytes_per_launch"]) * results_per_launch / float(kv["results"])
     except Exception:
         pass
