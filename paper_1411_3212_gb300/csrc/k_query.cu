@@ -241,27 +241,41 @@ struct CandLane {
     bool pj_starts;    // lane j's pair starts inside this tile
 };
 
-__device__ __forceinline__ CandLane cand_lane(unsigned long long t, unsigned long long ncand, uint32_t npairs,
-                                              int covering, const uint32_t *__restrict__ tile_p0,
+// The loads of a tile's pairs (lane j: pair tile_p0[t] + j), issued one tile
+// ahead of their use so that two tiles' load chains overlap in each warp.
+struct PairLoad {
+    uint32_t p0, po, q, f, b;
+};
+
+__device__ __forceinline__ PairLoad pair_load(unsigned long long t, uint32_t npairs,
+                                              const uint32_t *__restrict__ tile_p0,
                                               const uint32_t *__restrict__ pair_q,
                                               const uint32_t *__restrict__ pair_first,
                                               const uint32_t *__restrict__ pair_blo,
-                                              const unsigned long long *__restrict__ pair_off,
+                                              const unsigned long long *__restrict__ pair_off) {
+    PairLoad L;
+    L.p0 = __ldg(tile_p0 + t);
+    const uint32_t pj = L.p0 + (threadIdx.x & 31);
+    L.q = L.f = L.b = 0;
+    L.po = 0xffffffffu;
+    if (pj < npairs) {
+        L.po = (uint32_t)__ldg(pair_off + pj);
+        L.q = __ldg(pair_q + pj);
+        L.f = __ldg(pair_first + pj);
+        L.b = __ldg(pair_blo + pj);
+    }
+    return L;
+}
+
+__device__ __forceinline__ CandLane cand_lane(unsigned long long t, unsigned long long ncand, uint32_t npairs,
+                                              int covering, const PairLoad &L,
                                               const uint2 *__restrict__ qcells,
                                               const uint2 *__restrict__ leaf_box) {
     // candidate indices fit 32 bits (at most kMaxCandTiles tiles of 32)
     const uint32_t lane = threadIdx.x & 31;
     const uint32_t c0 = (uint32_t)t << 5;
-    const uint32_t p0 = __ldg(tile_p0 + t);
-    const uint32_t pj = p0 + lane;
-    uint32_t q_j = 0, f_j = 0, b_j = 0;
-    uint32_t po = 0xffffffffu;
-    if (pj < npairs) {
-        po = (uint32_t)__ldg(pair_off + pj);
-        q_j = __ldg(pair_q + pj);
-        f_j = __ldg(pair_first + pj);
-        b_j = __ldg(pair_blo + pj);
-    }
+    const uint32_t pj = L.p0 + lane;
+    const uint32_t q_j = L.q, f_j = L.f, b_j = L.b, po = L.po;
     CandLane r;
     r.pj_starts = pj < npairs && po >= c0 && po < c0 + 32u;
     r.po_j = r.pj_starts ? po - c0 : 0u;
@@ -310,16 +324,19 @@ cand_count_kernel(int covering, const uint32_t *__restrict__ tile_p0, const uint
     unsigned long long n_i = 0, n_c = 0;
     if (ntiles <= caps.cand_tiles) {
         const unsigned long long nw = (unsigned long long)gridDim.x * (blockDim.x >> 5);
-        for (unsigned long long t = (blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x) >> 5; t < ntiles;
-             t += nw) {
-            CandLane r = cand_lane(t, ncand, npairs, covering, tile_p0, pair_q, pair_first, pair_blo, pair_off,
-                                   qcells, leaf_box);
+        unsigned long long t = (blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x) >> 5;
+        PairLoad cur{};
+        if (t < ntiles) cur = pair_load(t, npairs, tile_p0, pair_q, pair_first, pair_blo, pair_off);
+        for (; t < ntiles; t += nw) {
+            PairLoad nxt = cur;                   // the next tile's pairs, loaded before this tile is used
+            if (t + nw < ntiles) nxt = pair_load(t + nw, npairs, tile_p0, pair_q, pair_first, pair_blo, pair_off);
+            CandLane r = cand_lane(t, ncand, npairs, covering, cur, qcells, leaf_box);
             const bool rec = r.code == 1 || (r.code == 2 && !r.cont);
             const uint32_t m = __ballot_sync(0xffffffffu, rec);
             const uint32_t notcont = __ballot_sync(0xffffffffu, !(r.valid && r.cont));
             const uint32_t slot0 = (uint32_t)(t << 5);
             if (lane == 0) tile_cnt[t] = __popc(m);
-            if (r.pj_starts) pair_rec[__ldg(tile_p0 + t) + lane] = slot0 + __popc(m & ((1u << r.po_j) - 1u));
+            if (r.pj_starts) pair_rec[cur.p0 + lane] = slot0 + __popc(m & ((1u << r.po_j) - 1u));
             if (r.code == 1) {
                 ++n_i;
                 const uint32_t rank = atomicAdd(leaf_nsub + r.leaf, 1u);   // row in the leaf's list
@@ -335,6 +352,7 @@ cand_count_kernel(int covering, const uint32_t *__restrict__ tile_p0, const uint
                                    __ldg(leaf_beg + r.leaf + len) - __ldg(leaf_beg + r.leaf));
                 }
             }
+            cur = nxt;
         }
     }
     n_i = warp_sum(n_i); n_c = warp_sum(n_c);
