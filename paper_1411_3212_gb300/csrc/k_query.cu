@@ -57,16 +57,22 @@ __global__ void zmap_kernel(const uint32_t *__restrict__ leaf_hi, const Info *in
     }
 }
 
-// First leaf whose interval ends at or after code z (L if none).
-__device__ __forceinline__ uint32_t leaf_at_or_after(uint32_t z, const uint32_t *__restrict__ leaf_hi,
-                                                     const uint32_t *__restrict__ zmap) {
-    const uint32_t c = z >> kZShift;
-    uint32_t a = __ldg(zmap + c), b = __ldg(zmap + c + 1);
-    while (a < b) {
-        uint32_t m = (a + b) >> 1;
-        if (__ldg(leaf_hi + m) >= z) b = m; else a = m + 1;
+// First leaf whose interval ends at or after code z1, and the same for z2
+// (L if none), the two binary searches advancing together so that their
+// dependent loads overlap.
+__device__ __forceinline__ void leaves_at_or_after2(uint32_t z1, uint32_t z2, const uint32_t *__restrict__ leaf_hi,
+                                                    const uint32_t *__restrict__ zmap, uint32_t &r1, uint32_t &r2) {
+    uint32_t a1 = __ldg(zmap + (z1 >> kZShift)), b1 = __ldg(zmap + (z1 >> kZShift) + 1);
+    uint32_t a2 = __ldg(zmap + (z2 >> kZShift)), b2 = __ldg(zmap + (z2 >> kZShift) + 1);
+    while (a1 < b1 || a2 < b2) {
+        const uint32_t m1 = (a1 + b1) >> 1, m2 = (a2 + b2) >> 1;
+        const uint32_t v1 = a1 < b1 ? __ldg(leaf_hi + m1) : 0u;
+        const uint32_t v2 = a2 < b2 ? __ldg(leaf_hi + m2) : 0u;
+        if (a1 < b1) { if (v1 >= z1) b1 = m1; else a1 = m1 + 1; }
+        if (a2 < b2) { if (v2 >= z2) b2 = m2; else a2 = m2 + 1; }
     }
-    return a;
+    r1 = a1;
+    r2 = a2;
 }
 
 // Query splitting works on aligned blocks of side 2^k cells, k the smallest
@@ -150,9 +156,9 @@ query_blocks_kernel(const float4 *__restrict__ rects, uint32_t Q, float x0, floa
             blk = (bi << k) | ((bj << k) << 16);
             const uint32_t blo = morton2(bi << k, bj << k);
             const uint32_t bhi = blo + ((1u << (2 * k)) - 1u);
-            f = leaf_at_or_after(blo, leaf_hi, zmap);
+            uint32_t g;
+            leaves_at_or_after2(blo, bhi, leaf_hi, zmap, f, g);
             if (f < L && __ldg(leaf_lo + f) <= bhi) {
-                const uint32_t g = leaf_at_or_after(bhi, leaf_hi, zmap);
                 const uint32_t last = (g < L && __ldg(leaf_lo + g) <= bhi) ? g : g - 1u;
                 cnt = last - f + 1u;
             }
