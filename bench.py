@@ -341,11 +341,12 @@ def run_gpu(args, name):
     flush = torch.empty(args.flush_mb * (1 << 20) // 4, dtype=torch.int32, device=dev)
 
     cap = args.leaf_cap or w["cap"]
+    covering = not args.no_covering
     if args.index == "ug":                               # uniform grid of 2^grid_level cells per axis
         idx = mqr.Index(bounds=(0.0, 0.0, 1.0, 1.0), leaf_cap=1, max_objects=nmax, index_kind=1,
-                        grid_level=args.grid_level)
+                        grid_level=args.grid_level, covering=covering)
     else:
-        idx = mqr.Index(bounds=(0.0, 0.0, 1.0, 1.0), leaf_cap=cap, max_objects=nmax)
+        idx = mqr.Index(bounds=(0.0, 0.0, 1.0, 1.0), leaf_cap=cap, max_objects=nmax, covering=covering)
     if batched:
         idx.set_worlds(ticks[0].obj_base)
         idx.set_query_worlds(ticks[0].q_base)
@@ -457,6 +458,7 @@ def run_gpu(args, name):
         "config": {"workload": w["desc"], "objects": nmax, "queries_per_tick": Q,
                    "index": "quadtree" if args.index == "quad" else "uniform grid level %d" % args.grid_level,
                    "leaf_cap": cap,
+                   "covering": "on" if covering else "off (every subquery tested)",
                    "output": args.kind, "parallelism": "replicas" if world > 1 else "single-gpu",
                    "l2": "flushed (%d MB write) between timed steps" % args.flush_mb,
                    "ticks": "%d distinct generated ticks, cycled over the %d timed steps" % (uniq, args.steps)},
@@ -769,6 +771,8 @@ def main():
     ap.add_argument("--served", action="store_true", help="run the served stream instead")
     ap.add_argument("--costmodel", action="store_true", help="learned per-tick index choice vs fixed")
     ap.add_argument("--region-bits", type=int, default=3, help="--costmodel: depth of the node-level regions")
+    ap.add_argument("--no-covering", action="store_true",
+                    help="ablation: no covering subqueries (every subquery goes through the containment tests)")
     ap.add_argument("--per-world", action="store_true", help="batched-256 worlds answered one context each")
     ap.add_argument("--rate", type=float, default=5.0e6, help="served: query arrivals per second")
     ap.add_argument("--dt-ms", type=float, default=10.0, help="served: tick duration")
