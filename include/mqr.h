@@ -390,6 +390,13 @@ mqr_status mqr_get_sorted(mqr_ctx *ctx, uint32_t *keys_host, uint32_t *ids_host,
  * accumulators.  Timing adds two event records per phase to the stream. */
 mqr_status mqr_set_timing(mqr_ctx *ctx, int enable);
 
+/* Per-phase timing of only the phases whose bit (1 << mqr_phase) is set in
+ * phase_mask: their device time is measured with two event records each,
+ * while kernel launches are counted for every phase (no events); 0 turns
+ * timing off.  Resets the accumulators.  Fewer event records perturb the
+ * tick less (each costs a few microseconds of stream time). */
+mqr_status mqr_set_timing_phases(mqr_ctx *ctx, uint32_t phase_mask);
+
 /* Per-phase device time and kernel-launch counts accumulated over the ticks
  * completed since timing was enabled. */
 mqr_status mqr_get_timing(const mqr_ctx *ctx, mqr_timing *out);

@@ -148,7 +148,8 @@ struct mqr_ctx {
     Info *info_host = nullptr;  // pinned
     Info last{};
     // per-phase timing (mqr_set_timing)
-    bool timing = false;
+    bool timing = false;            // launch counting on (mqr_set_timing / mqr_set_timing_phases)
+    uint32_t timing_mask = 0;       // the phases timed with events
     cudaEvent_t ev[MQR_NUM_PHASES][2] = {};
     bool ev_used[MQR_NUM_PHASES] = {};
     uint64_t ev_launches[MQR_NUM_PHASES] = {};
@@ -209,16 +210,21 @@ mqr_status check_launch(const char *what) {
     return MQR_OK;
 }
 
-// Phase timing: events around each phase's kernels when enabled.
+// Phase timing: events around the kernels of the phases in timing_mask;
+// launches are counted for every phase while timing is on.
 void phase_begin(mqr_ctx *c, int p) {
-    if (!c->timing) return;
+    if (!c->timing || !(c->timing_mask & (1u << p))) return;
     cudaEventRecord(c->ev[p][0], c->stream);
 }
 void phase_end(mqr_ctx *c, int p, uint64_t launches) {
     if (!c->timing) return;
-    cudaEventRecord(c->ev[p][1], c->stream);
-    c->ev_used[p] = true;
-    c->ev_launches[p] = launches;
+    if (c->timing_mask & (1u << p)) {
+        cudaEventRecord(c->ev[p][1], c->stream);
+        c->ev_used[p] = true;
+        c->ev_launches[p] = launches;
+    } else {
+        c->acc.launches[p] += launches;
+    }
 }
 // Called after the stream has been synchronised: fold the recorded phases
 // (and the update calls since the last tick) into the accumulators.
@@ -990,7 +996,8 @@ mqr_status mqr_apply_updates(mqr_ctx *c, const uint32_t *ids_dev, const float *x
     if (!ids_dev || !xy_dev) return fail(MQR_ERR_INVALID_ARG, "ids_dev / xy_dev is NULL");
     MQR_CUDA(cudaSetDevice(c->device));
     ++c->epoch;
-    const bool timed = c->timing && c->up_pending < mqr_ctx::kMaxPendingUpdates;
+    const bool timed = c->timing && (c->timing_mask & (1u << MQR_PHASE_UPDATES)) &&
+                       c->up_pending < mqr_ctx::kMaxPendingUpdates;
     if (timed) cudaEventRecord(c->up_ev[c->up_pending][0], c->stream);
     launch_apply_updates(c->stream, ids_dev, reinterpret_cast<const float2 *>(xy_dev), n, c->nmax,
                          c->epoch, c->stamp.p, c->pos.p, c->upd_err.p);
@@ -1373,21 +1380,26 @@ mqr_status mqr_get_sorted_async(mqr_ctx *c, uint32_t *ids_host, uint64_t cap, ui
     return MQR_OK;
 }
 
-mqr_status mqr_set_timing(mqr_ctx *c, int enable) {
+mqr_status mqr_set_timing_phases(mqr_ctx *c, uint32_t phase_mask) {
     if (!c) return fail(MQR_ERR_INVALID_ARG, "ctx is NULL");
     MQR_CUDA(cudaSetDevice(c->device));
-    if (enable && !c->ev[0][0]) {
+    if (phase_mask && !c->ev[0][0]) {
         for (int p = 0; p < MQR_NUM_PHASES; ++p)
             for (int k = 0; k < 2; ++k) MQR_CUDA(cudaEventCreate(&c->ev[p][k]));
         for (int p = 0; p < mqr_ctx::kMaxPendingUpdates; ++p)
             for (int k = 0; k < 2; ++k) MQR_CUDA(cudaEventCreate(&c->up_ev[p][k]));
     }
-    c->timing = enable != 0;
+    c->timing = phase_mask != 0;
+    c->timing_mask = phase_mask & ((1u << MQR_NUM_PHASES) - 1u);
     std::memset(&c->acc, 0, sizeof(c->acc));
     std::memset(c->ev_used, 0, sizeof(c->ev_used));
     c->up_pending = 0;
     c->up_launches = 0;
     return MQR_OK;
+}
+
+mqr_status mqr_set_timing(mqr_ctx *c, int enable) {
+    return mqr_set_timing_phases(c, enable ? (1u << MQR_NUM_PHASES) - 1u : 0u);
 }
 
 mqr_status mqr_get_timing(const mqr_ctx *c, mqr_timing *out) {

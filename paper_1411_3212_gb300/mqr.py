@@ -34,7 +34,8 @@ EXPORTS = ["mqr_config_default", "mqr_create", "mqr_create_ex", "mqr_apply_updat
            "mqr_cost_set_params", "mqr_cost_get_params", "mqr_cost_train", "mqr_cost_gradient", "mqr_cost_predict",
            "mqr_cost_destroy", "mqr_get_stats",
            "mqr_get_leaves",
-           "mqr_get_sorted", "mqr_set_timing", "mqr_get_timing", "mqr_sort_objects_noalloc",
+           "mqr_get_sorted", "mqr_set_timing", "mqr_set_timing_phases", "mqr_get_timing",
+           "mqr_sort_objects_noalloc",
            "mqr_last_error", "mqr_destroy"]
 
 MQR_NOALLOC_MAX_OBJECTS = 262144
@@ -124,6 +125,7 @@ def load(path: str = LIB_PATH):
         "mqr_get_leaves": ([P, P, u64, ctypes.POINTER(u64)], i32),
         "mqr_get_sorted": ([P, P, P, u64, ctypes.POINTER(u64)], i32),
         "mqr_set_timing": ([P, i32], i32),
+        "mqr_set_timing_phases": ([P, u32], i32),
         "mqr_get_timing": ([P, ctypes.POINTER(mqr_timing)], i32),
         "mqr_sort_objects_noalloc": ([mqr_rect, P, u32, P, P, P], i32),
         "mqr_last_error": ([], ctypes.c_char_p),
@@ -372,6 +374,14 @@ def mqr_set_timing(ctx, enable):
     _check(load().mqr_set_timing(ctx, 1 if enable else 0))
 
 
+def mqr_set_timing_phases(ctx, phases):
+    """Time only the named phases (launch counts for all); empty: off."""
+    mask = 0
+    for p in phases:
+        mask |= 1 << PHASES.index(p)
+    _check(load().mqr_set_timing_phases(ctx, mask))
+
+
 def mqr_get_timing(ctx):
     t = mqr_timing()
     _check(load().mqr_get_timing(ctx, ctypes.byref(t)))
@@ -478,8 +488,13 @@ class Index:
     def stats(self):
         return mqr_get_stats(self.ctx)
 
-    def set_timing(self, enable=True):
-        mqr_set_timing(self.ctx, enable)
+    def set_timing(self, enable=True, phases=None):
+        """Per-phase timing: all phases, or only the named ones (launches are
+        counted for all)."""
+        if enable and phases is not None:
+            mqr_set_timing_phases(self.ctx, phases)
+        else:
+            mqr_set_timing(self.ctx, enable)
 
     def timing(self):
         return mqr_get_timing(self.ctx)

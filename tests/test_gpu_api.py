@@ -200,6 +200,31 @@ def test_timing_counters(case):
     idx.close()
 
 
+def test_timing_of_selected_phases(case):
+    """Timing only the emit phase: its device time is measured, the other
+    phases get no events, and every phase's launches are still counted (the
+    same counts as with all phases timed)."""
+    torch, dev = torch_dev()
+    t, want = case
+    mqr, idx = mk(30000)
+    idx.apply_updates(to_dev(t.ids, dev), to_dev(t.xy, dev))
+    idx.tick(to_dev(t.rects, dev), kind="pairs")          # buffers grown: no retries below
+    counts = []
+    for phases in (None, ["emit"]):
+        idx.set_timing(True, phases=phases)
+        for _ in range(2):
+            idx.apply_updates(to_dev(t.ids, dev), to_dev(t.xy, dev))
+            idx.tick(to_dev(t.rects, dev), kind="pairs")
+        tm = idx.timing()
+        counts.append(tm["launches"])
+    assert tm["ms"]["emit"] > 0.0
+    for ph in ["updates", "keys", "sort", "leaves", "query_blocks", "candidates", "group", "filter", "result_scan"]:
+        assert tm["ms"][ph] == 0.0, ph
+    assert counts[0] == counts[1]
+    idx.set_timing(False)
+    idx.close()
+
+
 def test_uniform_grid_subquery_counts_match_oracle(case):
     """The uniform-grid variant (every leaf at grid_level) splits queries
     exactly as g(q) over the grid's non-empty cells."""
