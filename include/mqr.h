@@ -386,6 +386,27 @@ mqr_status mqr_get_leaves(mqr_ctx *ctx, uint32_t *leaves_host, uint64_t cap, uin
  * object id, for the *n present objects.  Either pointer may be NULL. */
 mqr_status mqr_get_sorted(mqr_ctx *ctx, uint32_t *keys_host, uint32_t *ids_host, uint64_t cap, uint64_t *n);
 
+/* Checkpoint of the object state (Sec. 2.2: the latest position of every
+ * object; the index is rebuilt from it every tick, Alg. 1): xy_host (float
+ * host array of 2 x max_objects, (x, y) per id) and present_host (uint8 host
+ * array of max_objects: 1 if the object was ever updated) receive the state
+ * as of the calls enqueued so far.  cap = the arrays' length in objects, at
+ * least max_objects.  Blocks.  Errors: INVALID_ARG, CAPACITY. */
+mqr_status mqr_export_state(mqr_ctx *ctx, float *xy_host, uint8_t *present_host, uint32_t cap);
+
+/* Restart from a checkpoint: the state of every object becomes xy_host /
+ * present_host (as mqr_export_state writes them; n = max_objects), as if one
+ * update call had set the present ones, so later updates win over it.  A
+ * context with the same bounds and configuration then answers every tick
+ * exactly as the one that exported.  Blocks.  Errors: INVALID_ARG. */
+mqr_status mqr_import_state(mqr_ctx *ctx, const float *xy_host, const uint8_t *present_host, uint32_t n);
+
+/* Test hook for failure handling: the next `after` device buffer allocations
+ * of any context succeed and the one after them fails as if the device were
+ * out of memory (the call that needed it returns OOM, its context stays
+ * usable); the hook then disarms itself.  after < 0 disarms it. */
+mqr_status mqr_debug_fail_allocation(int after);
+
 /* Enable (1) or disable (0) per-phase timing; enabling resets the
  * accumulators.  Timing adds two event records per phase to the stream. */
 mqr_status mqr_set_timing(mqr_ctx *ctx, int enable);

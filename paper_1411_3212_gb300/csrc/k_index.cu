@@ -48,6 +48,27 @@ void launch_apply_updates(cudaStream_t st, const uint32_t *ids, const float2 *xy
     write_winner_kernel<<<g, T, 0, st>>>(ids, xy, n, nmax, epoch, stamp, pos);
 }
 
+// Object state snapshots (checkpoint / restart): the present flags of the
+// slots out of the update stamps, and stamps back from flags (a restored
+// object counts as updated by the restoring call, so later calls win).
+__global__ void state_flags_kernel(const unsigned long long *__restrict__ stamp, uint32_t nmax,
+                                   uint8_t *__restrict__ present) {
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < nmax; i += gridDim.x * blockDim.x)
+        present[i] = stamp[i] != 0ull ? 1 : 0;
+}
+__global__ void state_stamps_kernel(const uint8_t *__restrict__ present, uint32_t nmax, unsigned long long epoch,
+                                    unsigned long long *__restrict__ stamp) {
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < nmax; i += gridDim.x * blockDim.x)
+        stamp[i] = present[i] ? (epoch << 32) : 0ull;
+}
+void launch_state_flags(cudaStream_t st, const unsigned long long *stamp, uint32_t nmax, uint8_t *present) {
+    if (nmax) state_flags_kernel<<<(nmax + 255) / 256, 256, 0, st>>>(stamp, nmax, present);
+}
+void launch_state_stamps(cudaStream_t st, const uint8_t *present, uint32_t nmax, unsigned long long epoch,
+                         unsigned long long *stamp) {
+    if (nmax) state_stamps_kernel<<<(nmax + 255) / 256, 256, 0, st>>>(present, nmax, epoch, stamp);
+}
+
 // ---------------------------------------------------------------------------
 // a2: Morton keys at l_max = 15 of every slot, fused with the digit
 // histograms of the four 8-bit passes of the object sort (bits 32..63 of the

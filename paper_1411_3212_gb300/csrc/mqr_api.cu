@@ -43,6 +43,9 @@ mqr_status cuda_fail(cudaError_t e, const char *what) {
 // Bumped whenever any device buffer is (re)allocated or freed: a captured
 // tick graph holds raw pointers, so it is only replayed while this is unchanged.
 std::atomic<unsigned long long> g_buf_gen{0};
+// Fault injection (mqr_debug_fail_allocation): the number of device buffer
+// allocations still to succeed before one fails; negative: disarmed.
+std::atomic<long long> g_fail_alloc_after{-1};
 
 // A device buffer that only grows (contents are not preserved on growth).
 template <typename T>
@@ -55,6 +58,8 @@ struct DevBuf {
         p = nullptr;
         n = 0;
         ++g_buf_gen;
+        if (g_fail_alloc_after.load() >= 0 && g_fail_alloc_after.fetch_sub(1) == 0)
+            return cudaErrorMemoryAllocation;      // injected failure (the hook disarms itself)
         cudaError_t e = cudaMalloc(&p, want * sizeof(T));
         if (e == cudaSuccess) n = want;
         return e;
@@ -141,6 +146,7 @@ struct mqr_ctx {
     uint32_t region_bits = 0;
     DevBuf<uint32_t> region_cap, region_cnt;
     DevBuf<double> region_stats;
+    DevBuf<uint8_t> state_flags;    // staging of mqr_export_state / mqr_import_state
     int last_emit_kind = -1;
     unsigned long long world_q_total = 0;
     bool world_q_set = false;
@@ -874,6 +880,7 @@ void mqr_destroy(mqr_ctx *c) {
     c->region_cap.release();
     c->region_cnt.release();
     c->region_stats.release();
+    c->state_flags.release();
     DevBuf<unsigned long long> *u64s[] = {&c->stamp, &c->keysA, &c->keysB, &c->out_off, &c->off_stage,
                                           &c->sortA, &c->sortB};
     for (auto *b : u64s) b->release();
@@ -1307,6 +1314,43 @@ mqr_status mqr_region_work(mqr_ctx *c, const float *rects_dev, uint32_t Q, uint3
     MQR_CUDA(cudaMemcpyAsync(out_host, c->region_stats.p, kRegionStats * R * sizeof(double),
                              cudaMemcpyDeviceToHost, c->stream));
     MQR_CUDA(cudaStreamSynchronize(c->stream));
+    return MQR_OK;
+}
+
+mqr_status mqr_export_state(mqr_ctx *c, float *xy_host, uint8_t *present_host, uint32_t cap) {
+    if (!c || !xy_host || !present_host) return fail(MQR_ERR_INVALID_ARG, "NULL argument");
+    if (cap < c->nmax) return fail(MQR_ERR_CAPACITY, "buffers must hold max_objects entries");
+    MQR_CUDA(cudaSetDevice(c->device));
+    if (!c->nmax) return MQR_OK;
+    MQR_CUDA(c->state_flags.ensure(c->nmax));
+    launch_state_flags(c->stream, c->stamp.p, c->nmax, c->state_flags.p);
+    MQR_CUDA(cudaGetLastError());
+    MQR_CUDA(cudaMemcpyAsync(xy_host, c->pos.p, (size_t)c->nmax * sizeof(float2), cudaMemcpyDeviceToHost,
+                             c->stream));
+    MQR_CUDA(cudaMemcpyAsync(present_host, c->state_flags.p, c->nmax, cudaMemcpyDeviceToHost, c->stream));
+    MQR_CUDA(cudaStreamSynchronize(c->stream));
+    return MQR_OK;
+}
+
+mqr_status mqr_import_state(mqr_ctx *c, const float *xy_host, const uint8_t *present_host, uint32_t n) {
+    if (!c || !xy_host || !present_host) return fail(MQR_ERR_INVALID_ARG, "NULL argument");
+    if (n != c->nmax) return fail(MQR_ERR_INVALID_ARG, "n must equal max_objects");
+    MQR_CUDA(cudaSetDevice(c->device));
+    if (!c->nmax) return MQR_OK;
+    MQR_CUDA(c->state_flags.ensure(c->nmax));
+    MQR_CUDA(cudaStreamSynchronize(c->stream));
+    ++c->epoch;                                    // restored objects: updated by this call
+    MQR_CUDA(cudaMemcpyAsync(c->pos.p, xy_host, (size_t)c->nmax * sizeof(float2), cudaMemcpyHostToDevice,
+                             c->stream));
+    MQR_CUDA(cudaMemcpyAsync(c->state_flags.p, present_host, c->nmax, cudaMemcpyHostToDevice, c->stream));
+    launch_state_stamps(c->stream, c->state_flags.p, c->nmax, c->epoch, c->stamp.p);
+    MQR_CUDA(cudaGetLastError());
+    MQR_CUDA(cudaStreamSynchronize(c->stream));    // the host buffers may be reused at once
+    return MQR_OK;
+}
+
+mqr_status mqr_debug_fail_allocation(int after) {
+    g_fail_alloc_after.store(after < 0 ? -1 : after);
     return MQR_OK;
 }
 

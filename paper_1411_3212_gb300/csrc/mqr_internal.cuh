@@ -328,6 +328,9 @@ void launch_apply_updates(cudaStream_t st, const uint32_t *ids, const float2 *xy
                           float2 *pos, unsigned long long *err);
 
 // a2: Morton keys of every slot + digit histograms of the 4 sort passes.
+void launch_state_flags(cudaStream_t st, const unsigned long long *stamp, uint32_t nmax, uint8_t *present);
+void launch_state_stamps(cudaStream_t st, const uint8_t *present, uint32_t nmax, unsigned long long epoch,
+                         unsigned long long *stamp);
 void launch_morton_keys(cudaStream_t st, const float2 *pos, const unsigned long long *stamp,
                         uint32_t nmax, float x0, float y0, float sx, float sy, Worlds worlds,
                         unsigned long long *keys, uint32_t *hist4x256, Info *info);

@@ -34,7 +34,8 @@ EXPORTS = ["mqr_config_default", "mqr_create", "mqr_create_ex", "mqr_apply_updat
            "mqr_cost_set_params", "mqr_cost_get_params", "mqr_cost_train", "mqr_cost_gradient", "mqr_cost_predict",
            "mqr_cost_destroy", "mqr_get_stats",
            "mqr_get_leaves",
-           "mqr_get_sorted", "mqr_set_timing", "mqr_set_timing_phases", "mqr_get_timing",
+           "mqr_get_sorted", "mqr_export_state", "mqr_import_state", "mqr_debug_fail_allocation",
+           "mqr_set_timing", "mqr_set_timing_phases", "mqr_get_timing",
            "mqr_sort_objects_noalloc",
            "mqr_last_error", "mqr_destroy"]
 
@@ -126,6 +127,9 @@ def load(path: str = LIB_PATH):
         "mqr_get_sorted": ([P, P, P, u64, ctypes.POINTER(u64)], i32),
         "mqr_set_timing": ([P, i32], i32),
         "mqr_set_timing_phases": ([P, u32], i32),
+        "mqr_export_state": ([P, P, P, u32], i32),
+        "mqr_import_state": ([P, P, P, u32], i32),
+        "mqr_debug_fail_allocation": ([i32], i32),
         "mqr_get_timing": ([P, ctypes.POINTER(mqr_timing)], i32),
         "mqr_sort_objects_noalloc": ([mqr_rect, P, u32, P, P, P], i32),
         "mqr_last_error": ([], ctypes.c_char_p),
@@ -374,6 +378,28 @@ def mqr_set_timing(ctx, enable):
     _check(load().mqr_set_timing(ctx, 1 if enable else 0))
 
 
+def mqr_export_state(ctx, max_objects):
+    """-> (xy float32[max_objects, 2], present uint8[max_objects])."""
+    xy = np.zeros((max_objects, 2), np.float32)
+    present = np.zeros(max_objects, np.uint8)
+    _check(load().mqr_export_state(ctx, xy.ctypes.data_as(ctypes.c_void_p), present.ctypes.data_as(ctypes.c_void_p),
+                                   max_objects))
+    return xy, present
+
+
+def mqr_import_state(ctx, xy, present):
+    xy = np.ascontiguousarray(xy, np.float32)
+    present = np.ascontiguousarray(present, np.uint8)
+    if xy.shape != (present.shape[0], 2):
+        raise ValueError("xy must be [n, 2] with n = len(present)")
+    _check(load().mqr_import_state(ctx, xy.ctypes.data_as(ctypes.c_void_p), present.ctypes.data_as(ctypes.c_void_p),
+                                   present.shape[0]))
+
+
+def mqr_debug_fail_allocation(after):
+    _check(load().mqr_debug_fail_allocation(int(after)))
+
+
 def mqr_set_timing_phases(ctx, phases):
     """Time only the named phases (launch counts for all); empty: off."""
     mask = 0
@@ -469,6 +495,12 @@ class Index:
 
     def set_region_caps(self, region_bits, caps=None):
         mqr_set_region_caps(self.ctx, region_bits, caps)
+
+    def export_state(self):
+        return mqr_export_state(self.ctx, self.max_objects)
+
+    def import_state(self, xy, present):
+        mqr_import_state(self.ctx, xy, present)
 
     def region_counts(self, region_bits):
         return mqr_region_counts(self.ctx, region_bits)
