@@ -576,9 +576,6 @@ def run_served(args):
     rects = np.concatenate(rects)
     log("served: %d queries over %d ticks generated in %.1f s" % (rects.shape[0], args.served_ticks,
                                                                   time.perf_counter() - t_gen))
-    batched = w["kind"] == "batched"
-    if batched:                                          # sizes come from the generated worlds
-        nmax, Q = int(ticks[0].ids.shape[0]), int(ticks[0].rects.shape[0])
     ids_d = torch.from_numpy(ticks[0].ids.view(np.int32)).to(dev)
     updates = [(ids_d, torch.from_numpy(t.xy).to(dev)) for t in ticks]
     rects_d = torch.from_numpy(rects).to(dev)
