@@ -111,21 +111,3 @@ def test_max_batch_bounds_the_offered_queue():
     assert be.calls == [(0, 4), (4, 8), (8, 10)]
     assert rep["answered"] == 10 and rep["queued_at_end"] == 0
 
-
-def test_region_caps_rule():
-    """Per-region capacities of the cost-model chooser: 2^(a + b log2 d_r)
-    with d_r the region's density over the mean; empty regions take 2^a."""
-    from paper_1411_3212_gb300.costmodel import region_caps
-    counts = np.array([300, 100, 0, 0])            # densities 3, 1, -, - (mean 1 per region)
-    np.testing.assert_array_equal(region_caps(counts, 1, 7, 0.0), [128] * 4)
-    np.testing.assert_array_equal(region_caps(counts, 1, 7, 1.0), [384, 128, 128, 128])
-    np.testing.assert_array_equal(region_caps(counts, 1, 7, -1.0), [43, 128, 128, 128])
-    np.testing.assert_array_equal(region_caps(counts, 1, 14, 1.0), [16384, 16384, 16384, 16384])
-    np.testing.assert_array_equal(region_caps([0, 0, 0, 0], 1, 3, 0.5), [8] * 4)
-    big = np.zeros(16, np.int64)
-    big[5] = 10 ** 6
-    big[6] = 1
-    c = region_caps(big, 2, 4, -1.0)
-    assert c[5] == 1 and c[6] == 16384 and c[0] == 16
-    with pytest.raises(ValueError):
-        region_caps(counts, 2, 7, 0.0)
