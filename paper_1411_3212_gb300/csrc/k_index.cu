@@ -72,17 +72,22 @@ void launch_state_stamps(cudaStream_t st, const uint8_t *present, uint32_t nmax,
 // ---------------------------------------------------------------------------
 // a2: Morton keys at l_max = 15 of every slot, fused with the digit
 // histograms of the four 8-bit passes of the object sort (bits 32..63 of the
-// packed key) and the count of present objects.
+// packed key), the first pass's per-tile digit counts (a block covers exactly
+// one sort tile) and the count of present objects.
 // ---------------------------------------------------------------------------
 constexpr int kMortonThreads = 256, kMortonItems = 16;
+static_assert(kMortonThreads * kMortonItems == kSortTile, "a Morton block is one sort tile");
 
 __global__ void __launch_bounds__(kMortonThreads)
 morton_kernel(const float2 *__restrict__ pos, const unsigned long long *__restrict__ stamp,
               uint32_t nmax, float x0, float y0, float sx, float sy, Worlds worlds,
-              unsigned long long *__restrict__ keys, uint32_t *__restrict__ hist, Info *info) {
+              unsigned long long *__restrict__ keys, uint32_t *__restrict__ hist,
+              uint32_t *__restrict__ tile_counts, Info *info) {
     __shared__ uint32_t s_hist[4 * 256];
+    __shared__ uint32_t s_tile[256];              // this tile's counts of the first digit
     __shared__ uint32_t s_cnt;
     for (int i = threadIdx.x; i < 4 * 256; i += kMortonThreads) s_hist[i] = 0;
+    for (int i = threadIdx.x; i < 256; i += kMortonThreads) s_tile[i] = 0;
     if (threadIdx.x == 0) s_cnt = 0;
     __syncthreads();
     uint32_t present = 0;
@@ -106,6 +111,7 @@ morton_kernel(const float2 *__restrict__ pos, const unsigned long long *__restri
             k = kAbsentKey;
         }
         keys[i] = ((unsigned long long)k << 32) | i;
+        atomicAdd(&s_tile[k & 255u], 1u);
         atomicAdd(&s_hist[0 * 256 + (k & 255u)], 1u);
         atomicAdd(&s_hist[1 * 256 + ((k >> 8) & 255u)], 1u);
         atomicAdd(&s_hist[2 * 256 + ((k >> 16) & 255u)], 1u);
@@ -116,16 +122,19 @@ morton_kernel(const float2 *__restrict__ pos, const unsigned long long *__restri
     __syncthreads();
     for (int i = threadIdx.x; i < 4 * 256; i += kMortonThreads)
         if (s_hist[i]) atomicAdd(hist + i, s_hist[i]);
+    const uint32_t tiles = (nmax + kSortTile - 1) / kSortTile;
+    for (int i = threadIdx.x; i < 256; i += kMortonThreads) tile_counts[(size_t)i * tiles + blockIdx.x] = s_tile[i];
     if (threadIdx.x == 0 && s_cnt) atomicAdd(&info->n_present, (unsigned long long)s_cnt);
 }
 
 void launch_morton_keys(cudaStream_t st, const float2 *pos, const unsigned long long *stamp,
                         uint32_t nmax, float x0, float y0, float sx, float sy, Worlds worlds,
-                        unsigned long long *keys, uint32_t *hist4x256, Info *info) {
+                        unsigned long long *keys, uint32_t *hist4x256, uint32_t *tile_counts, Info *info) {
     if (nmax == 0) return;
     uint32_t per = kMortonThreads * kMortonItems;
     morton_kernel<<<(nmax + per - 1) / per, kMortonThreads, 0, st>>>(pos, stamp, nmax, x0, y0, sx, sy,
-                                                                      worlds, keys, hist4x256, info);
+                                                                      worlds, keys, hist4x256, tile_counts,
+                                                                      info);
 }
 
 // ---------------------------------------------------------------------------
@@ -342,10 +351,10 @@ digit_scan_kernel(const uint32_t *__restrict__ counts, const uint32_t *__restric
 void launch_sort_pass_pre(cudaStream_t st, const unsigned long long *in, unsigned long long *out, uint32_t n,
                           int shift, const uint32_t *hist256, uint32_t *counts, uint32_t *offs,
                           unsigned long long *err, bool final_obj, const float2 *pos, uint32_t *skey,
-                          uint32_t *sid, float2 *sxy) {
+                          uint32_t *sid, float2 *sxy, bool counts_ready) {
     if (n == 0) return;
     const uint32_t tiles = (n + kSortTile - 1) / kSortTile;
-    tile_hist_kernel<<<tiles, kSortThreads, 0, st>>>(in, n, shift, counts);
+    if (!counts_ready) tile_hist_kernel<<<tiles, kSortThreads, 0, st>>>(in, n, shift, counts);
     digit_scan_kernel<<<256, 256, 0, st>>>(counts, hist256, n, offs);
     if (final_obj)
         onesweep_kernel<true, true><<<tiles, kSortThreads, 0, st>>>(in, out, n, shift, hist256, nullptr,

@@ -307,17 +307,18 @@ mqr_status enqueue_tick(mqr_ctx *c, const float4 *rects, uint32_t Q, int emit_ki
     // a2 + a3: keys and the 4-pass onesweep sort of (key << 32 | id).
     phase_begin(c, MQR_PHASE_KEYS);
     const Worlds worlds{c->world_obj.p, c->world_q.p, c->n_worlds, c->world_bits};
-    launch_morton_keys(st, c->pos.p, c->stamp.p, nmax, x0, y0, c->sx, c->sy, worlds, c->keysA.p, hist, info);
+    launch_morton_keys(st, c->pos.p, c->stamp.p, nmax, x0, y0, c->sx, c->sy, worlds, c->keysA.p, hist,
+                       c->sort_counts.p, info);
     phase_end(c, MQR_PHASE_KEYS, nmax ? 1 : 0);
     unsigned long long *src = c->keysA.p, *dst = c->keysB.p;
     phase_begin(c, MQR_PHASE_SORT);
     for (int p = 0; p < 4; ++p) {
         const bool fin = p == 3;
         launch_sort_pass_pre(st, src, dst, nmax, 32 + 8 * p, hist + 256 * p, c->sort_counts.p, c->sort_offs.p,
-                             err, fin, c->pos.p, c->skey.p, c->sid.p, c->sxy.p);
+                             err, fin, c->pos.p, c->skey.p, c->sid.p, c->sxy.p, p == 0);
         std::swap(src, dst);
     }
-    phase_end(c, MQR_PHASE_SORT, nmax ? 12 : 0);
+    phase_end(c, MQR_PHASE_SORT, nmax ? 11 : 0);     // the first pass's tile counts come from the key kernel
     // a4
     phase_begin(c, MQR_PHASE_LEAVES);
     const uint32_t cap = c->cfg.leaf_cap;

@@ -331,9 +331,10 @@ void launch_apply_updates(cudaStream_t st, const uint32_t *ids, const float2 *xy
 void launch_state_flags(cudaStream_t st, const unsigned long long *stamp, uint32_t nmax, uint8_t *present);
 void launch_state_stamps(cudaStream_t st, const uint8_t *present, uint32_t nmax, unsigned long long epoch,
                          unsigned long long *stamp);
+// tile_counts: the first sort pass's per-tile digit counts (256 x tiles).
 void launch_morton_keys(cudaStream_t st, const float2 *pos, const unsigned long long *stamp,
                         uint32_t nmax, float x0, float y0, float sx, float sy, Worlds worlds,
-                        unsigned long long *keys, uint32_t *hist4x256, Info *info);
+                        unsigned long long *keys, uint32_t *hist4x256, uint32_t *tile_counts, Info *info);
 
 // a3: one onesweep pass over n u64 keys, 8-bit digit at `shift`.  The final
 // pass of the object sort (`final_obj`) writes skey/sid/sxy instead of `out`.
@@ -345,10 +346,11 @@ void launch_onesweep_pass(cudaStream_t st, const unsigned long long *in, unsigne
 // The same pass without look-back: per-tile digit counts (counts/offs hold
 // 256 x ceil(n / kSortTile) u32 each), a per-digit scan over the tiles, then
 // the rank-and-scatter tile kernel with the precomputed offsets.
+// counts_ready: `counts` already holds the pass's per-tile digit counts.
 void launch_sort_pass_pre(cudaStream_t st, const unsigned long long *in, unsigned long long *out, uint32_t n,
                           int shift, const uint32_t *hist256, uint32_t *counts, uint32_t *offs,
                           unsigned long long *err, bool final_obj, const float2 *pos, uint32_t *skey,
-                          uint32_t *sid, float2 *sxy);
+                          uint32_t *sid, float2 *sxy, bool counts_ready);
 // Histograms (nd digit passes at shifts[]) of n u64 keys, for generic sorts.
 void launch_key_histograms(cudaStream_t st, const unsigned long long *keys, uint32_t n,
                            const int *shifts_host, int nd, uint32_t *hist);
