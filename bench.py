@@ -607,6 +607,68 @@ def run_served(args):
     print(json.dumps(line), flush=True)
 
 
+def run_autotune(args):
+    """--autotune: the leaf capacity (64..512), then the work-item kernels'
+    blocks per SM (2..16, coordinate descent) at that capacity, tuned by
+    timing on the workload's ticks; the tuned tick time against the
+    configured one (leaf_cap of the workload, 8 blocks per SM), L2 flushed
+    before every timed tick."""
+    import torch
+    from paper_1411_3212_gb300 import mqr
+    from paper_1411_3212_gb300.autotune import tune_launch_config, tune_leaf_cap
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    name = args.workload
+    w = WORKLOADS[name]
+    nmax = w["n"]
+    ticks = gen_ticks(name, 0, 6)
+    batched = w["kind"] == "batched"
+    if batched:                                          # sizes come from the generated worlds
+        nmax = int(ticks[0].ids.shape[0])
+    dticks = [(torch.from_numpy(t.ids.view(np.int32)).to(dev), torch.from_numpy(t.xy).to(dev),
+               torch.from_numpy(t.rects).to(dev)) for t in ticks[1:]]
+
+    def mk(cap):
+        index = mqr.Index(bounds=(0.0, 0.0, 1.0, 1.0), leaf_cap=cap, max_objects=nmax)
+        if batched:                                      # the worlds keep their sizes across ticks
+            index.set_worlds(ticks[0].obj_base)
+            index.set_query_worlds(ticks[0].q_base)
+        return index
+    best_cap, cap_table = tune_leaf_cap(mk, dticks, caps=(64, 128, 256, 512), reps=1)
+    idx = mk(best_cap)
+    best_launch, launch_table = tune_launch_config(idx, dticks, options=(2, 4, 8, 16), reps=1)
+    flush = torch.empty(args.flush_mb * (1 << 20) // 4, dtype=torch.int32, device=dev)
+
+    def timed(index):
+        ts = []
+        for k in range(args.steps):
+            ids, xy, rects = dticks[k % len(dticks)]
+            flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            index.apply_updates(ids, xy)
+            index.tick(rects, kind="pairs")
+            b.record()
+            b.synchronize()
+            ts.append(a.elapsed_time(b))
+        return float(np.mean(ts))
+    tuned_ms = timed(idx)
+    idx.close()
+    base = mk(w["cap"])
+    for ids, xy, rects in dticks:
+        base.apply_updates(ids, xy)
+        base.tick(rects, kind="pairs")
+    base_ms = timed(base)
+    base.close()
+    line = {"metric": "ms per tick, autotuned leaf capacity and launch shapes vs configured", "unit": "ms",
+            "config": {"workload": w["desc"], "steps": args.steps,
+                       "l2": "flushed (%d MB write) before every timed tick" % args.flush_mb},
+            "configured_ms": base_ms, "tuned_ms": tuned_ms, "leaf_cap": best_cap, "blocks_per_sm": best_launch,
+            "leaf_cap_table": {str(c): v["ms_per_tick"] for c, v in cap_table.items()},
+            "launch_table": [{"config": c, "ms": ms} for c, ms, _ in launch_table]}
+    print(json.dumps(line), flush=True)
+
+
 def run_per_world(args):
     """--per-world: the batched-worlds workload answered the plain way, one
     context per world and one tick per world in turn, for comparison with the
@@ -790,6 +852,8 @@ def main():
     ap.add_argument("--served", action="store_true", help="run the served stream instead")
     ap.add_argument("--costmodel", action="store_true", help="learned per-tick index choice vs fixed")
     ap.add_argument("--region-bits", type=int, default=3, help="--costmodel: depth of the node-level regions")
+    ap.add_argument("--autotune", action="store_true",
+                    help="tune the leaf capacity and the work-item kernels' launch shapes on the workload")
     ap.add_argument("--calib-ticks", type=int, default=5,
                     help="untimed ticks with events around every phase (the per-phase breakdown)")
     ap.add_argument("--no-covering", action="store_true",
@@ -811,6 +875,8 @@ def main():
         run_served(args)
     elif args.costmodel:
         run_costmodel(args)
+    elif args.autotune:
+        run_autotune(args)
     elif args.per_world:
         run_per_world(args)
     elif args.impl == "reference":

@@ -298,6 +298,21 @@ mqr_status mqr_set_query_worlds(mqr_ctx *ctx, const uint32_t *q_base_host);
  * INVALID_ARG. */
 mqr_status mqr_set_index(mqr_ctx *ctx, int index_kind, uint32_t leaf_cap, uint32_t grid_level);
 
+/* Launch shapes of the work-item kernels: blocks per SM of the candidate
+ * pass, the subquery compaction, the filter (Alg. 2) and the decoding / emit
+ * (Alg. 4); 0 keeps the default (8).  Their blocks draw work items from
+ * counters or stride over them, so the shapes change time, never results;
+ * block sizes are fixed per kernel by its register budget.  An autotuner
+ * (autotune.tune_launch_config) picks them by timing.  1 <= value <= 64.
+ * Call between ticks.  Errors: INVALID_ARG. */
+typedef struct {
+    uint32_t candidate_blocks_per_sm;
+    uint32_t compact_blocks_per_sm;
+    uint32_t filter_blocks_per_sm;
+    uint32_t emit_blocks_per_sm;
+} mqr_launch_config;
+mqr_status mqr_set_launch_config(mqr_ctx *ctx, const mqr_launch_config *cfg);
+
 /* Per-region split thresholds of the quadtree (Alg. 1's th_quad chosen per
  * region instead of once): the quadrants of level region_bits (1..4) are the
  * regions, numbered in Morton order (region r holds the keys whose top

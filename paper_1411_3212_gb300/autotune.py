@@ -1,4 +1,4 @@
-"""Leaf-capacity autotuning.
+"""Autotuning of the leaf capacity and of the work-item kernels' launch shapes.
 
 The quadtree's split threshold (th_quad, Alg. 1; the paper fixes it per
 experiment) trades fewer, larger leaves (more containment tests, Eq. of the
@@ -40,4 +40,50 @@ def tune_leaf_cap(make_index, ticks, caps=(32, 64, 128, 256, 512), kind="pairs",
         finally:
             idx.close()
     best = min(table, key=lambda c: table[c]["ms_per_tick"])
+    return best, table
+
+
+def _time_ticks(idx, ticks, kind, reps):
+    import torch
+    for ids, xy, rects in ticks:                       # warm-up: buffer growth, graph capture
+        idx.apply_updates(ids, xy)
+        idx.tick(rects, kind=kind)
+    torch.cuda.synchronize()
+    start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    results = 0
+    start.record()
+    for _ in range(reps):
+        for ids, xy, rects in ticks:
+            idx.apply_updates(ids, xy)
+            idx.tick(rects, kind=kind)
+            results += idx.stats()["n_results"]
+    end.record()
+    end.synchronize()
+    return start.elapsed_time(end) / (reps * len(ticks)), results // reps
+
+
+def tune_launch_config(idx, ticks, options=(2, 4, 8, 16), kind="pairs", reps=2):
+    """Blocks per SM of the candidate pass, the compaction, the filter and the
+    emit (mqr_set_launch_config), by coordinate descent: each kernel in turn
+    takes the option with the smallest tick time, the others held.  Block
+    sizes are fixed per kernel (register budgets); only the grids move, and
+    results must not.  Returns (best dict, table of (config, ms, results))."""
+    from .mqr import LAUNCH_KERNELS
+    best = {k: 8 for k in LAUNCH_KERNELS}
+    table = []
+    ms0, res0 = None, None
+    for k in LAUNCH_KERNELS:
+        timings = {}
+        for v in options:
+            cfg = dict(best, **{k: v})
+            idx.set_launch_config(**cfg)
+            ms, res = _time_ticks(idx, ticks, kind, reps)
+            if res0 is None:
+                res0 = res
+            if res != res0:
+                raise RuntimeError("launch shapes changed the results")
+            timings[v] = ms
+            table.append((cfg, ms, res))
+        best[k] = min(timings, key=timings.get)
+    idx.set_launch_config(**best)
     return best, table

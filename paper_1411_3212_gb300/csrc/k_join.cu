@@ -129,12 +129,12 @@ filter_kernel(const float4 *__restrict__ rects, const float2 *__restrict__ sxy,
     }
 }
 
-void launch_filter(cudaStream_t st, int num_sms, const float4 *rects, const float2 *sxy,
+void launch_filter(cudaStream_t st, int grid_blocks, const float4 *rects, const float2 *sxy,
                    const uint32_t *leaf_beg, const uint32_t *leaf_sub_off,
                    const uint32_t *leaf_word_off, const uint32_t *leaf_item_off,
                    const uint32_t *item_leaf, const uint32_t *isub, const uint32_t *sub_q,
                    uint32_t *sub_res, uint32_t *bitmap, uint32_t *ticket, Caps caps, const Info *info) {
-    filter_kernel<<<num_sms * 8, kFilterThreads, 0, st>>>(rects, sxy, leaf_beg, leaf_sub_off,
+    filter_kernel<<<grid_blocks, kFilterThreads, 0, st>>>(rects, sxy, leaf_beg, leaf_sub_off,
                                                           leaf_word_off, leaf_item_off, item_leaf, isub,
                                                           sub_q, sub_res, bitmap, ticket, caps, info);
 }
@@ -412,12 +412,12 @@ emit_kernel(const uint32_t *__restrict__ sub_q, const uint32_t *__restrict__ sub
     }
 }
 
-void launch_emit(cudaStream_t st, int num_sms, int emit_kind, const uint32_t *sub_q,
+void launch_emit(cudaStream_t st, int grid_blocks, int emit_kind, const uint32_t *sub_q,
                  const uint32_t *sub_leaf, const uint32_t *sub_len, const uint32_t *leaf_word_off,
                  const unsigned long long *out_off, const uint32_t *leaf_beg,
                  const uint32_t *sid, const uint32_t *bitmap, void *out, uint32_t wpr,
                  uint32_t *ticket, Caps caps, const Info *info) {
-    const int grid = num_sms * 8;
+    const int grid = grid_blocks;
     switch (emit_kind) {
         case kEmitPairs:
             emit_kernel<kEmitPairs><<<grid, kEmitThreads, 0, st>>>(sub_q, sub_leaf, sub_len, leaf_word_off, out_off,

@@ -411,13 +411,13 @@ tile_scan_kernel(const uint32_t *__restrict__ tile_cnt, uint32_t *__restrict__ t
     if (tid == 0 && base + 2048 >= ntiles) info->n_sub = s_prefix + total;
 }
 
-void launch_candidates(cudaStream_t st, int num_sms, int covering, const uint32_t *tile_p0,
+void launch_candidates(cudaStream_t st, int grid_blocks, int covering, const uint32_t *tile_p0,
                        const uint32_t *pair_q, const uint32_t *pair_first, const uint32_t *pair_blo,
                        const unsigned long long *pair_off, const uint2 *qcells, const uint2 *leaf_box,
                        const uint32_t *leaf_beg, uint32_t *tile_cnt, uint32_t *tile_off, uint32_t *leaf_nsub,
                        uint4 *pad, uint32_t *pair_rec, uint32_t *status, uint32_t *tile_counter, Caps caps,
                        Info *info) {
-    cand_count_kernel<<<num_sms * 8, 256, 0, st>>>(covering, tile_p0, pair_q, pair_first, pair_blo, pair_off,
+    cand_count_kernel<<<grid_blocks, 256, 0, st>>>(covering, tile_p0, pair_q, pair_first, pair_blo, pair_off,
                                                    qcells, leaf_box, leaf_beg, tile_cnt, leaf_nsub, pad,
                                                    pair_rec, caps, info);
     const unsigned long long scan_blocks = (caps.cand_tiles + kCandScanTile - 1) / kCandScanTile;
@@ -570,10 +570,10 @@ cand_compact_kernel(const uint4 *__restrict__ pad, const uint32_t *__restrict__ 
     }
 }
 
-void launch_compact(cudaStream_t st, int num_sms, const uint4 *pad, const uint32_t *tile_cnt,
+void launch_compact(cudaStream_t st, int grid_blocks, const uint4 *pad, const uint32_t *tile_cnt,
                     const uint32_t *tile_off, const uint32_t *leaf_sub_off, uint32_t *sub_q, uint32_t *sub_leaf,
                     uint32_t *sub_len, uint32_t *sub_res, uint32_t *isub, Caps caps, const Info *info) {
-    cand_compact_kernel<<<num_sms * 8, 256, 0, st>>>(pad, tile_cnt, tile_off, leaf_sub_off, sub_q, sub_leaf,
+    cand_compact_kernel<<<grid_blocks, 256, 0, st>>>(pad, tile_cnt, tile_off, leaf_sub_off, sub_q, sub_leaf,
                                                      sub_len, sub_res, isub, caps, info);
 }
 

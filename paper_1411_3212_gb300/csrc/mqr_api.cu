@@ -148,6 +148,9 @@ struct mqr_ctx {
     DevBuf<double> region_stats;
     DevBuf<uint8_t> state_flags;    // staging of mqr_export_state / mqr_import_state
     int last_emit_kind = -1;
+    // blocks per SM of the work-item kernels (mqr_set_launch_config)
+    uint32_t bps_cand = kDefaultBlocksPerSM, bps_compact = kDefaultBlocksPerSM, bps_filter = kDefaultBlocksPerSM,
+             bps_emit = kDefaultBlocksPerSM;
     unsigned long long world_q_total = 0;
     bool world_q_set = false;
 
@@ -351,7 +354,7 @@ mqr_status enqueue_tick(mqr_ctx *c, const float4 *rects, uint32_t Q, int emit_ki
     phase_end(c, MQR_PHASE_QUERY_BLOCKS, Q ? 2 : 1);
     // a7: candidates -> subquery records
     phase_begin(c, MQR_PHASE_CANDIDATES);
-    launch_candidates(st, c->num_sms, cov, c->tile_p0.p, c->pair_q.p, c->pair_first.p, c->pair_blo.p,
+    launch_candidates(st, c->num_sms * (int)c->bps_cand, cov, c->tile_p0.p, c->pair_q.p, c->pair_first.p, c->pair_blo.p,
                       c->pair_off.p, c->qcells.p, c->leaf_box.p, c->leaf_beg.p, c->tile_cnt.p,
                       c->tile_off.p, c->leaf_nsub.p, c->cand_pad.p, c->pair_rec.p,
                       at<uint32_t>(c, a.st_cand), ctr + 8, caps, info);
@@ -360,7 +363,7 @@ mqr_status enqueue_tick(mqr_ctx *c, const float4 *rects, uint32_t Q, int emit_ki
     phase_begin(c, MQR_PHASE_GROUP);
     launch_leaf_scan(st, nmax, c->leaf_beg.p, c->leaf_nsub.p, c->leaf_sub_off.p, c->leaf_word_off.p,
                      c->leaf_item_off.p, c->item_leaf.p, at<uint32_t>(c, a.st_lscan), ctr + 6, caps, info);
-    launch_compact(st, c->num_sms, c->cand_pad.p, c->tile_cnt.p, c->tile_off.p, c->leaf_sub_off.p, c->sub_q.p,
+    launch_compact(st, c->num_sms * (int)c->bps_compact, c->cand_pad.p, c->tile_cnt.p, c->tile_off.p, c->leaf_sub_off.p, c->sub_q.p,
                    c->sub_leaf.p, c->sub_len.p, c->sub_res.p, c->isub.p, caps, info);
     phase_end(c, MQR_PHASE_GROUP, nmax ? 2 : 1);
     // a10
@@ -374,7 +377,7 @@ mqr_status enqueue_tick(mqr_ctx *c, const float4 *rects, uint32_t Q, int emit_ki
         return check_launch("tick kernels");
     }
     phase_begin(c, MQR_PHASE_FILTER);
-    launch_filter(st, c->num_sms, rects, c->sxy.p, c->leaf_beg.p, c->leaf_sub_off.p,
+    launch_filter(st, c->num_sms * (int)c->bps_filter, rects, c->sxy.p, c->leaf_beg.p, c->leaf_sub_off.p,
                   c->leaf_word_off.p, c->leaf_item_off.p, c->item_leaf.p, c->isub.p, c->sub_q.p, c->sub_res.p,
                   c->bitmap.p, ctr + 10, caps, info);
     phase_end(c, MQR_PHASE_FILTER, 1);
@@ -387,7 +390,7 @@ mqr_status enqueue_tick(mqr_ctx *c, const float4 *rects, uint32_t Q, int emit_ki
     // a12 + a13
     if (out != nullptr && emit_kind >= 0) {
         phase_begin(c, MQR_PHASE_EMIT);
-        launch_emit(st, c->num_sms, emit_kind, c->sub_q.p, c->sub_leaf.p, c->sub_len.p, c->leaf_word_off.p,
+        launch_emit(st, c->num_sms * (int)c->bps_emit, emit_kind, c->sub_q.p, c->sub_leaf.p, c->sub_len.p, c->leaf_word_off.p,
                     c->out_off.p, c->leaf_beg.p, c->sid.p, c->bitmap.p, out,
                     bitmap_words_per_row(nmax), ctr + 9, caps, info);
         phase_end(c, MQR_PHASE_EMIT, 1);
@@ -657,7 +660,7 @@ mqr_status tick_device_impl(mqr_ctx *c, const float *rects_dev, uint32_t Q, int 
               c->item_leaf.n};
     Info *info = at<Info>(c, a.info);
     phase_begin(c, MQR_PHASE_OUTPUT_SORT);
-    launch_emit(c->stream, c->num_sms, kEmitKeys64, c->sub_q.p, c->sub_leaf.p, c->sub_len.p,
+    launch_emit(c->stream, c->num_sms * (int)c->bps_emit, kEmitKeys64, c->sub_q.p, c->sub_leaf.p, c->sub_len.p,
                 c->leaf_word_off.p, c->out_off.p, c->leaf_beg.p, c->sid.p, c->bitmap.p, c->sortA.p, wpr,
                 at<uint32_t>(c, a.counters) + 9, caps, info);
     s = check_launch("emit keys");
@@ -830,6 +833,23 @@ mqr_status mqr_set_index(mqr_ctx *c, int index_kind, uint32_t leaf_cap, uint32_t
     if (index_kind == MQR_INDEX_QUADTREE) c->cfg.leaf_cap = leaf_cap;
     else c->cfg.grid_level = grid_level;
     ++g_buf_gen;                                   // a captured tick holds the old configuration
+    return MQR_OK;
+}
+
+mqr_status mqr_set_launch_config(mqr_ctx *c, const mqr_launch_config *lc) {
+    if (!c || !lc) return fail(MQR_ERR_INVALID_ARG, "NULL argument");
+    const uint32_t v[4] = {lc->candidate_blocks_per_sm, lc->compact_blocks_per_sm, lc->filter_blocks_per_sm,
+                           lc->emit_blocks_per_sm};
+    for (uint32_t x : v)
+        if (x > 64) return fail(MQR_ERR_INVALID_ARG, "blocks per SM must be 0 (default) .. 64");
+    MQR_CUDA(cudaSetDevice(c->device));
+    MQR_CUDA(cudaStreamSynchronize(c->stream));
+    auto pick = [](uint32_t x) { return x ? x : (uint32_t)kDefaultBlocksPerSM; };
+    c->bps_cand = pick(v[0]);
+    c->bps_compact = pick(v[1]);
+    c->bps_filter = pick(v[2]);
+    c->bps_emit = pick(v[3]);
+    ++g_buf_gen;                                   // a captured tick holds the old launch shapes
     return MQR_OK;
 }
 
@@ -1245,7 +1265,7 @@ mqr_status mqr_tick_admit(mqr_ctx *c, const float *rects_dev, uint32_t Q, int ki
     }
     if (n > 0) {
         phase_begin(c, MQR_PHASE_EMIT);
-        launch_emit(c->stream, c->num_sms, ek, c->sub_q.p, c->sub_leaf.p, c->sub_len.p, c->leaf_word_off.p,
+        launch_emit(c->stream, c->num_sms * (int)c->bps_emit, ek, c->sub_q.p, c->sub_leaf.p, c->sub_len.p, c->leaf_word_off.p,
                     c->out_off.p, c->leaf_beg.p, c->sid.p, c->bitmap.p, out_dev,
                     bitmap_words_per_row(c->nmax), at<uint32_t>(c, a.counters) + 9, caps, info);
         phase_end(c, MQR_PHASE_EMIT, 1);

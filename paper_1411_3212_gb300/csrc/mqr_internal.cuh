@@ -394,7 +394,11 @@ void launch_query_blocks(cudaStream_t st, const float4 *rects, uint32_t Q, float
                          Info *info);
 // a7: candidates (warp tiles of 32) -> subquery records (query-major), the
 // first record of every pair (pair_rec[npairs+1]) and leaf_nsub.
-void launch_candidates(cudaStream_t st, int num_sms, int covering, const uint32_t *tile_p0,
+// The work-item kernels (candidates, compaction, filter, emit) take their
+// grid in blocks: they draw work from counters (or stride over it), so the
+// grid only sets how many blocks are resident (mqr_set_launch_config).
+constexpr int kDefaultBlocksPerSM = 8;
+void launch_candidates(cudaStream_t st, int grid_blocks, int covering, const uint32_t *tile_p0,
                        const uint32_t *pair_q, const uint32_t *pair_first, const uint32_t *pair_blo,
                        const unsigned long long *pair_off, const uint2 *qcells, const uint2 *leaf_box,
                        const uint32_t *leaf_beg, uint32_t *tile_cnt, uint32_t *tile_off, uint32_t *leaf_nsub,
@@ -409,12 +413,12 @@ void launch_leaf_scan(cudaStream_t st, uint32_t nmax, const uint32_t *leaf_beg,
                       uint32_t *status3, uint32_t *tile_counter, Caps caps, Info *info);
 
 // a7/a8 compaction of the padded records; intersecting ones into their leaf's list.
-void launch_compact(cudaStream_t st, int num_sms, const uint4 *pad, const uint32_t *tile_cnt,
+void launch_compact(cudaStream_t st, int grid_blocks, const uint4 *pad, const uint32_t *tile_cnt,
                     const uint32_t *tile_off, const uint32_t *leaf_sub_off, uint32_t *sub_q, uint32_t *sub_leaf,
                     uint32_t *sub_len, uint32_t *sub_res, uint32_t *isub, Caps caps, const Info *info);
 
 // a10: filtering into bitmap words + per-subquery counts.
-void launch_filter(cudaStream_t st, int num_sms, const float4 *rects, const float2 *sxy,
+void launch_filter(cudaStream_t st, int grid_blocks, const float4 *rects, const float2 *sxy,
                    const uint32_t *leaf_beg, const uint32_t *leaf_sub_off,
                    const uint32_t *leaf_word_off, const uint32_t *leaf_item_off,
                    const uint32_t *item_leaf, const uint32_t *isub, const uint32_t *sub_q,
@@ -429,7 +433,7 @@ void launch_result_scan(cudaStream_t st, unsigned long long sub_cap, const uint3
 // a12 + a13: emit results in query-major order.
 enum EmitKind { kEmitPairs = 0, kEmitIds = 1, kEmitBitmap = 2, kEmitKeys64 = 3, kEmitRuns = 4,
                 kEmitAtomic = 5 /* the atomic-append baseline (no bitmaps, unordered pairs) */ };
-void launch_emit(cudaStream_t st, int num_sms, int emit_kind, const uint32_t *sub_q,
+void launch_emit(cudaStream_t st, int grid_blocks, int emit_kind, const uint32_t *sub_q,
                  const uint32_t *sub_leaf, const uint32_t *sub_len, const uint32_t *leaf_word_off,
                  const unsigned long long *out_off, const uint32_t *leaf_beg,
                  const uint32_t *sid, const uint32_t *bitmap, void *out, uint32_t bitmap_words_per_row,

@@ -30,7 +30,7 @@ EXPORTS = ["mqr_config_default", "mqr_create", "mqr_create_ex", "mqr_apply_updat
            "mqr_apply_updates_host", "mqr_tick", "mqr_tick_host", "mqr_tick_host_async", "mqr_host_wait",
            "mqr_get_sorted_async",
            "mqr_tick_admit", "mqr_set_graph", "mqr_set_worlds",
-           "mqr_set_query_worlds", "mqr_set_index", "mqr_set_region_caps", "mqr_region_counts", "mqr_region_work", "mqr_cost_param_count", "mqr_cost_create",
+           "mqr_set_query_worlds", "mqr_set_index", "mqr_set_region_caps", "mqr_set_launch_config", "mqr_region_counts", "mqr_region_work", "mqr_cost_param_count", "mqr_cost_create",
            "mqr_cost_set_params", "mqr_cost_get_params", "mqr_cost_train", "mqr_cost_gradient", "mqr_cost_predict",
            "mqr_cost_destroy", "mqr_get_stats",
            "mqr_get_leaves",
@@ -60,6 +60,11 @@ class mqr_config(ctypes.Structure):
     _fields_ = [("max_objects", ctypes.c_uint32), ("leaf_cap", ctypes.c_uint32),
                 ("index_kind", ctypes.c_int32), ("grid_level", ctypes.c_uint32),
                 ("covering", ctypes.c_int32), ("reserved", ctypes.c_int32 * 3)]
+
+
+class mqr_launch_config(ctypes.Structure):
+    _fields_ = [("candidate_blocks_per_sm", ctypes.c_uint32), ("compact_blocks_per_sm", ctypes.c_uint32),
+                ("filter_blocks_per_sm", ctypes.c_uint32), ("emit_blocks_per_sm", ctypes.c_uint32)]
 
 
 class mqr_stats(ctypes.Structure):
@@ -112,6 +117,7 @@ def load(path: str = LIB_PATH):
         "mqr_set_query_worlds": ([P, P], i32),
         "mqr_set_index": ([P, i32, u32, u32], i32),
         "mqr_set_region_caps": ([P, u32, P], i32),
+        "mqr_set_launch_config": ([P, ctypes.POINTER(mqr_launch_config)], i32),
         "mqr_region_counts": ([P, u32, P], i32),
         "mqr_region_work": ([P, P, u32, u32, P], i32),
         "mqr_cost_param_count": ([], u32),
@@ -245,6 +251,15 @@ def mqr_set_region_caps(ctx, region_bits, caps=None):
         _check(load().mqr_set_region_caps(ctx, int(region_bits), arr.ctypes.data_as(ctypes.c_void_p)))
     else:
         _check(load().mqr_set_region_caps(ctx, 0, None))
+
+
+LAUNCH_KERNELS = ("candidate", "compact", "filter", "emit")
+
+
+def mqr_set_launch_config(ctx, candidate=0, compact=0, filter=0, emit=0):
+    """Blocks per SM of the work-item kernels (0: the default)."""
+    cfg = mqr_launch_config(int(candidate), int(compact), int(filter), int(emit))
+    _check(load().mqr_set_launch_config(ctx, ctypes.byref(cfg)))
 
 
 def mqr_region_counts(ctx, region_bits):
@@ -501,6 +516,9 @@ class Index:
 
     def import_state(self, xy, present):
         mqr_import_state(self.ctx, xy, present)
+
+    def set_launch_config(self, **blocks_per_sm):
+        mqr_set_launch_config(self.ctx, **blocks_per_sm)
 
     def region_counts(self, region_bits):
         return mqr_region_counts(self.ctx, region_bits)

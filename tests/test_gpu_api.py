@@ -7,7 +7,8 @@ import pytest
 
 import oracle
 from paper_1411_3212_gb300 import workloads
-from tests.gpu_util import assert_same_csr, expand_runs, oracle_state, to_dev, torch_dev  # noqa: F401
+from tests.gpu_util import (assert_same_csr, expand_runs, gpu_csr_sorted, gpu_pairs_as_csr, oracle_state,  # noqa: F401
+                            to_dev, torch_dev)
 
 pytestmark = pytest.mark.gpu
 
@@ -262,6 +263,30 @@ def test_leaf_cap_autotune_picks_a_capacity_with_identical_results(case):
     assert best in (8, 32, 128) and set(table) == {8, 32, 128}
     assert {v["results"] for v in table.values()} == {int(want[1].shape[0])}
     assert all(v["ms_per_tick"] > 0 for v in table.values())
+
+
+def test_launch_config_changes_time_not_results(case):
+    """Blocks per SM of the work-item kernels (down to one block per SM and up
+    to 32): every shape gives the oracle's result; out-of-range values are
+    rejected; the autotuner picks a shape among its options."""
+    torch, dev = torch_dev()
+    t, want = case
+    from paper_1411_3212_gb300.autotune import tune_launch_config
+    mqr, idx = mk(30000)
+    idx.apply_updates(to_dev(t.ids, dev), to_dev(t.xy, dev))
+    for cfg in [dict(candidate=1, compact=1, filter=1, emit=1), dict(candidate=16, compact=2, filter=4, emit=32),
+                dict()]:
+        idx.set_launch_config(**cfg)
+        assert_same_csr(gpu_csr_sorted(idx, t.rects, dev), want, str(cfg))
+        assert_same_csr(gpu_pairs_as_csr(idx, t.rects, dev), want, str(cfg))
+    with pytest.raises(mqr.MqrError):
+        idx.set_launch_config(filter=65)
+    ticks = [(to_dev(t.ids, dev), to_dev(t.xy, dev), to_dev(t.rects, dev))]
+    best, table = tune_launch_config(idx, ticks, options=(2, 8), reps=1)
+    assert set(best) == {"candidate", "compact", "filter", "emit"} and set(best.values()) <= {2, 8}
+    assert len(table) == 8 and len({r for _, _, r in table}) == 1
+    assert_same_csr(gpu_csr_sorted(idx, t.rects, dev), want, "tuned")
+    idx.close()
 
 
 def test_graph_mode_replays_identical_results():
