@@ -52,7 +52,14 @@ def test_export_import_restarts_exactly():
     b.close()
 
 
-def test_injected_allocation_failure_is_reported_and_recoverable():
+@pytest.fixture
+def disarm_hook():
+    yield
+    from paper_1411_3212_gb300 import mqr
+    mqr.mqr_debug_fail_allocation(-1)              # never leave the hook armed for other tests
+
+
+def test_injected_allocation_failure_is_reported_and_recoverable(disarm_hook):
     torch, dev = torch_dev()
     from paper_1411_3212_gb300 import mqr
     n = 20_000
