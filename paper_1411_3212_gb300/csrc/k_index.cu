@@ -413,10 +413,13 @@ leaves_kernel(const uint32_t *__restrict__ K, uint32_t cap, int uniform_grid, ui
     __shared__ uint8_t s_L[kLeafTile + 1];
     __shared__ uint32_t s_scan[kLeafThreads / 32 + 1];
     __shared__ uint32_t s_tile, s_prefix;
+    __shared__ uint32_t s_rcap[1 << (2 * kMaxRegionBits)];   // per-region capacities, loaded up front
 
     const int tid = threadIdx.x;
     const uint32_t N = (uint32_t)info->n_present;
     if (tid == 0) s_tile = atomicAdd(tile_counter, 1u);
+    if (region_bits)
+        for (uint32_t i = tid; i < (1u << (2 * region_bits)); i += kLeafThreads) s_rcap[i] = region_cap[i];
     __syncthreads();
     const uint32_t tile = s_tile;
     const long t0 = (long)tile * kLeafTile;
@@ -448,7 +451,7 @@ leaves_kernel(const uint32_t *__restrict__ K, uint32_t cap, int uniform_grid, ui
             const long a = r == r_lo ? pa : pa + s_first[r - r_lo];
             const long b = r == r_hi ? pb : pa + s_first[r + 1 - r_lo];
             if (a < b) {
-                const uint32_t rc = region_cap[r];
+                const uint32_t rc = s_rcap[r];
                 int rk = 0;
                 while ((2ull << rk) <= (unsigned long long)rc + 1) ++rk;   // floor(log2(rc+1))
                 const long rs = a - (long)rc;         // the window of position a starts here
