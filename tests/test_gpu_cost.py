@@ -99,6 +99,8 @@ def test_chooser_learns_the_cheapest_configuration():
         picks.append(c)
     assert all(c[0] == QUAD for c in picks)
     assert picks[-10:] == [(QUAD, 256)] * 10
+    # the gain over the method without the model (the fixed capacity 128)
+    assert np.mean([cost[c[1]] for c in picks[-10:]]) <= 0.93 * cost[128]
     ch.close()
 
 
@@ -118,6 +120,7 @@ def test_chooser_learns_a_region_candidate():
         ch.record(c, 4_000_000, 400_000, side, cost[c] * (1 + 0.01 * rng.normal()))
         picks.append(c)
     assert picks[-10:] == [(REGIONS, 3, 8, 0.25)] * 10
+    assert np.mean([cost[c] for c in picks[-10:]]) <= 0.85 * cost[(QUAD, 128)]   # gain over the fixed capacity
     ch.close()
 
 
@@ -157,4 +160,8 @@ def test_region_chooser_learns_per_region_optimum():
     got = np.log2(ch.choose().astype(np.float64))
     assert np.mean(np.abs(got - best) <= 1) >= 0.9, (got, best)
     assert np.mean(got == best) >= 0.6, (got, best)
+    # the gain over one fixed capacity for every region (128, the method without the model)
+    w_model, _ = work_for(np.exp2(got))
+    w_fixed, _ = work_for(np.full(R, 128.0))
+    assert w_model["tests"].sum() < 0.9 * w_fixed["tests"].sum()
     ch.close()
