@@ -177,7 +177,8 @@ void launch_key_histograms(cudaStream_t st, const unsigned long long *keys, uint
 // Status layout: status[digit * num_tiles + tile].
 // ---------------------------------------------------------------------------
 template <bool FINAL, bool PRE>
-__global__ void __launch_bounds__(kSortThreads, 3)     // 40 registers: 3 tiles in flight per SM
+__global__ void __launch_bounds__(kSortThreads, FINAL ? 2 : 3)   // 3 tiles in flight per SM (40 registers);
+                                                                  // 2 for the gathering last pass
 onesweep_kernel(const unsigned long long *__restrict__ in, unsigned long long *__restrict__ out,
                 uint32_t n, int shift, const uint32_t *__restrict__ hist256, uint32_t *status,
                 uint32_t *tile_counter, unsigned long long *err, const float2 *__restrict__ pos,
@@ -264,6 +265,34 @@ onesweep_kernel(const unsigned long long *__restrict__ in, unsigned long long *_
     __syncthreads();
 
     const uint32_t nvalid = n - base < (uint32_t)kSortTile ? n - base : (uint32_t)kSortTile;
+    if (FINAL) {
+        // The last pass gathers each object's position by id (random reads):
+        // all of a thread's gathers are issued before any store so they overlap.
+        float2 pv[kSortItems];
+        unsigned long long kv[kSortItems];
+        uint32_t ov[kSortItems];
+#pragma unroll
+        for (int j = 0; j < kSortItems; ++j) {
+            const uint32_t i = tid + j * kSortThreads;
+            ov[j] = n;                                  // n: nothing to write
+            if (i < nvalid) {
+                kv[j] = s_keys[i];
+                ov[j] = s_gbase[(uint32_t)(kv[j] >> shift) & 255u] + i;
+                const uint32_t kk = (uint32_t)(kv[j] >> 32);
+                if (ov[j] < n && kk != kAbsentKey) pv[j] = pos[(uint32_t)kv[j]];
+                if (ov[j] >= n) atomicOr(err, kErrInternal);
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < kSortItems; ++j) {
+            if (ov[j] >= n) continue;
+            const uint32_t kk = (uint32_t)(kv[j] >> 32);
+            skey[ov[j]] = kk;
+            sid[ov[j]] = (uint32_t)kv[j];
+            if (kk != kAbsentKey) sxy[ov[j]] = pv[j];
+        }
+        return;
+    }
     for (uint32_t i = tid; i < nvalid; i += kSortThreads) {
         unsigned long long key = s_keys[i];
         uint32_t dg = (uint32_t)(key >> shift) & 255u;
@@ -272,15 +301,7 @@ onesweep_kernel(const unsigned long long *__restrict__ in, unsigned long long *_
             atomicOr(err, kErrInternal);
             continue;
         }
-        if (FINAL) {
-            uint32_t id = (uint32_t)key;
-            uint32_t kk = (uint32_t)(key >> 32);
-            skey[o] = kk;
-            sid[o] = id;
-            if (kk != kAbsentKey) sxy[o] = pos[id];
-        } else {
-            out[o] = key;
-        }
+        out[o] = key;
     }
 }
 
