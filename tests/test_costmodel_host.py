@@ -38,3 +38,95 @@ def test_nonneg_lstsq_recovers_nonnegative_coefficients():
     keep = sol > 0
     ls, *_ = np.linalg.lstsq(A[:, keep], b, rcond=None)
     np.testing.assert_allclose(sol[keep], ls, atol=1e-9)
+
+
+class _Float64Model:
+    """The float64 reference network (oracle/cost_mlp.py) in place of the
+    device model, so that the choosers' logic runs without a GPU."""
+
+    def __init__(self, params):
+        from oracle import cost_mlp
+        self.mlp = cost_mlp
+        self.p = np.asarray(params, np.float64)
+        self.m = self.v = None
+        self.step = 0
+
+    def predict(self, X):
+        return self.mlp.forward(self.p, np.asarray(X, np.float64))[0]
+
+    def train(self, X, y, epochs, lr):
+        X = np.asarray(X, np.float64)
+        y = np.asarray(y, np.float64)
+        self.p, self.m, self.v, _ = self.mlp.adam(self.p, X, y, epochs=epochs, lr=lr, m=self.m, v=self.v,
+                                                  step0=self.step)
+        self.step += epochs
+        return self.mlp.loss(self.p, X, y)
+
+    def close(self):
+        pass
+
+
+@pytest.fixture
+def cpu_model(monkeypatch):
+    from paper_1411_3212_gb300 import mqr
+    monkeypatch.setattr(mqr, "CostModel", _Float64Model)
+
+
+def _work(R, objects, tests, **extra):
+    w = {k: np.zeros(R) for k in ("objects", "leaves", "queries", "side_log2_sum", "sub_intersecting",
+                                  "sub_covering", "tests", "results_intersecting", "results_covering")}
+    w["objects"] = np.asarray(objects, np.float64)
+    w["queries"] = w["objects"] / 10
+    w["side_log2_sum"] = w["queries"] * -9.0
+    w["tests"] = np.asarray(tests, np.float64)
+    for k, v in extra.items():
+        w[k] = np.asarray(v, np.float64)
+    return w
+
+
+def test_region_chooser_fits_unit_costs_exactly(cpu_model):
+    """Phase times that are exact non-negative combinations of the logged
+    work give back those unit costs, and the region costs they price."""
+    from paper_1411_3212_gb300.costmodel import RegionChooser
+    ch = RegionChooser(region_bits=1, caps=(64, 128), explore_rounds=2, retrain_every=1, epochs=5)
+    rng = np.random.default_rng(4)
+    for _ in range(6):
+        ch.choose()
+        w = _work(4, rng.integers(1000, 9000, 4), rng.uniform(1e5, 1e6, 4),
+                  sub_intersecting=rng.uniform(100, 900, 4), results_covering=rng.uniform(1e4, 1e5, 4))
+        ms = 2e-9 * w["tests"].sum() + 5e-7 * w["sub_intersecting"].sum() + 1e-9 * w["results_covering"].sum() + 0.1
+        ch.observe(w, {"filter": ms})
+    np.testing.assert_allclose(ch.unit_cost[[0, 1, 4]], [2e-9, 5e-7, 1e-9], rtol=1e-6)
+    assert np.all(ch.unit_cost >= 0)
+    np.testing.assert_allclose(ch.region_costs(w), 2e-9 * w["tests"] + 5e-7 * w["sub_intersecting"] +
+                               1e-9 * w["results_covering"], rtol=1e-6)
+
+
+def test_region_chooser_learns_per_region_optimum_on_cpu(cpu_model):
+    """The node-level chooser with the float64 network: regions whose best
+    capacity grows with their density get their own best capacity, a clear
+    gain over one capacity for all; empty regions keep the fallback."""
+    from paper_1411_3212_gb300.costmodel import RegionChooser
+    R = 16
+    rng = np.random.default_rng(3)
+    objects = np.exp2(rng.uniform(8, 18, R)).round()
+    objects[5] = 0                                            # an empty region
+    caps = np.array([32, 64, 128, 256, 512, 1024], np.float64)
+    best = np.clip(np.round(4 + (np.log2(np.maximum(objects, 1)) - 8) * 0.5), 5, 10)
+
+    def tick(cap_r):
+        cost = (1 + 0.3 * (np.log2(cap_r) - best) ** 2) * objects / 65536.0
+        return _work(R, objects, cost), {"filter": float(cost.sum())}
+
+    ch = RegionChooser(region_bits=2, caps=caps, explore_rounds=5, epsilon=0.0, retrain_every=10, first_epochs=600,
+                       seed=5)
+    ch.observe(*tick(np.full(R, 128.0)))
+    for _ in range(60):
+        ch.observe(*tick(ch.choose().astype(np.float64)))
+    got = ch.choose().astype(np.float64)
+    live = objects > 0
+    assert got[5] == 128                                      # the fallback for the empty region
+    assert np.mean(np.log2(got[live]) == best[live]) >= 0.6
+    model_cost = tick(got)[1]["filter"]
+    fixed_cost = tick(np.full(R, 128.0))[1]["filter"]
+    assert model_cost < 0.9 * fixed_cost
