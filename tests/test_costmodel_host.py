@@ -130,3 +130,41 @@ def test_region_chooser_learns_per_region_optimum_on_cpu(cpu_model):
     model_cost = tick(got)[1]["filter"]
     fixed_cost = tick(np.full(R, 128.0))[1]["filter"]
     assert model_cost < 0.9 * fixed_cost
+
+
+def test_index_chooser_on_cpu(cpu_model):
+    """The per-tick chooser with the float64 network: round-robin
+    exploration, then the cheapest configuration of a known cost (a region
+    rule here), a gain over the fixed capacity; applying a choice configures
+    an index through its calls."""
+    from paper_1411_3212_gb300.costmodel import GRID, QUAD, REGIONS, IndexChooser
+    cost = {(QUAD, 128): 1.9, (QUAD, 256): 1.8, (GRID, 8): 2.4, (REGIONS, 3, 8, 0.25): 1.6}
+    ch = IndexChooser(candidates=list(cost), seed=2, epsilon=0.0)
+    rng = np.random.default_rng(1)
+    picks = []
+    for k in range(40):
+        side = -9.0 + 0.05 * rng.normal()
+        c = ch.choose(4_000_000, 400_000, side)
+        ch.record(c, 4_000_000, 400_000, side, cost[c] * (1 + 0.01 * rng.normal()))
+        picks.append(c)
+    assert picks[:8] == list(cost) * 2                        # two exploration rounds
+    assert picks[-10:] == [(REGIONS, 3, 8, 0.25)] * 10
+    assert np.mean([cost[c] for c in picks[-10:]]) < 0.9 * cost[(QUAD, 128)]
+
+    calls = []
+
+    class FakeIndex:
+        def set_index(self, kind, leaf_cap=0, grid_level=0):
+            calls.append(("index", kind, leaf_cap, grid_level))
+
+        def set_region_caps(self, bits, caps=None):
+            calls.append(("regions", bits, None if caps is None else list(caps)))
+
+        def region_counts(self, bits):
+            return np.array([300] + [100] * (4 ** bits - 1))
+
+    ch.apply(FakeIndex(), (GRID, 8))
+    ch.apply(FakeIndex(), (REGIONS, 1, 7, 1.0))
+    assert calls[0] == ("regions", 0, None) and calls[1] == ("index", GRID, 0, 8)
+    assert calls[2] == ("index", QUAD, 128, 0)
+    assert calls[3][0] == "regions" and calls[3][1] == 1 and calls[3][2] == [256, 85, 85, 85]
