@@ -62,13 +62,16 @@ def _time_ticks(idx, ticks, kind, reps):
     return start.elapsed_time(end) / (reps * len(ticks)), results // reps
 
 
-def tune_launch_config(idx, ticks, options=(2, 4, 8, 16), kind="pairs", reps=2):
+def tune_launch_config(idx, ticks, options=(2, 4, 8, 16), kind="pairs", reps=2, timer=None):
     """Blocks per SM of the candidate pass, the compaction, the filter and the
     emit (mqr_set_launch_config), by coordinate descent: each kernel in turn
     takes the option with the smallest tick time, the others held.  Block
     sizes are fixed per kernel (register budgets); only the grids move, and
-    results must not.  Returns (best dict, table of (config, ms, results))."""
+    results must not.  timer(idx, ticks, kind, reps) -> (ms per tick,
+    results) defaults to CUDA-event timing of the ticks.  Returns (best dict,
+    table of (config, ms, results))."""
     from .mqr import LAUNCH_KERNELS
+    timer = timer or _time_ticks
     best = {k: 8 for k in LAUNCH_KERNELS}
     table = []
     ms0, res0 = None, None
@@ -77,7 +80,7 @@ def tune_launch_config(idx, ticks, options=(2, 4, 8, 16), kind="pairs", reps=2):
         for v in options:
             cfg = dict(best, **{k: v})
             idx.set_launch_config(**cfg)
-            ms, res = _time_ticks(idx, ticks, kind, reps)
+            ms, res = timer(idx, ticks, kind, reps)
             if res0 is None:
                 res0 = res
             if res != res0:

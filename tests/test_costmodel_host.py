@@ -1,4 +1,4 @@
-"""Host-side logic of the cost-model choosers (no GPU): the per-region
+"""Host-side logic of the choosers and tuners (no GPU): the per-region
 capacity rule and the non-negative least squares that fits unit costs of
 the logged work to the logged phase times."""
 import numpy as np
@@ -168,3 +168,32 @@ def test_index_chooser_on_cpu(cpu_model):
     assert calls[0] == ("regions", 0, None) and calls[1] == ("index", GRID, 0, 8)
     assert calls[2] == ("index", QUAD, 128, 0)
     assert calls[3][0] == "regions" and calls[3][1] == 1 and calls[3][2] == [256, 85, 85, 85]
+
+
+def test_launch_autotuner_coordinate_descent():
+    """The launch-shape tuner takes, kernel by kernel, the option with the
+    smallest time (others held), leaves the index at the best shapes, and
+    refuses shapes that change the results."""
+    from paper_1411_3212_gb300.autotune import tune_launch_config
+
+    class FakeIndex:
+        def __init__(self):
+            self.cfg = {}
+            self.applied = []
+
+        def set_launch_config(self, **cfg):
+            self.cfg = dict(cfg)
+            self.applied.append(dict(cfg))
+
+    target = {"candidate": 4, "compact": 16, "filter": 2, "emit": 8}
+
+    def timer(idx, ticks, kind, reps):
+        ms = 1.0 + sum(abs(np.log2(idx.cfg[k]) - np.log2(v)) for k, v in target.items())
+        return ms, 12345
+
+    idx = FakeIndex()
+    best, table = tune_launch_config(idx, [None], options=(2, 4, 8, 16), timer=timer)
+    assert best == target and idx.cfg == target and len(table) == 16
+    bad = FakeIndex()
+    with pytest.raises(RuntimeError):
+        tune_launch_config(bad, [None], options=(2, 8), timer=lambda i, t, k, r: (1.0, i.cfg["candidate"]))
