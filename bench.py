@@ -581,7 +581,7 @@ def run_served(args):
     rects_d = torch.from_numpy(rects).to(dev)
     idx = mqr.Index(bounds=(0.0, 0.0, 1.0, 1.0), leaf_cap=128, max_objects=world.n)
     be = GpuBackend(idx, updates, rects_d, kind="runs", budget_bytes=args.budget_mb << 20,
-                    copy_out=not args.no_copy_out)
+                    copy_out=not args.no_copy_out, overlap=not args.served_plain)
     max_batch = int(args.max_batch_factor * args.rate * dt) if args.max_batch_factor > 0 else None
     warm = TickServer(be, dt, max_batch=max_batch).run(arrivals[arrivals < 3 * dt], n_ticks=3)   # warm-up
     clocks = Clocks(0)
@@ -596,10 +596,12 @@ def run_served(args):
             "config": {"workload": "served-10M: %d objects (95%% in 16 Gaussian hotspots, sigma 0.005; 5%% "
                                    "uniform), Poisson arrivals %.3g queries/s, square sides log-uniform "
                                    "0.0005-0.004, ticks of %.1f ms, leaf_cap 128, covering-compressed output, "
-                                   "admission by %d MB of output per tick, %s"
+                                   "admission by %d MB of output per tick, %s%s"
                                    % (world.n, args.rate, args.dt_ms, args.budget_mb,
                                       "output kept on the device" if args.no_copy_out
-                                      else "output copied to pinned host memory"),
+                                      else "output copied to pinned host memory",
+                                      "; plain form: each tick's copy waited for before the next tick"
+                                      if args.served_plain else "; copies overlap the next tick"),
                        "ticks": args.served_ticks, "max_batch": max_batch},
             "served": rep, "warmup_ticks": warm["ticks"],
             "max_out_elems_per_tick": max((t.get("out_elems", 0) for t in per), default=0),
@@ -864,6 +866,8 @@ def main():
     ap.add_argument("--served-ticks", type=int, default=100)
     ap.add_argument("--served-objects", type=int, default=10_000_000)
     ap.add_argument("--budget-mb", type=int, default=1024, help="served: output memory per tick")
+    ap.add_argument("--served-plain", action="store_true",
+                    help="served: the plain form, no overlap of a tick's copy with the next tick")
     ap.add_argument("--max-batch-factor", type=float, default=1.5,
                     help="served: queries offered per tick, x the mean arrivals per tick (0: whole queue)")
     ap.add_argument("--no-copy-out", action="store_true", help="served: keep each tick's output on the device")

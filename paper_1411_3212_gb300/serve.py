@@ -128,9 +128,11 @@ class GpuBackend:
     float32[Q_total, 4] device, all queries in arrival order; budget_bytes:
     output memory per tick (each of two buffers).  copy_out: copy every
     tick's output to pinned host memory on a second stream; t_f is then the
-    end of that copy, else the end of the tick's kernels."""
+    end of that copy, else the end of the tick's kernels.  overlap=False is
+    the plain form: each tick's copy is waited for before the next tick starts
+    (no overlap of a tick's copy with the next tick's work)."""
 
-    def __init__(self, idx, updates, rects_dev, kind="runs", budget_bytes=1 << 30, copy_out=True):
+    def __init__(self, idx, updates, rects_dev, kind="runs", budget_bytes=1 << 30, copy_out=True, overlap=True):
         import torch
         from . import mqr
         self.torch, self.mqr = torch, mqr
@@ -147,6 +149,7 @@ class GpuBackend:
         self.buf_free = [None, None]
         self.n_answers = 0
         self.ref = None
+        self.overlap = overlap
 
     def start(self, t0):
         torch = self.torch
@@ -175,6 +178,8 @@ class GpuBackend:
                 self.host[b][:n].copy_(self.out[b][:n], non_blocking=True)
             ev.record(self.copy_stream)
         self.buf_free[b] = ev
+        if not self.overlap:
+            ev.synchronize()                             # plain: the copy ends before anything else starts
         return admitted, cnt, ev
 
     def finish(self, ev):
