@@ -69,3 +69,29 @@ def test_binding_fails_loudly_without_library(tmp_path):
             mqr.load(str(tmp_path / "missing.so"))
     finally:
         mqr._lib = saved
+
+
+def test_new_entry_points_reject_bad_arguments_without_a_gpu(lib):
+    """NULL contexts and out-of-range arguments of the region, launch-shape,
+    checkpoint and timing calls are refused before any CUDA call; the
+    binding checks array shapes before calling the library."""
+    import numpy as np
+    from paper_1411_3212_gb300 import mqr
+    E = mqr.MQR_ERR_INVALID_ARG
+    caps = (ctypes.c_uint32 * 4)(1, 2, 3, 4)
+    assert lib.mqr_set_region_caps(None, 1, caps) == E
+    assert lib.mqr_region_counts(None, 1, caps) == E
+    out = (ctypes.c_double * 36)()
+    assert lib.mqr_region_work(None, None, 0, 1, out) == E
+    lc = mqr.mqr_launch_config(8, 8, 8, 8)
+    assert lib.mqr_set_launch_config(None, ctypes.byref(lc)) == E
+    assert lib.mqr_export_state(None, None, None, 0) == E
+    assert lib.mqr_import_state(None, None, None, 0) == E
+    assert lib.mqr_set_timing_phases(None, 1) == E
+    assert lib.mqr_debug_fail_allocation(-1) == mqr.MQR_OK
+    with pytest.raises(ValueError):
+        mqr.mqr_set_region_caps(None, 2, np.ones(4, np.uint32))      # 4^2 thresholds expected
+    with pytest.raises(ValueError):
+        mqr.mqr_import_state(None, np.zeros((10, 2), np.float32), np.zeros(9, np.uint8))
+    with pytest.raises(mqr.MqrError):
+        mqr.mqr_set_launch_config(None, filter=8)
