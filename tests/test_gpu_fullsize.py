@@ -2,7 +2,8 @@
 4M-object hotspot workload with 400,000 queries per tick (leaf_cap 128,
 quadtree, pair-list output), the 1M-object uniform walk (quadtree and the
 uniform grid it is compared with), the 256 batched worlds (12.3M objects) and
-the 10M-object served state with admission.  Every query's result count is
+the 10M-object served state with admission, and hotspot-4M under per-region
+capacities.  Every query's result count is
 compared with the oracle's, and the complete id lists of a random sample of
 queries are compared exactly; covering-compressed outputs must give the same
 counts.
@@ -179,4 +180,35 @@ def test_served_10m_full_size_admission():
     counts[heads + 1] = 0
     csum = np.concatenate([[0], np.cumsum(counts)])
     np.testing.assert_array_equal(csum[eoff[1:]] - csum[eoff[:-1]], want_cnt[:adm])
+    idx.close()
+
+
+def test_hotspot_4m_per_region_capacities_full_size():
+    """The per-region thresholds the cost-model chooser settles on at
+    hotspot-4M (regions of depth 3, capacity 2^(8 + 0.25 log2 density)): every
+    query's count against the oracle, sampled lists, and the leaf table's
+    capacity rule checked on the GPU's own leaves."""
+    torch, dev = torch_dev()
+    from paper_1411_3212_gb300 import mqr
+    from paper_1411_3212_gb300.costmodel import region_caps
+    w = workloads.HotspotWalk(n=4_000_000, q=400_000, seed=0)
+    idx = mqr.Index(bounds=(0.0, 0.0, 1.0, 1.0), leaf_cap=128, max_objects=w.n)
+    st = oracle.State(w.n)
+    rng = np.random.default_rng(9)
+    t = w.next_tick()
+    idx.apply_updates(to_dev(t.ids, dev), to_dev(t.xy, dev))
+    st.apply_updates(t.ids, t.xy)
+    idx.tick(to_dev(t.rects, dev), kind="count")
+    caps = region_caps(idx.region_counts(3), 3, 8, 0.25)
+    idx.set_region_caps(3, caps)
+    t = w.next_tick()
+    idx.apply_updates(to_dev(t.ids, dev), to_dev(t.xy, dev))
+    st.apply_updates(t.ids, t.xy)
+    _check_counts_and_sample(idx, st, t.rects, to_dev(t.rects, dev), 0.002, rng, 500, dev, "per-region caps")
+    # capacity rule on the leaves: a leaf above l_max holds at most its region's capacity
+    lv = idx.leaves().astype(np.int64)
+    region = (lv[:, 1] << (2 * (15 - lv[:, 0]))) >> (2 * (15 - 3))
+    size = lv[:, 3] - lv[:, 2]
+    assert np.all((size <= caps[region]) | (lv[:, 0] == 15))
+    assert lv[:, 0].min() >= 3
     idx.close()
