@@ -455,6 +455,15 @@ mqr_status enqueue_or_replay(mqr_ctx *c, const float4 *rects, uint32_t Q, int em
                              unsigned long long out_cap_elems, unsigned long long *offsets, const Arena &a,
                              Caps &caps) {
     if (!c->graph_on || c->timing) return enqueue_tick(c, rects, Q, emit_kind, out, out_cap_elems, offsets, a, caps);
+    // The captured tick reads the queries from the context's own buffer, so a
+    // caller that passes each tick's queries in a different buffer still
+    // replays the same graph (one device-to-device copy of 16 B per query).
+    MQR_CUDA(c->q_rects.ensure(std::max<size_t>(Q, 1)));
+    const float4 *staged = reinterpret_cast<const float4 *>(c->q_rects.p);
+    if (Q && rects != staged)
+        MQR_CUDA(cudaMemcpyAsync(c->q_rects.p, rects, (size_t)Q * sizeof(float4), cudaMemcpyDeviceToDevice,
+                                 c->stream));
+    rects = staged;
     const mqr_ctx::GraphKey key{rects, out, offsets, Q, out_cap_elems, g_buf_gen.load(), c->n_worlds, emit_kind};
     if (!c->gexec || !(key == c->gkey)) {
         if (c->gexec) {
