@@ -10,7 +10,8 @@ Functions (each citing the paper passage its C routine follows):
   apply_updates  -- Sec. 2.2 batch processing, last update of a tick wins.
   join_grid      -- Def. 1 result sets through a uniform grid (exact).
   join_brute     -- Def. 1 by testing every (query, object) pair.
-  count_grid     -- per-query result counts (Def. 1).
+  count_grid     -- per-query result counts (Def. 1), optionally with an
+                    order-independent 64-bit checksum of each result set.
   bitmap         -- query x object bitmap of a result (bitmap layout of the
                     filtering phase, Sec. 5.4, taken over the whole Q x N).
   cell / scale / morton / keys -- Morton codes at l_max = 15 (Alg. 1).
@@ -64,7 +65,7 @@ def _load():
     lib.orc_join_brute.restype = i64
     lib.orc_join_grid.argtypes = [P, P, u32, P, u32, f64, f64, f64, f64, f64, P, ctypes.POINTER(P)]
     lib.orc_join_grid.restype = i64
-    lib.orc_count_grid.argtypes = [P, P, u32, P, u32, f64, f64, f64, f64, f64, P]
+    lib.orc_count_grid.argtypes = [P, P, u32, P, u32, f64, f64, f64, f64, f64, P, P]
     lib.orc_count_grid.restype = i64
     lib.orc_bitmap.argtypes = [P, P, u32, u32, P]
     lib.orc_bitmap.restype = None
@@ -151,18 +152,21 @@ def join_grid(state: State, rects, bounds=(0.0, 0.0, 1.0, 1.0), cell_side=0.01):
     return _csr_from_c(lib, Q, off, p, total)
 
 
-def count_grid(state: State, rects, bounds=(0.0, 0.0, 1.0, 1.0), cell_side=0.01):
-    """Per-query result counts (Def. 1) -> u64[Q]."""
+def count_grid(state: State, rects, bounds=(0.0, 0.0, 1.0, 1.0), cell_side=0.01, with_hash=False):
+    """Per-query result counts (Def. 1) -> u64[Q]; with_hash: (counts,
+    hashes), hashes[q] = sum modulo 2^64 of splitmix64's output function of
+    (q << 32 | id) over the ids of query q's result set."""
     lib = _load()
     rects = _f32(rects, (4,))
     Q = rects.shape[0]
     cnt = np.zeros(Q, np.uint64)
+    hs = np.zeros(Q, np.uint64) if with_hash else None
     x0, y0, x1, y1 = (float(b) for b in bounds)
     r = lib.orc_count_grid(_ptr(state.pos), _ptr(state.present), state.nmax, _ptr(rects), Q,
-                           x0, y0, x1, y1, float(cell_side), _ptr(cnt))
+                           x0, y0, x1, y1, float(cell_side), _ptr(cnt), _ptr(hs) if with_hash else None)
     if r < 0:
         raise MemoryError("oracle allocation failed")
-    return cnt
+    return (cnt, hs) if with_hash else cnt
 
 
 def bitmap(offsets, ids, nmax: int):

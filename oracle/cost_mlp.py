@@ -5,8 +5,10 @@ A multilayer perceptron 5 -> 64 -> 64 -> 1 with ReLU hidden layers, mean
 squared error, and full-batch Adam (Kingma and Ba, 2015: beta1 0.9, beta2
 0.999, eps 1e-8, bias-corrected moments), written out step by step in numpy
 float64.  Parameter vector layout (the same as the C ABI's): W1[64][5],
-b1[64], W2[64][64], b2[64], W3[64], b3.  Pinned in the CPU tests by finite
-differences of the loss.
+b1[64], W2[64][64], b2[64], W3[64], b3.  Pinned in the CPU tests: the forward
+pass by a network whose output is worked out by hand, one Adam step by
+bias-corrected moments worked out by hand, and the gradient by finite
+differences of the (pinned) loss.
 """
 from __future__ import annotations
 
@@ -71,6 +73,21 @@ def grad(p, X, y):
     return np.concatenate([g[name].reshape(-1) for name, _ in SIZES])
 
 
+BETA1, BETA2, EPS = 0.9, 0.999, 1e-8
+
+
+def adam_step(p, g, m, v, t, lr):
+    """One Adam update (Kingma and Ba 2015, Algorithm 1) at step t >= 1 with
+    gradient g: moments m <- b1 m + (1 - b1) g, v <- b2 v + (1 - b2) g^2,
+    bias-corrected m^ = m / (1 - b1^t), v^ = v / (1 - b2^t), and
+    p <- p - lr m^ / (sqrt(v^) + eps).  Returns (p, m, v)."""
+    m = BETA1 * m + (1.0 - BETA1) * g
+    v = BETA2 * v + (1.0 - BETA2) * g * g
+    mhat = m / (1.0 - BETA1 ** t)
+    vhat = v / (1.0 - BETA2 ** t)
+    return p - lr * mhat / (np.sqrt(vhat) + EPS), m, v
+
+
 def adam(p, X, y, epochs, lr, m=None, v=None, step0=0):
     """`epochs` full-batch Adam steps; returns (p, m, v, loss before the last step)."""
     p = np.array(p, np.float64)
@@ -79,11 +96,5 @@ def adam(p, X, y, epochs, lr, m=None, v=None, step0=0):
     last = None
     for e in range(epochs):
         last = loss(p, X, y)
-        g = grad(p, X, y)
-        t = step0 + e + 1
-        m = 0.9 * m + 0.1 * g
-        v = 0.999 * v + 0.001 * g * g
-        mhat = m / (1.0 - 0.9 ** t)
-        vhat = v / (1.0 - 0.999 ** t)
-        p = p - lr * mhat / (np.sqrt(vhat) + 1e-8)
+        p, m, v = adam_step(p, grad(p, X, y), m, v, step0 + e + 1, lr)
     return p, m, v, last

@@ -18,6 +18,8 @@
  *                         double precision on purpose: any monotone cell
  *                         function gives the exact Def. 1 answer.
  *   - orc_join_brute    : Def. 1 by testing every (query, object) pair.
+ *   - orc_count_grid    : Def. 1 result counts per query, and optionally an
+ *                         order-independent checksum of each result set.
  *   - orc_cell / orc_morton / orc_keys : the Morton code z(i,j) of the
  *                         2^15 x 2^15 grid at l_max = 15 (Sec. 5.3 index
  *                         creation, Alg. 1 GPUcalculateMortonHash), with the
@@ -216,13 +218,27 @@ int64_t orc_join_grid(const float *pos, const uint8_t *present, uint32_t nmax,
     return (int64_t)v.n;
 }
 
-/* Per-query result counts only (Def. 1 through the same uniform grid, no id
- * list): used to check large workloads on every query while ids are checked
- * on a sample. */
+/* Order-independent checksum of one result (query q, object id): the
+ * splitmix64 output function (Steele, Lea & Flood 2014; Vigna's constants)
+ * applied to (q << 32 | id).  A query's checksum is the sum of its results'
+ * values modulo 2^64, so any permutation of a result list gives the same
+ * checksum while a missing, extra or changed id changes it. */
+static uint64_t orc_result_hash(uint32_t q, uint32_t id)
+{
+    uint64_t z = ((uint64_t)q << 32) | id;
+    z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ull;
+    z = (z ^ (z >> 27)) * 0x94d049bb133111ebull;
+    return z ^ (z >> 31);
+}
+
+/* Per-query result counts (Def. 1 through the same uniform grid, no id
+ * list) and, if hashes is not NULL, each query's checksum of its results
+ * (orc_result_hash summed over the Def. 1 result set): used to check large
+ * workloads on every query without storing their id lists. */
 int64_t orc_count_grid(const float *pos, const uint8_t *present, uint32_t nmax,
                        const float *rects, uint32_t Q,
                        double x0, double y0, double x1, double y1,
-                       double cell_side, uint64_t *counts)
+                       double cell_side, uint64_t *counts, uint64_t *hashes)
 {
     if (!(cell_side > 0.0)) cell_side = 1e-12;
     double gx = floor((x1 - x0) / cell_side), gy = floor((y1 - y0) / cell_side);
@@ -252,7 +268,7 @@ int64_t orc_count_grid(const float *pos, const uint8_t *present, uint32_t nmax,
     uint64_t total = 0;
     for (uint32_t q = 0; q < Q; ++q) {
         const float *r = rects + 4 * (size_t)q;
-        uint64_t cnt = 0;
+        uint64_t cnt = 0, h = 0;
         if (!orc_query_is_empty(r)) {
             uint32_t i0 = orc_grid_cell(r[0], x0, cwx, GX), i1 = orc_grid_cell(r[2], x0, cwx, GX);
             uint32_t j0 = orc_grid_cell(r[1], y0, cwy, GY), j1 = orc_grid_cell(r[3], y0, cwy, GY);
@@ -261,11 +277,15 @@ int64_t orc_count_grid(const float *pos, const uint8_t *present, uint32_t nmax,
                     size_t c = (size_t)cj * GX + ci;
                     for (uint64_t k = cstart[c]; k < cstart[c + 1]; ++k) {
                         uint32_t id = cell_ids[k];
-                        cnt += (uint64_t)orc_in_rect(pos[2 * (size_t)id], pos[2 * (size_t)id + 1], r);
+                        if (orc_in_rect(pos[2 * (size_t)id], pos[2 * (size_t)id + 1], r)) {
+                            cnt += 1;
+                            if (hashes) h += orc_result_hash(q, id);
+                        }
                     }
                 }
         }
         counts[q] = cnt;
+        if (hashes) hashes[q] = h;
         total += cnt;
     }
     free(cstart); free(cell_of); free(cell_ids); free(fill);
