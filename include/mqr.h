@@ -401,6 +401,21 @@ mqr_status mqr_get_leaves(mqr_ctx *ctx, uint32_t *leaves_host, uint64_t cap, uin
  * object id, for the *n present objects.  Either pointer may be NULL. */
 mqr_status mqr_get_sorted(mqr_ctx *ctx, uint32_t *keys_host, uint32_t *ids_host, uint64_t cap, uint64_t *n);
 
+/* The join's leaf footprint in the last completed tick: out_host[0] = the
+ * leaves that produced at least one result (every leaf of a covering run,
+ * Sec. 5.6, and the leaf of every intersecting subquery with a non-zero
+ * result count, Sec. 5.4), out_host[1] = the objects in those leaves,
+ * out_host[2] = the leaves with at least one intersecting subquery (the
+ * cells the filtering of Alg. 2 tests), out_host[3] = the objects in those.
+ * Decoding (Alg. 4) must read the ids of the first kind of leaf at least
+ * once, filtering the positions of the second: 4 * out_host[1] and
+ * 8 * out_host[3] bytes of the join's algorithmic traffic.
+ * out_host: uint64 host array of 4.  Computed on the device from the tick's
+ * subquery records and leaf table (valid until the next tick); a measurement,
+ * not a step of the method.  Blocks.  Errors: INVALID_ARG (NULL, no tick yet,
+ * the atomic-baseline kind), OOM, CUDA. */
+mqr_status mqr_result_footprint(mqr_ctx *ctx, uint64_t *out_host);
+
 /* Checkpoint of the object state (Sec. 2.2: the latest position of every
  * object; the index is rebuilt from it every tick, Alg. 1): xy_host (float
  * host array of 2 x max_objects, (x, y) per id) and present_host (uint8 host
@@ -421,6 +436,17 @@ mqr_status mqr_import_state(mqr_ctx *ctx, const float *xy_host, const uint8_t *p
  * out of memory (the call that needed it returns OOM, its context stays
  * usable); the hook then disarms itself.  after < 0 disarms it. */
 mqr_status mqr_debug_fail_allocation(int after);
+
+/* Test hook for the bounded device-side waits: enable != 0 arms it, and the
+ * next tick that runs the result-count scan (Sec. 5.5; any context) runs it
+ * with the status of its first tile withheld and a 1 ms wait limit, so that
+ * every later tile's look-back wait runs out: that tick returns
+ * MQR_ERR_TIMEOUT, writes no output, and leaves its context usable (the next
+ * tick is answered normally).  The hook then disarms itself; enable = 0
+ * disarms it.  The wait gives up on its own: nothing faults or hangs.  The
+ * tick needs more than one scan tile (over 2,048 subquery records) for a
+ * wait to happen. */
+mqr_status mqr_debug_stall_scan(int enable);
 
 /* Enable (1) or disable (0) per-phase timing; enabling resets the
  * accumulators.  Timing adds two event records per phase to the stream. */

@@ -6,9 +6,12 @@
 
 namespace mqr {
 
+// The tick's buffers held everything and no bounded wait of an earlier
+// kernel gave up (after a timeout the offsets may be partial sums, so the
+// kernels that write through them do nothing; the host reports the timeout).
 __device__ __forceinline__ bool tick_buffers_ok(const Info *info, const Caps &caps) {
     return info->n_sub <= caps.sub && info->n_sub_i <= caps.sub_i && info->n_words <= caps.words &&
-           info->n_items <= caps.items;
+           info->n_items <= caps.items && !(info->err & kErrTimeout);
 }
 
 // ---------------------------------------------------------------------------
@@ -149,7 +152,7 @@ void launch_filter(cudaStream_t st, int grid_blocks, const float4 *rects, const 
 __global__ void __launch_bounds__(kResThreads)
 result_scan_kernel(const uint32_t *__restrict__ sub_res, const uint32_t *__restrict__ sub_leaf,
                    unsigned long long *__restrict__ out_off, unsigned long long *status,
-                   uint32_t *tile_counter, uint32_t run_elems, Caps caps, Info *info) {
+                   uint32_t *tile_counter, uint32_t run_elems, Caps caps, Info *info, int stall_test) {
     __shared__ unsigned long long s_scan[kResThreads / 32 + 1];
     __shared__ unsigned long long s_cov, s_res;
     __shared__ uint32_t s_tile;
@@ -181,7 +184,10 @@ result_scan_kernel(const uint32_t *__restrict__ sub_res, const uint32_t *__restr
     unsigned long long total;
     unsigned long long off = block_excl_scan<kResThreads>(t, &total, s_scan);
     if (tid < 32) {
-        const unsigned long long pre = lookback_warp<unsigned long long>(status, tile, total, &info->err);
+        unsigned long long pre = 0;
+        if (!stall_test) pre = lookback_warp<unsigned long long>(status, tile, total, &info->err);
+        else if (tile > 0) pre = lookback_warp<unsigned long long>(status, tile, total, &info->err, kStallWaitNs);
+        // (stall test: tile 0 never publishes, so every later tile's wait runs out)
         if (tid == 0) s_prefix = pre;
     }
     cov = warp_sum(cov);
@@ -211,11 +217,12 @@ result_scan_kernel(const uint32_t *__restrict__ sub_res, const uint32_t *__restr
 void launch_result_scan(cudaStream_t st, unsigned long long sub_cap, const uint32_t *sub_res,
                         const uint32_t *sub_leaf, unsigned long long *out_off,
                         unsigned long long *status, uint32_t *tile_counter, uint32_t run_elems, Caps caps,
-                        Info *info) {
+                        Info *info, bool stall_test) {
     unsigned long long tiles = (sub_cap + kResTile - 1) / kResTile;
     if (tiles == 0) tiles = 1;
     result_scan_kernel<<<(unsigned)tiles, kResThreads, 0, st>>>(sub_res, sub_leaf, out_off, status,
-                                                               tile_counter, run_elems, caps, info);
+                                                               tile_counter, run_elems, caps, info,
+                                                               stall_test ? 1 : 0);
 }
 
 // ---------------------------------------------------------------------------

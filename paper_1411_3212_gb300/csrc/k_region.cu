@@ -123,4 +123,66 @@ cudaError_t launch_region_work(cudaStream_t st, int num_sms, const uint32_t *lea
     return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------------------
+// The join's leaf footprint in the last tick: a covering run marks every
+// leaf of its run as producing results; an intersecting subquery marks its
+// leaf as tested, and as producing results when its result count is
+// non-zero.  out[0] / out[1] = leaves producing results / their objects,
+// out[2] / out[3] = tested leaves / their objects.  A measurement of the
+// tick, not a step of it.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(kRegionThreads)
+footprint_mark_kernel(const uint32_t *__restrict__ sub_leaf, const uint32_t *__restrict__ sub_len,
+                      const uint32_t *__restrict__ sub_res, unsigned long long n_sub, uint32_t n_leaves,
+                      uint8_t *__restrict__ mark) {
+    const unsigned long long nthreads = (unsigned long long)gridDim.x * kRegionThreads;
+    for (unsigned long long k = (unsigned long long)blockIdx.x * kRegionThreads + threadIdx.x; k < n_sub;
+         k += nthreads) {
+        const uint32_t v = sub_leaf[k];
+        const uint32_t first = v & 0x7fffffffu;
+        if (v & 0x80000000u) {
+            const uint32_t end = min(first + sub_len[k], n_leaves);
+            for (uint32_t j = first; j < end; ++j) atomicOr(reinterpret_cast<unsigned int *>(mark + (j & ~3u)),
+                                                            1u << (8u * (j & 3u)));
+        } else if (first < n_leaves) {
+            const uint32_t bits = sub_res[k] != 0u ? 3u : 2u;
+            atomicOr(reinterpret_cast<unsigned int *>(mark + (first & ~3u)), bits << (8u * (first & 3u)));
+        }
+    }
+}
+
+__global__ void __launch_bounds__(kRegionThreads)
+footprint_sum_kernel(const uint8_t *__restrict__ mark, const uint32_t *__restrict__ leaf_beg, uint32_t n_leaves,
+                     unsigned long long *__restrict__ out) {
+    const unsigned long long nthreads = (unsigned long long)gridDim.x * kRegionThreads;
+    unsigned long long s[4] = {0, 0, 0, 0};
+    for (unsigned long long l = (unsigned long long)blockIdx.x * kRegionThreads + threadIdx.x; l < n_leaves;
+         l += nthreads) {
+        const uint32_t m = mark[l];
+        if (m) {
+            const unsigned long long n = leaf_beg[l + 1] - leaf_beg[l];
+            if (m & 1u) { s[0] += 1; s[1] += n; }
+            if (m & 2u) { s[2] += 1; s[3] += n; }
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        s[i] = warp_sum_u64(s[i]);
+        if ((threadIdx.x & 31) == 0 && s[i]) atomicAdd(out + i, s[i]);
+    }
+}
+
+cudaError_t launch_footprint(cudaStream_t st, int num_sms, const uint32_t *sub_leaf, const uint32_t *sub_len,
+                             const uint32_t *sub_res, unsigned long long n_sub, const uint32_t *leaf_beg,
+                             uint32_t n_leaves, uint8_t *mark, unsigned long long *out) {
+    // mark holds n_leaves rounded up to 4 bytes (marked with 32-bit atomics)
+    cudaError_t e = cudaMemsetAsync(out, 0, 4 * sizeof(unsigned long long), st);
+    if (e == cudaSuccess && n_leaves) e = cudaMemsetAsync(mark, 0, (n_leaves + 3u) & ~3u, st);
+    if (e != cudaSuccess) return e;
+    if (n_sub) footprint_mark_kernel<<<num_sms * 4, kRegionThreads, 0, st>>>(sub_leaf, sub_len, sub_res, n_sub,
+                                                                             n_leaves, mark);
+    if (n_leaves) footprint_sum_kernel<<<num_sms * 2, kRegionThreads, 0, st>>>(mark, leaf_beg, n_leaves, out);
+    return cudaGetLastError();
+}
+
 }  // namespace mqr

@@ -46,6 +46,9 @@ std::atomic<unsigned long long> g_buf_gen{0};
 // Fault injection (mqr_debug_fail_allocation): the number of device buffer
 // allocations still to succeed before one fails; negative: disarmed.
 std::atomic<long long> g_fail_alloc_after{-1};
+// Failure-handling test hook (mqr_debug_stall_scan): the next result scan
+// runs with a withheld look-back status and a 1 ms wait limit.
+std::atomic<bool> g_stall_scan{false};
 
 // A device buffer that only grows (contents are not preserved on growth).
 template <typename T>
@@ -146,6 +149,8 @@ struct mqr_ctx {
     uint32_t region_bits = 0;
     DevBuf<uint32_t> region_cap, region_cnt;
     DevBuf<double> region_stats;
+    DevBuf<uint8_t> fp_mark;        // mqr_result_footprint: leaf marks and the two sums
+    DevBuf<unsigned long long> fp_sum;
     DevBuf<uint8_t> state_flags;    // staging of mqr_export_state / mqr_import_state
     int last_emit_kind = -1;
     // blocks per SM of the work-item kernels (mqr_set_launch_config)
@@ -385,7 +390,7 @@ mqr_status enqueue_tick(mqr_ctx *c, const float4 *rects, uint32_t Q, int emit_ki
     phase_begin(c, MQR_PHASE_RESULT_SCAN);
     launch_result_scan(st, caps.sub, c->sub_res.p, c->sub_leaf.p, c->out_off.p,
                        at<unsigned long long>(c, a.st_res), ctr + 7, emit_kind == kEmitRuns ? 2u : 0u, caps,
-                       info);
+                       info, g_stall_scan.exchange(false));
     phase_end(c, MQR_PHASE_RESULT_SCAN, 1);
     // a12 + a13
     if (out != nullptr && emit_kind >= 0) {
@@ -454,7 +459,8 @@ mqr_status grow_sub(mqr_ctx *c, unsigned long long need) {
 mqr_status enqueue_or_replay(mqr_ctx *c, const float4 *rects, uint32_t Q, int emit_kind, void *out,
                              unsigned long long out_cap_elems, unsigned long long *offsets, const Arena &a,
                              Caps &caps) {
-    if (!c->graph_on || c->timing) return enqueue_tick(c, rects, Q, emit_kind, out, out_cap_elems, offsets, a, caps);
+    if (!c->graph_on || c->timing || g_stall_scan.load())
+        return enqueue_tick(c, rects, Q, emit_kind, out, out_cap_elems, offsets, a, caps);
     // The captured tick reads the queries from the context's own buffer, so a
     // caller that passes each tick's queries in a different buffer still
     // replays the same graph (one device-to-device copy of 16 B per query).
@@ -1031,6 +1037,8 @@ mqr_status mqr_apply_updates(mqr_ctx *c, const uint32_t *ids_dev, const float *x
     if (!c) return fail(MQR_ERR_INVALID_ARG, "ctx is NULL");
     if (n == 0) return MQR_OK;
     if (!ids_dev || !xy_dev) return fail(MQR_ERR_INVALID_ARG, "ids_dev / xy_dev is NULL");
+    if ((reinterpret_cast<uintptr_t>(xy_dev) & 7u) || (reinterpret_cast<uintptr_t>(ids_dev) & 3u))
+        return fail(MQR_ERR_INVALID_ARG, "xy_dev must be 8-byte and ids_dev 4-byte aligned");
     MQR_CUDA(cudaSetDevice(c->device));
     ++c->epoch;
     const bool timed = c->timing && (c->timing_mask & (1u << MQR_PHASE_UPDATES)) &&
@@ -1186,8 +1194,9 @@ static mqr_status tick_host_impl(mqr_ctx *c, const float *rects_host, uint32_t Q
     }
     const float *rd = reinterpret_cast<const float *>(c->q_rects.p);
     // Device staging buffer: as large as the caller's buffer allows, grown on
-    // demand (the tick's device state stays valid, so only the output is
-    // produced again after a growth).
+    // demand to the size needed plus a quarter (at most the caller's buffer),
+    // so that ticks of slowly growing output do not grow it every time; the
+    // tick is then answered again.
     size_t want = out_capacity_bytes;
     if (kind == MQR_OUT_BITMAP) want = std::min<uint64_t>(want, (uint64_t)Q * bitmap_words_per_row(c->nmax) * 4);
     if (kind == MQR_OUT_COUNT) want = 0;
@@ -1196,8 +1205,9 @@ static mqr_status tick_host_impl(mqr_ctx *c, const float *rects_host, uint32_t Q
     if (s == MQR_ERR_CAPACITY && kind != MQR_OUT_COUNT) {
         uint64_t need = kind == MQR_OUT_BITMAP ? *out_count * 4 : *out_count * out_elem_bytes(kind);
         if (need > out_capacity_bytes) return s;
-        MQR_CUDA(stage.ensure(std::max<size_t>(need, 1)));
-        s = tick_device(c, rd, Q, kind, stage.p, need, out_count, offs_dev);
+        const size_t grow = std::min<uint64_t>(need + need / 4, want);
+        MQR_CUDA(stage.ensure(std::max<size_t>(std::max<size_t>(grow, need), 1)));
+        s = tick_device(c, rd, Q, kind, stage.p, std::min<size_t>(stage.n, want), out_count, offs_dev);
     }
     if (s != MQR_OK) return s;
     uint64_t bytes = kind == MQR_OUT_BITMAP ? *out_count * 4
@@ -1344,6 +1354,29 @@ mqr_status mqr_region_work(mqr_ctx *c, const float *rects_dev, uint32_t Q, uint3
     MQR_CUDA(cudaMemcpyAsync(out_host, c->region_stats.p, kRegionStats * R * sizeof(double),
                              cudaMemcpyDeviceToHost, c->stream));
     MQR_CUDA(cudaStreamSynchronize(c->stream));
+    return MQR_OK;
+}
+
+mqr_status mqr_result_footprint(mqr_ctx *c, uint64_t *out_host) {
+    if (!c || !out_host) return fail(MQR_ERR_INVALID_ARG, "NULL argument");
+    if (!c->have_tick) return fail(MQR_ERR_INVALID_ARG, "no tick has completed yet");
+    if (c->last_emit_kind == kEmitAtomic)
+        return fail(MQR_ERR_INVALID_ARG, "the last tick used the atomic baseline (no per-subquery counts)");
+    MQR_CUDA(cudaSetDevice(c->device));
+    const uint32_t L = (uint32_t)c->last.n_leaves;
+    MQR_CUDA(c->fp_mark.ensure(std::max<size_t>(((size_t)L + 3) & ~(size_t)3, 4)));
+    MQR_CUDA(c->fp_sum.ensure(4));
+    MQR_CUDA(launch_footprint(c->stream, c->num_sms, c->sub_leaf.p, c->sub_len.p, c->sub_res.p, c->last.n_sub,
+                              c->leaf_beg.p, L, c->fp_mark.p, c->fp_sum.p));
+    unsigned long long h[4] = {0, 0, 0, 0};
+    MQR_CUDA(cudaMemcpyAsync(h, c->fp_sum.p, sizeof(h), cudaMemcpyDeviceToHost, c->stream));
+    MQR_CUDA(cudaStreamSynchronize(c->stream));
+    for (int i = 0; i < 4; ++i) out_host[i] = h[i];
+    return MQR_OK;
+}
+
+mqr_status mqr_debug_stall_scan(int enable) {
+    g_stall_scan.store(enable != 0);
     return MQR_OK;
 }
 

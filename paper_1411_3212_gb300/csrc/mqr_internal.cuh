@@ -224,7 +224,8 @@ __device__ __forceinline__ void status_store(unsigned long long *p, unsigned lon
 // lane), and returns (to every lane) the exclusive prefix of all earlier
 // tiles, then publishes the inclusive prefix.
 template <typename T>
-__device__ T lookback_warp(T *status, uint32_t tile, T agg, unsigned long long *err) {
+__device__ T lookback_warp(T *status, uint32_t tile, T agg, unsigned long long *err,
+                           unsigned long long wait_ns = kWaitNs) {
     using B = StatusBits<T>;
     const int lane = threadIdx.x & 31;
     if (tile == 0) {
@@ -249,7 +250,7 @@ __device__ T lookback_warp(T *status, uint32_t tile, T agg, unsigned long long *
                 if (lane == 0) {
                     unsigned long long now = global_ns();
                     if (t0 == 0) t0 = now;
-                    else if (now - t0 > kWaitNs) expired = true;
+                    else if (now - t0 > wait_ns) expired = true;
                 }
                 expired = __shfl_sync(0xffffffffu, expired, 0);
                 if (expired) break;
@@ -365,6 +366,12 @@ cudaError_t launch_region_work(cudaStream_t st, int num_sms, const uint32_t *lea
                                uint32_t n_leaves, const uint32_t *sub_leaf, const uint32_t *sub_len,
                                const uint32_t *sub_res, unsigned long long n_sub, const float4 *rects, uint32_t Q,
                                float x0, float y0, float sx, float sy, uint32_t region_bits, double *out);
+// The last tick's leaf footprint: leaves producing results and their objects
+// (out[0], out[1]), tested leaves and their objects (out[2], out[3]); mark
+// holds (n_leaves + 3) & ~3 bytes.
+cudaError_t launch_footprint(cudaStream_t st, int num_sms, const uint32_t *sub_leaf, const uint32_t *sub_len,
+                             const uint32_t *sub_res, unsigned long long n_sub, const uint32_t *leaf_beg,
+                             uint32_t n_leaves, uint8_t *mark, unsigned long long *out);
 cudaError_t launch_region_counts(cudaStream_t st, const uint32_t *skey, uint32_t n, uint32_t region_bits,
                                  uint32_t *counts);
 void launch_build_leaves(cudaStream_t st, const uint32_t *skey, uint32_t nmax, uint32_t cap,
@@ -425,10 +432,15 @@ void launch_filter(cudaStream_t st, int grid_blocks, const float4 *rects, const 
                    uint32_t *sub_res, uint32_t *bitmap, uint32_t *ticket, Caps caps, const Info *info);
 
 // a11: result offsets out_off[k] (u64, exclusive) over subquery records.
+// stall_test: the failure-handling test hook (mqr_debug_stall_scan): tile 0
+// withholds its look-back status and the other tiles wait kStallWaitNs only,
+// so their bounded waits run out and the tick reports a timeout.
 constexpr int kResThreads = 256, kResItems = 8, kResTile = kResThreads * kResItems;
+constexpr unsigned long long kStallWaitNs = 1000000ull;   // 1 ms
 void launch_result_scan(cudaStream_t st, unsigned long long sub_cap, const uint32_t *sub_res,
                         const uint32_t *sub_leaf, unsigned long long *out_off,
-                        unsigned long long *status, uint32_t *tile_counter, uint32_t run_elems, Caps caps, Info *info);
+                        unsigned long long *status, uint32_t *tile_counter, uint32_t run_elems, Caps caps, Info *info,
+                        bool stall_test = false);
 
 // a12 + a13: emit results in query-major order.
 enum EmitKind { kEmitPairs = 0, kEmitIds = 1, kEmitBitmap = 2, kEmitKeys64 = 3, kEmitRuns = 4,

@@ -106,6 +106,9 @@ extern "C" mqr_status mqr_sort_objects_noalloc(mqr_rect bounds, const float *xy_
         return nfail(MQR_ERR_INVALID_ARG, "xy_dev / keys_out_dev / ids_out_dev is NULL");
     if (!(bounds.xmax > bounds.xmin) || !(bounds.ymax > bounds.ymin))
         return nfail(MQR_ERR_INVALID_ARG, "bounds must have xmax > xmin and ymax > ymin");
+    if (n > 0 && ((reinterpret_cast<uintptr_t>(xy_dev) & 7u) ||
+                  ((reinterpret_cast<uintptr_t>(keys_out_dev) | reinterpret_cast<uintptr_t>(ids_out_dev)) & 3u)))
+        return nfail(MQR_ERR_INVALID_ARG, "xy_dev must be 8-byte and keys_out_dev / ids_out_dev 4-byte aligned");
     if (n == 0) return MQR_OK;
     unsigned char *s = nullptr;
     mqr_status st = scratch_ptr(&s);

@@ -34,7 +34,8 @@ EXPORTS = ["mqr_config_default", "mqr_create", "mqr_create_ex", "mqr_apply_updat
            "mqr_cost_set_params", "mqr_cost_get_params", "mqr_cost_train", "mqr_cost_gradient", "mqr_cost_predict",
            "mqr_cost_destroy", "mqr_get_stats",
            "mqr_get_leaves",
-           "mqr_get_sorted", "mqr_export_state", "mqr_import_state", "mqr_debug_fail_allocation",
+           "mqr_get_sorted", "mqr_result_footprint", "mqr_export_state", "mqr_import_state",
+           "mqr_debug_fail_allocation", "mqr_debug_stall_scan",
            "mqr_set_timing", "mqr_set_timing_phases", "mqr_get_timing",
            "mqr_sort_objects_noalloc",
            "mqr_last_error", "mqr_destroy"]
@@ -136,6 +137,8 @@ def load(path: str = LIB_PATH):
         "mqr_export_state": ([P, P, P, u32], i32),
         "mqr_import_state": ([P, P, P, u32], i32),
         "mqr_debug_fail_allocation": ([i32], i32),
+        "mqr_debug_stall_scan": ([i32], i32),
+        "mqr_result_footprint": ([P, P], i32),
         "mqr_get_timing": ([P, ctypes.POINTER(mqr_timing)], i32),
         "mqr_sort_objects_noalloc": ([mqr_rect, P, u32, P, P, P], i32),
         "mqr_last_error": ([], ctypes.c_char_p),
@@ -415,6 +418,19 @@ def mqr_debug_fail_allocation(after):
     _check(load().mqr_debug_fail_allocation(int(after)))
 
 
+def mqr_debug_stall_scan(enable=True):
+    _check(load().mqr_debug_stall_scan(1 if enable else 0))
+
+
+def mqr_result_footprint(ctx):
+    """-> dict of the last tick's leaf footprint: leaves with results and
+    their objects, tested leaves and their objects."""
+    out = np.zeros(4, np.uint64)
+    _check(load().mqr_result_footprint(ctx, out.ctypes.data))
+    return {"result_leaves": int(out[0]), "result_leaf_objects": int(out[1]),
+            "tested_leaves": int(out[2]), "tested_leaf_objects": int(out[3])}
+
+
 def mqr_set_timing_phases(ctx, phases):
     """Time only the named phases (launch counts for all); empty: off."""
     mask = 0
@@ -534,6 +550,9 @@ class Index:
 
     def set_query_worlds(self, q_base):
         mqr_set_query_worlds(self.ctx, q_base)
+
+    def footprint(self):
+        return mqr_result_footprint(self.ctx)
 
     def stats(self):
         return mqr_get_stats(self.ctx)

@@ -95,3 +95,21 @@ def test_new_entry_points_reject_bad_arguments_without_a_gpu(lib):
         mqr.mqr_import_state(None, np.zeros((10, 2), np.float32), np.zeros(9, np.uint8))
     with pytest.raises(mqr.MqrError):
         mqr.mqr_set_launch_config(None, filter=8)
+
+
+def test_noalloc_rejects_misaligned_pointers_before_any_cuda_call(lib):
+    """The allocation-free sort reads float2 positions and writes uint32
+    keys and ids: pointers that are not 8- / 4-byte aligned are refused with
+    INVALID_ARG before anything is launched (these fake addresses are never
+    dereferenced)."""
+    from paper_1411_3212_gb300 import mqr
+    b = mqr.mqr_rect(0.0, 0.0, 1.0, 1.0)
+    assert lib.mqr_sort_objects_noalloc(b, 0x10004, 10, 0x20000, 0x30000, None) == mqr.MQR_ERR_INVALID_ARG
+    assert "aligned" in mqr.mqr_last_error()
+    assert lib.mqr_sort_objects_noalloc(b, 0x10000, 10, 0x20002, 0x30000, None) == mqr.MQR_ERR_INVALID_ARG
+    assert lib.mqr_sort_objects_noalloc(b, 0x10000, 10, 0x20000, 0x30001, None) == mqr.MQR_ERR_INVALID_ARG
+    assert lib.mqr_sort_objects_noalloc(b, 0x10000, mqr.MQR_NOALLOC_MAX_OBJECTS + 1, 0x20000, 0x30000,
+                                        None) == mqr.MQR_ERR_INVALID_ARG
+    assert lib.mqr_debug_stall_scan(0) == mqr.MQR_OK
+    fp = (ctypes.c_uint64 * 4)()
+    assert lib.mqr_result_footprint(None, fp) == mqr.MQR_ERR_INVALID_ARG

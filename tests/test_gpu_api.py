@@ -395,3 +395,48 @@ def test_async_runs_with_async_sorted_ids():
             assert_same_csr((o, ids), (woff, wids))
     finally:
         mqr.mqr_destroy(ctx)
+
+
+def test_result_footprint_against_the_oracle(case):
+    """mqr_result_footprint: the leaves holding at least one result object and
+    the leaves with at least one intersecting subquery, with their objects,
+    from the oracle's Alg. 1 leaves, g(q) and Def. 1 result sets."""
+    torch, dev = torch_dev()
+    t, want = case
+    from paper_1411_3212_gb300 import mqr
+    cap = 32
+    mqr_, idx = mk(30000, cap)
+    idx.apply_updates(to_dev(t.ids, dev), to_dev(t.xy, dev))
+    idx.tick(to_dev(t.rects, dev), kind="pairs")
+    fp = idx.footprint()
+    st = oracle_state(30000, [(t.ids, t.xy)])
+    k = oracle.keys(st)
+    order = np.argsort(k, kind="stable")
+    leaves = oracle.quadtree(k[order], cap)
+    pos = np.empty(30000, np.int64)
+    pos[order] = np.arange(30000)
+    size = (leaves["end"] - leaves["begin"]).astype(np.int64)
+    res_leaf = np.zeros(len(leaves), bool)
+    hit = np.searchsorted(leaves["begin"], pos[want[1]], side="right") - 1
+    res_leaf[hit] = True
+    tested = np.zeros(len(leaves), bool)
+    for q in range(t.rects.shape[0]):
+        lv, cov = oracle.subqueries(leaves, t.rects[q])
+        tested[lv[cov == 0]] = True
+    assert fp == {"result_leaves": int(res_leaf.sum()), "result_leaf_objects": int(size[res_leaf].sum()),
+                  "tested_leaves": int(tested.sum()), "tested_leaf_objects": int(size[tested].sum())}
+    idx.close()
+
+
+def test_misaligned_update_arrays_rejected(case):
+    torch, dev = torch_dev()
+    t, want = case
+    from paper_1411_3212_gb300 import mqr
+    mqr_, idx = mk(30000)
+    ids = to_dev(t.ids, dev)
+    xy = torch.zeros(2 * 30000 + 2, dtype=torch.float32, device=dev)
+    with pytest.raises(mqr.MqrError, match="aligned"):
+        mqr.mqr_apply_updates(idx.ctx, ids, xy.data_ptr() + 4, 30000)
+    with pytest.raises(mqr.MqrError, match="aligned"):
+        mqr.mqr_apply_updates(idx.ctx, ids.data_ptr() + 2, xy, 30000)
+    idx.close()

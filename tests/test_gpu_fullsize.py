@@ -8,14 +8,56 @@ compared with the oracle's, and the complete id lists of a random sample of
 queries are compared exactly; covering-compressed outputs must give the same
 counts.
 """
+import multiprocessing
+from concurrent.futures import ProcessPoolExecutor
+
 import numpy as np
 import pytest
 
 import oracle
 from paper_1411_3212_gb300 import workloads
 from tests.gpu_util import to_dev, torch_dev
+from tests.result_hash import per_query_hash
 
 pytestmark = pytest.mark.gpu
+
+
+def _oracle_counts_and_hashes(n, ids, xy, rects):
+    """One tick of the oracle in a worker process: every query's Def. 1
+    result count and checksum (cell 0.002)."""
+    st = oracle.State(n)
+    st.apply_updates(ids, xy)
+    return oracle.count_grid(st, rects, cell_side=0.002, with_hash=True)
+
+
+def test_hotspot_4m_every_query_checksum_five_ticks():
+    """Ticks 1-5 of hotspot-4M at the bench's launch configuration (leaf_cap
+    128, quadtree, pair-list output): every query's result count and its
+    order-independent checksum of (query, id) equal the oracle's, so every
+    query's complete id set is compared.  The oracle's ticks run in spawned
+    worker processes while the GPU answers."""
+    torch, dev = torch_dev()
+    from paper_1411_3212_gb300 import mqr
+    w = workloads.HotspotWalk(n=4_000_000, q=400_000, seed=0)
+    ticks = [w.next_tick() for _ in range(5)]
+    with ProcessPoolExecutor(max_workers=5, mp_context=multiprocessing.get_context("spawn")) as pool:
+        futs = [pool.submit(_oracle_counts_and_hashes, w.n, t.ids, t.xy, t.rects) for t in ticks]
+        idx = mqr.Index(bounds=(0.0, 0.0, 1.0, 1.0), leaf_cap=128, max_objects=w.n)
+        got = []
+        for t in ticks:
+            idx.apply_updates(to_dev(t.ids, dev), to_dev(t.xy, dev))
+            pairs, offs = idx.tick(to_dev(t.rects, dev), kind="pairs")
+            off = offs.cpu().numpy().view(np.uint64)
+            p = pairs[: int(off[-1])].cpu().numpy().view(np.uint32)
+            assert np.all(np.diff(p[:, 0].astype(np.int64)) >= 0)          # grouped by ascending query
+            got.append((np.diff(off.astype(np.int64)), per_query_hash(p, off)))
+            del pairs, p
+        idx.close()
+        for k, (f, (cnt, hs)) in enumerate(zip(futs, got)):
+            want_cnt, want_hs = f.result()
+            np.testing.assert_array_equal(cnt, want_cnt.astype(np.int64), err_msg="tick %d counts" % (k + 1))
+            bad = np.nonzero(hs != want_hs)[0]
+            assert bad.size == 0, "tick %d: %d queries' id sets differ, first %d" % (k + 1, bad.size, bad[:1])
 
 
 def test_hotspot_4m_full_size_counts_and_sampled_lists():

@@ -86,3 +86,47 @@ def test_injected_allocation_failure_is_reported_and_recoverable(disarm_hook):
     assert_same_csr(gpu_csr_sorted(idx, big, dev), oracle.join_grid(st, big, cell_side=0.02), "after OOM")
     assert_same_csr(gpu_csr_sorted(idx, small, dev), oracle.join_grid(st, small, cell_side=0.01), "small again")
     idx.close()
+
+
+@pytest.fixture
+def disarm_stall():
+    yield
+    from paper_1411_3212_gb300 import mqr
+    mqr.mqr_debug_stall_scan(False)                # never leave the hook armed for other tests
+
+
+def test_bounded_wait_times_out_and_the_context_recovers(disarm_stall):
+    """The result-count scan's look-back waits are bounded: with the test hook
+    armed, the scan's first tile withholds its status and the other tiles'
+    waits give up after 1 ms; the tick reports MQR_ERR_TIMEOUT and writes no
+    output, and the following ticks are exact (the hook disarms itself)."""
+    import time
+    torch, dev = torch_dev()
+    from paper_1411_3212_gb300 import mqr
+    n, Q = 40_000, 8_000
+    rng = np.random.default_rng(17)
+    xy = rng.random((n, 2)).astype(np.float32)
+    ids = np.arange(n, dtype=np.uint32)
+    rects = workloads.squares_around(xy[rng.integers(0, n, Q)], 0.02)
+    st = oracle_state(n, [(ids, xy)])
+    want = oracle.join_grid(st, rects, cell_side=0.02)
+    idx = mqr.Index(bounds=(0.0, 0.0, 1.0, 1.0), leaf_cap=32, max_objects=n)
+    idx.apply_updates(to_dev(ids, dev), to_dev(xy, dev))
+    assert_same_csr(gpu_csr_sorted(idx, rects, dev), want, "before")
+    s = idx.stats()
+    assert s["n_sub_intersecting"] + s["n_covering_runs"] > 4 * 2048      # several scan tiles wait
+    rects_d = to_dev(rects, dev)
+    out = torch.full((2 * int(want[0][-1]) + 2048,), -1, dtype=torch.int32, device=dev)
+    mqr.mqr_debug_stall_scan(True)
+    t0 = time.perf_counter()
+    status, _ = mqr.mqr_tick(idx.ctx, rects_d, Q, mqr.MQR_OUT_PAIRS, out, out.numel() * 4, check=False)
+    dt = time.perf_counter() - t0
+    assert status == mqr.MQR_ERR_TIMEOUT, mqr.mqr_last_error()
+    assert "deadline" in mqr.mqr_last_error()
+    assert dt < 1.0                                 # the 1 ms test limit, not the 2 s one
+    assert bool((out == -1).all().item())           # the emit wrote nothing after the timeout
+    # the hook disarmed itself and the context answers exactly again
+    assert_same_csr(gpu_csr_sorted(idx, rects, dev), want, "after the timeout")
+    status, cnt = mqr.mqr_tick(idx.ctx, rects_d, Q, mqr.MQR_OUT_PAIRS, out, out.numel() * 4)
+    assert status == mqr.MQR_OK and cnt == int(want[0][-1])
+    idx.close()
