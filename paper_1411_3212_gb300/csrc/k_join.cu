@@ -264,6 +264,29 @@ __device__ __forceinline__ void emit_rel(void *out, unsigned long long base, uin
     }
 }
 
+// Address (as an integer) of output element pos, for the kinds written by
+// position; the bitmap kind is written by (query, id) and ignores it.
+template <int KIND>
+__device__ __forceinline__ unsigned long long out_elem_addr(void *out, unsigned long long pos) {
+    const size_t eb = (KIND == kEmitIds) ? 4u : 8u;
+    return reinterpret_cast<unsigned long long>(out) + pos * eb;
+}
+
+// Write result (q, id) at element rel after the element at address base.
+template <int KIND>
+__device__ __forceinline__ void emit_at(unsigned long long base, uint32_t rel, uint32_t q, uint32_t id, void *out,
+                                        uint32_t wpr) {
+    if (KIND == kEmitPairs || KIND == kEmitRuns) {
+        reinterpret_cast<uint2 *>(base)[rel] = make_uint2(q, id);
+    } else if (KIND == kEmitIds) {
+        reinterpret_cast<uint32_t *>(base)[rel] = id;
+    } else if (KIND == kEmitBitmap) {
+        atomicOr(reinterpret_cast<uint32_t *>(out) + (size_t)q * wpr + (id >> 5), 1u << (id & 31u));
+    } else {
+        reinterpret_cast<unsigned long long *>(base)[rel] = ((unsigned long long)q << 32) | id;
+    }
+}
+
 constexpr int kEmitThreads = 256;
 constexpr int kEmitWarps = kEmitThreads / 32;
 constexpr int kRunSteps = 2;      // strided warp steps issued together in a covering run
@@ -350,14 +373,24 @@ __device__ __forceinline__ uint32_t emit_words(void *out, unsigned long long off
     return run;
 }
 
+// Intersecting records of at most kUnitMaxWords bitmap words (leaves of at
+// most 256 objects) are decoded word-parallel: every word of the batch's such
+// records is a "unit"; a round of 32 units is set up lane-parallel (lane l:
+// the word of unit l, its record, and its output position from a segmented
+// scan of the words' popcounts), then the warp writes the round's units one
+// after another (Alg. 4: lane i writes the result of bit i, coalesced), so
+// the per-record bookkeeping is paid once per 32 words instead of once per
+// record, and only the ids of set bits are loaded.
+constexpr uint32_t kUnitMaxWords = 8;
+constexpr int kUnitUnroll = 2;            // units whose id loads are issued together
+
 // One warp per batch of 32 consecutive subquery records (query-major order,
 // so the output is written front to back): lane j loads the metadata of
-// record j into the warp's shared-memory slots, then the warp handles the
-// records one by one, reading each record's metadata with broadcast loads.
-// Intersecting records are decoded two words at a time.  The kernel is held
-// to 32 registers so that 64 warps per SM hide the load latency.
+// record j into the warp's shared-memory slots; the batch's small
+// intersecting records are decoded as units (above), then its covering runs
+// and larger intersecting records one by one, with broadcast metadata.
 template <int KIND>
-__global__ void __launch_bounds__(kEmitThreads, 8)
+__global__ void __launch_bounds__(kEmitThreads, 6)
 emit_kernel(const uint32_t *__restrict__ sub_q, const uint32_t *__restrict__ sub_leaf,
             const uint32_t *__restrict__ sub_len, const uint32_t *__restrict__ leaf_word_off,
             const unsigned long long *__restrict__ out_off, const uint32_t *__restrict__ leaf_beg,
@@ -366,6 +399,11 @@ emit_kernel(const uint32_t *__restrict__ sub_q, const uint32_t *__restrict__ sub
     // per record: {q, bitmap row, first sorted object, objects | covering flag} and its output offset
     __shared__ uint4 s_rec[kEmitWarps][32];
     __shared__ unsigned long long s_off[kEmitWarps][32];
+    // per unit of the batch: record (low 5 bits) and word of the record (high 3 bits)
+    __shared__ uint8_t s_map[kEmitWarps][32 * kUnitMaxWords];
+    // per unit of a round: {word, first object of the word, q} and the address of its first output element
+    __shared__ uint4 s_unit[kEmitWarps][32];
+    __shared__ unsigned long long s_uptr[kEmitWarps][32];
     if (!tick_buffers_ok(info, caps)) return;
     uint32_t nsub = (uint32_t)info->n_sub;
     if (info->emit_end) nsub = min(nsub, (uint32_t)info->emit_end);     // admitted prefix only
@@ -382,6 +420,8 @@ emit_kernel(const uint32_t *__restrict__ sub_q, const uint32_t *__restrict__ sub
     for (; batch < nbatch; batch = __shfl_sync(0xffffffffu, next, 0)) {
         if (lane == 0) next = atomicAdd(ticket, 1u);
         const uint32_t k = batch * 32u + lane;
+        uint32_t nw = 0;
+        bool rest = false;
         if (k < nsub) {
             const uint32_t sl = __ldg(sub_leaf + k);
             const uint32_t first = sl & 0x7fffffffu;
@@ -390,13 +430,68 @@ emit_kernel(const uint32_t *__restrict__ sub_q, const uint32_t *__restrict__ sub
             const uint32_t len = cov ? lr : 1u;
             const uint32_t b = __ldg(leaf_beg + first);
             const uint32_t e = __ldg(leaf_beg + first + len);
-            const uint32_t row = cov ? 0u : __ldg(leaf_word_off + first) + lr * ((e - b + 31u) >> 5);
+            const uint32_t wl = (e - b + 31u) >> 5;
+            const uint32_t row = cov ? 0u : __ldg(leaf_word_off + first) + lr * wl;
             s_rec[wib][lane] = make_uint4(__ldg(sub_q + k), row, b, (e - b) | (cov ? 0x80000000u : 0u));
             s_off[wib][lane] = __ldg(out_off + k);
+            if (!cov && wl <= kUnitMaxWords) nw = wl;
+            else rest = true;
         }
+        // the batch's units: record j owns units [base, base + nw)
+        const uint32_t incl = warp_incl_scan(nw);
+        const uint32_t base = incl - nw;
+        const uint32_t nunits = __shfl_sync(0xffffffffu, incl, 31);
+        for (uint32_t i = 0; i < nw; ++i) s_map[wib][base + i] = (uint8_t)(lane | (i << 5));
         __syncwarp();
-        const uint32_t nrec = min(32u, nsub - batch * 32u);
-        for (uint32_t j = 0; j < nrec; ++j) {
+        // hits of the record continuing from the previous round, and that record
+        uint32_t carry = 0, carry_r = 0xffffffffu;
+        for (uint32_t u0 = 0; u0 < nunits; u0 += 32) {
+            const uint32_t u = u0 + lane;
+            const bool have = u < nunits;
+            uint32_t r = 32u, w = 0u;
+            uint4 unit = make_uint4(0u, 0u, 0u, 0u);      // lanes past the last unit: an empty word
+            if (have) {
+                const uint32_t m = s_map[wib][u];
+                r = m & 31u;
+                const uint4 rec = s_rec[wib][r];
+                const uint32_t wi = m >> 5;
+                w = __ldg(bitmap + rec.y + wi);
+                unit = make_uint4(w, rec.z + 32u * wi, rec.x, 0u);
+            }
+            // segmented inclusive scan of the popcounts over units of one record
+            // (a record's units are consecutive): key r in the high half
+            const uint32_t c = __popc(w);
+            uint32_t v = (r << 16) | c;
+#pragma unroll
+            for (int d = 1; d < 32; d <<= 1) {
+                const uint32_t y = __shfl_up_sync(0xffffffffu, v, d);
+                if (lane >= d && (y >> 16) == (v >> 16)) v += y & 0xffffu;
+            }
+            const uint32_t incl_c = (v & 0xffffu) + (r == carry_r ? carry : 0u);
+            s_unit[wib][lane] = unit;
+            if (have) s_uptr[wib][lane] = out_elem_addr<KIND>(out, s_off[wib][r] + (incl_c - c));
+            carry = __shfl_sync(0xffffffffu, incl_c, 31);
+            carry_r = __shfl_sync(0xffffffffu, r, 31);
+            __syncwarp();
+            const uint32_t nun = min(32u, nunits - u0);
+            for (uint32_t t0 = 0; t0 < nun; t0 += kUnitUnroll) {
+                uint32_t id[kUnitUnroll];
+                uint4 ut[kUnitUnroll];
+#pragma unroll
+                for (int t = 0; t < kUnitUnroll; ++t) {      // slots past nun hold empty words
+                    ut[t] = s_unit[wib][(t0 + t) & 31u];
+                    if (ut[t].x & (1u << lane)) id[t] = __ldg(sid + ut[t].y + lane);
+                }
+#pragma unroll
+                for (int t = 0; t < kUnitUnroll; ++t)
+                    if (ut[t].x & (1u << lane))
+                        emit_at<KIND>(s_uptr[wib][(t0 + t) & 31u], __popc(ut[t].x & lt), ut[t].z, id[t], out, wpr);
+            }
+            __syncwarp();
+        }
+        // covering runs and intersecting records of larger leaves, one by one
+        for (uint32_t rm = __ballot_sync(0xffffffffu, rest); rm; rm &= rm - 1u) {
+            const uint32_t j = __ffs(rm) - 1;
             const uint4 r = s_rec[wib][j];
             const unsigned long long offj = s_off[wib][j];
             const uint32_t n = r.w & 0x7fffffffu;
@@ -404,10 +499,10 @@ emit_kernel(const uint32_t *__restrict__ sub_q, const uint32_t *__restrict__ sub
                 emit_run<KIND>(out, offj, r.x, sid, r.z, n, wpr, lane);
                 continue;
             }
-            const uint32_t nw = (n + 31u) >> 5;
+            const uint32_t nwr = (n + 31u) >> 5;
             uint32_t run = 0;
-            for (uint32_t w0 = 0; w0 < nw; w0 += 2) {
-                const uint32_t cnt = min(2u, nw - w0);
+            for (uint32_t w0 = 0; w0 < nwr; w0 += 2) {
+                const uint32_t cnt = min(2u, nwr - w0);
                 const uint32_t myw = (uint32_t)lane < cnt ? __ldg(bitmap + r.y + w0 + lane) : 0u;
                 const uint32_t *ids = sid + r.z + w0 * 32u;
                 const uint32_t nv = n - w0 * 32u;
