@@ -643,7 +643,7 @@ def run_served(args):
     percentiles and beta (answered queries per second of processing)."""
     import torch
     from paper_1411_3212_gb300 import mqr, workloads
-    from paper_1411_3212_gb300.serve import GpuBackend, TickServer
+    from paper_1411_3212_gb300.serve import GpuBackend, PlainBackend, SlotBackend, TickServer
     dev = torch.device("cuda", 0)
     torch.cuda.set_device(dev)
     dt = args.dt_ms / 1000.0
@@ -672,33 +672,61 @@ def run_served(args):
     ids_d = torch.from_numpy(ticks[0].ids.view(np.int32)).to(dev)
     updates = [(ids_d, torch.from_numpy(t.xy).to(dev)) for t in ticks]
     rects_d = torch.from_numpy(rects).to(dev)
-    idx = mqr.Index(bounds=(0.0, 0.0, 1.0, 1.0), leaf_cap=128, max_objects=world.n)
-    be = GpuBackend(idx, updates, rects_d, kind="runs", budget_bytes=args.budget_mb << 20,
-                    copy_out=not args.no_copy_out, overlap=not args.served_plain)
     max_batch = int(args.max_batch_factor * args.rate * dt) if args.max_batch_factor > 0 else None
-    warm = TickServer(be, dt, max_batch=max_batch).run(arrivals[arrivals < 3 * dt], n_ticks=3)   # warm-up
-    clocks = Clocks(0)
-    clocks.start()
-    rep = TickServer(be, dt, max_batch=max_batch).run(arrivals, n_ticks=args.served_ticks,
-                                                      drain_ticks=args.served_ticks)
-    clk = clocks.stop()
-    idx.close()
-    per = rep.pop("per_tick")
-    line = {"metric": "served queries/s (beta, Lemma 2)", "value": rep["beta_queries_per_s"],
+    budget = args.budget_mb << 20
+
+    def serve(make_backend):
+        """One served run on the arrivals above: 3 warm-up ticks, then the
+        stream; a fresh context per run."""
+        idx = mqr.Index(bounds=(0.0, 0.0, 1.0, 1.0), leaf_cap=128, max_objects=world.n)
+        be = make_backend(idx)
+        TickServer(be, dt, max_batch=max_batch).run(arrivals[arrivals < 3 * dt], n_ticks=3)   # warm-up
+        clocks = Clocks(0)
+        clocks.start()
+        rep = TickServer(be, dt, max_batch=max_batch).run(arrivals, n_ticks=args.served_ticks,
+                                                          drain_ticks=args.served_ticks)
+        rep["clocks"] = clocks.stop()
+        per = rep.pop("per_tick")
+        rep["max_out_elems_per_tick"] = max((t.get("out_elems", 0) for t in per), default=0)
+        if hasattr(be, "close"):
+            be.close()
+        idx.close()
+        return rep
+
+    copy_out = not args.no_copy_out
+    modes = [m for m in args.served_modes.split(",") if m]
+    reps = {}
+    for m in modes:
+        if m == "slots":
+            reps[m] = serve(lambda idx: SlotBackend(idx, updates, rects_d, kind="runs", budget_bytes=budget,
+                                                    copy_out=copy_out, n_slots=args.served_slots))
+        elif m == "admit":
+            reps[m] = serve(lambda idx: GpuBackend(idx, updates, rects_d, kind="runs", budget_bytes=budget,
+                                                   copy_out=copy_out, overlap=not args.served_plain))
+        elif m == "plain":
+            reps[m] = serve(lambda idx: PlainBackend(idx, updates, rects_d, kind="runs", copy_out=copy_out))
+        else:
+            raise SystemExit("unknown served mode %r" % m)
+        log("served %s: %s" % (m, json.dumps({k: reps[m][k] for k in ("tick_latency_ms", "beta_queries_per_s")})))
+    head = reps[modes[0]]
+    desc = {"slots": "continuous batching on %d join slots against one snapshot per tick (mqr_snapshot, "
+                     "mqr_slot_begin / mqr_slot_end), each slot admitted against %d MB / %d of output"
+                     % (args.served_slots, args.budget_mb, args.served_slots),
+            "admit": "one admitted batch per tick (mqr_tick_admit, %d MB of output), copies overlapping the next "
+                     "tick" % args.budget_mb,
+            "plain": "the plain fixed-capacity quadtree: one blocking mqr_tick per tick on the whole batch, the "
+                     "copy waited for"}
+    line = {"metric": "served queries/s (beta, Lemma 2)", "value": head["beta_queries_per_s"],
             "unit": "queries/s", "n_gpus": 1, "higher_is_better": True, "dtype": "f32", "data": "synthetic",
             "config": {"workload": "served-10M: %d objects (95%% in 16 Gaussian hotspots, sigma 0.005; 5%% "
                                    "uniform), Poisson arrivals %.3g queries/s, square sides log-uniform "
-                                   "0.0005-0.004, ticks of %.1f ms, leaf_cap 128, covering-compressed output, "
-                                   "admission by %d MB of output per tick, %s%s"
-                                   % (world.n, args.rate, args.dt_ms, args.budget_mb,
+                                   "0.0005-0.004, ticks of %.1f ms, leaf_cap 128, covering-compressed output, %s"
+                                   % (world.n, args.rate, args.dt_ms,
                                       "output kept on the device" if args.no_copy_out
-                                      else "output copied to pinned host memory",
-                                      "; plain form: each tick's copy waited for before the next tick"
-                                      if args.served_plain else "; copies overlap the next tick"),
-                       "ticks": args.served_ticks, "max_batch": max_batch},
-            "served": rep, "warmup_ticks": warm["ticks"],
-            "max_out_elems_per_tick": max((t.get("out_elems", 0) for t in per), default=0),
-            "clocks": clk}
+                                      else "output copied to pinned host memory"),
+                       "ticks": args.served_ticks, "max_batch": max_batch, "mode": modes[0],
+                       "modes": {m: desc[m] for m in modes}},
+            "served": head, "by_mode": reps}
     print(json.dumps(line), flush=True)
 
 
@@ -960,6 +988,9 @@ def main():
     ap.add_argument("--served-ticks", type=int, default=100)
     ap.add_argument("--served-objects", type=int, default=10_000_000)
     ap.add_argument("--budget-mb", type=int, default=1024, help="served: output memory per tick")
+    ap.add_argument("--served-modes", default="slots,admit,plain",
+                    help="served: backends run on the same arrivals (slots, admit, plain); the first is the headline")
+    ap.add_argument("--served-slots", type=int, default=2, help="served: join slots of the slots mode")
     ap.add_argument("--served-plain", action="store_true",
                     help="served: the plain form, no overlap of a tick's copy with the next tick")
     ap.add_argument("--max-batch-factor", type=float, default=1.5,

@@ -260,6 +260,55 @@ mqr_status mqr_tick_admit(mqr_ctx *ctx, const float *rects_dev, uint32_t Q, int 
                           uint64_t out_capacity_bytes, uint32_t *admitted, uint64_t *out_count,
                           uint64_t *offsets_dev);
 
+/* Join slots: continuous batching of query batches against one snapshot of
+ * the object state (the served-stream model of Sec. 2.4, Def. 2-3 and
+ * Lemmas 1-2: batches that arrive while others are on the GPU start at once
+ * and their work overlaps on the device; the timeslice semantics of Sec. 2.3
+ * hold because every batch of a snapshot sees the same positions).
+ *
+ * mqr_snapshot builds the index (Morton keys, sort, leaves; Alg. 1) of the
+ * context's current state on the context's stream and returns without
+ * waiting; the slots of the context then answer batches against it, each on
+ * its own stream and with its own per-query buffers, reading the snapshot's
+ * index without copying it.  The next mqr_snapshot (or mqr_tick) of the
+ * context overwrites the index, so every slot's join must have been ended
+ * first (else INVALID_ARG); position updates may be applied while joins run
+ * (they belong to the next snapshot).
+ *
+ * mqr_slot_create: a slot of ctx (its own CUDA stream, about 16 bytes per
+ * object of per-leaf lists, per-query buffers grown on demand).  Errors:
+ * INVALID_ARG, OOM, CUDA.  mqr_slot_destroy: waits for the slot's work and
+ * frees it; NULL is a no-op.  Destroying a context makes its remaining slots
+ * unusable (destroy them too).  Batched worlds are not supported by slots. */
+typedef struct mqr_slot mqr_slot;
+mqr_status mqr_slot_create(mqr_ctx *ctx, mqr_slot **out);
+void mqr_slot_destroy(mqr_slot *slot);
+mqr_status mqr_snapshot(mqr_ctx *ctx);
+
+/* Start answering Q queries (rects_dev as for mqr_tick) on the slot against
+ * the context's last snapshot, with admission by output memory as in
+ * mqr_tick_admit: the longest prefix of the queries whose output fits
+ * out_capacity_bytes is answered (decided on the device from the exact
+ * counts, before anything is written).  kind: PAIRS, CSR or RUNS (RUNS
+ * refers to the snapshot's sorted ids, mqr_get_sorted of the context).
+ * offsets_dev: NULL or uint64[Q+1] device (entries 0 .. admitted valid).
+ * Returns once the work is enqueued on the slot's stream; rects_dev, out_dev
+ * and offsets_dev must stay valid until mqr_slot_end.  One join per slot at a
+ * time.  Errors: INVALID_ARG (no snapshot, a join pending, bad kind or
+ * alignment), OOM, CUDA. */
+mqr_status mqr_slot_begin(mqr_slot *slot, const float *rects_dev, uint32_t Q, int kind, void *out_dev,
+                          uint64_t out_capacity_bytes, uint64_t *offsets_dev);
+
+/* Wait for the slot's join (answering it again if an internal buffer had to
+ * grow) and report *admitted (queries answered: a prefix) and *out_count
+ * (output elements written).  Errors: INVALID_ARG (nothing pending; or an
+ * update id >= max_objects was ignored, after the join was answered),
+ * TIMEOUT, CUDA, OOM. */
+mqr_status mqr_slot_end(mqr_slot *slot, uint32_t *admitted, uint64_t *out_count);
+
+/* Counters of the slot's last join (as mqr_get_stats). */
+mqr_status mqr_slot_get_stats(const mqr_slot *slot, mqr_stats *out);
+
 /* Graph mode (enable = 1): the tick's ~20 kernel launches are captured once
  * into a CUDA graph and the graph is replayed by later ticks with the same
  * arguments (rects_dev, Q, kind, out_dev, capacity, offsets_dev) while no

@@ -406,7 +406,7 @@ emit_kernel(const uint32_t *__restrict__ sub_q, const uint32_t *__restrict__ sub
     __shared__ unsigned long long s_uptr[kEmitWarps][32];
     if (!tick_buffers_ok(info, caps)) return;
     uint32_t nsub = (uint32_t)info->n_sub;
-    if (info->emit_end) nsub = min(nsub, (uint32_t)info->emit_end);     // admitted prefix only
+    if (info->emit_end) nsub = min(nsub, (uint32_t)info->emit_end);     // admitted prefix only (low 32 bits)
     if (KIND != kEmitBitmap && out_off[nsub] > caps.out) return;
     const int lane = threadIdx.x & 31;
     const int wib = threadIdx.x >> 5;
@@ -598,7 +598,7 @@ __global__ void admit_kernel(uint32_t Q, const unsigned long long *__restrict__ 
             }
             info->admitted = q;
             info->admitted_out = offsets[q];
-            info->emit_end = rec;
+            info->emit_end = (1ull << 63) | rec;       // bit 63: the output is cut (rec may be 0)
         }
     }
 }

@@ -14,6 +14,7 @@
 #include <cstring>
 #include <new>
 #include <string>
+#include <vector>
 
 #include "../../include/mqr.h"
 #include "mqr_internal.cuh"
@@ -175,6 +176,28 @@ struct mqr_ctx {
     unsigned long long last_q = 0, retries = 0;
     bool have_tick = false;
     bool bad_id = false;   // an update id >= max_objects was seen since the last report
+    // snapshots and join slots (mqr_snapshot, mqr_slot_*): a context's index is
+    // shared read-only by its slots; snap_info holds the index counters of the
+    // last snapshot (objects present, leaves, deepest level, error bits)
+    cudaEvent_t snap_ready = nullptr;
+    DevBuf<unsigned long long> snap_info;
+    bool have_snapshot = false;
+    bool snap_pending = false;      // a snapshot was enqueued after the last completed tick
+    bool index_valid = false;       // c->last's index counters describe the current index
+    std::vector<mqr_ctx *> slots;
+    // a slot: its context, the event after its last join, the pending join
+    mqr_ctx *parent = nullptr;
+    cudaEvent_t slot_done = nullptr;
+    bool slot_busy = false;
+    struct SlotJob {
+        const float4 *rects;
+        uint32_t Q;
+        int emit_kind, kind;
+        void *out;
+        unsigned long long cap;
+        unsigned long long *offsets;
+        Caps caps;
+    } job{};
 };
 
 namespace {
@@ -290,22 +313,27 @@ size_t out_elem_bytes(int kind) {
     }
 }
 
-// Enqueue the whole pipeline up to the result scan (and the emit when the
-// caller's buffer is given).  Returns after enqueueing.
-mqr_status enqueue_tick(mqr_ctx *c, const float4 *rects, uint32_t Q, int emit_kind, void *out,
-                        unsigned long long out_cap_elems, unsigned long long *offsets,
-                        const Arena &a, Caps &caps) {
+// Wait (on the context's stream) until no slot still reads the index that
+// the next index build overwrites.
+mqr_status wait_for_slots(mqr_ctx *c) {
+    for (mqr_ctx *sl : c->slots)
+        if (sl->slot_done) MQR_CUDA(cudaStreamWaitEvent(c->stream, sl->slot_done, 0));
+    return MQR_OK;
+}
+
+// a2 - a4: Morton keys, the onesweep sort and the leaves of the current
+// state, then the snapshot's counters for the slots.  The arena is zeroed and
+// the update kernels' error bits carried in first.
+mqr_status enqueue_index(mqr_ctx *c, const Arena &a) {
     cudaStream_t st = c->stream;
     Info *info = at<Info>(c, a.info);
     uint32_t *hist = at<uint32_t>(c, a.hist);
-    // tile/ticket counters: 0-3 sort passes, 4 leaves, 5 query blocks, 6 leaf scan, 7 result scan,
-    // 8 candidate scan, 9 emit batches, 10 filter items; 12-13 the output sort's error word
     uint32_t *ctr = at<uint32_t>(c, a.counters);
     unsigned long long *err = &info->err;
     const float x0 = c->bounds.xmin, y0 = c->bounds.ymin;
     const uint32_t nmax = c->nmax;
-    const int cov = c->cfg.covering ? 1 : 0;
-
+    mqr_status s = wait_for_slots(c);
+    if (s != MQR_OK) return s;
     MQR_CUDA(cudaMemsetAsync(c->arena.p, 0, a.total, st));
     // Carry the update kernels' sticky error bits into this tick.
     MQR_CUDA(cudaMemcpyAsync(&info->err, c->upd_err.p, sizeof(unsigned long long),
@@ -343,6 +371,34 @@ mqr_status enqueue_tick(mqr_ctx *c, const float4 *rects, uint32_t Q, int emit_ki
         leaf_launches += 1 + kexp;
     }
     phase_end(c, MQR_PHASE_LEAVES, leaf_launches);
+    if (!c->slots.empty()) {
+        // the index counters (n_present, n_leaves, max_level) and the error bits for the slots
+        MQR_CUDA(cudaMemcpyAsync(c->snap_info.p, info, 3 * sizeof(unsigned long long), cudaMemcpyDeviceToDevice, st));
+        MQR_CUDA(cudaMemcpyAsync(c->snap_info.p + 3, &info->err, sizeof(unsigned long long),
+                                 cudaMemcpyDeviceToDevice, st));
+        MQR_CUDA(cudaEventRecord(c->snap_ready, st));
+    }
+    return check_launch("index kernels");
+}
+
+// a5 - a14 for Q queries against the index of ix (ix == c for a plain tick,
+// the slot's context for a slot): query splitting, grouping, filtering, the
+// result scan and the emit.  admit: the output is limited to the longest
+// prefix of queries that fits out_cap_elems (per-query offsets, then the
+// admission kernel, then the emit of the admitted records: no host round
+// trip); offsets is then required.
+mqr_status enqueue_join(mqr_ctx *c, const mqr_ctx *ix, const float4 *rects, uint32_t Q, int emit_kind, void *out,
+                        unsigned long long out_cap_elems, unsigned long long *offsets, const Arena &a, Caps &caps,
+                        bool admit) {
+    cudaStream_t st = c->stream;
+    Info *info = at<Info>(c, a.info);
+    // tile/ticket counters: 0-3 sort passes, 4 leaves, 5 query blocks, 6 leaf scan, 7 result scan,
+    // 8 candidate scan, 9 emit batches, 10 filter items; 12-13 the output sort's error word
+    uint32_t *ctr = at<uint32_t>(c, a.counters);
+    const float x0 = c->bounds.xmin, y0 = c->bounds.ymin;
+    const uint32_t nmax = c->nmax;
+    const int cov = c->cfg.covering ? 1 : 0;
+    const Worlds worlds{ix->world_obj.p, ix->world_q.p, ix->n_worlds, ix->world_bits};
     // a5 + a6: coarse lookup table, blocks and candidate counts per query
     caps.sub = c->sub_q.n;
     caps.sub_i = c->isub.n;
@@ -351,22 +407,24 @@ mqr_status enqueue_tick(mqr_ctx *c, const float4 *rects, uint32_t Q, int emit_ki
     caps.cand_tiles = a.cand_tiles;
     caps.items = c->item_leaf.n;
     phase_begin(c, MQR_PHASE_QUERY_BLOCKS);
-    launch_zmap(st, c->leaf_hi.p, info, c->zmap.p);
-    launch_query_blocks(st, rects, Q, x0, y0, c->sx, c->sy, worlds, c->leaf_lo.p, c->leaf_hi.p, c->zmap.p,
+    launch_zmap(st, ix->leaf_hi.p, info, c->zmap.p);
+    launch_query_blocks(st, rects, Q, x0, y0, c->sx, c->sy, worlds, ix->leaf_lo.p, ix->leaf_hi.p, c->zmap.p,
                         c->qcells.p, c->cand_off.p, c->pair_q.p, c->pair_first.p, c->pair_blo.p,
                         c->pair_off.p, c->qpair.p, c->tile_p0.p, a.cand_tiles,
                         at<uint32_t>(c, a.st_qb_p), at<unsigned long long>(c, a.st_qb_c), ctr + 5, info);
     phase_end(c, MQR_PHASE_QUERY_BLOCKS, Q ? 2 : 1);
     // a7: candidates -> subquery records
     phase_begin(c, MQR_PHASE_CANDIDATES);
+    if (c != ix)      // a slot's per-leaf subquery counts start at zero (the index build zeroes its own)
+        MQR_CUDA(cudaMemsetAsync(c->leaf_nsub.p, 0, (size_t)std::max<uint32_t>(nmax, 1) * sizeof(uint32_t), st));
     launch_candidates(st, c->num_sms * (int)c->bps_cand, cov, c->tile_p0.p, c->pair_q.p, c->pair_first.p, c->pair_blo.p,
-                      c->pair_off.p, c->qcells.p, c->leaf_box.p, c->leaf_beg.p, c->tile_cnt.p,
+                      c->pair_off.p, c->qcells.p, ix->leaf_box.p, ix->leaf_beg.p, c->tile_cnt.p,
                       c->tile_off.p, c->leaf_nsub.p, c->cand_pad.p, c->pair_rec.p,
                       at<uint32_t>(c, a.st_cand), ctr + 8, caps, info);
     phase_end(c, MQR_PHASE_CANDIDATES, 2);
     // a8: group intersecting subqueries by leaf; compact the records
     phase_begin(c, MQR_PHASE_GROUP);
-    launch_leaf_scan(st, nmax, c->leaf_beg.p, c->leaf_nsub.p, c->leaf_sub_off.p, c->leaf_word_off.p,
+    launch_leaf_scan(st, nmax, ix->leaf_beg.p, c->leaf_nsub.p, c->leaf_sub_off.p, c->leaf_word_off.p,
                      c->leaf_item_off.p, c->item_leaf.p, at<uint32_t>(c, a.st_lscan), ctr + 6, caps, info);
     launch_compact(st, c->num_sms * (int)c->bps_compact, c->cand_pad.p, c->tile_cnt.p, c->tile_off.p, c->leaf_sub_off.p, c->sub_q.p,
                    c->sub_leaf.p, c->sub_len.p, c->sub_res.p, c->isub.p, caps, info);
@@ -375,14 +433,14 @@ mqr_status enqueue_tick(mqr_ctx *c, const float4 *rects, uint32_t Q, int emit_ki
     if (emit_kind == kEmitAtomic) {
         // the atomic-append baseline: no bitmaps, no result scan, no decoding
         phase_begin(c, MQR_PHASE_FILTER);
-        launch_atomic_baseline(st, c->num_sms, rects, c->sxy.p, c->sid.p, c->leaf_beg.p, c->leaf_sub_off.p,
+        launch_atomic_baseline(st, c->num_sms, rects, ix->sxy.p, ix->sid.p, ix->leaf_beg.p, c->leaf_sub_off.p,
                                c->leaf_item_off.p, c->item_leaf.p, c->isub.p, c->sub_q.p, c->sub_leaf.p,
                                c->sub_len.p, out, out ? out_cap_elems : 0, ctr + 10, caps, info);
         phase_end(c, MQR_PHASE_FILTER, 2);
         return check_launch("tick kernels");
     }
     phase_begin(c, MQR_PHASE_FILTER);
-    launch_filter(st, c->num_sms * (int)c->bps_filter, rects, c->sxy.p, c->leaf_beg.p, c->leaf_sub_off.p,
+    launch_filter(st, c->num_sms * (int)c->bps_filter, rects, ix->sxy.p, ix->leaf_beg.p, c->leaf_sub_off.p,
                   c->leaf_word_off.p, c->leaf_item_off.p, c->item_leaf.p, c->isub.p, c->sub_q.p, c->sub_res.p,
                   c->bitmap.p, ctr + 10, caps, info);
     phase_end(c, MQR_PHASE_FILTER, 1);
@@ -392,20 +450,53 @@ mqr_status enqueue_tick(mqr_ctx *c, const float4 *rects, uint32_t Q, int emit_ki
                        at<unsigned long long>(c, a.st_res), ctr + 7, emit_kind == kEmitRuns ? 2u : 0u, caps,
                        info, g_stall_scan.exchange(false));
     phase_end(c, MQR_PHASE_RESULT_SCAN, 1);
+    if (admit) {
+        // per-query offsets, then the longest prefix of queries that fits
+        phase_begin(c, MQR_PHASE_OFFSETS);
+        launch_query_offsets(st, Q, c->qpair.p, c->pair_rec.p, c->tile_off.p, c->out_off.p, offsets, caps, info);
+        launch_admit(st, Q, offsets, out ? out_cap_elems : 0, c->qpair.p, c->pair_rec.p, c->tile_off.p, caps, info);
+        phase_end(c, MQR_PHASE_OFFSETS, 2);
+    }
     // a12 + a13
     if (out != nullptr && emit_kind >= 0) {
         phase_begin(c, MQR_PHASE_EMIT);
         launch_emit(st, c->num_sms * (int)c->bps_emit, emit_kind, c->sub_q.p, c->sub_leaf.p, c->sub_len.p, c->leaf_word_off.p,
-                    c->out_off.p, c->leaf_beg.p, c->sid.p, c->bitmap.p, out,
+                    c->out_off.p, ix->leaf_beg.p, ix->sid.p, c->bitmap.p, out,
                     bitmap_words_per_row(nmax), ctr + 9, caps, info);
         phase_end(c, MQR_PHASE_EMIT, 1);
     }
-    if (offsets != nullptr) {
+    if (offsets != nullptr && !admit) {
         phase_begin(c, MQR_PHASE_OFFSETS);
         launch_query_offsets(st, Q, c->qpair.p, c->pair_rec.p, c->tile_off.p, c->out_off.p, offsets, caps, info);
         phase_end(c, MQR_PHASE_OFFSETS, 1);
     }
     return check_launch("tick kernels");
+}
+
+// The whole pipeline of a plain tick: the index, then the join.  Returns
+// after enqueueing.
+mqr_status enqueue_tick(mqr_ctx *c, const float4 *rects, uint32_t Q, int emit_kind, void *out,
+                        unsigned long long out_cap_elems, unsigned long long *offsets,
+                        const Arena &a, Caps &caps, bool admit) {
+    mqr_status s = enqueue_index(c, a);
+    if (s != MQR_OK) return s;
+    return enqueue_join(c, c, rects, Q, emit_kind, out, out_cap_elems, offsets, a, caps, admit);
+}
+
+// A slot's join against its context's last snapshot: the slot waits for the
+// snapshot, takes its index counters and error bits, then runs the join on
+// its own stream and buffers.
+mqr_status enqueue_slot(mqr_ctx *c, const float4 *rects, uint32_t Q, int emit_kind, void *out,
+                        unsigned long long out_cap_elems, unsigned long long *offsets, const Arena &a, Caps &caps) {
+    const mqr_ctx *ix = c->parent;
+    Info *info = at<Info>(c, a.info);
+    MQR_CUDA(cudaMemsetAsync(c->arena.p, 0, a.total, c->stream));
+    MQR_CUDA(cudaStreamWaitEvent(c->stream, ix->snap_ready, 0));
+    MQR_CUDA(cudaMemcpyAsync(info, ix->snap_info.p, 3 * sizeof(unsigned long long), cudaMemcpyDeviceToDevice,
+                             c->stream));
+    MQR_CUDA(cudaMemcpyAsync(&info->err, ix->snap_info.p + 3, sizeof(unsigned long long), cudaMemcpyDeviceToDevice,
+                             c->stream));
+    return enqueue_join(c, ix, rects, Q, emit_kind, out, out_cap_elems, offsets, a, caps, true);
 }
 
 // Make sure every per-tick buffer that depends on Q or on the capacities
@@ -458,9 +549,10 @@ mqr_status grow_sub(mqr_ctx *c, unsigned long long need) {
 // (relaxed capture mode), instantiated and launched.
 mqr_status enqueue_or_replay(mqr_ctx *c, const float4 *rects, uint32_t Q, int emit_kind, void *out,
                              unsigned long long out_cap_elems, unsigned long long *offsets, const Arena &a,
-                             Caps &caps) {
-    if (!c->graph_on || c->timing || g_stall_scan.load())
-        return enqueue_tick(c, rects, Q, emit_kind, out, out_cap_elems, offsets, a, caps);
+                             Caps &caps, bool admit) {
+    // slots wait on the index build through events, which a replayed graph does not record
+    if (!c->graph_on || c->timing || g_stall_scan.load() || !c->slots.empty() || admit)
+        return enqueue_tick(c, rects, Q, emit_kind, out, out_cap_elems, offsets, a, caps, admit);
     // The captured tick reads the queries from the context's own buffer, so a
     // caller that passes each tick's queries in a different buffer still
     // replays the same graph (one device-to-device copy of 16 B per query).
@@ -477,7 +569,7 @@ mqr_status enqueue_or_replay(mqr_ctx *c, const float4 *rects, uint32_t Q, int em
             c->gexec = nullptr;
         }
         MQR_CUDA(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeRelaxed));
-        mqr_status s = enqueue_tick(c, rects, Q, emit_kind, out, out_cap_elems, offsets, a, caps);
+        mqr_status s = enqueue_tick(c, rects, Q, emit_kind, out, out_cap_elems, offsets, a, caps, false);
         cudaGraph_t g = nullptr;
         cudaError_t e = cudaStreamEndCapture(c->stream, &g);
         if (s != MQR_OK) {
@@ -502,67 +594,88 @@ mqr_status enqueue_or_replay(mqr_ctx *c, const float4 *rects, uint32_t Q, int em
     return MQR_OK;
 }
 
+// One attempt of a tick (or of a slot's join): enqueue its kernels and the
+// copy of its counters to the host.  Returns after enqueueing.
+mqr_status attempt_enqueue(mqr_ctx *c, const float4 *rects, uint32_t Q, int emit_kind, void *out,
+                           unsigned long long out_cap_elems, unsigned long long *offsets, bool admit, Caps &caps) {
+    Arena a = arena_layout(c->nmax, Q, c->sub_q.n, c->cand_tiles);
+    MQR_CUDA(c->arena.ensure(a.total));
+    caps = Caps{};
+    mqr_status s = c->parent ? enqueue_slot(c, rects, Q, emit_kind, out, out_cap_elems, offsets, a, caps)
+                             : enqueue_or_replay(c, rects, Q, emit_kind, out, out_cap_elems, offsets, a, caps, admit);
+    if (s != MQR_OK) return s;
+    MQR_CUDA(cudaMemcpyAsync(c->info_host, c->arena.p + a.info, sizeof(Info), cudaMemcpyDeviceToHost, c->stream));
+    return MQR_OK;
+}
+
+// After the stream has completed an attempt: its errors, and whether an
+// internal buffer was too small (then it is grown and *again is set: the
+// attempt must be repeated).
+mqr_status attempt_check(mqr_ctx *c, uint32_t Q, int emit_kind, const Caps &caps, bool *again) {
+    *again = false;
+    Info in = *c->info_host;
+    c->last = in;
+    c->last_q = Q;
+    c->last_emit_kind = emit_kind;
+    c->have_tick = true;
+    c->index_valid = true;
+    c->snap_pending = false;
+    if (in.err & kErrTimeout) return fail(MQR_ERR_TIMEOUT, "a device-side wait exceeded its deadline");
+    if (in.err & kErrInternal) return fail(MQR_ERR_INTERNAL, "device index out of range");
+    if (in.err & kErrBadId) c->bad_id = true;
+    const unsigned long long need_tiles = (in.n_cand + 31) / 32;
+    if (need_tiles > caps.cand_tiles) {
+        if (need_tiles > kMaxCandTiles)
+            return fail(MQR_ERR_INVALID_ARG, "too many candidate leaves in one tick (limit 2^32)");
+        c->cand_tiles = std::min<unsigned long long>(grow_to(need_tiles), kMaxCandTiles);
+        c->tile_p0.release(); c->tile_cnt.release(); c->tile_off.release(); c->cand_pad.release();
+        MQR_CUDA(c->tile_p0.ensure(c->cand_tiles));
+        MQR_CUDA(c->tile_cnt.ensure(c->cand_tiles));
+        MQR_CUDA(c->tile_off.ensure(c->cand_tiles));
+        MQR_CUDA(c->cand_pad.ensure(c->cand_tiles * 32));
+        *again = true;
+    } else if (in.n_sub > caps.sub) {
+        mqr_status s = grow_sub(c, in.n_sub);
+        if (s != MQR_OK) return s;
+        *again = true;
+    } else {
+        if (in.n_sub_i > caps.sub_i) {
+            c->isub.release();
+            MQR_CUDA(c->isub.ensure(grow_to(in.n_sub_i)));
+            *again = true;
+        }
+        if (in.n_items > caps.items) {
+            c->item_leaf.release();
+            MQR_CUDA(c->item_leaf.ensure(grow_to(in.n_items)));
+            *again = true;
+        }
+        if (in.n_words > caps.words) {
+            if (in.n_words > 0xffffffffull)
+                return fail(MQR_ERR_CAPACITY, "more than 2^32 bitmap words in one tick");
+            c->bitmap.release();
+            MQR_CUDA(c->bitmap.ensure(grow_to(in.n_words)));
+            *again = true;
+        }
+    }
+    return MQR_OK;
+}
+
 // Run the pipeline until every internal buffer was large enough; leaves the
 // tick's device state valid and c->last filled.  `out` may be null (then
-// nothing is emitted).
+// nothing is emitted).  admit: see enqueue_join.
 mqr_status run_tick(mqr_ctx *c, const float4 *rects, uint32_t Q, int emit_kind, void *out,
-                    unsigned long long out_cap_elems, unsigned long long *offsets) {
+                    unsigned long long out_cap_elems, unsigned long long *offsets, bool admit = false) {
     mqr_status s = ensure_tick_buffers(c, Q);
     if (s != MQR_OK) return s;
     c->retries = 0;
     for (int attempt = 0; attempt < 8; ++attempt) {
-        Arena a = arena_layout(c->nmax, Q, c->sub_q.n, c->cand_tiles);
-        MQR_CUDA(c->arena.ensure(a.total));
         Caps caps{};
-        s = enqueue_or_replay(c, rects, Q, emit_kind, out, out_cap_elems, offsets, a, caps);
+        s = attempt_enqueue(c, rects, Q, emit_kind, out, out_cap_elems, offsets, admit, caps);
         if (s != MQR_OK) return s;
-        MQR_CUDA(cudaMemcpyAsync(c->info_host, c->arena.p + a.info, sizeof(Info), cudaMemcpyDeviceToHost,
-                                 c->stream));
         MQR_CUDA(cudaStreamSynchronize(c->stream));
-        Info in = *c->info_host;
-        c->last = in;
-        c->last_q = Q;
-        c->last_emit_kind = emit_kind;
-        c->have_tick = true;
-        if (in.err & kErrTimeout)
-            return fail(MQR_ERR_TIMEOUT, "a device-side wait exceeded its deadline");
-        if (in.err & kErrInternal) return fail(MQR_ERR_INTERNAL, "device index out of range");
-        if (in.err & kErrBadId) c->bad_id = true;
         bool again = false;
-        const unsigned long long need_tiles = (in.n_cand + 31) / 32;
-        if (need_tiles > caps.cand_tiles) {
-            if (need_tiles > kMaxCandTiles)
-                return fail(MQR_ERR_INVALID_ARG, "too many candidate leaves in one tick (limit 2^32)");
-            c->cand_tiles = std::min<unsigned long long>(grow_to(need_tiles), kMaxCandTiles);
-            c->tile_p0.release(); c->tile_cnt.release(); c->tile_off.release(); c->cand_pad.release();
-            MQR_CUDA(c->tile_p0.ensure(c->cand_tiles));
-            MQR_CUDA(c->tile_cnt.ensure(c->cand_tiles));
-            MQR_CUDA(c->tile_off.ensure(c->cand_tiles));
-            MQR_CUDA(c->cand_pad.ensure(c->cand_tiles * 32));
-            again = true;
-        } else if (in.n_sub > caps.sub) {
-            s = grow_sub(c, in.n_sub);
-            if (s != MQR_OK) return s;
-            again = true;
-        } else {
-            if (in.n_sub_i > caps.sub_i) {
-                c->isub.release();
-                MQR_CUDA(c->isub.ensure(grow_to(in.n_sub_i)));
-                again = true;
-            }
-            if (in.n_items > caps.items) {
-                c->item_leaf.release();
-                MQR_CUDA(c->item_leaf.ensure(grow_to(in.n_items)));
-                again = true;
-            }
-            if (in.n_words > caps.words) {
-                if (in.n_words > 0xffffffffull)
-                    return fail(MQR_ERR_CAPACITY, "more than 2^32 bitmap words in one tick");
-                c->bitmap.release();
-                MQR_CUDA(c->bitmap.ensure(grow_to(in.n_words)));
-                again = true;
-            }
-        }
+        s = attempt_check(c, Q, emit_kind, caps, &again);
+        if (s != MQR_OK) return s;
         if (!again) {
             phases_collect(c, true);
             return MQR_OK;
@@ -612,6 +725,36 @@ mqr_status sort_result_keys(mqr_ctx *c, uint64_t n, uint32_t Q, unsigned long lo
     if (herr & kErrTimeout) return fail(MQR_ERR_TIMEOUT, "a device-side wait exceeded its deadline");
     if (herr) return fail(MQR_ERR_INTERNAL, "device index out of range in the result sort");
     return MQR_OK;
+}
+
+// The index counters of the latest index build (a tick's or a snapshot's)
+// in c->last; waits for a pending snapshot.
+mqr_status index_ready(mqr_ctx *c) {
+    if (c->snap_pending) {
+        unsigned long long h[4] = {0, 0, 0, 0};
+        MQR_CUDA(cudaMemcpyAsync(h, c->snap_info.p, sizeof(h), cudaMemcpyDeviceToHost, c->stream));
+        MQR_CUDA(cudaStreamSynchronize(c->stream));
+        c->last.n_present = h[0];
+        c->last.n_leaves = h[1];
+        c->last.max_level = h[2];
+        c->snap_pending = false;
+        c->index_valid = true;
+        c->have_tick = false;       // the join records no longer match the index
+    }
+    if (!c->index_valid) return fail(MQR_ERR_INVALID_ARG, "no tick or snapshot has completed yet");
+    return MQR_OK;
+}
+
+// Queries answered and output elements written by an admitted tick: the
+// admission kernel marks emit_end (bit 63 set) when the output had to be cut.
+void admission_counts(const Info &in, uint32_t Q, uint32_t *admitted, uint64_t *out_count) {
+    if (in.emit_end) {
+        *admitted = (uint32_t)in.admitted;
+        *out_count = in.admitted_out;
+    } else {
+        *admitted = Q;
+        *out_count = in.n_out;
+    }
 }
 
 mqr_status tick_device_impl(mqr_ctx *c, const float *rects_dev, uint32_t Q, int kind, void *out_dev,
@@ -907,6 +1050,18 @@ void mqr_destroy(mqr_ctx *c) {
     cudaGetDevice(&prev);
     cudaSetDevice(c->device);
     if (c->stream) cudaStreamSynchronize(c->stream);
+    if (c->parent) {                       // a slot leaves its context's list
+        auto &v = c->parent->slots;
+        v.erase(std::remove(v.begin(), v.end(), c), v.end());
+    }
+    for (mqr_ctx *sl : c->slots) {         // slots outliving their context become unusable
+        if (sl->stream) cudaStreamSynchronize(sl->stream);
+        sl->parent = nullptr;
+    }
+    c->slots.clear();
+    if (c->slot_done) cudaEventDestroy(c->slot_done);
+    if (c->snap_ready) cudaEventDestroy(c->snap_ready);
+    c->snap_info.release();
     DevBuf<float2> *f2[] = {&c->pos, &c->sxy, &c->up_xy};
     for (auto *b : f2) b->release();
     if (c->gexec) cudaGraphExecDestroy(c->gexec);
@@ -1070,8 +1225,16 @@ mqr_status mqr_apply_updates_host(mqr_ctx *c, const uint32_t *ids_host, const fl
     return MQR_OK;
 }
 
+static bool slots_busy(const mqr_ctx *c) {
+    for (const mqr_ctx *sl : c->slots)
+        if (sl->slot_busy) return true;
+    return false;
+}
+
 static mqr_status tick_args(mqr_ctx *c, const void *rects, uint32_t Q, int kind, uint64_t *out_count) {
     if (!c) return fail(MQR_ERR_INVALID_ARG, "ctx is NULL");
+    if (c->parent) return fail(MQR_ERR_INVALID_ARG, "a slot answers through mqr_slot_begin / mqr_slot_end");
+    if (slots_busy(c)) return fail(MQR_ERR_INVALID_ARG, "a slot of this context has a join pending (mqr_slot_end)");
     if (!out_count) return fail(MQR_ERR_INVALID_ARG, "out_count is NULL");
     if (Q > 0 && !rects) return fail(MQR_ERR_INVALID_ARG, "rects is NULL");
     if (Q >= (1u << 30)) return fail(MQR_ERR_INVALID_ARG, "Q must be < 2^30");
@@ -1263,39 +1426,155 @@ mqr_status mqr_tick_admit(mqr_ctx *c, const float *rects_dev, uint32_t Q, int ki
         offs = c->off_stage.p;
     }
     const int ek = kind == MQR_OUT_PAIRS ? kEmitPairs : (kind == MQR_OUT_CSR ? kEmitIds : kEmitRuns);
-    // exact counts and per-query offsets first (no output written) ...
-    s = run_tick(c, rects, Q, ek, nullptr, 0, offs);
-    if (s != MQR_OK) return s;
+    // one pass: exact counts and per-query offsets, the longest prefix of
+    // queries whose output fits (on the device), the emit of that prefix
     const unsigned long long cap_elems = out_dev ? out_capacity_bytes / out_elem_bytes(kind) : 0;
-    Arena a = arena_layout(c->nmax, Q, c->sub_q.n, c->cand_tiles);
-    Caps caps{c->sub_q.n, c->isub.n, std::min<size_t>(c->bitmap.n, 0xffffffffull), cap_elems, c->cand_tiles,
-              c->item_leaf.n};
-    Info *info = at<Info>(c, a.info);
-    uint32_t A = Q;
-    unsigned long long n = c->last.n_out;
-    // ... then the longest prefix of queries whose output fits
-    if (n > cap_elems) {
-        launch_admit(c->stream, Q, offs, cap_elems, c->qpair.p, c->pair_rec.p, c->tile_off.p, caps, info);
-        MQR_CUDA(cudaGetLastError());
-        MQR_CUDA(cudaMemcpyAsync(c->info_host, info, sizeof(Info), cudaMemcpyDeviceToHost, c->stream));
-        MQR_CUDA(cudaStreamSynchronize(c->stream));
-        A = (uint32_t)c->info_host->admitted;
-        n = c->info_host->admitted_out;
-    }
-    if (n > 0) {
-        phase_begin(c, MQR_PHASE_EMIT);
-        launch_emit(c->stream, c->num_sms * (int)c->bps_emit, ek, c->sub_q.p, c->sub_leaf.p, c->sub_len.p, c->leaf_word_off.p,
-                    c->out_off.p, c->leaf_beg.p, c->sid.p, c->bitmap.p, out_dev,
-                    bitmap_words_per_row(c->nmax), at<uint32_t>(c, a.counters) + 9, caps, info);
-        phase_end(c, MQR_PHASE_EMIT, 1);
-        s = check_launch("emit");
-        if (s != MQR_OK) return s;
-        MQR_CUDA(cudaStreamSynchronize(c->stream));
-        phases_collect(c, false);
-    }
-    *admitted = A;
-    *out_count = n;
+    s = run_tick(c, rects, Q, ek, out_dev, cap_elems, offs, true);
+    if (s != MQR_OK) return s;
+    admission_counts(c->last, Q, admitted, out_count);
     return MQR_OK;
+}
+
+mqr_status mqr_snapshot(mqr_ctx *c) {
+    if (!c) return fail(MQR_ERR_INVALID_ARG, "ctx is NULL");
+    if (c->parent) return fail(MQR_ERR_INVALID_ARG, "a slot has no index of its own");
+    if (c->slots.empty()) return fail(MQR_ERR_INVALID_ARG, "no slot of this context (mqr_slot_create)");
+    if (slots_busy(c)) return fail(MQR_ERR_INVALID_ARG, "a slot of this context has a join pending (mqr_slot_end)");
+    MQR_CUDA(cudaSetDevice(c->device));
+    Arena a = arena_layout(c->nmax, 0, c->sub_q.n, c->cand_tiles);
+    MQR_CUDA(c->arena.ensure(a.total));
+    mqr_status s = enqueue_index(c, a);
+    if (s != MQR_OK) return s;
+    c->have_snapshot = true;
+    c->snap_pending = true;
+    return MQR_OK;
+}
+
+mqr_status mqr_slot_create(mqr_ctx *c, mqr_slot **out) {
+    if (!c || !out) return fail(MQR_ERR_INVALID_ARG, "NULL argument");
+    *out = nullptr;
+    if (c->parent) return fail(MQR_ERR_INVALID_ARG, "a slot cannot have slots");
+    MQR_CUDA(cudaSetDevice(c->device));
+    MQR_CUDA(cudaStreamSynchronize(c->stream));
+    if (!c->snap_ready) {
+        MQR_CUDA(cudaEventCreateWithFlags(&c->snap_ready, cudaEventDisableTiming));
+        MQR_CUDA(c->snap_info.ensure(4));
+    }
+    mqr_ctx *sl = new (std::nothrow) mqr_ctx();
+    if (!sl) return fail(MQR_ERR_OOM, "host allocation failed");
+    sl->parent = c;
+    sl->device = c->device;
+    sl->num_sms = c->num_sms;
+    sl->cfg = c->cfg;
+    sl->bounds = c->bounds;
+    sl->sx = c->sx;
+    sl->sy = c->sy;
+    sl->nmax = c->nmax;
+    c->slots.push_back(sl);                       // from here on mqr_destroy(sl) cleans up
+    auto bail = [&](cudaError_t e, const char *what) {
+        mqr_status st = cuda_fail(e, what);
+        mqr_destroy(sl);
+        return st;
+    };
+    cudaError_t e;
+    if ((e = cudaStreamCreateWithFlags(&sl->stream, cudaStreamNonBlocking)) != cudaSuccess)
+        return bail(e, "cudaStreamCreate");
+    sl->own_stream = true;
+    if ((e = cudaEventCreateWithFlags(&sl->slot_done, cudaEventDisableTiming)) != cudaSuccess)
+        return bail(e, "cudaEventCreate");
+    const size_t n = std::max<size_t>(c->nmax, 1);
+    if ((e = sl->leaf_nsub.ensure(n)) || (e = sl->leaf_sub_off.ensure(n + 1)) || (e = sl->leaf_word_off.ensure(n + 1)) ||
+        (e = sl->leaf_item_off.ensure(n + 1)))
+        return bail(e, "cudaMalloc (slot leaf lists)");
+    if ((e = cudaMallocHost(&sl->info_host, sizeof(Info))) != cudaSuccess) return bail(e, "cudaMallocHost");
+    *out = reinterpret_cast<mqr_slot *>(sl);
+    return MQR_OK;
+}
+
+void mqr_slot_destroy(mqr_slot *slot) { mqr_destroy(reinterpret_cast<mqr_ctx *>(slot)); }
+
+mqr_status mqr_slot_begin(mqr_slot *slot, const float *rects_dev, uint32_t Q, int kind, void *out_dev,
+                          uint64_t out_capacity_bytes, uint64_t *offsets_dev) {
+    mqr_ctx *sl = reinterpret_cast<mqr_ctx *>(slot);
+    if (!sl) return fail(MQR_ERR_INVALID_ARG, "slot is NULL");
+    mqr_ctx *c = sl->parent;
+    if (!c) return fail(MQR_ERR_INVALID_ARG, "the slot's context was destroyed");
+    if (sl->slot_busy) return fail(MQR_ERR_INVALID_ARG, "the slot has a join pending (mqr_slot_end)");
+    if (!c->have_snapshot) return fail(MQR_ERR_INVALID_ARG, "no snapshot of the context yet (mqr_snapshot)");
+    if (Q > 0 && !rects_dev) return fail(MQR_ERR_INVALID_ARG, "rects_dev is NULL");
+    if (Q >= (1u << 30)) return fail(MQR_ERR_INVALID_ARG, "Q must be < 2^30");
+    if (kind != MQR_OUT_PAIRS && kind != MQR_OUT_CSR && kind != MQR_OUT_RUNS)
+        return fail(MQR_ERR_INVALID_ARG, "slots support the PAIRS, CSR and RUNS kinds");
+    if (c->n_worlds) return fail(MQR_ERR_INVALID_ARG, "slots are not available with batched worlds");
+    if (out_dev && (reinterpret_cast<uintptr_t>(out_dev) & 15u))
+        return fail(MQR_ERR_INVALID_ARG, "out_dev must be 16-byte aligned");
+    if (offsets_dev && (reinterpret_cast<uintptr_t>(offsets_dev) & 7u))
+        return fail(MQR_ERR_INVALID_ARG, "offsets_dev must be 8-byte aligned");
+    MQR_CUDA(cudaSetDevice(sl->device));
+    // the join follows its context's current configuration
+    sl->cfg = c->cfg;
+    sl->bps_cand = c->bps_cand;
+    sl->bps_compact = c->bps_compact;
+    sl->bps_filter = c->bps_filter;
+    sl->bps_emit = c->bps_emit;
+    unsigned long long *offs = reinterpret_cast<unsigned long long *>(offsets_dev);
+    if (!offs) {
+        MQR_CUDA(sl->off_stage.ensure((size_t)Q + 1));
+        offs = sl->off_stage.p;
+    }
+    mqr_status s = ensure_tick_buffers(sl, Q);
+    if (s != MQR_OK) return s;
+    const int ek = kind == MQR_OUT_PAIRS ? kEmitPairs : (kind == MQR_OUT_CSR ? kEmitIds : kEmitRuns);
+    const unsigned long long cap_elems = out_dev ? out_capacity_bytes / out_elem_bytes(kind) : 0;
+    const float4 *rects = reinterpret_cast<const float4 *>(rects_dev);
+    sl->retries = 0;
+    Caps caps{};
+    s = attempt_enqueue(sl, rects, Q, ek, out_dev, cap_elems, offs, true, caps);
+    if (s != MQR_OK) return s;
+    MQR_CUDA(cudaEventRecord(sl->slot_done, sl->stream));
+    sl->job = mqr_ctx::SlotJob{rects, Q, ek, kind, out_dev, cap_elems, offs, caps};
+    sl->slot_busy = true;
+    return MQR_OK;
+}
+
+mqr_status mqr_slot_end(mqr_slot *slot, uint32_t *admitted, uint64_t *out_count) {
+    mqr_ctx *sl = reinterpret_cast<mqr_ctx *>(slot);
+    if (!sl || !admitted || !out_count) return fail(MQR_ERR_INVALID_ARG, "NULL argument");
+    if (!sl->slot_busy) return fail(MQR_ERR_INVALID_ARG, "no join pending on the slot (mqr_slot_begin)");
+    *admitted = 0;
+    *out_count = 0;
+    MQR_CUDA(cudaSetDevice(sl->device));
+    mqr_ctx::SlotJob &j = sl->job;
+    mqr_status s = MQR_OK;
+    bool done = false;
+    for (int attempt = 0; attempt < 8 && s == MQR_OK && !done; ++attempt) {
+        if (attempt > 0) {                       // an internal buffer grew: answer again
+            s = attempt_enqueue(sl, j.rects, j.Q, j.emit_kind, j.out, j.cap, j.offsets, true, j.caps);
+            if (s != MQR_OK) break;
+            ++sl->retries;
+        }
+        cudaError_t e = cudaStreamSynchronize(sl->stream);
+        if (e != cudaSuccess) { s = cuda_fail(e, "cudaStreamSynchronize"); break; }
+        bool again = false;
+        s = attempt_check(sl, j.Q, j.emit_kind, j.caps, &again);
+        done = !again;
+    }
+    if (s == MQR_OK && !done) s = fail(MQR_ERR_INTERNAL, "buffer growth did not converge");
+    if (s == MQR_OK && (cudaEventRecord(sl->slot_done, sl->stream) != cudaSuccess))
+        s = fail(MQR_ERR_CUDA, "cudaEventRecord");
+    sl->slot_busy = false;
+    if (s != MQR_OK) return s;
+    admission_counts(sl->last, j.Q, admitted, out_count);
+    if (sl->bad_id) {
+        sl->bad_id = false;
+        return fail(MQR_ERR_INVALID_ARG, "an update id was >= max_objects (ignored); the join was answered without it");
+    }
+    return MQR_OK;
+}
+
+mqr_status mqr_slot_get_stats(const mqr_slot *slot, mqr_stats *out) {
+    if (!slot) return fail(MQR_ERR_INVALID_ARG, "slot is NULL");
+    return mqr_get_stats(reinterpret_cast<const mqr_ctx *>(slot), out);
 }
 
 mqr_status mqr_get_stats(const mqr_ctx *c, mqr_stats *o) {
@@ -1324,7 +1603,10 @@ mqr_status mqr_get_stats(const mqr_ctx *c, mqr_stats *o) {
 mqr_status mqr_region_counts(mqr_ctx *c, uint32_t region_bits, uint32_t *counts_host) {
     if (!c || !counts_host) return fail(MQR_ERR_INVALID_ARG, "NULL argument");
     if (region_bits < 1 || region_bits > kMaxRegionBits) return fail(MQR_ERR_INVALID_ARG, "region_bits must be 1..4");
-    if (!c->have_tick) return fail(MQR_ERR_INVALID_ARG, "no tick has completed yet");
+    {
+        mqr_status si = index_ready(c);
+        if (si != MQR_OK) return si;
+    }
     const size_t R = (size_t)1 << (2 * region_bits);
     MQR_CUDA(cudaSetDevice(c->device));
     MQR_CUDA(c->region_cnt.ensure(R));
@@ -1338,6 +1620,7 @@ mqr_status mqr_region_counts(mqr_ctx *c, uint32_t region_bits, uint32_t *counts_
 mqr_status mqr_region_work(mqr_ctx *c, const float *rects_dev, uint32_t Q, uint32_t region_bits, double *out_host) {
     if (!c || !out_host) return fail(MQR_ERR_INVALID_ARG, "NULL argument");
     if (region_bits < 1 || region_bits > kMaxRegionBits) return fail(MQR_ERR_INVALID_ARG, "region_bits must be 1..4");
+    if (c->snap_pending) (void)index_ready(c);   // a newer snapshot invalidates the join records
     if (!c->have_tick) return fail(MQR_ERR_INVALID_ARG, "no tick has completed yet");
     if (c->last_emit_kind == kEmitAtomic)
         return fail(MQR_ERR_INVALID_ARG, "the last tick used the atomic baseline (no per-subquery counts)");
@@ -1359,6 +1642,7 @@ mqr_status mqr_region_work(mqr_ctx *c, const float *rects_dev, uint32_t Q, uint3
 
 mqr_status mqr_result_footprint(mqr_ctx *c, uint64_t *out_host) {
     if (!c || !out_host) return fail(MQR_ERR_INVALID_ARG, "NULL argument");
+    if (c->snap_pending) (void)index_ready(c);   // a newer snapshot invalidates the join records
     if (!c->have_tick) return fail(MQR_ERR_INVALID_ARG, "no tick has completed yet");
     if (c->last_emit_kind == kEmitAtomic)
         return fail(MQR_ERR_INVALID_ARG, "the last tick used the atomic baseline (no per-subquery counts)");
@@ -1419,7 +1703,10 @@ mqr_status mqr_debug_fail_allocation(int after) {
 
 mqr_status mqr_get_leaves(mqr_ctx *c, uint32_t *leaves_host, uint64_t cap, uint64_t *n) {
     if (!c || !n) return fail(MQR_ERR_INVALID_ARG, "NULL argument");
-    if (!c->have_tick) return fail(MQR_ERR_INVALID_ARG, "no tick has completed yet");
+    {
+        mqr_status si = index_ready(c);
+        if (si != MQR_OK) return si;
+    }
     const uint64_t L = c->last.n_leaves;
     *n = L;
     if (L == 0) return MQR_OK;
@@ -1451,7 +1738,10 @@ mqr_status mqr_get_leaves(mqr_ctx *c, uint32_t *leaves_host, uint64_t cap, uint6
 
 mqr_status mqr_get_sorted(mqr_ctx *c, uint32_t *keys_host, uint32_t *ids_host, uint64_t cap, uint64_t *n) {
     if (!c || !n) return fail(MQR_ERR_INVALID_ARG, "NULL argument");
-    if (!c->have_tick) return fail(MQR_ERR_INVALID_ARG, "no tick has completed yet");
+    {
+        mqr_status si = index_ready(c);
+        if (si != MQR_OK) return si;
+    }
     const uint64_t N = c->last.n_present;
     *n = N;
     if (N == 0) return MQR_OK;
@@ -1465,7 +1755,10 @@ mqr_status mqr_get_sorted(mqr_ctx *c, uint32_t *keys_host, uint32_t *ids_host, u
 
 mqr_status mqr_get_sorted_async(mqr_ctx *c, uint32_t *ids_host, uint64_t cap, uint64_t *n) {
     if (!c || !n || !ids_host) return fail(MQR_ERR_INVALID_ARG, "NULL argument");
-    if (!c->have_tick) return fail(MQR_ERR_INVALID_ARG, "no tick has completed yet");
+    {
+        mqr_status si = index_ready(c);
+        if (si != MQR_OK) return si;
+    }
     if (!c->copy_stream) return fail(MQR_ERR_INVALID_ARG, "no mqr_tick_host_async before");
     const uint64_t N = c->last.n_present;
     *n = N;

@@ -52,7 +52,7 @@ struct Info {
     unsigned long long n_pairs;      // (query, block) pairs of query splitting
     unsigned long long n_cand;       // candidate (query, leaf) pairs
     unsigned long long n_out;        // output elements (R, or R_I + 2 per covering run for the run kind)
-    unsigned long long emit_end;     // admission: emit records [0, emit_end) only (0 = all)
+    unsigned long long emit_end;     // admission: 0 = emit all, else (bit 63 |) emit records [0, low 32 bits) only
     unsigned long long admitted;     // admission: queries [0, admitted) answered
     unsigned long long admitted_out; // admission: their output elements
 };

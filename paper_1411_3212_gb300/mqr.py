@@ -29,7 +29,8 @@ KINDS = {"pairs": MQR_OUT_PAIRS, "pairs_sorted": MQR_OUT_PAIRS_SORTED, "csr": MQ
 EXPORTS = ["mqr_config_default", "mqr_create", "mqr_create_ex", "mqr_apply_updates",
            "mqr_apply_updates_host", "mqr_tick", "mqr_tick_host", "mqr_tick_host_async", "mqr_host_wait",
            "mqr_get_sorted_async",
-           "mqr_tick_admit", "mqr_set_graph", "mqr_set_worlds",
+           "mqr_tick_admit", "mqr_snapshot", "mqr_slot_create", "mqr_slot_destroy", "mqr_slot_begin",
+           "mqr_slot_end", "mqr_slot_get_stats", "mqr_set_graph", "mqr_set_worlds",
            "mqr_set_query_worlds", "mqr_set_index", "mqr_set_region_caps", "mqr_set_launch_config", "mqr_region_counts", "mqr_region_work", "mqr_cost_param_count", "mqr_cost_create",
            "mqr_cost_set_params", "mqr_cost_get_params", "mqr_cost_train", "mqr_cost_gradient", "mqr_cost_predict",
            "mqr_cost_destroy", "mqr_get_stats",
@@ -113,6 +114,12 @@ def load(path: str = LIB_PATH):
         "mqr_host_wait": ([P], i32),
         "mqr_get_sorted_async": ([P, P, u64, ctypes.POINTER(u64)], i32),
         "mqr_tick_admit": ([P, P, u32, i32, P, u64, ctypes.POINTER(u32), ctypes.POINTER(u64), P], i32),
+        "mqr_snapshot": ([P], i32),
+        "mqr_slot_create": ([P, pctx], i32),
+        "mqr_slot_destroy": ([P], None),
+        "mqr_slot_begin": ([P, P, u32, i32, P, u64, P], i32),
+        "mqr_slot_end": ([P, ctypes.POINTER(u32), ctypes.POINTER(u64)], i32),
+        "mqr_slot_get_stats": ([P, ctypes.POINTER(mqr_stats)], i32),
         "mqr_set_graph": ([P, i32], i32),
         "mqr_set_worlds": ([P, u32, P], i32),
         "mqr_set_query_worlds": ([P, P], i32),
@@ -235,6 +242,70 @@ def mqr_tick_admit(ctx, rects_dev, Q, kind, out_dev, out_capacity_bytes, offsets
     _check(load().mqr_tick_admit(ctx, _ptr(rects_dev), Q, kind, _ptr(out_dev), out_capacity_bytes,
                                  ctypes.byref(adm), ctypes.byref(cnt), _ptr(offsets_dev)))
     return int(adm.value), int(cnt.value)
+
+
+def mqr_snapshot(ctx):
+    _check(load().mqr_snapshot(ctx))
+
+
+def mqr_slot_create(ctx):
+    out = ctypes.c_void_p()
+    _check(load().mqr_slot_create(ctx, ctypes.byref(out)))
+    return out.value
+
+
+def mqr_slot_destroy(slot):
+    if slot:
+        load().mqr_slot_destroy(slot)
+
+
+def mqr_slot_begin(slot, rects_dev, Q, kind, out_dev, out_capacity_bytes, offsets_dev=None):
+    _check(load().mqr_slot_begin(slot, _ptr(rects_dev), Q, kind, _ptr(out_dev), out_capacity_bytes,
+                                 _ptr(offsets_dev)))
+
+
+def mqr_slot_end(slot):
+    """Returns (admitted, out_count)."""
+    a = ctypes.c_uint32(0)
+    n = ctypes.c_uint64(0)
+    _check(load().mqr_slot_end(slot, ctypes.byref(a), ctypes.byref(n)))
+    return int(a.value), int(n.value)
+
+
+def mqr_slot_get_stats(slot):
+    s = mqr_stats()
+    _check(load().mqr_slot_get_stats(slot, ctypes.byref(s)))
+    return s.as_dict()
+
+
+class Slot:
+    """A join slot of an Index (mqr_slot_*): answers batches against the
+    index's last snapshot on its own CUDA stream."""
+
+    def __init__(self, index):
+        self.index = index
+        self.slot = mqr_slot_create(index.ctx)
+
+    def begin(self, rects, kind, out, capacity_bytes, offsets=None):
+        mqr_slot_begin(self.slot, rects, int(rects.shape[0]), KINDS[kind] if isinstance(kind, str) else kind,
+                       out, capacity_bytes, offsets)
+
+    def end(self):
+        return mqr_slot_end(self.slot)
+
+    def stats(self):
+        return mqr_slot_get_stats(self.slot)
+
+    def close(self):
+        if self.slot:
+            mqr_slot_destroy(self.slot)
+            self.slot = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def mqr_set_graph(ctx, enable):
@@ -550,6 +621,12 @@ class Index:
 
     def set_query_worlds(self, q_base):
         mqr_set_query_worlds(self.ctx, q_base)
+
+    def snapshot(self):
+        mqr_snapshot(self.ctx)
+
+    def slot(self):
+        return Slot(self)
 
     def footprint(self):
         return mqr_result_footprint(self.ctx)

@@ -185,3 +185,118 @@ class GpuBackend:
     def finish(self, ev):
         ev.synchronize()
         return self.t_ref + self.ref.elapsed_time(ev) / 1000.0
+
+
+class SlotBackend(GpuBackend):
+    """Continuous batching on join slots (mqr_slot_*): every tick takes one
+    snapshot of the object state (mqr_snapshot) after the tick's updates, and
+    the offered queries are split into n_slots consecutive parts answered by
+    the slots concurrently, each on its own stream, so that the parts' kernels
+    overlap on the device; each part is admitted against its slot's share of
+    the output memory (budget_bytes / n_slots) and copied to pinned host
+    memory as soon as its slot ends, while the other slots still run.  The
+    batch's answered queries are the longest prefix of fully answered parts
+    plus the admitted prefix of the first cut part (a part after a cut one is
+    answered again in a later tick, and its answer here is not reported)."""
+
+    def __init__(self, idx, updates, rects_dev, kind="runs", budget_bytes=1 << 30, copy_out=True, n_slots=2):
+        import torch
+        from . import mqr
+        self.torch, self.mqr = torch, mqr
+        self.idx, self.updates, self.rects = idx, updates, rects_dev
+        self.kind = mqr.KINDS[kind]
+        self.elem = 4 if self.kind == mqr.MQR_OUT_CSR else 8
+        self.n_slots = int(n_slots)
+        self.budget = int(budget_bytes) // self.n_slots // 16 * 16          # per slot
+        dev = rects_dev.device
+        self.slots = [idx.slot() for _ in range(self.n_slots)]
+        self.out = [torch.empty(self.budget // 4, dtype=torch.int32, device=dev) for _ in range(self.n_slots)]
+        self.copy_out = copy_out
+        self.host = [torch.empty(self.budget // 4, dtype=torch.int32).pin_memory() for _ in range(self.n_slots)] \
+            if copy_out else None
+        self.copy_stream = torch.cuda.Stream(device=dev)
+        self.buf_free = [None] * self.n_slots
+        self.last_parts = []        # (lo, admitted, out_count, slot) of the last answer, for checks
+        self.ref = None
+
+    def begin_tick(self, k):
+        ids, xy = self.updates[k % len(self.updates)]
+        self.idx.apply_updates(ids, xy)
+        self.idx.snapshot()
+
+    def answer(self, lo, hi):
+        torch, mqr = self.torch, self.mqr
+        n = hi - lo
+        cuts = [lo + (n * i) // self.n_slots for i in range(self.n_slots + 1)]
+        begun = []
+        for i in range(self.n_slots):
+            a, b = cuts[i], cuts[i + 1]
+            if b <= a:
+                continue
+            if self.buf_free[i] is not None:
+                self.buf_free[i].synchronize()           # the copy that last read this slot's output is done
+            self.slots[i].begin(self.rects[a:b], self.kind, self.out[i], self.budget)
+            begun.append((i, a, b))
+        admitted, out_count, last_ev, cut = 0, 0, None, False
+        self.last_parts = []
+        for i, a, b in begun:
+            adm, cnt = self.slots[i].end()               # every begun join is ended
+            if cut:
+                continue                                  # after a cut part: answered again later
+            ev = torch.cuda.Event(enable_timing=True)
+            with torch.cuda.stream(self.copy_stream):
+                if self.copy_out and cnt:
+                    m = cnt * self.elem // 4
+                    self.host[i][:m].copy_(self.out[i][:m], non_blocking=True)
+                ev.record(self.copy_stream)
+            self.buf_free[i] = ev
+            self.last_parts.append((a, adm, cnt, i))
+            admitted += adm
+            out_count += cnt
+            cut = adm < b - a
+            last_ev = ev
+        return admitted, out_count, last_ev
+
+    def close(self):
+        for sl in self.slots:
+            sl.close()
+
+
+class PlainBackend(GpuBackend):
+    """The plain fixed-capacity GPU quadtree: every tick answers the whole
+    offered batch with one blocking mqr_tick (device output buffer grown when
+    a batch needs more), then copies the result to pinned host memory and
+    waits for it before the next tick; no admission, no overlap."""
+
+    def __init__(self, idx, updates, rects_dev, kind="runs", copy_out=True):
+        import torch
+        from . import mqr
+        self.torch, self.mqr = torch, mqr
+        self.idx, self.updates, self.rects = idx, updates, rects_dev
+        self.kind = mqr.KINDS[kind]
+        self.elem = 4 if self.kind == mqr.MQR_OUT_CSR else 8
+        dev = rects_dev.device
+        self.out = torch.empty(1 << 20, dtype=torch.int32, device=dev)
+        self.copy_out = copy_out
+        self.host = torch.empty(1 << 20, dtype=torch.int32).pin_memory() if copy_out else None
+        self.copy_stream = torch.cuda.current_stream(dev)
+        self.ref = None
+
+    def answer(self, lo, hi):
+        torch, mqr = self.torch, self.mqr
+        st, cnt = mqr.mqr_tick(self.idx.ctx, self.rects[lo:hi], hi - lo, self.kind, self.out, self.out.numel() * 4)
+        if st == mqr.MQR_ERR_CAPACITY:
+            self.out = torch.empty(int(cnt * self.elem * 1.25) // 4 + 1024, dtype=torch.int32,
+                                   device=self.rects.device)
+            st, cnt = mqr.mqr_tick(self.idx.ctx, self.rects[lo:hi], hi - lo, self.kind, self.out,
+                                   self.out.numel() * 4)
+        mqr._check(st)
+        m = cnt * self.elem // 4
+        if self.copy_out and m:
+            if self.host.numel() < m:
+                self.host = torch.empty(int(m * 1.25) + 1024, dtype=torch.int32).pin_memory()
+            self.host[:m].copy_(self.out[:m], non_blocking=True)
+        ev = torch.cuda.Event(enable_timing=True)
+        ev.record(self.copy_stream)
+        ev.synchronize()
+        return hi - lo, cnt, ev
