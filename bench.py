@@ -566,6 +566,88 @@ def run_gpu(args, name):
     print(json.dumps(line), flush=True)
 
 
+def run_gpu_slots(args, name):
+    """--slots S: every step applies the tick's updates, takes one snapshot of
+    the state (mqr_snapshot) and answers the tick's queries split into S
+    consecutive parts on S join slots concurrently (mqr_slot_begin / _end),
+    each slot on its own stream; the step's CUDA events are recorded on the
+    context's stream, the end event after the stream has waited for every
+    slot.  Same workload, ticks and L2 flush as the plain bench."""
+    import torch
+    from paper_1411_3212_gb300 import mqr
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    w = WORKLOADS[name]
+    nmax, Q = w["n"], w["q"]
+    uniq = min(args.steps, args.unique_ticks)
+    ticks = gen_ticks(name, 0, args.warmup + uniq)
+    ids_d = torch.from_numpy(ticks[0].ids.view(np.int32)).to(dev)
+    xy_d = [torch.from_numpy(t.xy).to(dev) for t in ticks]
+    rect_d = [torch.from_numpy(t.rects).to(dev) for t in ticks]
+    flush = torch.empty(args.flush_mb * (1 << 20) // 4, dtype=torch.int32, device=dev)
+    S = args.slots
+    cut = [(Q * j) // S for j in range(S + 1)]
+    parts = [[r[cut[j]:cut[j + 1]] for j in range(S)] for r in rect_d]
+    idx = mqr.Index(bounds=(0.0, 0.0, 1.0, 1.0), leaf_cap=args.leaf_cap or w["cap"], max_objects=nmax)
+    stream = torch.cuda.current_stream()
+    slots = [idx.slot() for _ in range(S)]
+    kind = mqr.KINDS[args.kind]
+    elem = 4 if kind == mqr.MQR_OUT_CSR else 8
+    outs = [torch.empty(1 << 20, dtype=torch.int32, device=dev) for _ in range(S)]
+
+    def begin(i):
+        idx.apply_updates(ids_d, xy_d[i])
+        idx.snapshot()
+        for j in range(S):
+            slots[j].begin(parts[i][j], kind, outs[j], outs[j].numel() * 4)
+        for sl in slots:
+            stream.wait_stream(sl.stream)
+
+    def end(i):
+        """-> results of the step; a part cut by a too-small buffer grows it
+        and is answered again (on the same snapshot)."""
+        res = 0
+        for j in range(S):
+            adm, cnt = slots[j].end()
+            while adm < parts[i][j].shape[0]:
+                outs[j] = torch.empty(max(2 * outs[j].numel(), 1 << 20), dtype=torch.int32, device=dev)
+                slots[j].begin(parts[i][j], kind, outs[j], outs[j].numel() * 4)
+                adm, cnt = slots[j].end()
+            res += slots[j].stats()["n_results"]
+        return res
+
+    for i in range(args.warmup):
+        begin(i)
+        end(i)
+    torch.cuda.synchronize()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    clocks = Clocks(0)
+    clocks.start()
+    torch.cuda.synchronize()
+    results = 0
+    for k in range(args.steps):
+        i = args.warmup + (k % uniq)
+        flush.zero_()
+        evs[k][0].record(stream)
+        begin(i)
+        evs[k][1].record(stream)
+        results += end(i)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    step_ms = [a.elapsed_time(b) for a, b in evs]
+    for sl in slots:
+        sl.close()
+    idx.close()
+    srt = sorted(step_ms)
+    total = sum(step_ms)
+    print(json.dumps({"metric": "queries/s", "value": Q * args.steps / (total / 1000.0), "unit": "queries/s",
+                      "ms_per_step": total / args.steps, "steps": args.steps, "warmup": args.warmup,
+                      "tick_latency_ms": {"p50": srt[len(srt) // 2], "p99": srt[min(len(srt) - 1, int(0.99 * len(srt)))]},
+                      "config": {"workload": w["desc"], "slots": S, "output": args.kind,
+                                 "l2": "flushed (%d MB write) between timed steps" % args.flush_mb},
+                      "results_per_step": results / args.steps, "clocks": clk}), flush=True)
+
+
 def run_e2e(args, idx, ticks, kind, elem, Q, dev):
     """End to end through the host-buffer entry points: every step copies the
     tick's updates and queries in from pinned host memory and its output back
@@ -983,6 +1065,8 @@ def main():
     ap.add_argument("--no-covering", action="store_true",
                     help="ablation: no covering subqueries (every subquery goes through the containment tests)")
     ap.add_argument("--per-world", action="store_true", help="batched-256 worlds answered one context each")
+    ap.add_argument("--slots", type=int, default=0,
+                    help="answer each tick's queries split over this many concurrent join slots")
     ap.add_argument("--rate", type=float, default=5.0e6, help="served: query arrivals per second")
     ap.add_argument("--dt-ms", type=float, default=10.0, help="served: tick duration")
     ap.add_argument("--served-ticks", type=int, default=100)
@@ -1008,6 +1092,8 @@ def main():
         run_autotune(args)
     elif args.per_world:
         run_per_world(args)
+    elif args.slots > 0:
+        run_gpu_slots(args, args.workload)
     elif args.impl == "reference":
         run_reference(args, args.workload)
     else:

@@ -275,13 +275,14 @@ mqr_status mqr_tick_admit(mqr_ctx *ctx, const float *rects_dev, uint32_t Q, int 
  * first (else INVALID_ARG); position updates may be applied while joins run
  * (they belong to the next snapshot).
  *
- * mqr_slot_create: a slot of ctx (its own CUDA stream, about 16 bytes per
- * object of per-leaf lists, per-query buffers grown on demand).  Errors:
- * INVALID_ARG, OOM, CUDA.  mqr_slot_destroy: waits for the slot's work and
+ * mqr_slot_create: a slot of ctx working on cuda_stream (a cudaStream_t the
+ * caller owns, which should be another stream than the context's; NULL: the
+ * slot creates its own), with about 16 bytes per object of per-leaf lists
+ * and per-query buffers grown on demand.  Errors: INVALID_ARG, OOM, CUDA.  mqr_slot_destroy: waits for the slot's work and
  * frees it; NULL is a no-op.  Destroying a context makes its remaining slots
  * unusable (destroy them too).  Batched worlds are not supported by slots. */
 typedef struct mqr_slot mqr_slot;
-mqr_status mqr_slot_create(mqr_ctx *ctx, mqr_slot **out);
+mqr_status mqr_slot_create(mqr_ctx *ctx, void *cuda_stream, mqr_slot **out);
 void mqr_slot_destroy(mqr_slot *slot);
 mqr_status mqr_snapshot(mqr_ctx *ctx);
 

@@ -1450,7 +1450,7 @@ mqr_status mqr_snapshot(mqr_ctx *c) {
     return MQR_OK;
 }
 
-mqr_status mqr_slot_create(mqr_ctx *c, mqr_slot **out) {
+mqr_status mqr_slot_create(mqr_ctx *c, void *cuda_stream, mqr_slot **out) {
     if (!c || !out) return fail(MQR_ERR_INVALID_ARG, "NULL argument");
     *out = nullptr;
     if (c->parent) return fail(MQR_ERR_INVALID_ARG, "a slot cannot have slots");
@@ -1477,9 +1477,13 @@ mqr_status mqr_slot_create(mqr_ctx *c, mqr_slot **out) {
         return st;
     };
     cudaError_t e;
-    if ((e = cudaStreamCreateWithFlags(&sl->stream, cudaStreamNonBlocking)) != cudaSuccess)
-        return bail(e, "cudaStreamCreate");
-    sl->own_stream = true;
+    if (cuda_stream) {
+        sl->stream = reinterpret_cast<cudaStream_t>(cuda_stream);
+    } else {
+        if ((e = cudaStreamCreateWithFlags(&sl->stream, cudaStreamNonBlocking)) != cudaSuccess)
+            return bail(e, "cudaStreamCreate");
+        sl->own_stream = true;
+    }
     if ((e = cudaEventCreateWithFlags(&sl->slot_done, cudaEventDisableTiming)) != cudaSuccess)
         return bail(e, "cudaEventCreate");
     const size_t n = std::max<size_t>(c->nmax, 1);

@@ -115,7 +115,7 @@ def load(path: str = LIB_PATH):
         "mqr_get_sorted_async": ([P, P, u64, ctypes.POINTER(u64)], i32),
         "mqr_tick_admit": ([P, P, u32, i32, P, u64, ctypes.POINTER(u32), ctypes.POINTER(u64), P], i32),
         "mqr_snapshot": ([P], i32),
-        "mqr_slot_create": ([P, pctx], i32),
+        "mqr_slot_create": ([P, P, pctx], i32),
         "mqr_slot_destroy": ([P], None),
         "mqr_slot_begin": ([P, P, u32, i32, P, u64, P], i32),
         "mqr_slot_end": ([P, ctypes.POINTER(u32), ctypes.POINTER(u64)], i32),
@@ -248,9 +248,9 @@ def mqr_snapshot(ctx):
     _check(load().mqr_snapshot(ctx))
 
 
-def mqr_slot_create(ctx):
+def mqr_slot_create(ctx, cuda_stream=None):
     out = ctypes.c_void_p()
-    _check(load().mqr_slot_create(ctx, ctypes.byref(out)))
+    _check(load().mqr_slot_create(ctx, cuda_stream, ctypes.byref(out)))
     return out.value
 
 
@@ -280,11 +280,14 @@ def mqr_slot_get_stats(slot):
 
 class Slot:
     """A join slot of an Index (mqr_slot_*): answers batches against the
-    index's last snapshot on its own CUDA stream."""
+    index's last snapshot on its own CUDA stream (a torch stream: `stream`,
+    created if not given)."""
 
-    def __init__(self, index):
+    def __init__(self, index, stream=None):
+        import torch
         self.index = index
-        self.slot = mqr_slot_create(index.ctx)
+        self.stream = stream if stream is not None else torch.cuda.Stream(device=torch.cuda.current_device())
+        self.slot = mqr_slot_create(index.ctx, ctypes.c_void_p(self.stream.cuda_stream))
 
     def begin(self, rects, kind, out, capacity_bytes, offsets=None):
         mqr_slot_begin(self.slot, rects, int(rects.shape[0]), KINDS[kind] if isinstance(kind, str) else kind,
@@ -625,8 +628,8 @@ class Index:
     def snapshot(self):
         mqr_snapshot(self.ctx)
 
-    def slot(self):
-        return Slot(self)
+    def slot(self, stream=None):
+        return Slot(self, stream)
 
     def footprint(self):
         return mqr_result_footprint(self.ctx)
