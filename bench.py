@@ -2,7 +2,10 @@
 
 One step = one tick of the whole hot path: the tick's position updates of
 every object (mqr_apply_updates) followed by the spatial join of the tick's
-queries through the PR-quadtree (mqr_tick), pair-list output.
+queries through the PR-quadtree (mqr_tick), pair-list output; the tick's
+kernels are replayed as one captured CUDA graph (mqr_set_graph; --no-graph:
+plain launches), with CUDA events around the dominant phase as event nodes
+of the graph.
 
 Default workload (N=1): 4,000,000 objects, 90% in 64 Gaussian hotspots (sigma
 log-uniform 0.002-0.02) and 10% uniform, random walk sigma 0.0005 with
@@ -173,10 +176,10 @@ def read_peaks():
 
 
 def read_traffic(kernel, results_per_launch):
-    """Per-launch DRAM bytes of `kernel` from the committed ncu summary, scaled
-    by the results the timed launches processed (the captured launch is a
-    different tick), if the CUDA sources have not changed since it was taken
-    (else None)."""
+    """Per-launch DRAM bytes of `kernel` from the committed ncu summary (a
+    smaller case of the same workload recipe), scaled by the results the
+    timed launches processed, if the CUDA sources have not changed since it
+    was taken (else None)."""
     try:
         kv = {}
         with open(TRAFFIC_FILE) as f:
@@ -185,8 +188,7 @@ def read_traffic(kernel, results_per_launch):
                 if line and not line.startswith("#") and "=" in line:
                     k, v = line.split("=", 1)
                     kv[k.strip()] = v.strip()
-        if (kv.get("kernel") == kernel and kernel in KERNEL_SOURCES and kv.get("source_hash") == source_hash(kernel)
-                and kv.get("workload") == "hotspot4m"):
+        if kv.get("kernel") == kernel and kernel in KERNEL_SOURCES and kv.get("source_hash") == source_hash(kernel):
             return float(kv["dram_bytes_per_launch"]) * results_per_launch / float(kv["results"])
     except Exception:
         pass
@@ -436,11 +438,12 @@ def run_gpu(args, name):
     cand = {p: calib["ms"][p] for p in calib_bytes if calib["launches"].get(p, 0) > 0}
     if cand:
         dom = max(cand, key=cand.get)
+    idx.set_timing(True, phases=[dom])
     if args.graph:
-        idx.set_timing(False)
-        for k in range(2):                               # capture the tick's graph before the timed region
+        # capture the tick's graph (with the dominant phase's event nodes)
+        # before the timed region, then restart the accumulators
+        for k in range(2):
             step(args.warmup + (k % uniq))
-    else:
         idx.set_timing(True, phases=[dom])
     clocks = Clocks(local if world > 1 else 0)
     stream = torch.cuda.current_stream()
@@ -448,7 +451,17 @@ def run_gpu(args, name):
     bytes_acc = {}
     fp_acc = {}
     results = 0
+    # the clock sampler starts under the same tick load about 0.25 s before
+    # the timed region (a timed region of 20 ticks lasts ~40 ms, one or two
+    # samples); those ticks are untimed and their accumulators are reset
     clocks.start()
+    t_pre = time.perf_counter()
+    k = 0
+    while time.perf_counter() - t_pre < args.clock_lead_s:
+        flush.zero_()
+        step(args.warmup + (k % uniq))
+        k += 1
+    idx.set_timing(True, phases=[dom])
     barrier(dist, dev)
     t_wall = time.perf_counter()
     for k in range(args.steps):
@@ -478,10 +491,6 @@ def run_gpu(args, name):
     value = world * Q * args.steps / (total_ms / 1000.0)
 
     # roofline of the dominant kernel phase, timed live in the timed region
-    if args.graph:          # graph replay: no events in the timed region; the calibration ticks' launches
-        per_tick = sum(calib["launches"].values()) / max(calib["ticks"], 1)
-        timing = {"ms": {p: 0.0 for p in mqr.PHASES}, "launches": {p: 0 for p in mqr.PHASES}, "ticks": args.steps}
-        timing["launches"]["emit"] = int(round(per_tick * args.steps))
     launches = max(timing["launches"][dom], 1)
     per_launch_ms = timing["ms"][dom] / launches
     per_launch_bytes = bytes_acc[dom] / launches
@@ -501,6 +510,9 @@ def run_gpu(args, name):
                 "peak_nominal": NOMINAL_HBM_GBS, "frac_nominal": achieved / NOMINAL_HBM_GBS,
                 "peak_source": "%s (MEASURED_PEAKS.json hbm_gbs)" % peak_kind if peak_kind == "measured" else "fallback 6.8 TB/s",
                 "traffic": traffic,
+                "traffic_from": "ncu dram__bytes_read.sum + dram__bytes_write.sum of one emit launch at hotspot-2M "
+                                "(profiles/emit_kernel_traffic.txt), scaled by the timed launches' results"
+                                if traffic else None,
                 "frac_dram": traffic_gbs / peak if traffic_gbs else None,
                 "algorithmic_bytes_per_launch": per_launch_bytes, "launch_ms": per_launch_ms,
                 "launches": launches,
@@ -545,11 +557,12 @@ def run_gpu(args, name):
                    "covering": "on" if covering else "off (every subquery tested)",
                    "output": args.kind, "parallelism": "replicas" if world > 1 else "single-gpu",
                    "l2": "flushed (%d MB write) between timed steps" % args.flush_mb,
+                   "launch": "one captured CUDA graph per tick (replayed)" if args.graph else "plain kernel launches",
                    "ticks": "%d distinct generated ticks, cycled over the %d timed steps" % (uniq, args.steps)},
         "tick_latency_ms": {"p50": srt[len(srt) // 2], "p99": srt[min(len(srt) - 1, int(0.99 * len(srt)))],
                             "max": srt[-1]},
         "join_kernels": {"phases": join, "GB/s": join_gbs, "frac_of_peak": join_gbs / peak},
-        "roofline": None if args.graph else roofline,
+        "roofline": roofline,
         "cpu_baseline": cpu,
         "e2e": e2e,
         "e2e_covering_compressed": e2e_runs,
@@ -557,6 +570,8 @@ def run_gpu(args, name):
         "launches_between_steps": "per step, after its end event: the L2 flush and the two footprint-statistics "
                                   "kernels of mqr_result_footprint (not in gpu_launches or the step times)",
         "clocks": clk,
+        "clocks_window": "nvidia-smi sampled every 25 ms from %.2f s of untimed ticks before the timed region to its "
+                         "end" % args.clock_lead_s,
         "phases": phases,
         "phases_from": "%d untimed calibration ticks with events around every phase (the timed region records "
                        "events around the %s phase only)" % (max(args.calib_ticks, 1), dom),
@@ -858,6 +873,23 @@ def run_autotune(args):
             ts.append(a.elapsed_time(b))
         return float(np.mean(ts))
     tuned_ms = timed(idx)
+    world = None
+    if batched:
+        # per-world capacities: worlds labelled by kind (even: uniform, odd: 8 hotspots) and size
+        from paper_1411_3212_gb300.autotune import tune_world_caps
+        sizes = np.diff(ticks[0].obj_base.astype(np.int64))
+        labels = ["%s-%s" % ("uniform" if wi % 2 == 0 else "hotspot",
+                             "small" if n < 8192 else ("mid" if n < 65536 else "large"))
+                  for wi, n in enumerate(sizes)]
+        wbits = 0
+        while 4 ** wbits < len(sizes):
+            wbits += 1
+        best_w, _, wtable = tune_world_caps(idx, dticks, wbits, labels, caps=(32, 64, 128, 256, 512), reps=1)
+        world_ms = timed(idx)
+        idx.set_region_caps(0)
+        world = {"labels": "kind (uniform / 8-hotspot) x size (< 8,192, < 65,536, more objects)",
+                 "capacity_per_label": best_w, "ms": world_ms, "evaluations": len(wtable),
+                 "worlds_per_label": {l: labels.count(l) for l in sorted(set(labels))}}
     idx.close()
     base = mk(w["cap"])
     for ids, xy, rects in dticks:
@@ -869,6 +901,7 @@ def run_autotune(args):
             "config": {"workload": w["desc"], "steps": args.steps,
                        "l2": "flushed (%d MB write) before every timed tick" % args.flush_mb},
             "configured_ms": base_ms, "tuned_ms": tuned_ms, "leaf_cap": best_cap, "blocks_per_sm": best_launch,
+            "per_world_caps": world,
             "leaf_cap_table": {str(c): v["ms_per_tick"] for c, v in cap_table.items()},
             "launch_table": [{"config": c, "ms": ms} for c, ms, _ in launch_table]}
     print(json.dumps(line), flush=True)
@@ -939,8 +972,8 @@ def run_costmodel(args):
     same ticks."""
     import torch
     from paper_1411_3212_gb300 import mqr
-    from paper_1411_3212_gb300.costmodel import (GRID, QUAD, REGIONS, WORK_KINDS, IndexChooser, RegionChooser,
-                                                 mean_log2_side)
+    from paper_1411_3212_gb300.costmodel import (GRID, QUAD, REGIONS, WORK_KINDS, ArgminChooser, IndexChooser,
+                                                 RegionChooser, mean_log2_side)
     dev = torch.device("cuda", 0)
     torch.cuda.set_device(dev)
     name = args.workload
@@ -990,6 +1023,17 @@ def run_costmodel(args):
         ch.record(c, nmax, Q, sides[i], ms)
         chosen.append(c)
         times.append(ms)
+    # the same candidates chosen by the argmin of their measured times (no network)
+    ach = ArgminChooser(candidates=cands, fallback=(QUAD, w["cap"]), seed=0)
+    achosen, atimes = [], []
+    for k in range(args.steps):
+        i = args.warmup + (k % uniq)
+        c = ach.choose(nmax, Q, sides[i])
+        ach.apply(idx, c)
+        ms = timed(i)
+        ach.record(c, nmax, Q, sides[i], ms)
+        achosen.append(c)
+        atimes.append(ms)
     # node level: per-region capacities from the MLP over region features
     rch = RegionChooser(region_bits=args.region_bits, fallback=w["cap"], seed=0)
     rtimes = []
@@ -1012,9 +1056,11 @@ def run_costmodel(args):
         if c[0] == GRID:
             return "grid level %d" % c[1]
         return "regions %d: cap 2^(%g %+g log2 density)" % (c[1], c[2], c[3])
-    counts = {}
+    counts, acounts = {}, {}
     for c in chosen[-tail:]:
         counts[label(c)] = counts.get(label(c), 0) + 1
+    for c in achosen[-tail:]:
+        acounts[label(c)] = acounts.get(label(c), 0) + 1
     explored = {}
     for c, ms in zip(chosen[:2 * len(cands)], times[:2 * len(cands)]):   # the round-robin exploration
         explored.setdefault(label(c), []).append(ms)
@@ -1025,6 +1071,9 @@ def run_costmodel(args):
             "explore_ms_mean": float(np.mean(times[:2 * len(cands)])), "chosen_last_half": counts,
             "explored_ms": {k: float(np.mean(v)) for k, v in explored.items()},
             "model_loss": getattr(ch, "loss", None),
+            "argmin": {"what": "the same candidates, exploration and exploration rate; the candidate with the smallest "
+                               "mean measured time (no network)",
+                       "ms_mean": float(np.mean(atimes[-tail:])), "chosen_last_half": acounts},
             "regions": {"region_bits": args.region_bits, "ms_mean": float(np.mean(rtimes[-tail:])),
                         "explore_ms_mean": float(np.mean(rtimes[:rch.explore_ticks])),
                         "capacities_last_tick": {str(int(c)): int((final_caps == c).sum())
@@ -1053,13 +1102,17 @@ def main():
                     help="--impl reference: queries joined per step (of the tick's queries)")
     ap.add_argument("--leaf-cap", type=int, default=0, help="override the workload's leaf capacity")
     ap.add_argument("--index", default="quad", choices=["quad", "ug"], help="quadtree or uniform grid")
-    ap.add_argument("--graph", action="store_true", help="replay the tick as a captured CUDA graph")
+    ap.add_argument("--no-graph", action="store_true",
+                    help="plain kernel launches instead of replaying each tick as one captured CUDA graph")
+    ap.add_argument("--graph", action="store_true", help="(the default) replay the tick as a captured CUDA graph")
     ap.add_argument("--grid-level", type=int, default=8, help="uniform grid: 2^level cells per axis")
     ap.add_argument("--served", action="store_true", help="run the served stream instead")
     ap.add_argument("--costmodel", action="store_true", help="learned per-tick index choice vs fixed")
     ap.add_argument("--region-bits", type=int, default=3, help="--costmodel: depth of the node-level regions")
     ap.add_argument("--autotune", action="store_true",
                     help="tune the leaf capacity and the work-item kernels' launch shapes on the workload")
+    ap.add_argument("--clock-lead-s", type=float, default=0.25,
+                    help="seconds of untimed ticks under the clock sampler before the timed region")
     ap.add_argument("--calib-ticks", type=int, default=5,
                     help="untimed ticks with events around every phase (the per-phase breakdown)")
     ap.add_argument("--no-covering", action="store_true",
@@ -1081,6 +1134,7 @@ def main():
                     help="served: queries offered per tick, x the mean arrivals per tick (0: whole queue)")
     ap.add_argument("--no-copy-out", action="store_true", help="served: keep each tick's output on the device")
     args = ap.parse_args()
+    args.graph = not args.no_graph
     if args.warmup < 3:
         log("warm-up raised to 3 steps")
         args.warmup = 3

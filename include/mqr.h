@@ -314,9 +314,13 @@ mqr_status mqr_slot_get_stats(const mqr_slot *slot, mqr_stats *out);
  * into a CUDA graph and the graph is replayed by later ticks with the same
  * arguments (rects_dev, Q, kind, out_dev, capacity, offsets_dev) while no
  * internal buffer was reallocated; anything else captures again.  Results
- * are identical to the plain launches.  Phase timing (mqr_set_timing) turns
- * replay off while enabled.  enable = 0 frees the graph.  Library design
- * convenience, not a step of the method. */
+ * are identical to the plain launches.  Phase timing (mqr_set_timing,
+ * mqr_set_timing_phases) works under replay: the timed phases' event records
+ * are event-record nodes of the captured graph, recorded by every replay (a
+ * change of the timed phases captures again).  Ticks with slots on the
+ * context, admission (mqr_tick_admit) or the sorted kinds' output sort run as
+ * plain launches.  enable = 0 frees the graph.  Library design convenience,
+ * not a step of the method. */
 mqr_status mqr_set_graph(mqr_ctx *ctx, int enable);
 
 /* Batched independent worlds in one index (many small instances of the

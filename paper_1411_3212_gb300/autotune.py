@@ -90,3 +90,50 @@ def tune_launch_config(idx, ticks, options=(2, 4, 8, 16), kind="pairs", reps=2, 
         best[k] = min(timings, key=timings.get)
     idx.set_launch_config(**best)
     return best, table
+
+
+def tune_world_caps(idx, ticks, world_bits, classes, caps=(32, 64, 128, 256, 512), kind="pairs", reps=2,
+                    timer=None, start=128, sweeps=1):
+    """Per-world leaf capacities of batched worlds.  World w's quadtree is
+    the node of depth world_bits whose Morton prefix is w (mqr_set_worlds),
+    so the per-region capacities of mqr_set_region_caps at region_bits =
+    world_bits give every world its own th_quad.  classes[w] labels world w
+    (worlds of one label share a capacity); coordinate descent over the
+    labels: each label in turn takes the capacity in `caps` with the smallest
+    tick time, the others held (`sweeps` passes).  Results must not change.
+    timer(idx, ticks, kind, reps) -> (ms per tick, results) as for
+    tune_launch_config.  Returns (best capacity per label, the capacity of
+    every region, table of (assignment, ms, results))."""
+    import numpy as np
+    timer = timer or _time_ticks
+    classes = list(classes)
+    labels = sorted(set(classes))
+    n_regions = 4 ** world_bits
+    if len(classes) > n_regions:
+        raise ValueError("more worlds than regions of depth world_bits")
+
+    def region_vector(assign):
+        v = np.full(n_regions, start, np.uint32)
+        for w, c in enumerate(classes):
+            v[w] = assign[c]
+        return v
+
+    best = {c: start for c in labels}
+    table, res0 = [], None
+    for _ in range(sweeps):
+        for c in labels:
+            timings = {}
+            for cap in caps:
+                assign = dict(best, **{c: cap})
+                idx.set_region_caps(world_bits, region_vector(assign))
+                ms, res = timer(idx, ticks, kind, reps)
+                if res0 is None:
+                    res0 = res
+                if res != res0:
+                    raise RuntimeError("per-world capacities changed the results")
+                timings[cap] = ms
+                table.append((assign, ms, res))
+            best[c] = min(timings, key=timings.get)
+    vec = region_vector(best)
+    idx.set_region_caps(world_bits, vec)
+    return best, vec, table

@@ -108,26 +108,71 @@ class IndexChooser:
             self.trained = True
 
     def apply(self, idx, cand):
-        """Configure the index for the next tick (between ticks: leaves are
-        rebuilt every tick, results never change)."""
-        kind = cand[0]
-        if kind == REGIONS:
-            _, rb, a, b = cand
-            try:
-                counts = idx.region_counts(rb)          # densities of the previous tick
-            except mqr.MqrError:                        # no tick yet: one capacity
-                counts = np.ones(4 ** rb, np.uint32)
-            idx.set_index(QUAD, leaf_cap=int(min(2 ** a, MAX_REGION_CAP)))
-            idx.set_region_caps(rb, region_caps(counts, rb, a, b))
-            return
-        idx.set_region_caps(0)
-        if kind == QUAD:
-            idx.set_index(QUAD, leaf_cap=cand[1])
-        else:
-            idx.set_index(GRID, grid_level=cand[1])
+        apply_config(idx, cand)
 
     def close(self):
         self.model.close()
+
+
+class ArgminChooser:
+    """The same choice without a network, as the learned chooser's baseline:
+    the same round-robin exploration and exploration rate, then the candidate
+    whose measured tick times (its last `window` records) have the smallest
+    mean.  It knows only the configurations it has timed, on the conditions
+    under which it timed them; the network also predicts from the tick's
+    features."""
+
+    def __init__(self, candidates=((QUAD, 64), (QUAD, 128), (QUAD, 256), (QUAD, 512)),
+                 fallback=(QUAD, 128), explore_rounds=2, epsilon=0.1, window=8, seed=0):
+        self.cands = [tuple(c) for c in candidates]
+        self.fallback = tuple(fallback)
+        self.explore_rounds = explore_rounds
+        self.epsilon = epsilon
+        self.window = window
+        self.rng = np.random.default_rng(seed)
+        self.times = {c: [] for c in self.cands}
+        self.n_choices = 0
+
+    def choose(self, n_objects=0, n_queries=0, mean_log2_side=0.0):
+        k = self.n_choices
+        self.n_choices += 1
+        if k < self.explore_rounds * len(self.cands):                 # round-robin exploration
+            return self.cands[k % len(self.cands)]
+        if self.rng.random() < self.epsilon:
+            return self.cands[int(self.rng.integers(len(self.cands)))]
+        timed = [c for c in self.cands if self.times[c]]
+        if not timed:
+            return self.fallback
+        return min(timed, key=lambda c: float(np.mean(self.times[c][-self.window:])))
+
+    def record(self, cand, n_objects, n_queries, mean_log2_side, ms):
+        self.times[tuple(cand)].append(float(ms))
+
+    def apply(self, idx, cand):
+        apply_config(idx, cand)
+
+    def close(self):
+        pass
+
+
+def apply_config(idx, cand):
+    """Configure the index for the next tick (between ticks: leaves are
+    rebuilt every tick, results never change)."""
+    kind = cand[0]
+    if kind == REGIONS:
+        _, rb, a, b = cand
+        try:
+            counts = idx.region_counts(rb)          # densities of the previous tick
+        except mqr.MqrError:                        # no tick yet: one capacity
+            counts = np.ones(4 ** rb, np.uint32)
+        idx.set_index(QUAD, leaf_cap=int(min(2 ** a, MAX_REGION_CAP)))
+        idx.set_region_caps(rb, region_caps(counts, rb, a, b))
+        return
+    idx.set_region_caps(0)
+    if kind == QUAD:
+        idx.set_index(QUAD, leaf_cap=cand[1])
+    else:
+        idx.set_index(GRID, grid_level=cand[1])
 
 
 # Phases whose time depends on the split thresholds (the rest -- updates,

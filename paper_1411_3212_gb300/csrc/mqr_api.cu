@@ -131,18 +131,40 @@ struct mqr_ctx {
     DevBuf<unsigned long long> upd_err;  // sticky error word of the update kernels
     // captured tick (mqr_set_graph): replayed while its inputs are unchanged
     bool graph_on = false;
-    cudaGraphExec_t gexec = nullptr;
+    // captured ticks, replayed while their inputs are unchanged: a few are
+    // kept (least recently used evicted), so that ticks alternating between
+    // output buffers (the two staging buffers of the asynchronous host path)
+    // replay too
+    static constexpr int kGraphCache = 4;
     struct GraphKey {
         const void *rects, *out, *offsets;
         unsigned long long Q, out_cap, gen, n_worlds;
         int emit_kind;
+        uint32_t timing_mask;       // phases timed by event nodes of the graph (0: none)
         bool operator==(const GraphKey &o) const {
             return rects == o.rects && out == o.out && offsets == o.offsets && Q == o.Q &&
-                   out_cap == o.out_cap && gen == o.gen && n_worlds == o.n_worlds && emit_kind == o.emit_kind;
+                   out_cap == o.out_cap && gen == o.gen && n_worlds == o.n_worlds && emit_kind == o.emit_kind &&
+                   timing_mask == o.timing_mask;
         }
-    } gkey{};
-    Caps gcaps{};
+    };
+    struct GraphEntry {
+        GraphKey key{};
+        cudaGraphExec_t exec = nullptr;
+        Caps caps{};
+        bool ev_phase[MQR_NUM_PHASES] = {};
+        uint64_t ev_launches[MQR_NUM_PHASES] = {};
+        uint64_t launches[MQR_NUM_PHASES] = {};
+        unsigned long long used = 0;
+    } graphs[kGraphCache];
+    unsigned long long graph_clock = 0;
     unsigned long long graph_replays = 0, graph_captures = 0;
+    // phase timing inside a captured tick: the timed phases' events are
+    // external event-record nodes of the graph (recorded by every replay);
+    // the other phases' launches are counted once at capture and added per replay
+    bool capturing = false;
+    bool graph_ev_phase[MQR_NUM_PHASES] = {};
+    uint64_t graph_ev_launches[MQR_NUM_PHASES] = {};
+    uint64_t graph_launches[MQR_NUM_PHASES] = {};
     // batched independent worlds (mqr_set_worlds): id and query ranges per world
     uint32_t n_worlds = 0, world_bits = 0;
     DevBuf<uint32_t> world_obj, world_q;
@@ -249,18 +271,50 @@ mqr_status check_launch(const char *what) {
 
 // Phase timing: events around the kernels of the phases in timing_mask;
 // launches are counted for every phase while timing is on.
+// While a tick is captured into a graph, the records become external
+// event-record nodes, so that every replay records them.
+void record_phase_event(mqr_ctx *c, cudaEvent_t ev) {
+    if (c->capturing) cudaEventRecordWithFlags(ev, c->stream, cudaEventRecordExternal);
+    else cudaEventRecord(ev, c->stream);
+}
 void phase_begin(mqr_ctx *c, int p) {
     if (!c->timing || !(c->timing_mask & (1u << p))) return;
-    cudaEventRecord(c->ev[p][0], c->stream);
+    record_phase_event(c, c->ev[p][0]);
 }
 void phase_end(mqr_ctx *c, int p, uint64_t launches) {
     if (!c->timing) return;
     if (c->timing_mask & (1u << p)) {
-        cudaEventRecord(c->ev[p][1], c->stream);
-        c->ev_used[p] = true;
-        c->ev_launches[p] = launches;
+        record_phase_event(c, c->ev[p][1]);
+        if (c->capturing) {
+            c->graph_ev_phase[p] = true;
+            c->graph_ev_launches[p] = launches;
+        } else {
+            c->ev_used[p] = true;
+            c->ev_launches[p] = launches;
+        }
+    } else if (c->capturing) {
+        c->graph_launches[p] += launches;
     } else {
         c->acc.launches[p] += launches;
+    }
+}
+// After a graph launch: the replay recorded the timed phases' events and
+// launched the captured kernels.
+void phases_replayed(mqr_ctx *c, const mqr_ctx::GraphEntry &g) {
+    if (!c->timing) return;
+    for (int p = 0; p < MQR_NUM_PHASES; ++p) {
+        if (g.ev_phase[p]) {
+            c->ev_used[p] = true;
+            c->ev_launches[p] = g.ev_launches[p];
+        }
+        c->acc.launches[p] += g.launches[p];
+    }
+}
+
+void free_graphs(mqr_ctx *c) {
+    for (auto &g : c->graphs) {
+        if (g.exec) cudaGraphExecDestroy(g.exec);
+        g = mqr_ctx::GraphEntry{};
     }
 }
 // Called after the stream has been synchronised: fold the recorded phases
@@ -551,7 +605,7 @@ mqr_status enqueue_or_replay(mqr_ctx *c, const float4 *rects, uint32_t Q, int em
                              unsigned long long out_cap_elems, unsigned long long *offsets, const Arena &a,
                              Caps &caps, bool admit) {
     // slots wait on the index build through events, which a replayed graph does not record
-    if (!c->graph_on || c->timing || g_stall_scan.load() || !c->slots.empty() || admit)
+    if (!c->graph_on || g_stall_scan.load() || !c->slots.empty() || admit)
         return enqueue_tick(c, rects, Q, emit_kind, out, out_cap_elems, offsets, a, caps, admit);
     // The captured tick reads the queries from the context's own buffer, so a
     // caller that passes each tick's queries in a different buffer still
@@ -562,14 +616,24 @@ mqr_status enqueue_or_replay(mqr_ctx *c, const float4 *rects, uint32_t Q, int em
         MQR_CUDA(cudaMemcpyAsync(c->q_rects.p, rects, (size_t)Q * sizeof(float4), cudaMemcpyDeviceToDevice,
                                  c->stream));
     rects = staged;
-    const mqr_ctx::GraphKey key{rects, out, offsets, Q, out_cap_elems, g_buf_gen.load(), c->n_worlds, emit_kind};
-    if (!c->gexec || !(key == c->gkey)) {
-        if (c->gexec) {
-            cudaGraphExecDestroy(c->gexec);
-            c->gexec = nullptr;
-        }
+    const mqr_ctx::GraphKey key{rects, out, offsets, Q, out_cap_elems, g_buf_gen.load(), c->n_worlds, emit_kind,
+                                c->timing ? c->timing_mask : 0u};
+    mqr_ctx::GraphEntry *ge = nullptr;
+    for (auto &g : c->graphs)
+        if (g.exec && g.key == key) ge = &g;
+    if (!ge) {
+        ge = &c->graphs[0];                   // a free entry, else the least recently used
+        for (auto &g : c->graphs)
+            if (!g.exec || (ge->exec && g.used < ge->used)) ge = &g;
+        if (ge->exec) cudaGraphExecDestroy(ge->exec);
+        *ge = mqr_ctx::GraphEntry{};
         MQR_CUDA(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeRelaxed));
+        std::memset(c->graph_ev_phase, 0, sizeof(c->graph_ev_phase));
+        std::memset(c->graph_ev_launches, 0, sizeof(c->graph_ev_launches));
+        std::memset(c->graph_launches, 0, sizeof(c->graph_launches));
+        c->capturing = true;
         mqr_status s = enqueue_tick(c, rects, Q, emit_kind, out, out_cap_elems, offsets, a, caps, false);
+        c->capturing = false;
         cudaGraph_t g = nullptr;
         cudaError_t e = cudaStreamEndCapture(c->stream, &g);
         if (s != MQR_OK) {
@@ -577,20 +641,25 @@ mqr_status enqueue_or_replay(mqr_ctx *c, const float4 *rects, uint32_t Q, int em
             return s;
         }
         if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
-        e = cudaGraphInstantiate(&c->gexec, g, 0);
+        e = cudaGraphInstantiate(&ge->exec, g, 0);
         cudaGraphDestroy(g);
         if (e != cudaSuccess) {
-            c->gexec = nullptr;
+            ge->exec = nullptr;
             return cuda_fail(e, "cudaGraphInstantiate");
         }
-        c->gkey = key;
-        c->gcaps = caps;
+        ge->key = key;
+        ge->caps = caps;
+        std::memcpy(ge->ev_phase, c->graph_ev_phase, sizeof(ge->ev_phase));
+        std::memcpy(ge->ev_launches, c->graph_ev_launches, sizeof(ge->ev_launches));
+        std::memcpy(ge->launches, c->graph_launches, sizeof(ge->launches));
         ++c->graph_captures;
     } else {
-        caps = c->gcaps;
+        caps = ge->caps;
         ++c->graph_replays;
     }
-    MQR_CUDA(cudaGraphLaunch(c->gexec, c->stream));
+    ge->used = ++c->graph_clock;
+    MQR_CUDA(cudaGraphLaunch(ge->exec, c->stream));
+    phases_replayed(c, *ge);
     return MQR_OK;
 }
 
@@ -1064,8 +1133,7 @@ void mqr_destroy(mqr_ctx *c) {
     c->snap_info.release();
     DevBuf<float2> *f2[] = {&c->pos, &c->sxy, &c->up_xy};
     for (auto *b : f2) b->release();
-    if (c->gexec) cudaGraphExecDestroy(c->gexec);
-    c->gexec = nullptr;
+    free_graphs(c);
     c->world_obj.release();
     c->world_q.release();
     c->region_cap.release();
@@ -1249,10 +1317,7 @@ mqr_status mqr_set_graph(mqr_ctx *c, int enable) {
     MQR_CUDA(cudaSetDevice(c->device));
     MQR_CUDA(cudaStreamSynchronize(c->stream));
     c->graph_on = enable != 0;
-    if (!c->graph_on && c->gexec) {
-        cudaGraphExecDestroy(c->gexec);
-        c->gexec = nullptr;
-    }
+    if (!c->graph_on) free_graphs(c);
     return MQR_OK;
 }
 

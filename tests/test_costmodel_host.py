@@ -197,3 +197,56 @@ def test_launch_autotuner_coordinate_descent():
     bad = FakeIndex()
     with pytest.raises(RuntimeError):
         tune_launch_config(bad, [None], options=(2, 8), timer=lambda i, t, k, r: (1.0, i.cfg["candidate"]))
+
+
+def test_argmin_chooser_picks_the_cheapest_measured_configuration():
+    """The network-free baseline: the same two exploration rounds, then the
+    configuration with the smallest mean measured time; with no record of a
+    candidate it falls back."""
+    from paper_1411_3212_gb300.costmodel import GRID, QUAD, ArgminChooser
+    cost = {(QUAD, 128): 1.9, (QUAD, 256): 1.7, (GRID, 8): 2.4}
+    ch = ArgminChooser(candidates=list(cost), seed=1, epsilon=0.0)
+    rng = np.random.default_rng(3)
+    picks = []
+    for k in range(20):
+        c = ch.choose()
+        ch.record(c, 0, 0, 0.0, cost[c] * (1 + 0.01 * rng.normal()))
+        picks.append(c)
+    assert picks[:6] == list(cost) * 2
+    assert picks[-10:] == [(QUAD, 256)] * 10
+    # a drift that makes another configuration cheaper is seen only through what is re-timed
+    fresh = ArgminChooser(candidates=list(cost), explore_rounds=0, epsilon=0.0, fallback=(GRID, 8))
+    assert fresh.choose() == (GRID, 8)
+
+
+def test_world_capacity_tuner_coordinate_descent():
+    """Per-world capacities: every label takes the capacity of the smallest
+    time with the others held; worlds get their label's capacity in their
+    region (world w = region w at depth world_bits); the results stay fixed."""
+    from paper_1411_3212_gb300.autotune import tune_world_caps
+    optimum = {"small": 64, "big": 512}
+    classes = ["small", "big", "small", "big", "big"]        # 5 worlds, world_bits 2 (16 regions)
+
+    class FakeIndex:
+        caps = None
+
+        def set_region_caps(self, bits, caps):
+            assert bits == 2 and len(caps) == 16
+            self.caps = np.array(caps)
+
+    def timer(idx, ticks, kind, reps):
+        ms = 0.0
+        for w, c in enumerate(classes):
+            ms += abs(np.log2(idx.caps[w]) - np.log2(optimum[c]))
+        return 1.0 + ms, 12345
+    fi = FakeIndex()
+    best, vec, table = tune_world_caps(fi, [], 2, classes, caps=(32, 64, 128, 256, 512), timer=timer)
+    assert best == optimum
+    assert list(vec[:5]) == [64, 512, 64, 512, 512] and list(vec[5:]) == [128] * 11
+    assert list(fi.caps) == list(vec)
+    assert len(table) == 10
+
+    def bad_timer(idx, ticks, kind, reps):
+        return 1.0, int(idx.caps[0])
+    with pytest.raises(RuntimeError, match="changed the results"):
+        tune_world_caps(FakeIndex(), [], 2, classes, timer=bad_timer)

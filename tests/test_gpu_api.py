@@ -321,6 +321,43 @@ def test_graph_mode_replays_identical_results():
     plain.close()
 
 
+def test_phase_timing_under_graph_replay():
+    """Graph mode with phase timing: the timed phase's events are event nodes
+    of the captured graph, so every replayed tick adds its time and launch
+    counts (the same counts as plain launches), and the results stay those
+    of the plain launches and the oracle."""
+    torch, dev = torch_dev()
+    from paper_1411_3212_gb300 import mqr
+    w = workloads.HotspotWalk(n=20000, q=1500, hotspots=4, side_lo=0.002, side_hi=0.04, seed=32)
+    ticks = [w.next_tick() for _ in range(5)]
+    g = mqr.Index(bounds=(0.0, 0.0, 1.0, 1.0), leaf_cap=32, max_objects=20000)
+    plain = mqr.Index(bounds=(0.0, 0.0, 1.0, 1.0), leaf_cap=32, max_objects=20000)
+    g.set_graph(True)
+    for idx in (g, plain):
+        idx.set_timing(True, phases=["emit"])
+    st = oracle.State(20000)
+    for k, t in enumerate(ticks):
+        rd = to_dev(t.rects, dev)
+        st.apply_updates(t.ids, t.xy)
+        outs = []
+        for idx in (g, plain):
+            idx.apply_updates(to_dev(t.ids, dev), to_dev(t.xy, dev))
+            res, off = idx.tick(rd, kind="pairs")
+            outs.append((res.cpu().numpy().copy(), off.cpu().numpy().copy()))
+        np.testing.assert_array_equal(outs[0][0], outs[1][0])
+        np.testing.assert_array_equal(outs[0][1], outs[1][1])
+        woff, _ = oracle.join_grid(st, t.rects, cell_side=0.01)
+        np.testing.assert_array_equal(outs[0][1].view(np.uint64), woff)
+    tg, tp = g.timing(), plain.timing()
+    assert tg["ticks"] == tp["ticks"] >= len(ticks)       # (an output buffer that grew answers a tick again)
+    assert tg["launches"] == tp["launches"]
+    assert tg["launches"]["emit"] >= len(ticks)
+    assert tg["ms"]["emit"] > 0.0 and tg["ms"]["filter"] == 0.0     # only the timed phase has events
+    g.set_graph(False)
+    g.close()
+    plain.close()
+
+
 def test_async_host_ticks_overlap_and_match_the_oracle():
     """mqr_tick_host_async: four ticks in a row, each copying into its own
     page-locked host buffer while the next runs; after mqr_host_wait every
