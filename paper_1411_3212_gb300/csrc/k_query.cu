@@ -333,6 +333,12 @@ cand_count_kernel(int covering, const uint32_t *__restrict__ tile_p0, const uint
         unsigned long long t = (blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x) >> 5;
         PairLoad cur{};
         if (t < ntiles) cur = pair_load(t, npairs, tile_p0, pair_q, pair_first, pair_blo, pair_off);
+        // the record of the previous tile, written one iteration later so that
+        // the latency of its leaf-list atomic (or of its run's leaf bounds)
+        // overlaps this tile's loads and classification
+        bool pend = false;
+        uint32_t pend_slot = 0;
+        uint4 pend_rec = make_uint4(0u, 0u, 0u, 0u);
         for (; t < ntiles; t += nw) {
             PairLoad nxt = cur;                   // the next tile's pairs, loaded before this tile is used
             if (t + nw < ntiles) nxt = pair_load(t + nw, npairs, tile_p0, pair_q, pair_first, pair_blo, pair_off);
@@ -343,23 +349,28 @@ cand_count_kernel(int covering, const uint32_t *__restrict__ tile_p0, const uint
             const uint32_t slot0 = (uint32_t)(t << 5);
             if (lane == 0) tile_cnt[t] = __popc(m);
             if (r.pj_starts) pair_rec[cur.p0 + lane] = slot0 + __popc(m & ((1u << r.po_j) - 1u));
+            if (pend) pad[pend_slot] = pend_rec;
+            pend = false;
             if (r.code == 1) {
                 ++n_i;
-                const uint32_t rank = atomicAdd(leaf_nsub + r.leaf, 1u);   // row in the leaf's list
-                pad[slot0 + __popc(m & lt)] = make_uint4(r.q, r.leaf, rank, 0u);
+                pend = true;
+                pend_slot = slot0 + __popc(m & lt);
+                pend_rec = make_uint4(r.q, r.leaf, atomicAdd(leaf_nsub + r.leaf, 1u), 0u);   // row in the leaf's list
             } else if (r.code == 2) {
                 ++n_c;
                 if (!r.cont) {
                     const uint32_t after = notcont & ~(lt | (1u << lane));   // later lanes that end the run
                     const uint32_t end = after ? (uint32_t)(__ffs(after) - 1) : 32u;
                     const uint32_t len = end - lane;
-                    pad[slot0 + __popc(m & lt)] =
-                        make_uint4(r.q, r.leaf | 0x80000000u, len,
-                                   __ldg(leaf_beg + r.leaf + len) - __ldg(leaf_beg + r.leaf));
+                    pend = true;
+                    pend_slot = slot0 + __popc(m & lt);
+                    pend_rec = make_uint4(r.q, r.leaf | 0x80000000u, len,
+                                          __ldg(leaf_beg + r.leaf + len) - __ldg(leaf_beg + r.leaf));
                 }
             }
             cur = nxt;
         }
+        if (pend) pad[pend_slot] = pend_rec;
     }
     n_i = warp_sum(n_i); n_c = warp_sum(n_c);
     if (lane == 0) {
@@ -528,45 +539,61 @@ cand_compact_kernel(const uint4 *__restrict__ pad, const uint32_t *__restrict__ 
                     const uint32_t *__restrict__ tile_off, const uint32_t *__restrict__ leaf_sub_off,
                     uint32_t *__restrict__ sub_q, uint32_t *__restrict__ sub_leaf, uint32_t *__restrict__ sub_len,
                     uint32_t *__restrict__ sub_res, uint32_t *__restrict__ isub, Caps caps, const Info *info) {
-    constexpr int U = 4;   // independent slots per thread per step: their load chains overlap
+    // U independent slots per thread per step; the next step's slots are
+    // loaded while the current step's leaf-list offsets are fetched and its
+    // records stored, so only one dependent load is exposed per step
+    constexpr int U = 2;
     const unsigned long long ntiles = (info->n_cand + 31) >> 5;
     if (ntiles > caps.cand_tiles || info->n_sub > caps.sub || info->n_sub_i > caps.sub_i) return;
     const unsigned long long nslots = ntiles << 5;
     const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
-    for (unsigned long long s0 = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; s0 < nslots;
-         s0 += U * stride) {
-        bool ok[U];
-        uint4 v[U];
-        uint32_t k[U], so[U];
+    struct Slot {
+        bool ok;
+        uint4 v;
+        uint32_t k;
+    };
+    auto load = [&](unsigned long long s0, Slot (&sl)[U]) {
 #pragma unroll
         for (int u = 0; u < U; ++u) {
             const unsigned long long s = s0 + u * stride;
-            ok[u] = s < nslots && ((uint32_t)s & 31u) < __ldg(tile_cnt + (s >> 5));
+            sl[u].ok = s < nslots && ((uint32_t)s & 31u) < __ldg(tile_cnt + (s >> 5));
         }
 #pragma unroll
         for (int u = 0; u < U; ++u) {
             const unsigned long long s = s0 + u * stride;
-            if (ok[u]) {
-                v[u] = __ldg(pad + s);
-                k[u] = __ldg(tile_off + (s >> 5)) + ((uint32_t)s & 31u);
+            if (sl[u].ok) {
+                sl[u].v = __ldg(pad + s);
+                sl[u].k = __ldg(tile_off + (s >> 5)) + ((uint32_t)s & 31u);
             }
         }
+    };
+    unsigned long long s0 = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x;
+    Slot cur[U];
+    load(s0, cur);
+    for (; s0 < nslots; s0 += U * stride) {
+        Slot nxt[U];
+        load(s0 + U * stride, nxt);
+        uint32_t so[U];
 #pragma unroll
         for (int u = 0; u < U; ++u)
-            if (ok[u] && !(v[u].y & 0x80000000u)) so[u] = __ldg(leaf_sub_off + v[u].y);
+            if (cur[u].ok && !(cur[u].v.y & 0x80000000u)) so[u] = __ldg(leaf_sub_off + cur[u].v.y);
 #pragma unroll
         for (int u = 0; u < U; ++u) {
-            if (!ok[u]) continue;
-            sub_q[k[u]] = v[u].x;
-            sub_leaf[k[u]] = v[u].y;
-            sub_len[k[u]] = v[u].z;           // run length, or rank in the leaf's list (its bitmap row)
-            if (v[u].y & 0x80000000u) {
-                sub_res[k[u]] = v[u].w;
+            if (!cur[u].ok) continue;
+            const uint4 v = cur[u].v;
+            const uint32_t k = cur[u].k;
+            sub_q[k] = v.x;
+            sub_leaf[k] = v.y;
+            sub_len[k] = v.z;           // run length, or rank in the leaf's list (its bitmap row)
+            if (v.y & 0x80000000u) {
+                sub_res[k] = v.w;
             } else {
-                sub_res[k[u]] = 0;
-                isub[so[u] + v[u].z] = k[u];
+                sub_res[k] = 0;
+                isub[so[u] + v.z] = k;
             }
         }
+#pragma unroll
+        for (int u = 0; u < U; ++u) cur[u] = nxt[u];
     }
 }
 
