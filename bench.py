@@ -59,6 +59,11 @@ WORKLOADS = {
                          "half queried by 300,000 squares of side log-uniform 0.0003-0.001, 25% uniform in the "
                          "right half queried by 10,000 squares of side log-uniform 0.01-0.04; random walk "
                          "sigma 0.0005 inside each half; leaf_cap 128, pair-list output"),
+    "alternating4m": dict(kind="alternating", n=4_000_000, q=400_000, cap=128,
+                          desc="alternating-4M: the hotspot-4M objects; even ticks 400,000 squares of side "
+                               "log-uniform 0.0002-0.001, odd ticks 4,000 squares of side log-uniform 0.005-0.02 "
+                               "(two query regimes that prefer different index configurations); leaf_cap 128, "
+                               "pair-list output"),
     "uniform16k": dict(kind="small", n=16384, q=1024, cap=64,
                        desc="uniform-16K: 16,384 uniform objects, 1,024 queries of side 0.01, leaf_cap 64"),
     "batched256": dict(kind="batched", n=0, q=0, cap=128,
@@ -87,6 +92,8 @@ def make_world(name, seed):
         return workloads.BatchedWorlds(n_worlds=256, seed=seed)
     if w["kind"] == "mixed":
         return workloads.MixedDensity(n=w["n"], seed=seed)
+    if w["kind"] == "alternating":
+        return workloads.AlternatingQueries(n=w["n"], seed=seed)
 
     class Small:
         def __init__(self):
@@ -988,13 +995,15 @@ def run_costmodel(args):
     idx = mqr.Index(bounds=(0.0, 0.0, 1.0, 1.0), leaf_cap=w["cap"], max_objects=nmax)
     out = torch.empty(1, dtype=torch.int32, device=dev)
 
+    qs = [int(r.shape[0]) for r in rect_d]           # queries of each tick (the alternating workload varies them)
+
     def tick(i):
         nonlocal out
         idx.apply_updates(ids_d, xy_d[i])
-        st, cnt = mqr.mqr_tick(idx.ctx, rect_d[i], Q, mqr.MQR_OUT_PAIRS, out, out.numel() * 4)
+        st, cnt = mqr.mqr_tick(idx.ctx, rect_d[i], qs[i], mqr.MQR_OUT_PAIRS, out, out.numel() * 4)
         if st == mqr.MQR_ERR_CAPACITY:
             out = torch.empty(int(cnt * 2 * 1.3) + 1024, dtype=torch.int32, device=dev)
-            st, cnt = mqr.mqr_tick(idx.ctx, rect_d[i], Q, mqr.MQR_OUT_PAIRS, out, out.numel() * 4)
+            st, cnt = mqr.mqr_tick(idx.ctx, rect_d[i], qs[i], mqr.MQR_OUT_PAIRS, out, out.numel() * 4)
         mqr._check(st)
 
     flush = torch.empty(args.flush_mb * (1 << 20) // 4, dtype=torch.int32, device=dev)
@@ -1017,10 +1026,10 @@ def run_costmodel(args):
     chosen, times = [], []
     for k in range(args.steps):
         i = args.warmup + (k % uniq)
-        c = ch.choose(nmax, Q, sides[i])
+        c = ch.choose(nmax, qs[i], sides[i])
         ch.apply(idx, c)
         ms = timed(i)
-        ch.record(c, nmax, Q, sides[i], ms)
+        ch.record(c, nmax, qs[i], sides[i], ms)
         chosen.append(c)
         times.append(ms)
     # the same candidates chosen by the argmin of their measured times (no network)
@@ -1028,10 +1037,10 @@ def run_costmodel(args):
     achosen, atimes = [], []
     for k in range(args.steps):
         i = args.warmup + (k % uniq)
-        c = ach.choose(nmax, Q, sides[i])
+        c = ach.choose(nmax, qs[i], sides[i])
         ach.apply(idx, c)
         ms = timed(i)
-        ach.record(c, nmax, Q, sides[i], ms)
+        ach.record(c, nmax, qs[i], sides[i], ms)
         achosen.append(c)
         atimes.append(ms)
     # node level: per-region capacities from the MLP over region features

@@ -12,6 +12,8 @@
 // load-balanced pass (no per-query serial walk), and a leaf larger than a
 // block is kept once, by the block holding the lower-left corner of its
 // intersection with the query (the paper's minimal-grid-coordinates rule).
+#include <algorithm>
+
 #include "mqr_internal.cuh"
 
 namespace mqr {
@@ -449,82 +451,96 @@ leaf_scan_kernel(const uint32_t *__restrict__ leaf_beg, const uint32_t *__restri
                  uint32_t *__restrict__ leaf_item_off,
                  uint32_t *__restrict__ item_leaf, uint32_t *status3, uint32_t num_tiles,
                  uint32_t *tile_counter, Caps caps, Info *info) {
-    __shared__ uint32_t s_scan[kLeafScanThreads / 32 + 1];
+    constexpr int NW = kLeafScanThreads / 32;
+    __shared__ uint3 s_warp[NW];
     __shared__ uint32_t s_tile, s_p[3];
-    const int tid = threadIdx.x;
-    if (tid == 0) s_tile = atomicAdd(tile_counter, 1u);
-    __syncthreads();
-    const uint32_t tile = s_tile;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const uint32_t L = (uint32_t)info->n_leaves;
-    const uint32_t base = tile * kLeafScanTile;
-    if (base >= L) return;
-    const uint32_t lb = base + tid * kLeafScanItems;
+    // the grid is a few blocks per SM; each takes tiles from the counter in
+    // order (a tile's look-back only waits for tiles already taken)
+    for (;;) {
+        if (tid == 0) s_tile = atomicAdd(tile_counter, 1u);
+        __syncthreads();
+        const uint32_t tile = s_tile;
+        const uint32_t base = tile * kLeafScanTile;
+        if (base >= L) break;
+        const uint32_t lb = base + tid * kLeafScanItems;
 
-    uint32_t ns[kLeafScanItems], nw[kLeafScanItems], ni[kLeafScanItems];
-    uint32_t t_s = 0, t_w = 0, t_i = 0;
-    unsigned long long objs = 0, tests = 0;
+        uint32_t ns[kLeafScanItems], nw[kLeafScanItems], ni[kLeafScanItems];
+        uint32_t t_s = 0, t_w = 0, t_i = 0;
+        unsigned long long objs = 0, tests = 0;
 #pragma unroll
-    for (int e = 0; e < kLeafScanItems; ++e) {
-        uint32_t l = lb + e;
-        ns[e] = nw[e] = ni[e] = 0;
-        if (l < L) {
-            uint32_t s = leaf_nsub[l];
-            uint32_t n = leaf_beg[l + 1] - leaf_beg[l];
-            ns[e] = s;
-            nw[e] = s * ((n + 31u) >> 5);
-            ni[e] = s ? ((n + 255u) >> 8) * ((s + 31u) >> 5) : 0u;
-            if (s) objs += (unsigned long long)n * ((s + 31u) >> 5);
-            tests += (unsigned long long)n * s;                 // containment tests of the leaf
+        for (int e = 0; e < kLeafScanItems; ++e) {
+            uint32_t l = lb + e;
+            ns[e] = nw[e] = ni[e] = 0;
+            if (l < L) {
+                uint32_t sq = leaf_nsub[l];
+                uint32_t n = leaf_beg[l + 1] - leaf_beg[l];
+                ns[e] = sq;
+                nw[e] = sq * ((n + 31u) >> 5);
+                ni[e] = sq ? ((n + 255u) >> 8) * ((sq + 31u) >> 5) : 0u;
+                if (sq) objs += (unsigned long long)n * ((sq + 31u) >> 5);
+                tests += (unsigned long long)n * sq;                 // containment tests of the leaf
+            }
+            t_s += ns[e]; t_w += nw[e]; t_i += ni[e];
         }
-        t_s += ns[e]; t_w += nw[e]; t_i += ni[e];
-    }
-    uint32_t tot_s, tot_w, tot_i;
-    uint32_t o_s = block_excl_scan<kLeafScanThreads>(t_s, &tot_s, s_scan);
-    uint32_t o_w = block_excl_scan<kLeafScanThreads>(t_w, &tot_w, s_scan);
-    uint32_t o_i = block_excl_scan<kLeafScanThreads>(t_i, &tot_i, s_scan);
-    objs = warp_sum(objs);
-    tests = warp_sum(tests);
-    if ((tid & 31) == 0 && objs) atomicAdd(&info->n_item_objs, objs);
-    if ((tid & 31) == 0 && tests) atomicAdd(&info->n_tests, tests);
-    if (tid < 96) {
-        const int w = tid >> 5;
-        const uint32_t agg = w == 0 ? tot_s : (w == 1 ? tot_w : tot_i);
-        const uint32_t pre = lookback_warp<uint32_t>(status3 + (size_t)w * num_tiles, tile, agg, &info->err);
-        if ((tid & 31) == 0) s_p[w] = pre;
-    }
-    __syncthreads();
-    o_s += s_p[0]; o_w += s_p[1]; o_i += s_p[2];
+        // one block scan of the three counts together
+        uint32_t i_s = warp_incl_scan(t_s), i_w = warp_incl_scan(t_w), i_i = warp_incl_scan(t_i);
+        if (lane == 31) s_warp[warp] = make_uint3(i_s, i_w, i_i);
+        objs = warp_sum(objs);
+        tests = warp_sum(tests);
+        if (lane == 0 && objs) atomicAdd(&info->n_item_objs, objs);
+        if (lane == 0 && tests) atomicAdd(&info->n_tests, tests);
+        __syncthreads();
+        uint32_t w_s = 0, w_w = 0, w_i = 0, tot_s = 0, tot_w = 0, tot_i = 0;
 #pragma unroll
-    for (int e = 0; e < kLeafScanItems; ++e) {
-        uint32_t l = lb + e;
-        if (l < L) {
-            leaf_sub_off[l] = o_s;
-            leaf_word_off[l] = o_w;
-            leaf_item_off[l] = o_i;
-            for (uint32_t t = 0; t < ni[e]; ++t)
-                if (o_i + t < caps.items) item_leaf[o_i + t] = l;
+        for (int w = 0; w < NW; ++w) {
+            const uint3 v = s_warp[w];
+            if (w < warp) { w_s += v.x; w_w += v.y; w_i += v.z; }
+            tot_s += v.x; tot_w += v.y; tot_i += v.z;
         }
-        o_s += ns[e]; o_w += nw[e]; o_i += ni[e];
-    }
-    if (tid == 0 && base + kLeafScanTile >= L) {
-        leaf_sub_off[L] = s_p[0] + tot_s;
-        leaf_word_off[L] = s_p[1] + tot_w;
-        leaf_item_off[L] = s_p[2] + tot_i;
-        info->n_words = s_p[1] + tot_w;
-        info->n_items = s_p[2] + tot_i;
+        uint32_t o_s = w_s + i_s - t_s, o_w = w_w + i_w - t_w, o_i = w_i + i_i - t_i;
+        if (tid < 96) {
+            const uint32_t agg = warp == 0 ? tot_s : (warp == 1 ? tot_w : tot_i);
+            const uint32_t pre = lookback_warp<uint32_t>(status3 + (size_t)warp * num_tiles, tile, agg, &info->err);
+            if (lane == 0) s_p[warp] = pre;
+        }
+        __syncthreads();
+        o_s += s_p[0]; o_w += s_p[1]; o_i += s_p[2];
+#pragma unroll
+        for (int e = 0; e < kLeafScanItems; ++e) {
+            uint32_t l = lb + e;
+            if (l < L) {
+                leaf_sub_off[l] = o_s;
+                leaf_word_off[l] = o_w;
+                leaf_item_off[l] = o_i;
+                for (uint32_t t = 0; t < ni[e]; ++t)
+                    if (o_i + t < caps.items) item_leaf[o_i + t] = l;
+            }
+            o_s += ns[e]; o_w += nw[e]; o_i += ni[e];
+        }
+        if (tid == 0 && base + kLeafScanTile >= L) {
+            leaf_sub_off[L] = s_p[0] + tot_s;
+            leaf_word_off[L] = s_p[1] + tot_w;
+            leaf_item_off[L] = s_p[2] + tot_i;
+            info->n_words = s_p[1] + tot_w;
+            info->n_items = s_p[2] + tot_i;
+        }
+        __syncthreads();            // s_tile, s_warp and s_p are reused by the next tile
     }
 }
 
-void launch_leaf_scan(cudaStream_t st, uint32_t nmax, const uint32_t *leaf_beg,
+void launch_leaf_scan(cudaStream_t st, int num_sms, uint32_t nmax, const uint32_t *leaf_beg,
                       const uint32_t *leaf_nsub, uint32_t *leaf_sub_off, uint32_t *leaf_word_off,
                       uint32_t *leaf_item_off, uint32_t *item_leaf,
                       uint32_t *status3, uint32_t *tile_counter, Caps caps, Info *info) {
     if (nmax == 0) return;
     uint32_t tiles = (nmax + kLeafScanTile - 1) / kLeafScanTile;
-    leaf_scan_kernel<<<tiles, kLeafScanThreads, 0, st>>>(leaf_beg, leaf_nsub, leaf_sub_off,
-                                                         leaf_word_off, leaf_item_off,
-                                                         item_leaf, status3, tiles, tile_counter, caps,
-                                                         info);
+    const uint32_t grid = std::min<uint32_t>(tiles, (uint32_t)num_sms * 2u);
+    leaf_scan_kernel<<<grid, kLeafScanThreads, 0, st>>>(leaf_beg, leaf_nsub, leaf_sub_off,
+                                                        leaf_word_off, leaf_item_off,
+                                                        item_leaf, status3, tiles, tile_counter, caps,
+                                                        info);
 }
 
 // ---------------------------------------------------------------------------

@@ -478,7 +478,7 @@ mqr_status enqueue_join(mqr_ctx *c, const mqr_ctx *ix, const float4 *rects, uint
     phase_end(c, MQR_PHASE_CANDIDATES, 2);
     // a8: group intersecting subqueries by leaf; compact the records
     phase_begin(c, MQR_PHASE_GROUP);
-    launch_leaf_scan(st, nmax, ix->leaf_beg.p, c->leaf_nsub.p, c->leaf_sub_off.p, c->leaf_word_off.p,
+    launch_leaf_scan(st, c->num_sms, nmax, ix->leaf_beg.p, c->leaf_nsub.p, c->leaf_sub_off.p, c->leaf_word_off.p,
                      c->leaf_item_off.p, c->item_leaf.p, at<uint32_t>(c, a.st_lscan), ctr + 6, caps, info);
     launch_compact(st, c->num_sms * (int)c->bps_compact, c->cand_pad.p, c->tile_cnt.p, c->tile_off.p, c->leaf_sub_off.p, c->sub_q.p,
                    c->sub_leaf.p, c->sub_len.p, c->sub_res.p, c->isub.p, caps, info);

@@ -414,7 +414,7 @@ void launch_candidates(cudaStream_t st, int grid_blocks, int covering, const uin
 
 // a8: scans over leaves -> leaf_sub_off, leaf_word_off, leaf_item_off, item_leaf.
 constexpr int kLeafScanThreads = 256, kLeafScanItems = 8, kLeafScanTile = kLeafScanThreads * kLeafScanItems;
-void launch_leaf_scan(cudaStream_t st, uint32_t nmax, const uint32_t *leaf_beg,
+void launch_leaf_scan(cudaStream_t st, int num_sms, uint32_t nmax, const uint32_t *leaf_beg,
                       const uint32_t *leaf_nsub, uint32_t *leaf_sub_off, uint32_t *leaf_word_off,
                       uint32_t *leaf_item_off, uint32_t *item_leaf,
                       uint32_t *status3, uint32_t *tile_counter, Caps caps, Info *info);

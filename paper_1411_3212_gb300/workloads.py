@@ -164,6 +164,30 @@ class HotspotWalk:
 
 
 # ----------------------------------------------------------------------------
+# Alternating queries: the hotspot world, whose ticks alternate between two
+# query regimes -- many small squares (even ticks) and few large ones (odd
+# ticks).  The best index configuration differs between the regimes, so a
+# chooser that ignores the tick's features can only find one compromise.
+# Both regimes come from HotspotWalk generators of one seed, whose object
+# positions are drawn from their own random streams and therefore agree.
+# ----------------------------------------------------------------------------
+class AlternatingQueries:
+    def __init__(self, n: int = 4_000_000, q_small: int = 400_000, small_lo: float = 0.0002,
+                 small_hi: float = 0.001, q_large: int = 4_000, large_lo: float = 0.005, large_hi: float = 0.02,
+                 seed: int = 0):
+        self.n = n
+        self.regimes = [HotspotWalk(n=n, q=q_small, side_lo=small_lo, side_hi=small_hi, seed=seed),
+                        HotspotWalk(n=n, q=q_large, side_lo=large_lo, side_hi=large_hi, seed=seed)]
+        self._t = 0
+
+    def next_tick(self) -> Tick:
+        ticks = [g.next_tick() for g in self.regimes]     # both advance: the same positions
+        t = ticks[self._t % 2]
+        self._t += 1
+        return t
+
+
+# ----------------------------------------------------------------------------
 # Mixed density: the left half of the square holds Gaussian hotspots (a
 # fraction frac_dense of the objects) queried by many small squares, the right
 # half a uniform sparse population queried by few large squares; objects

@@ -66,3 +66,20 @@ def test_batched_worlds_ranges():
         pts = t.xy[a:b]
         d = np.min(np.abs(c[:, None, 0] - pts[None, :, 0]) + np.abs(c[:, None, 1] - pts[None, :, 1]), axis=1)
         assert np.all(d < 1e-5)
+
+
+def test_alternating_queries_share_the_hotspot_positions():
+    """The two query regimes alternate tick by tick on the objects of one
+    hotspot world: positions equal HotspotWalk's of the same seed, query
+    counts and sides follow the regime of the tick."""
+    w = workloads.AlternatingQueries(n=30_000, q_small=3_000, small_lo=0.0002, small_hi=0.001, q_large=40,
+                                     large_lo=0.005, large_hi=0.02, seed=4)
+    ref = workloads.HotspotWalk(n=30_000, q=1, seed=4)
+    for k in range(4):
+        t, r = w.next_tick(), ref.next_tick()
+        np.testing.assert_array_equal(t.xy, r.xy)
+        side = np.maximum(t.rects[:, 2] - t.rects[:, 0], t.rects[:, 3] - t.rects[:, 1])
+        if k % 2 == 0:
+            assert t.rects.shape[0] == 3_000 and side.max() <= 0.00101
+        else:
+            assert t.rects.shape[0] == 40 and side.min() >= 0.00499
