@@ -110,6 +110,13 @@ def gen_ticks(name, seed, count):
     return [world.next_tick() for _ in range(count)]
 
 
+def replica_ticks(name, rank, count):
+    """The ticks of rank `rank`'s replica world: every rank answers an
+    independent world of the same recipe (its own seed), so the job's
+    throughput is the sum over ranks and no data crosses ranks."""
+    return gen_ticks(name, 1000 * rank, count)
+
+
 # ----------------------------------------------------------------------------
 # algorithmic bytes per phase (the data the method must move)
 # ----------------------------------------------------------------------------
@@ -382,7 +389,7 @@ def run_gpu(args, name):
 
     t_gen = time.perf_counter()
     uniq = min(args.steps, args.unique_ticks)          # timed steps cycle over these ticks
-    ticks = gen_ticks(name, 1000 * rank, args.warmup + uniq)
+    ticks = replica_ticks(name, rank, args.warmup + uniq)
     log("rank %d: generated %d ticks in %.1f s" % (rank, len(ticks), time.perf_counter() - t_gen))
 
     batched = w["kind"] == "batched"
