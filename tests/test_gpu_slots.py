@@ -154,3 +154,81 @@ def test_served_stream_on_slots_answers_every_query_once():
         np.testing.assert_array_equal(pairs[order, 1], wids)
     np.testing.assert_array_equal(got, 1)
     idx.close()
+
+
+def test_slot_edge_cases_and_updates_during_a_join():
+    """Q = 0 on a slot; end without begin and a second begin are refused;
+    updates applied while a join runs belong to the next snapshot (the
+    running join answers the snapshot's positions); a slot of a destroyed
+    context refuses to answer."""
+    torch, dev = torch_dev()
+    from paper_1411_3212_gb300 import mqr
+    n = 20_000
+    rng = np.random.default_rng(9)
+    xy0 = rng.random((n, 2)).astype(np.float32)
+    xy1 = rng.random((n, 2)).astype(np.float32)
+    ids = np.arange(n, dtype=np.uint32)
+    rects = workloads.squares_around(xy0[rng.integers(0, n, 500)], 0.03)
+    idx = mqr.Index(bounds=(0.0, 0.0, 1.0, 1.0), leaf_cap=32, max_objects=n)
+    sl = idx.slot()
+    idx.apply_updates(to_dev(ids, dev), to_dev(xy0, dev))
+    idx.snapshot()
+    out = torch.empty(1 << 22, dtype=torch.int32, device=dev)
+    with pytest.raises(mqr.MqrError, match="no join pending"):
+        sl.end()
+    sl.begin(to_dev(np.zeros((0, 4), np.float32), dev), "pairs", out, out.numel() * 4)
+    assert sl.end() == (0, 0)
+    offs = torch.zeros(rects.shape[0] + 1, dtype=torch.int64, device=dev)
+    sl.begin(to_dev(rects, dev), "pairs", out, out.numel() * 4, offs)
+    with pytest.raises(mqr.MqrError, match="pending"):
+        sl.begin(to_dev(rects, dev), "pairs", out, out.numel() * 4)
+    idx.apply_updates(to_dev(ids, dev), to_dev(xy1, dev))        # the next snapshot's positions
+    adm, cnt = sl.end()
+    want = oracle.join_grid(oracle_state(n, [(ids, xy0)]), rects, cell_side=0.03)
+    assert adm == rects.shape[0] and cnt == int(want[0][-1])
+    counts, got = decode(mqr, mqr.MQR_OUT_PAIRS, out.cpu().numpy(), cnt, offs.cpu().numpy().view(np.uint64), adm,
+                         None)
+    np.testing.assert_array_equal(got, want[1])
+    # the updates show in the next snapshot
+    idx.snapshot()
+    sl.begin(to_dev(rects, dev), "pairs", out, out.numel() * 4, offs)
+    adm, cnt = sl.end()
+    want1 = oracle.join_grid(oracle_state(n, [(ids, xy1)]), rects, cell_side=0.03)
+    counts, got = decode(mqr, mqr.MQR_OUT_PAIRS, out.cpu().numpy(), cnt, offs.cpu().numpy().view(np.uint64), adm,
+                         None)
+    np.testing.assert_array_equal(got, want1[1])
+    idx.close()
+    with pytest.raises(mqr.MqrError, match="destroyed"):
+        sl.begin(to_dev(rects, dev), "pairs", out, out.numel() * 4)
+    sl.close()
+
+
+def test_graph_cache_alternating_outputs_and_eviction():
+    """Graph mode keeps a few captured ticks: ticks alternating between five
+    output buffers (more than it keeps, so captures are evicted and made
+    again) all answer exactly."""
+    torch, dev = torch_dev()
+    from paper_1411_3212_gb300 import mqr
+    n = 20_000
+    w = workloads.HotspotWalk(n=n, q=1200, hotspots=4, side_lo=0.002, side_hi=0.03, seed=41)
+    idx = mqr.Index(bounds=(0.0, 0.0, 1.0, 1.0), leaf_cap=32, max_objects=n)
+    idx.set_graph(True)
+    outs = [torch.empty(1 << 21, dtype=torch.int32, device=dev) for _ in range(5)]
+    offs = torch.zeros(1201, dtype=torch.int64, device=dev)
+    st = oracle.State(n)
+    for k in range(12):
+        t = w.next_tick() if k % 3 == 0 else t
+        if k % 3 == 0:
+            idx.apply_updates(to_dev(t.ids, dev), to_dev(t.xy, dev))
+            st.apply_updates(t.ids, t.xy)
+            want = oracle.join_grid(st, t.rects, cell_side=0.01)
+        out = outs[(k * 2) % 5]
+        status, cnt = mqr.mqr_tick(idx.ctx, to_dev(t.rects, dev), t.rects.shape[0], mqr.MQR_OUT_PAIRS, out,
+                                   out.numel() * 4, offs)
+        assert status == mqr.MQR_OK and cnt == int(want[0][-1])
+        np.testing.assert_array_equal(offs.cpu().numpy().view(np.uint64), want[0])
+        p = out[: 2 * cnt].cpu().numpy().view(np.uint32).reshape(-1, 2)
+        order = np.lexsort((p[:, 1], p[:, 0]))
+        np.testing.assert_array_equal(p[order, 1], want[1])
+    idx.set_graph(False)
+    idx.close()
