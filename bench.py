@@ -719,10 +719,11 @@ def run_e2e(args, idx, ticks, kind, elem, Q, dev):
         mqr.mqr_apply_updates_host(idx.ctx, ids_h, xy_h[i_max])
         mqr._check(mqr.mqr_tick_host_async(idx.ctx, rect_h[i_max], Q, kind, oh, oh.nbytes)[0])
     mqr.mqr_host_wait(idx.ctx)
-    d2h, regrown = [], 0
+    d2h, regrown, t_calls = [], 0, []
     runs = kind == mqr.MQR_OUT_RUNS
     t_all = time.perf_counter()
     for k, i in enumerate(order):
+        t_calls.append(time.perf_counter())
         mqr.mqr_apply_updates_host(idx.ctx, ids_h, xy_h[i])
         oh = out_hs[k & 1]
         st, cnt = mqr.mqr_tick_host_async(idx.ctx, rect_h[i], Q, kind, oh, oh.nbytes, check=False)
@@ -738,9 +739,13 @@ def run_e2e(args, idx, ticks, kind, elem, Q, dev):
         d2h.append(cnt * elem + ns * 4)
     mqr.mqr_host_wait(idx.ctx)
     total = time.perf_counter() - t_all
+    t_calls.append(t_all + total)
+    gaps = [1000.0 * (b - a) for a, b in zip(t_calls[:-1], t_calls[1:])]
     return {"value": Q * steps / total, "unit": "queries/s",
             "h2d_bytes_per_step": int(n * 12 + Q * 16), "d2h_bytes_per_step": int(sum(d2h) / steps),
             "ms_per_step": 1000.0 * total / steps, "steps": steps, "buffer_regrowths": regrown,
+            "d2h_GB_per_s": sum(d2h) / total / 1e9,
+            "host_ms_per_step": {"min": min(gaps), "median": statistics.median(gaps), "max": max(gaps)},
             "api": "mqr_apply_updates_host + mqr_tick_host_async%s, mqr_host_wait at the end (pinned host "
                    "buffers; each tick's copy overlaps the next tick)" % (" + mqr_get_sorted_async" if runs else "")}
 
