@@ -151,7 +151,7 @@ def phase_bytes(s, n_updates, nmax, n_out=None, fp=None, elem=8):
 
 
 PHASE_FORMULA = {
-    "emit": "8*out_elems + 4*bitmap_words + 20*records + 4*objects of the leaves with results",
+    "emit": "out_elem_bytes*out_elems + 4*bitmap_words + 20*records + 4*result_leaf_objects",
     "filter": "8*objects of the tested leaves + 24*intersecting subqueries + 4*bitmap_words",
     "sort": "80*max_objects (3 passes x 16 B + last pass 32 B per key)",
 }
@@ -492,6 +492,11 @@ def run_gpu(args, name):
             bytes_acc[ph] = bytes_acc.get(ph, 0) + b
         for key, v in (fp or {}).items():
             fp_acc[key] = fp_acc.get(key, 0) + v
+        st_k = idx.stats()
+        for key, v in (("out_elems", cnt), ("bitmap_words", st_k["n_bitmap_words"]),
+                       ("records", st_k["n_sub_intersecting"] + st_k["n_covering_runs"]),
+                       ("results", st_k["n_results"])):
+            fp_acc[key] = fp_acc.get(key, 0) + v
     barrier(dist, dev)
     wall = time.perf_counter() - t_wall
     clk = clocks.stop()
@@ -531,7 +536,10 @@ def run_gpu(args, name):
                 "algorithmic_bytes_per_launch": per_launch_bytes, "launch_ms": per_launch_ms,
                 "launches": launches,
                 "bytes_formula": PHASE_FORMULA.get(dom),
-                "footprint_per_launch": {k: v / launches for k, v in fp_acc.items()} if dom == "emit" else None}
+                # the byte formula's terms averaged over the timed launches:
+                # elem * out_elems + 4 * bitmap_words + 20 * records + 4 * result_leaf_objects
+                "terms_per_launch": {k: v / launches for k, v in fp_acc.items()} if dom == "emit" else None,
+                "out_elem_bytes": elem}
     join = ["filter", "emit"]
     join_ms = sum(calib["ms"][p] for p in join)
     join_bytes = sum(calib_bytes.get(p, 0) for p in join)
