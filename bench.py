@@ -517,8 +517,8 @@ def run_gpu(args, name):
     achieved = per_launch_bytes / (per_launch_ms / 1000.0) / 1e9 if per_launch_ms > 0 else 0.0
     kernel_names = {"emit": "emit_kernel", "filter": "filter_kernel",
                     "sort": "tile_hist_kernel+digit_scan_kernel+onesweep_kernel",
-                    "query_blocks": "zmap_kernel+query_blocks_kernel", "candidates": "cand_count_kernel+tile_scan_kernel",
-                    "group": "leaf_scan_kernel+cand_compact_kernel",
+                    "query_blocks": "zmap_kernel+query_blocks_kernel", "candidates": "cand_write_kernel",
+                    "group": "leaf_scan_kernel+leaf_lists_kernel",
                     "leaves": "leaves_kernel", "keys": "morton_kernel", "updates": "stamp_kernel+write_winner_kernel",
                     "result_scan": "result_scan_kernel"}
     kname = kernel_names.get(dom, dom)

@@ -353,8 +353,10 @@ mqr_status mqr_set_query_worlds(mqr_ctx *ctx, const uint32_t *q_base_host);
 mqr_status mqr_set_index(mqr_ctx *ctx, int index_kind, uint32_t leaf_cap, uint32_t grid_level);
 
 /* Launch shapes of the work-item kernels: blocks per SM of the candidate
- * pass, the subquery compaction, the filter (Alg. 2) and the decoding / emit
- * (Alg. 4); 0 keeps the default (8).  Their blocks draw work items from
+ * pass (which also places the subquery records), the pass that files the
+ * intersecting subqueries into their leaves' lists (compact_blocks_per_sm),
+ * the filter (Alg. 2) and the decoding / emit (Alg. 4); 0 keeps the default
+ * (8).  Their blocks draw work items from
  * counters or stride over them, so the shapes change time, never results;
  * block sizes are fixed per kernel by its register budget.  An autotuner
  * (autotune.tune_launch_config) picks them by timing.  1 <= value <= 64.

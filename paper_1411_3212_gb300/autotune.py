@@ -63,8 +63,8 @@ def _time_ticks(idx, ticks, kind, reps):
 
 
 def tune_launch_config(idx, ticks, options=(2, 4, 8, 16), kind="pairs", reps=2, timer=None):
-    """Blocks per SM of the candidate pass, the compaction, the filter and the
-    emit (mqr_set_launch_config), by coordinate descent: each kernel in turn
+    """Blocks per SM of the candidate pass, the leaf-list pass, the filter and
+    the emit (mqr_set_launch_config), by coordinate descent: each kernel in turn
     takes the option with the smallest tick time, the others held.  Block
     sizes are fixed per kernel (register budgets); only the grids move, and
     results must not.  timer(idx, ticks, kind, reps) -> (ms per tick,

@@ -546,9 +546,9 @@ void launch_emit(cudaStream_t st, int grid_blocks, int emit_kind, const uint32_t
 
 // Per-query offsets: the first record of query q is the first record of its
 // first (query, block) pair (queries without pairs take the next pair's);
-// pair_rec holds that record's padded candidate slot 32t + rank.
+// pair_rec holds that record's index.
 __global__ void query_offsets_kernel(uint32_t Q, const uint32_t *__restrict__ qpair,
-                                     const uint32_t *__restrict__ pair_rec, const uint32_t *__restrict__ tile_off,
+                                     const uint32_t *__restrict__ pair_rec,
                                      const unsigned long long *__restrict__ out_off,
                                      unsigned long long *__restrict__ offsets, Caps caps,
                                      const Info *info) {
@@ -561,21 +561,17 @@ __global__ void query_offsets_kernel(uint32_t Q, const uint32_t *__restrict__ qp
             continue;
         }
         const uint32_t p = qpair[q];
-        uint32_t rec = nsub;
-        if (p < npairs) {
-            const uint32_t slot = pair_rec[p];
-            rec = tile_off[slot >> 5] + (slot & 31u);
-        }
+        const uint32_t rec = p < npairs ? pair_rec[p] : nsub;
         offsets[q] = out_off[rec];
     }
 }
 
 void launch_query_offsets(cudaStream_t st, uint32_t Q, const uint32_t *qpair, const uint32_t *pair_rec,
-                          const uint32_t *tile_off, const unsigned long long *out_off,
-                          unsigned long long *offsets, Caps caps, const Info *info) {
+                          const unsigned long long *out_off, unsigned long long *offsets, Caps caps,
+                          const Info *info) {
     uint32_t g = (Q + 1 + 255) / 256;
     if (g > 4096) g = 4096;
-    query_offsets_kernel<<<g, 256, 0, st>>>(Q, qpair, pair_rec, tile_off, out_off, offsets, caps, info);
+    query_offsets_kernel<<<g, 256, 0, st>>>(Q, qpair, pair_rec, out_off, offsets, caps, info);
 }
 
 // Admission by output memory (served streams): with offsets the per-query
@@ -584,18 +580,14 @@ void launch_query_offsets(cudaStream_t st, uint32_t Q, const uint32_t *qpair, co
 // then stops before A's first record.
 __global__ void admit_kernel(uint32_t Q, const unsigned long long *__restrict__ offsets, unsigned long long cap,
                              const uint32_t *__restrict__ qpair, const uint32_t *__restrict__ pair_rec,
-                             const uint32_t *__restrict__ tile_off, Caps caps, Info *info) {
+                             Caps caps, Info *info) {
     if (!tick_buffers_ok(info, caps)) return;
     const uint32_t nsub = (uint32_t)info->n_sub;
     const uint32_t npairs = (uint32_t)info->n_pairs;
     for (uint32_t q = blockIdx.x * blockDim.x + threadIdx.x; q < Q; q += gridDim.x * blockDim.x) {
         if (offsets[q] <= cap && offsets[q + 1] > cap) {
             const uint32_t p = qpair[q];
-            uint32_t rec = nsub;
-            if (p < npairs) {
-                const uint32_t slot = pair_rec[p];
-                rec = tile_off[slot >> 5] + (slot & 31u);
-            }
+            const uint32_t rec = p < npairs ? pair_rec[p] : nsub;
             info->admitted = q;
             info->admitted_out = offsets[q];
             info->emit_end = (1ull << 63) | rec;       // bit 63: the output is cut (rec may be 0)
@@ -604,12 +596,11 @@ __global__ void admit_kernel(uint32_t Q, const unsigned long long *__restrict__ 
 }
 
 void launch_admit(cudaStream_t st, uint32_t Q, const unsigned long long *offsets, unsigned long long cap,
-                  const uint32_t *qpair, const uint32_t *pair_rec, const uint32_t *tile_off, Caps caps,
-                  Info *info) {
+                  const uint32_t *qpair, const uint32_t *pair_rec, Caps caps, Info *info) {
     uint32_t g = (Q + 255) / 256;
     if (g > 4096) g = 4096;
     if (g == 0) g = 1;
-    admit_kernel<<<g, 256, 0, st>>>(Q, offsets, cap, qpair, pair_rec, tile_off, caps, info);
+    admit_kernel<<<g, 256, 0, st>>>(Q, offsets, cap, qpair, pair_rec, caps, info);
 }
 
 // ---------------------------------------------------------------------------

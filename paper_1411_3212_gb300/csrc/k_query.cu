@@ -225,20 +225,23 @@ void launch_query_blocks(cudaStream_t st, const float4 *rects, uint32_t Q, float
 
 // ---------------------------------------------------------------------------
 // a7: candidate leaves -> subquery records, in warp tiles of 32 consecutive
-// candidates (no shared memory, no block barriers).  The pairs touching a
-// tile are the 32 pairs from tile_p0[t] on (every pair has >= 1 candidate);
-// lane j loads pair tile_p0[t] + j, the pair starts inside the tile are
-// gathered in one bit mask, and the pair of lane L is found by a popcount.
-// Consecutive covering leaves of one pair inside one tile form one covering
-// run (their objects are one contiguous range of the sorted objects).
-// One classification pass writes each tile's records into the tile's 32
-// padded slots (slot 32t + rank) and counts them; a scan of the per-tile
-// counts gives every tile its first record; a compaction pass moves the
-// records to their places.  Record k: sub_q[k] = query, sub_leaf[k] = first
-// leaf (bit 31 set for a covering run), sub_len[k] = run length, sub_res[k] =
-// result count (covering: the run's objects; intersecting: 0, filled by the
-// filter).  Records are in query-major order.  pair_rec[p] = padded slot of
-// pair p's first record (or of the record after it, if p has none).
+// candidates.  The pairs touching a tile are the 32 pairs from tile_p0[t] on
+// (every pair has >= 1 candidate); lane j loads pair tile_p0[t] + j, the pair
+// starts inside the tile are gathered in one bit mask, and the pair of lane L
+// is found by a popcount.  Consecutive covering leaves of one pair inside one
+// tile form one covering run (their objects are one contiguous range of the
+// sorted objects).
+// One pass classifies and places the records: a block takes chunks of
+// kCandChunkTiles consecutive tiles in ticket order (each warp kCandWarpTiles
+// of them), gathers the chunk's records in shared memory in tile order, finds
+// the chunk's first record by a decoupled look-back over the chunks before
+// it, and stores the records there, coalesced.  Record k: sub_q[k] = query,
+// sub_leaf[k] = first leaf (bit 31 set for a covering run), sub_len[k] = run
+// length (covering) or the record's row in its leaf's list (intersecting: the
+// rank drawn from the leaf's counter leaf_nsub), sub_res[k] = result count
+// (covering: the run's objects; intersecting: 0, filled by the filter).
+// Records are in query-major order.  pair_rec[p] = the index of pair p's
+// first record (or of the record after it, if p has none).
 // ---------------------------------------------------------------------------
 struct CandLane {
     bool valid;
@@ -314,65 +317,118 @@ __device__ __forceinline__ CandLane cand_lane(unsigned long long t, unsigned lon
 }
 
 __global__ void __launch_bounds__(256)
-cand_count_kernel(int covering, const uint32_t *__restrict__ tile_p0, const uint32_t *__restrict__ pair_q,
+cand_write_kernel(int covering, const uint32_t *__restrict__ tile_p0, const uint32_t *__restrict__ pair_q,
                   const uint32_t *__restrict__ pair_first, const uint32_t *__restrict__ pair_blo,
                   const unsigned long long *__restrict__ pair_off, const uint2 *__restrict__ qcells,
-                  const uint2 *__restrict__ leaf_box,
-                  const uint32_t *__restrict__ leaf_beg, uint32_t *__restrict__ tile_cnt,
-                  uint32_t *__restrict__ leaf_nsub, uint4 *__restrict__ pad, uint32_t *__restrict__ pair_rec,
-                  Caps caps, Info *info) {
+                  const uint2 *__restrict__ leaf_box, const uint32_t *__restrict__ leaf_beg,
+                  uint32_t *__restrict__ leaf_nsub, uint32_t *__restrict__ pair_rec,
+                  uint32_t *__restrict__ sub_q, uint32_t *__restrict__ sub_leaf, uint32_t *__restrict__ sub_len,
+                  uint32_t *__restrict__ sub_res, unsigned long long *status, uint32_t *chunk_counter, Caps caps,
+                  Info *info) {
+    constexpr int NW = 256 / 32;
+    static_assert(kCandChunkTiles == NW * kCandWarpTiles, "a chunk is the block's warps' tiles");
+    __shared__ uint4 s_rec[NW][kCandWarpTiles * 32];     // the warp's records, in tile order
+    __shared__ uint32_t s_warp[NW];
+    __shared__ uint32_t s_chunk;
+    __shared__ unsigned long long s_prefix;
     __shared__ unsigned long long s_red[2];
-    if (threadIdx.x < 2) s_red[threadIdx.x] = 0;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    if (tid < 2) s_red[tid] = 0;
     __syncthreads();
     const unsigned long long ncand = info->n_cand;
     const uint32_t npairs = (uint32_t)info->n_pairs;
     const unsigned long long ntiles = (ncand + 31) >> 5;
-    const uint32_t lane = threadIdx.x & 31;
+    const unsigned long long nchunks = (ntiles + kCandChunkTiles - 1) / kCandChunkTiles;
     const uint32_t lt = lanemask_lt();
+    uint4 *my = s_rec[warp];
     unsigned long long n_i = 0, n_c = 0;
-    if (ntiles <= caps.cand_tiles) {
-        const unsigned long long nw = (unsigned long long)gridDim.x * (blockDim.x >> 5);
-        unsigned long long t = (blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x) >> 5;
-        PairLoad cur{};
-        if (t < ntiles) cur = pair_load(t, npairs, tile_p0, pair_q, pair_first, pair_blo, pair_off);
-        // the record of the previous tile, written one iteration later so that
-        // the latency of its leaf-list atomic (or of its run's leaf bounds)
-        // overlaps this tile's loads and classification
+    // every block takes the same branch (ntiles and the capacity are uniform)
+    while (ntiles <= caps.cand_tiles) {
+        if (tid == 0) s_chunk = atomicAdd(chunk_counter, 1u);
+        __syncthreads();
+        const uint32_t chunk = s_chunk;
+        if (chunk >= nchunks) break;
+        const unsigned long long t0 = (unsigned long long)chunk * kCandChunkTiles + warp * kCandWarpTiles;
+        // prel[j]: the first record of the lane's pair starting in tile j,
+        // counted from the warp's first record (~0u: no pair starts there)
+        uint32_t prel[kCandWarpTiles];
+        uint32_t wcnt = 0;
+        // a record is stored one tile later, so that the latency of its leaf
+        // counter atomic (or of its run's leaf bounds) overlaps the next
+        // tile's loads and classification
         bool pend = false;
-        uint32_t pend_slot = 0;
+        uint32_t pend_pos = 0;
         uint4 pend_rec = make_uint4(0u, 0u, 0u, 0u);
-        for (; t < ntiles; t += nw) {
-            PairLoad nxt = cur;                   // the next tile's pairs, loaded before this tile is used
-            if (t + nw < ntiles) nxt = pair_load(t + nw, npairs, tile_p0, pair_q, pair_first, pair_blo, pair_off);
-            CandLane r = cand_lane(t, ncand, npairs, covering, cur, qcells, leaf_box);
-            const bool rec = r.code == 1 || (r.code == 2 && !r.cont);
-            const uint32_t m = __ballot_sync(0xffffffffu, rec);
-            const uint32_t notcont = __ballot_sync(0xffffffffu, !(r.valid && r.cont));
-            const uint32_t slot0 = (uint32_t)(t << 5);
-            if (lane == 0) tile_cnt[t] = __popc(m);
-            if (r.pj_starts) pair_rec[cur.p0 + lane] = slot0 + __popc(m & ((1u << r.po_j) - 1u));
-            if (pend) pad[pend_slot] = pend_rec;
-            pend = false;
-            if (r.code == 1) {
-                ++n_i;
-                pend = true;
-                pend_slot = slot0 + __popc(m & lt);
-                pend_rec = make_uint4(r.q, r.leaf, atomicAdd(leaf_nsub + r.leaf, 1u), 0u);   // row in the leaf's list
-            } else if (r.code == 2) {
-                ++n_c;
-                if (!r.cont) {
-                    const uint32_t after = notcont & ~(lt | (1u << lane));   // later lanes that end the run
-                    const uint32_t end = after ? (uint32_t)(__ffs(after) - 1) : 32u;
-                    const uint32_t len = end - lane;
+        PairLoad cur{};
+        if (t0 < ntiles) cur = pair_load(t0, npairs, tile_p0, pair_q, pair_first, pair_blo, pair_off);
+#pragma unroll
+        for (int j = 0; j < kCandWarpTiles; ++j) {
+            const unsigned long long t = t0 + j;
+            prel[j] = ~0u;
+            if (t < ntiles) {                                   // warp-uniform
+                PairLoad nxt = cur;
+                if (j + 1 < kCandWarpTiles && t + 1 < ntiles)
+                    nxt = pair_load(t + 1, npairs, tile_p0, pair_q, pair_first, pair_blo, pair_off);
+                const CandLane r = cand_lane(t, ncand, npairs, covering, cur, qcells, leaf_box);
+                const bool rec = r.code == 1 || (r.code == 2 && !r.cont);
+                const uint32_t m = __ballot_sync(0xffffffffu, rec);
+                const uint32_t notcont = __ballot_sync(0xffffffffu, !(r.valid && r.cont));
+                if (r.pj_starts) prel[j] = wcnt + __popc(m & ((1u << r.po_j) - 1u));
+                if (pend) my[pend_pos] = pend_rec;
+                pend = false;
+                if (r.code == 1) {
+                    ++n_i;
                     pend = true;
-                    pend_slot = slot0 + __popc(m & lt);
-                    pend_rec = make_uint4(r.q, r.leaf | 0x80000000u, len,
-                                          __ldg(leaf_beg + r.leaf + len) - __ldg(leaf_beg + r.leaf));
+                    pend_pos = wcnt + __popc(m & lt);
+                    pend_rec = make_uint4(r.q, r.leaf, atomicAdd(leaf_nsub + r.leaf, 1u), 0u);
+                } else if (r.code == 2) {
+                    ++n_c;
+                    if (!r.cont) {
+                        const uint32_t after = notcont & ~(lt | (1u << lane));   // later lanes that end the run
+                        const uint32_t end = after ? (uint32_t)(__ffs(after) - 1) : 32u;
+                        const uint32_t len = end - lane;
+                        pend = true;
+                        pend_pos = wcnt + __popc(m & lt);
+                        pend_rec = make_uint4(r.q, r.leaf | 0x80000000u, len,
+                                              __ldg(leaf_beg + r.leaf + len) - __ldg(leaf_beg + r.leaf));
+                    }
                 }
+                wcnt += __popc(m);
+                cur = nxt;
             }
-            cur = nxt;
         }
-        if (pend) pad[pend_slot] = pend_rec;
+        if (pend) my[pend_pos] = pend_rec;
+        if (lane == 0) s_warp[warp] = wcnt;
+        __syncthreads();
+        uint32_t woff = 0, total = 0;
+#pragma unroll
+        for (int w = 0; w < NW; ++w) {
+            const uint32_t v = s_warp[w];
+            if (w < warp) woff += v;
+            total += v;
+        }
+        if (warp == 0) {
+            const unsigned long long pre =
+                lookback_warp<unsigned long long>(status, chunk, (unsigned long long)total, &info->err);
+            if (lane == 0) s_prefix = pre;
+        }
+        __syncthreads();
+        const unsigned long long base = s_prefix + woff;
+        for (uint32_t i = lane; i < wcnt; i += 32) {
+            const unsigned long long k = base + i;
+            if (k < caps.sub) {
+                const uint4 v = my[i];
+                sub_q[k] = v.x;
+                sub_leaf[k] = v.y;
+                sub_len[k] = v.z;
+                sub_res[k] = v.w;
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < kCandWarpTiles; ++j)
+            if (prel[j] != ~0u) pair_rec[__ldg(tile_p0 + t0 + j) + lane] = (uint32_t)(base + prel[j]);
+        if (tid == 0 && chunk + 1 == nchunks) info->n_sub = s_prefix + total;
+        __syncthreads();            // s_chunk, s_warp, s_prefix and s_rec are reused by the next chunk
     }
     n_i = warp_sum(n_i); n_c = warp_sum(n_c);
     if (lane == 0) {
@@ -386,56 +442,15 @@ cand_count_kernel(int covering, const uint32_t *__restrict__ tile_p0, const uint
     }
 }
 
-// Exclusive scan of the per-tile record counts -> tile_off; n_sub = total.
-__global__ void __launch_bounds__(256)
-tile_scan_kernel(const uint32_t *__restrict__ tile_cnt, uint32_t *__restrict__ tile_off, uint32_t *status,
-                 uint32_t *tile_counter, Caps caps, Info *info) {
-    __shared__ uint32_t s_scan[256 / 32 + 1];
-    __shared__ uint32_t s_tile, s_prefix;
-    const int tid = threadIdx.x;
-    if (tid == 0) s_tile = atomicAdd(tile_counter, 1u);
-    __syncthreads();
-    const unsigned long long ntiles = (info->n_cand + 31) >> 5;
-    if (ntiles > caps.cand_tiles) return;
-    const uint32_t blk = s_tile;
-    const unsigned long long base = (unsigned long long)blk * 2048;
-    if (base >= ntiles) return;
-    uint32_t v[8], t = 0;
-#pragma unroll
-    for (int e = 0; e < 8; ++e) {
-        const unsigned long long i = base + tid * 8 + e;
-        v[e] = i < ntiles ? tile_cnt[i] : 0u;
-        t += v[e];
-    }
-    uint32_t total;
-    uint32_t off = block_excl_scan<256>(t, &total, s_scan);
-    if (tid < 32) {
-        const uint32_t pre = lookback_warp<uint32_t>(status, blk, total, &info->err);
-        if (tid == 0) s_prefix = pre;
-    }
-    __syncthreads();
-    off += s_prefix;
-#pragma unroll
-    for (int e = 0; e < 8; ++e) {
-        const unsigned long long i = base + tid * 8 + e;
-        if (i < ntiles) tile_off[i] = off;
-        off += v[e];
-    }
-    if (tid == 0 && base + 2048 >= ntiles) info->n_sub = s_prefix + total;
-}
-
 void launch_candidates(cudaStream_t st, int grid_blocks, int covering, const uint32_t *tile_p0,
                        const uint32_t *pair_q, const uint32_t *pair_first, const uint32_t *pair_blo,
                        const unsigned long long *pair_off, const uint2 *qcells, const uint2 *leaf_box,
-                       const uint32_t *leaf_beg, uint32_t *tile_cnt, uint32_t *tile_off, uint32_t *leaf_nsub,
-                       uint4 *pad, uint32_t *pair_rec, uint32_t *status, uint32_t *tile_counter, Caps caps,
-                       Info *info) {
-    cand_count_kernel<<<grid_blocks, 256, 0, st>>>(covering, tile_p0, pair_q, pair_first, pair_blo, pair_off,
-                                                   qcells, leaf_box, leaf_beg, tile_cnt, leaf_nsub, pad,
-                                                   pair_rec, caps, info);
-    const unsigned long long scan_blocks = (caps.cand_tiles + kCandScanTile - 1) / kCandScanTile;
-    tile_scan_kernel<<<(unsigned)(scan_blocks ? scan_blocks : 1), 256, 0, st>>>(tile_cnt, tile_off, status,
-                                                                              tile_counter, caps, info);
+                       const uint32_t *leaf_beg, uint32_t *leaf_nsub, uint32_t *pair_rec, uint32_t *sub_q,
+                       uint32_t *sub_leaf, uint32_t *sub_len, uint32_t *sub_res, unsigned long long *status,
+                       uint32_t *chunk_counter, Caps caps, Info *info) {
+    cand_write_kernel<<<grid_blocks, 256, 0, st>>>(covering, tile_p0, pair_q, pair_first, pair_blo, pair_off,
+                                                   qcells, leaf_box, leaf_beg, leaf_nsub, pair_rec, sub_q,
+                                                   sub_leaf, sub_len, sub_res, status, chunk_counter, caps, info);
 }
 
 // ---------------------------------------------------------------------------
@@ -544,80 +559,40 @@ void launch_leaf_scan(cudaStream_t st, int num_sms, uint32_t nmax, const uint32_
 }
 
 // ---------------------------------------------------------------------------
-// a7/a8 compaction: padded slot 32t + r (r < the tile's count) -> record
-// k = tile_off[t] + r.  An intersecting record also takes its place in its
-// leaf's list (its rank there came from the count pass's per-leaf atomic
-// count, and is kept in sub_len: it is the record's bitmap row in the leaf),
-// so the grouping by leaf needs no second pass.
+// a8: every intersecting record takes its place in its leaf's list: isub[
+// leaf_sub_off[leaf] + row] = k, with row the rank the candidate pass drew
+// from the leaf's counter (kept in sub_len: the record's bitmap row in the
+// leaf).  Four records per thread per step, their loads issued together.
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(256)
-cand_compact_kernel(const uint4 *__restrict__ pad, const uint32_t *__restrict__ tile_cnt,
-                    const uint32_t *__restrict__ tile_off, const uint32_t *__restrict__ leaf_sub_off,
-                    uint32_t *__restrict__ sub_q, uint32_t *__restrict__ sub_leaf, uint32_t *__restrict__ sub_len,
-                    uint32_t *__restrict__ sub_res, uint32_t *__restrict__ isub, Caps caps, const Info *info) {
-    // U independent slots per thread per step; the next step's slots are
-    // loaded while the current step's leaf-list offsets are fetched and its
-    // records stored, so only one dependent load is exposed per step
-    constexpr int U = 2;
-    const unsigned long long ntiles = (info->n_cand + 31) >> 5;
-    if (ntiles > caps.cand_tiles || info->n_sub > caps.sub || info->n_sub_i > caps.sub_i) return;
-    const unsigned long long nslots = ntiles << 5;
+leaf_lists_kernel(const uint32_t *__restrict__ sub_leaf, const uint32_t *__restrict__ sub_len,
+                  const uint32_t *__restrict__ leaf_sub_off, uint32_t *__restrict__ isub, Caps caps,
+                  const Info *info) {
+    constexpr int U = 4;
+    const unsigned long long nsub = info->n_sub;
+    if (nsub > caps.sub || info->n_sub_i > caps.sub_i) return;
     const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
-    struct Slot {
-        bool ok;
-        uint4 v;
-        uint32_t k;
-    };
-    auto load = [&](unsigned long long s0, Slot (&sl)[U]) {
+    for (unsigned long long k0 = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; k0 < nsub;
+         k0 += U * stride) {
+        uint32_t leaf[U], row[U], off[U];
 #pragma unroll
         for (int u = 0; u < U; ++u) {
-            const unsigned long long s = s0 + u * stride;
-            sl[u].ok = s < nslots && ((uint32_t)s & 31u) < __ldg(tile_cnt + (s >> 5));
+            const unsigned long long k = k0 + u * stride;
+            leaf[u] = k < nsub ? __ldg(sub_leaf + k) : 0x80000000u;
+            row[u] = k < nsub ? __ldg(sub_len + k) : 0u;
         }
-#pragma unroll
-        for (int u = 0; u < U; ++u) {
-            const unsigned long long s = s0 + u * stride;
-            if (sl[u].ok) {
-                sl[u].v = __ldg(pad + s);
-                sl[u].k = __ldg(tile_off + (s >> 5)) + ((uint32_t)s & 31u);
-            }
-        }
-    };
-    unsigned long long s0 = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x;
-    Slot cur[U];
-    load(s0, cur);
-    for (; s0 < nslots; s0 += U * stride) {
-        Slot nxt[U];
-        load(s0 + U * stride, nxt);
-        uint32_t so[U];
 #pragma unroll
         for (int u = 0; u < U; ++u)
-            if (cur[u].ok && !(cur[u].v.y & 0x80000000u)) so[u] = __ldg(leaf_sub_off + cur[u].v.y);
+            if (!(leaf[u] & 0x80000000u)) off[u] = __ldg(leaf_sub_off + leaf[u]);
 #pragma unroll
-        for (int u = 0; u < U; ++u) {
-            if (!cur[u].ok) continue;
-            const uint4 v = cur[u].v;
-            const uint32_t k = cur[u].k;
-            sub_q[k] = v.x;
-            sub_leaf[k] = v.y;
-            sub_len[k] = v.z;           // run length, or rank in the leaf's list (its bitmap row)
-            if (v.y & 0x80000000u) {
-                sub_res[k] = v.w;
-            } else {
-                sub_res[k] = 0;
-                isub[so[u] + v.z] = k;
-            }
-        }
-#pragma unroll
-        for (int u = 0; u < U; ++u) cur[u] = nxt[u];
+        for (int u = 0; u < U; ++u)
+            if (!(leaf[u] & 0x80000000u)) isub[off[u] + row[u]] = (uint32_t)(k0 + u * stride);
     }
 }
 
-void launch_compact(cudaStream_t st, int grid_blocks, const uint4 *pad, const uint32_t *tile_cnt,
-                    const uint32_t *tile_off, const uint32_t *leaf_sub_off, uint32_t *sub_q, uint32_t *sub_leaf,
-                    uint32_t *sub_len, uint32_t *sub_res, uint32_t *isub, Caps caps, const Info *info) {
-    cand_compact_kernel<<<grid_blocks, 256, 0, st>>>(pad, tile_cnt, tile_off, leaf_sub_off, sub_q, sub_leaf,
-                                                     sub_len, sub_res, isub, caps, info);
+void launch_leaf_lists(cudaStream_t st, int grid_blocks, const uint32_t *sub_leaf, const uint32_t *sub_len,
+                       const uint32_t *leaf_sub_off, uint32_t *isub, Caps caps, const Info *info) {
+    leaf_lists_kernel<<<grid_blocks, 256, 0, st>>>(sub_leaf, sub_len, leaf_sub_off, isub, caps, info);
 }
 
 }  // namespace mqr

@@ -108,8 +108,7 @@ struct mqr_ctx {
     DevBuf<uint32_t> sub_q, sub_leaf, sub_len, sub_res, isub, bitmap, item_leaf;
     DevBuf<unsigned long long> out_off;
     // query splitting: coarse lookup table, per-query cells, (query, block) pairs
-    DevBuf<uint32_t> zmap, pair_q, pair_first, pair_blo, pair_rec, qpair, tile_p0, tile_cnt, tile_off;
-    DevBuf<uint4> cand_pad;          // padded records, 32 slots per candidate tile
+    DevBuf<uint32_t> zmap, pair_q, pair_first, pair_blo, pair_rec, qpair, tile_p0;
     DevBuf<uint2> qcells;
     DevBuf<unsigned long long> cand_off, pair_off;
     unsigned long long cand_tiles = 0;
@@ -252,7 +251,8 @@ Arena arena_layout(uint32_t nmax, uint32_t Q, unsigned long long sub_cap, unsign
     a.st_lscan = take((size_t)3 * a.lscan_tiles * sizeof(uint32_t));
     a.st_qb_p = take((size_t)a.qb_tiles * sizeof(uint32_t));
     a.st_qb_c = take((size_t)a.qb_tiles * sizeof(unsigned long long));
-    a.st_cand = take((size_t)((a.cand_tiles + kCandScanTile - 1) / kCandScanTile + 1) * sizeof(uint32_t));
+    a.st_cand = take((size_t)((a.cand_tiles + kCandChunkTiles - 1) / kCandChunkTiles + 1) *
+                     sizeof(unsigned long long));
     a.st_res = take((size_t)a.res_tiles * sizeof(unsigned long long));
     a.total = o;
     return a;
@@ -472,16 +472,17 @@ mqr_status enqueue_join(mqr_ctx *c, const mqr_ctx *ix, const float4 *rects, uint
     if (c != ix)      // a slot's per-leaf subquery counts start at zero (the index build zeroes its own)
         MQR_CUDA(cudaMemsetAsync(c->leaf_nsub.p, 0, (size_t)std::max<uint32_t>(nmax, 1) * sizeof(uint32_t), st));
     launch_candidates(st, c->num_sms * (int)c->bps_cand, cov, c->tile_p0.p, c->pair_q.p, c->pair_first.p, c->pair_blo.p,
-                      c->pair_off.p, c->qcells.p, ix->leaf_box.p, ix->leaf_beg.p, c->tile_cnt.p,
-                      c->tile_off.p, c->leaf_nsub.p, c->cand_pad.p, c->pair_rec.p,
-                      at<uint32_t>(c, a.st_cand), ctr + 8, caps, info);
-    phase_end(c, MQR_PHASE_CANDIDATES, 2);
-    // a8: group intersecting subqueries by leaf; compact the records
+                      c->pair_off.p, c->qcells.p, ix->leaf_box.p, ix->leaf_beg.p, c->leaf_nsub.p, c->pair_rec.p,
+                      c->sub_q.p, c->sub_leaf.p, c->sub_len.p, c->sub_res.p,
+                      at<unsigned long long>(c, a.st_cand), ctr + 8, caps, info);
+    phase_end(c, MQR_PHASE_CANDIDATES, 1);
+    // a8: group intersecting subqueries by leaf: the leaves' list offsets,
+    // then every intersecting record into its leaf's list
     phase_begin(c, MQR_PHASE_GROUP);
     launch_leaf_scan(st, c->num_sms, nmax, ix->leaf_beg.p, c->leaf_nsub.p, c->leaf_sub_off.p, c->leaf_word_off.p,
                      c->leaf_item_off.p, c->item_leaf.p, at<uint32_t>(c, a.st_lscan), ctr + 6, caps, info);
-    launch_compact(st, c->num_sms * (int)c->bps_compact, c->cand_pad.p, c->tile_cnt.p, c->tile_off.p, c->leaf_sub_off.p, c->sub_q.p,
-                   c->sub_leaf.p, c->sub_len.p, c->sub_res.p, c->isub.p, caps, info);
+    launch_leaf_lists(st, c->num_sms * (int)c->bps_compact, c->sub_leaf.p, c->sub_len.p, c->leaf_sub_off.p,
+                      c->isub.p, caps, info);
     phase_end(c, MQR_PHASE_GROUP, nmax ? 2 : 1);
     // a10
     if (emit_kind == kEmitAtomic) {
@@ -507,8 +508,8 @@ mqr_status enqueue_join(mqr_ctx *c, const mqr_ctx *ix, const float4 *rects, uint
     if (admit) {
         // per-query offsets, then the longest prefix of queries that fits
         phase_begin(c, MQR_PHASE_OFFSETS);
-        launch_query_offsets(st, Q, c->qpair.p, c->pair_rec.p, c->tile_off.p, c->out_off.p, offsets, caps, info);
-        launch_admit(st, Q, offsets, out ? out_cap_elems : 0, c->qpair.p, c->pair_rec.p, c->tile_off.p, caps, info);
+        launch_query_offsets(st, Q, c->qpair.p, c->pair_rec.p, c->out_off.p, offsets, caps, info);
+        launch_admit(st, Q, offsets, out ? out_cap_elems : 0, c->qpair.p, c->pair_rec.p, caps, info);
         phase_end(c, MQR_PHASE_OFFSETS, 2);
     }
     // a12 + a13
@@ -521,7 +522,7 @@ mqr_status enqueue_join(mqr_ctx *c, const mqr_ctx *ix, const float4 *rects, uint
     }
     if (offsets != nullptr && !admit) {
         phase_begin(c, MQR_PHASE_OFFSETS);
-        launch_query_offsets(st, Q, c->qpair.p, c->pair_rec.p, c->tile_off.p, c->out_off.p, offsets, caps, info);
+        launch_query_offsets(st, Q, c->qpair.p, c->pair_rec.p, c->out_off.p, offsets, caps, info);
         phase_end(c, MQR_PHASE_OFFSETS, 1);
     }
     return check_launch("tick kernels");
@@ -569,9 +570,6 @@ mqr_status ensure_tick_buffers(mqr_ctx *c, uint32_t Q) {
     c->cand_tiles = std::min<unsigned long long>(
         std::max<unsigned long long>(c->cand_tiles, std::max<unsigned long long>(1 << 16, 2ull * Q)), kMaxCandTiles);
     MQR_CUDA(c->tile_p0.ensure(c->cand_tiles));
-    MQR_CUDA(c->tile_cnt.ensure(c->cand_tiles));
-    MQR_CUDA(c->tile_off.ensure(c->cand_tiles));
-    MQR_CUDA(c->cand_pad.ensure(c->cand_tiles * 32));
     if (c->sub_q.n == 0) {
         MQR_CUDA(c->sub_q.ensure(sub0));
         MQR_CUDA(c->sub_leaf.ensure(sub0));
@@ -697,11 +695,8 @@ mqr_status attempt_check(mqr_ctx *c, uint32_t Q, int emit_kind, const Caps &caps
         if (need_tiles > kMaxCandTiles)
             return fail(MQR_ERR_INVALID_ARG, "too many candidate leaves in one tick (limit 2^32)");
         c->cand_tiles = std::min<unsigned long long>(grow_to(need_tiles), kMaxCandTiles);
-        c->tile_p0.release(); c->tile_cnt.release(); c->tile_off.release(); c->cand_pad.release();
+        c->tile_p0.release();
         MQR_CUDA(c->tile_p0.ensure(c->cand_tiles));
-        MQR_CUDA(c->tile_cnt.ensure(c->cand_tiles));
-        MQR_CUDA(c->tile_off.ensure(c->cand_tiles));
-        MQR_CUDA(c->cand_pad.ensure(c->cand_tiles * 32));
         *again = true;
     } else if (in.n_sub > caps.sub) {
         mqr_status s = grow_sub(c, in.n_sub);
@@ -1147,10 +1142,8 @@ void mqr_destroy(mqr_ctx *c) {
                                 &c->leaf_sub_off, &c->leaf_word_off, &c->leaf_item_off,
                                 &c->sub_q, &c->sub_leaf, &c->sub_len, &c->sub_res,
                                 &c->isub, &c->bitmap, &c->item_leaf, &c->up_ids, &c->zmap, &c->pair_q,
-                                &c->pair_first, &c->pair_blo, &c->pair_rec, &c->qpair, &c->tile_p0,
-                                &c->tile_cnt, &c->tile_off};
+                                &c->pair_first, &c->pair_blo, &c->pair_rec, &c->qpair, &c->tile_p0};
     for (auto *b : u32s) b->release();
-    c->cand_pad.release();
     c->qcells.release();
     c->leaf_box.release();
     c->cand_off.release();

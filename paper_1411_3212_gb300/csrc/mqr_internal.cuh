@@ -387,8 +387,9 @@ constexpr uint32_t kZCells = 1u << (2 * kZLevel);
 constexpr int kZShift = 2 * (kLevels - kZLevel);
 constexpr int kQBThreads = 256;                       // threads per block of query_blocks
 constexpr int kQBQueries = kQBThreads / 9;            // queries per block (9 block slots each)
-constexpr unsigned long long kMaxCandTiles = (1ull << 27) - 1;   // candidates and slots 32t + rank fit 32 bits
-constexpr int kCandScanTile = 2048;                   // warp tiles per block of the tile-count scan
+constexpr unsigned long long kMaxCandTiles = (1ull << 27) - 1;   // candidates and record indices fit 32 bits
+constexpr int kCandWarpTiles = 8;                     // warp tiles of one warp in one chunk of the candidate pass
+constexpr int kCandChunkTiles = 8 * kCandWarpTiles;   // warp tiles of one chunk (a block of 256 threads)
 
 void launch_zmap(cudaStream_t st, const uint32_t *leaf_hi, const Info *info, uint32_t *zmap);
 // a5 + a6: blocks, leaf ranges and candidate counts per query, scanned.
@@ -399,18 +400,20 @@ void launch_query_blocks(cudaStream_t st, const float4 *rects, uint32_t Q, float
                          uint32_t *qpair, uint32_t *tile_p0, unsigned long long tile_cap,
                          uint32_t *status_p, unsigned long long *status_c, uint32_t *tile_counter,
                          Info *info);
-// a7: candidates (warp tiles of 32) -> subquery records (query-major), the
-// first record of every pair (pair_rec[npairs+1]) and leaf_nsub.
-// The work-item kernels (candidates, compaction, filter, emit) take their
+// a7: candidates (warp tiles of 32) -> subquery records (query-major),
+// placed in one pass (chunks of tiles in ticket order, a look-back over the
+// chunks' record counts in status[]), the first record of every pair
+// (pair_rec[npairs+1]) and the per-leaf counts leaf_nsub.
+// The work-item kernels (candidates, leaf lists, filter, emit) take their
 // grid in blocks: they draw work from counters (or stride over it), so the
 // grid only sets how many blocks are resident (mqr_set_launch_config).
 constexpr int kDefaultBlocksPerSM = 8;
 void launch_candidates(cudaStream_t st, int grid_blocks, int covering, const uint32_t *tile_p0,
                        const uint32_t *pair_q, const uint32_t *pair_first, const uint32_t *pair_blo,
                        const unsigned long long *pair_off, const uint2 *qcells, const uint2 *leaf_box,
-                       const uint32_t *leaf_beg, uint32_t *tile_cnt, uint32_t *tile_off, uint32_t *leaf_nsub,
-                       uint4 *pad, uint32_t *pair_rec, uint32_t *status, uint32_t *tile_counter, Caps caps,
-                       Info *info);
+                       const uint32_t *leaf_beg, uint32_t *leaf_nsub, uint32_t *pair_rec, uint32_t *sub_q,
+                       uint32_t *sub_leaf, uint32_t *sub_len, uint32_t *sub_res, unsigned long long *status,
+                       uint32_t *chunk_counter, Caps caps, Info *info);
 
 // a8: scans over leaves -> leaf_sub_off, leaf_word_off, leaf_item_off, item_leaf.
 constexpr int kLeafScanThreads = 256, kLeafScanItems = 8, kLeafScanTile = kLeafScanThreads * kLeafScanItems;
@@ -419,10 +422,9 @@ void launch_leaf_scan(cudaStream_t st, int num_sms, uint32_t nmax, const uint32_
                       uint32_t *leaf_item_off, uint32_t *item_leaf,
                       uint32_t *status3, uint32_t *tile_counter, Caps caps, Info *info);
 
-// a7/a8 compaction of the padded records; intersecting ones into their leaf's list.
-void launch_compact(cudaStream_t st, int grid_blocks, const uint4 *pad, const uint32_t *tile_cnt,
-                    const uint32_t *tile_off, const uint32_t *leaf_sub_off, uint32_t *sub_q, uint32_t *sub_leaf,
-                    uint32_t *sub_len, uint32_t *sub_res, uint32_t *isub, Caps caps, const Info *info);
+// a8: the intersecting records into their leaves' lists (isub).
+void launch_leaf_lists(cudaStream_t st, int grid_blocks, const uint32_t *sub_leaf, const uint32_t *sub_len,
+                       const uint32_t *leaf_sub_off, uint32_t *isub, Caps caps, const Info *info);
 
 // a10: filtering into bitmap words + per-subquery counts.
 void launch_filter(cudaStream_t st, int grid_blocks, const float4 *rects, const float2 *sxy,
@@ -466,13 +468,12 @@ cudaError_t launch_cost_predict(cudaStream_t st, const float *params, const floa
 
 // Admission by output memory: queries [0, A) whose output fits cap elements.
 void launch_admit(cudaStream_t st, uint32_t Q, const unsigned long long *offsets, unsigned long long cap,
-                  const uint32_t *qpair, const uint32_t *pair_rec, const uint32_t *tile_off, Caps caps,
-                  Info *info);
+                  const uint32_t *qpair, const uint32_t *pair_rec, Caps caps, Info *info);
 
 // Per-query offsets: off[q] = out_off[pair_rec[qpair[q]]].
 void launch_query_offsets(cudaStream_t st, uint32_t Q, const uint32_t *qpair, const uint32_t *pair_rec,
-                          const uint32_t *tile_off, const unsigned long long *out_off,
-                          unsigned long long *offsets, Caps caps, const Info *info);
+                          const unsigned long long *out_off, unsigned long long *offsets, Caps caps,
+                          const Info *info);
 
 // (qidx << 32 | id) keys -> pairs (qidx, id) or ids.
 void launch_keys_to_output(cudaStream_t st, const unsigned long long *keys, uint64_t n,
