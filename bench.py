@@ -553,11 +553,14 @@ def run_gpu(args, name):
 
     # end to end through the host-buffer entry points; the optional legs
     # record their failure in the line instead of losing it
-    e2e = e2e_runs = None
+    e2e = e2e_runs = e2e_csr = None
     if not args.no_e2e:
         e2e = guarded("e2e", run_e2e, args, idx, ticks, kind, elem, Q, dev)
         if kind == mqr.MQR_OUT_PAIRS:
-            # the same ticks with covering runs reported compressed (RUNS kind)
+            # the same ticks and answers as per-query id lists (CSR: 4-byte ids
+            # and Q + 1 offsets), and with covering runs reported compressed
+            # (RUNS kind)
+            e2e_csr = guarded("e2e_csr", run_e2e, args, idx, ticks, mqr.MQR_OUT_CSR, 4, Q, dev)
             e2e_runs = guarded("e2e_covering_compressed", run_e2e, args, idx, ticks, mqr.MQR_OUT_RUNS, 8, Q, dev)
 
     cpu = None
@@ -587,6 +590,7 @@ def run_gpu(args, name):
         "roofline": roofline,
         "cpu_baseline": cpu,
         "e2e": e2e,
+        "e2e_csr": e2e_csr,
         "e2e_covering_compressed": e2e_runs,
         "gpu_launches": gpu_launches,
         "launches_between_steps": "per step, after its end event: the L2 flush and the two footprint-statistics "
@@ -694,7 +698,8 @@ def run_e2e(args, idx, ticks, kind, elem, Q, dev):
     from the exact output size of every replayed tick (an untimed counting
     tick each); a tick that still does not fit grows them and is answered
     again.  For the covering-compressed kind the step also copies the tick's
-    sorted ids (what a consumer needs to expand the runs)."""
+    sorted ids (what a consumer needs to expand the runs); for CSR, the
+    per-query offsets."""
     import torch
     from paper_1411_3212_gb300 import mqr
     n = ticks[0].ids.shape[0]
@@ -706,11 +711,13 @@ def run_e2e(args, idx, ticks, kind, elem, Q, dev):
     xy_h = {i: torch.from_numpy(ticks[i].xy).pin_memory().numpy() for i in set(order)}
     rect_h = {i: torch.from_numpy(ticks[i].rects).pin_memory().numpy() for i in set(order)}
     ids_d = torch.from_numpy(ticks[0].ids.view(np.int32)).to(dev)
+    csr = kind == mqr.MQR_OUT_CSR
+    offs_d = torch.empty(Q + 1, dtype=torch.int64, device=dev) if csr else None
     # exact output size of every replayed tick (a zero-capacity tick reports it)
     need, i_max = -1, order[0]
     for i in sorted(set(order)):
         idx.apply_updates(ids_d, torch.from_numpy(ticks[i].xy).to(dev))
-        st, cnt = mqr.mqr_tick(idx.ctx, torch.from_numpy(ticks[i].rects).to(dev), Q, kind, None, 0, None)
+        st, cnt = mqr.mqr_tick(idx.ctx, torch.from_numpy(ticks[i].rects).to(dev), Q, kind, None, 0, offs_d)
         if st not in (mqr.MQR_OK, mqr.MQR_ERR_CAPACITY):
             mqr._check(st)
         if cnt > need:
@@ -721,11 +728,12 @@ def run_e2e(args, idx, ticks, kind, elem, Q, dev):
         return [torch.empty(elems * elem // 4, dtype=torch.int32).pin_memory().numpy() for _ in range(2)]
 
     out_hs = alloc(cap_elems)
+    off_hs = [torch.empty(Q + 1, dtype=torch.int64).pin_memory().numpy() if csr else None for _ in range(2)]
     # warm both device staging buffers of the asynchronous path on the
     # largest replayed tick, so that no timed tick grows them
-    for oh in out_hs:
+    for oh, ofh in zip(out_hs, off_hs):
         mqr.mqr_apply_updates_host(idx.ctx, ids_h, xy_h[i_max])
-        mqr._check(mqr.mqr_tick_host_async(idx.ctx, rect_h[i_max], Q, kind, oh, oh.nbytes)[0])
+        mqr._check(mqr.mqr_tick_host_async(idx.ctx, rect_h[i_max], Q, kind, oh, oh.nbytes, ofh)[0])
     mqr.mqr_host_wait(idx.ctx)
     d2h, regrown, t_calls = [], 0, []
     runs = kind == mqr.MQR_OUT_RUNS
@@ -733,18 +741,18 @@ def run_e2e(args, idx, ticks, kind, elem, Q, dev):
     for k, i in enumerate(order):
         t_calls.append(time.perf_counter())
         mqr.mqr_apply_updates_host(idx.ctx, ids_h, xy_h[i])
-        oh = out_hs[k & 1]
-        st, cnt = mqr.mqr_tick_host_async(idx.ctx, rect_h[i], Q, kind, oh, oh.nbytes, check=False)
+        oh, ofh = out_hs[k & 1], off_hs[k & 1]
+        st, cnt = mqr.mqr_tick_host_async(idx.ctx, rect_h[i], Q, kind, oh, oh.nbytes, ofh, check=False)
         if st == mqr.MQR_ERR_CAPACITY:      # not expected: every replayed tick was counted above
             mqr.mqr_host_wait(idx.ctx)
             cap_elems = int(cnt * 1.1) + 4096
             out_hs = alloc(cap_elems)
             oh = out_hs[k & 1]
             regrown += 1
-            st, cnt = mqr.mqr_tick_host_async(idx.ctx, rect_h[i], Q, kind, oh, oh.nbytes, check=False)
+            st, cnt = mqr.mqr_tick_host_async(idx.ctx, rect_h[i], Q, kind, oh, oh.nbytes, ofh, check=False)
         mqr._check(st)
         ns = mqr.mqr_get_sorted_async(idx.ctx, sid_h) if runs else 0
-        d2h.append(cnt * elem + ns * 4)
+        d2h.append(cnt * elem + ns * 4 + (8 * (Q + 1) if csr else 0))
     mqr.mqr_host_wait(idx.ctx)
     total = time.perf_counter() - t_all
     t_calls.append(t_all + total)
@@ -755,7 +763,8 @@ def run_e2e(args, idx, ticks, kind, elem, Q, dev):
             "d2h_GB_per_s": sum(d2h) / total / 1e9,
             "host_ms_per_step": {"min": min(gaps), "median": statistics.median(gaps), "max": max(gaps)},
             "api": "mqr_apply_updates_host + mqr_tick_host_async%s, mqr_host_wait at the end (pinned host "
-                   "buffers; each tick's copy overlaps the next tick)" % (" + mqr_get_sorted_async" if runs else "")}
+                   "buffers; each tick's copy overlaps the next tick)" %
+                   (" + mqr_get_sorted_async" if runs else " with the per-query offsets" if csr else "")}
 
 
 def run_served(args):

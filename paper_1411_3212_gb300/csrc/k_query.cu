@@ -80,7 +80,8 @@ __device__ __forceinline__ void leaves_at_or_after2(uint32_t z1, uint32_t z2, co
 // Query splitting works on aligned blocks of side 2^k cells, k the smallest
 // value with 2^(k+1) >= the query's larger extent, so that a query meets at
 // most 3 x 3 blocks.  The leaves meeting one block are a contiguous range of
-// the leaf table (leaves and blocks are both aligned quadtree quadrants).
+// the leaf table (leaves and blocks are both aligned quadtree quadrants), and
+// so are those meeting the query's part of the block.
 __device__ __forceinline__ uint32_t block_log2(uint32_t i0, uint32_t i1, uint32_t j0, uint32_t j1) {
     const uint32_t e = max(i1 - i0, j1 - j0) + 1u;
     return e <= 1u ? 0u : 31u - __clz(e - 1u);       // = ceil(log2 e) - 1
@@ -156,12 +157,17 @@ query_blocks_kernel(const float4 *__restrict__ rects, uint32_t Q, float x0, floa
         if (slot == 0) qcells[q] = make_uint2(c.i0 | (c.i1 << 16), c.j0 | (c.j1 << 16));
         if (bi <= (c.i1 >> k) && bj <= (c.j1 >> k)) {
             blk = (bi << k) | ((bj << k) << 16);
-            const uint32_t blo = morton2(bi << k, bj << k);
-            const uint32_t bhi = blo + ((1u << (2 * k)) - 1u);
+            // the leaves meeting the query inside this block lie in the Morton
+            // interval of the query's part of the block (an axis-aligned cell
+            // rectangle's codes lie between those of its lower-left and
+            // upper-right cells), a sub-interval of the block's
+            const uint32_t side = (1u << k) - 1u;
+            const uint32_t zlo = morton2(max(c.i0, bi << k), max(c.j0, bj << k));
+            const uint32_t zhi = morton2(min(c.i1, (bi << k) + side), min(c.j1, (bj << k) + side));
             uint32_t g;
-            leaves_at_or_after2(blo, bhi, leaf_hi, zmap, f, g);
-            if (f < L && __ldg(leaf_lo + f) <= bhi) {
-                const uint32_t last = (g < L && __ldg(leaf_lo + g) <= bhi) ? g : g - 1u;
+            leaves_at_or_after2(zlo, zhi, leaf_hi, zmap, f, g);
+            if (f < L && __ldg(leaf_lo + f) <= zhi) {
+                const uint32_t last = (g < L && __ldg(leaf_lo + g) <= zhi) ? g : g - 1u;
                 cnt = last - f + 1u;
             }
         }
