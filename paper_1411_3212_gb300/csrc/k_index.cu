@@ -429,7 +429,9 @@ leaves_kernel(const uint32_t *__restrict__ K, uint32_t cap, int uniform_grid, ui
               const uint8_t *__restrict__ Mk_global, uint32_t *status,
               uint32_t *tile_counter, uint32_t *__restrict__ leaf_lo, uint32_t *__restrict__ leaf_hi,
               uint32_t *__restrict__ leaf_beg, uint32_t *__restrict__ leaf_nsub, uint2 *__restrict__ leaf_box,
-              Info *info) {
+              uint32_t tstride, Info *info) {
+    // two window tables of tstride bytes each (kLeafTile + the largest
+    // capacity in use + 1) in dynamic shared memory
     extern __shared__ uint8_t dsm[];
     __shared__ uint8_t s_L[kLeafTile + 1];
     __shared__ uint32_t s_scan[kLeafThreads / 32 + 1];
@@ -477,7 +479,7 @@ leaves_kernel(const uint32_t *__restrict__ K, uint32_t cap, int uniform_grid, ui
                 while ((2ull << rk) <= (unsigned long long)rc + 1) ++rk;   // floor(log2(rc+1))
                 const long rs = a - (long)rc;         // the window of position a starts here
                 const int S = (int)(b - rs);
-                uint8_t *A = dsm, *B = dsm + (kLeafTile + kLeafCapSmem + 1);
+                uint8_t *A = dsm, *B = dsm + tstride;
                 for (int j = tid; j < S; j += kLeafThreads) A[j] = window_enc(K, rs + j, rc, N);
                 __syncthreads();
                 for (int st = 0; st < rk; ++st) {
@@ -504,7 +506,7 @@ leaves_kernel(const uint32_t *__restrict__ K, uint32_t cap, int uniform_grid, ui
         // Shared-memory sparse table over positions [rs, tend), rs = t0-cap-1.
         const long rs = t0 - (long)cap - 1;
         const int S = (int)(tend - rs);
-        uint8_t *A = dsm, *B = dsm + (kLeafTile + kLeafCapSmem + 1);
+        uint8_t *A = dsm, *B = dsm + tstride;
         for (int j = tid; j < S; j += kLeafThreads) A[j] = window_enc(K, rs + j, cap, N);
         __syncthreads();
         for (int s = 0; s < kexp; ++s) {
@@ -630,11 +632,14 @@ void launch_build_leaves(cudaStream_t st, const uint32_t *skey, uint32_t nmax, u
     while ((2ull << kexp) <= (unsigned long long)cap + 1) ++kexp;   // floor(log2(cap+1))
     const uint8_t *mk = nullptr;
     size_t dyn = 0;
+    uint32_t tstride = 0;
     if (region_bits) {
-        dyn = 2 * (size_t)(kLeafTile + kLeafCapSmem + 1);        // every region capacity <= kLeafCapSmem
+        tstride = kLeafTile + kLeafCapSmem + 1;                   // every region capacity <= kLeafCapSmem
+        dyn = 2 * (size_t)tstride;
     } else if (!uniform_grid && cap < nmax) {
         if (cap <= (uint32_t)kLeafCapSmem) {
-            dyn = 2 * (size_t)(kLeafTile + kLeafCapSmem + 1);
+            tstride = (kLeafTile + cap + 1 + 15) / 16 * 16;       // the window table of this capacity
+            dyn = 2 * (size_t)tstride;
         } else {
             uint32_t size = nmax + cap + 1;   // cap < nmax: fits the 2*nmax+2 buffers
             window_enc_kernel<<<1024, 256, 0, st>>>(skey, cap, size, info, mk_a);
@@ -649,7 +654,7 @@ void launch_build_leaves(cudaStream_t st, const uint32_t *skey, uint32_t nmax, u
     leaves_kernel<<<tiles, kLeafThreads, dyn, st>>>(skey, cap, uniform_grid, grid_level, min_level, region_bits,
                                                     region_cap, kexp, mk,
                                                     status, tile_counter, leaf_lo, leaf_hi, leaf_beg,
-                                                    leaf_nsub, leaf_box, info);
+                                                    leaf_nsub, leaf_box, tstride, info);
 }
 
 }  // namespace mqr

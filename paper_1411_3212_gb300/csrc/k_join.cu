@@ -169,13 +169,30 @@ result_scan_kernel(const uint32_t *__restrict__ sub_res, const uint32_t *__restr
         return;
     }
     const uint32_t kb = base + tid * kResItems;
+    const bool whole = kb + kResItems <= nsub;      // the thread's records are all present: vector loads
+    uint32_t rr[kResItems], ll[kResItems];
+    if (whole) {
+        static_assert(kResItems == 8, "two 16-byte loads per array");
+        const uint4 r0 = __ldg(reinterpret_cast<const uint4 *>(sub_res + kb));
+        const uint4 r1 = __ldg(reinterpret_cast<const uint4 *>(sub_res + kb) + 1);
+        const uint4 l0 = __ldg(reinterpret_cast<const uint4 *>(sub_leaf + kb));
+        const uint4 l1 = __ldg(reinterpret_cast<const uint4 *>(sub_leaf + kb) + 1);
+        rr[0] = r0.x; rr[1] = r0.y; rr[2] = r0.z; rr[3] = r0.w; rr[4] = r1.x; rr[5] = r1.y; rr[6] = r1.z; rr[7] = r1.w;
+        ll[0] = l0.x; ll[1] = l0.y; ll[2] = l0.z; ll[3] = l0.w; ll[4] = l1.x; ll[5] = l1.y; ll[6] = l1.z; ll[7] = l1.w;
+    } else {
+#pragma unroll
+        for (int e = 0; e < kResItems; ++e) {
+            const uint32_t k = kb + e;
+            rr[e] = k < nsub ? sub_res[k] : 0u;
+            ll[e] = k < nsub ? sub_leaf[k] : 0u;
+        }
+    }
     uint32_t v[kResItems];
     unsigned long long t = 0, cov = 0, res = 0;
 #pragma unroll
     for (int e = 0; e < kResItems; ++e) {
-        const uint32_t k = kb + e;
-        const uint32_t r = k < nsub ? sub_res[k] : 0u;
-        const bool c = k < nsub && (sub_leaf[k] & 0x80000000u);
+        const uint32_t r = rr[e];
+        const bool c = (ll[e] & 0x80000000u) != 0u;
         v[e] = (c && run_elems) ? run_elems : r;
         t += v[e];
         res += r;
@@ -198,11 +215,22 @@ result_scan_kernel(const uint32_t *__restrict__ sub_res, const uint32_t *__restr
     }
     __syncthreads();
     off += s_prefix;
+    if (whole) {
+        ulonglong2 *o2 = reinterpret_cast<ulonglong2 *>(out_off + kb);     // kb is a multiple of 8
 #pragma unroll
-    for (int e = 0; e < kResItems; ++e) {
-        uint32_t k = kb + e;
-        if (k < nsub) out_off[k] = off;
-        off += v[e];
+        for (int e = 0; e < kResItems; e += 2) {
+            const unsigned long long a0 = off;
+            off += v[e];
+            o2[e / 2] = make_ulonglong2(a0, off);
+            off += v[e + 1];
+        }
+    } else {
+#pragma unroll
+        for (int e = 0; e < kResItems; ++e) {
+            uint32_t k = kb + e;
+            if (k < nsub) out_off[k] = off;
+            off += v[e];
+        }
     }
     if (tid == 0) {
         if (s_cov) atomicAdd(&info->n_results_cov, s_cov);
