@@ -410,7 +410,17 @@ __device__ __forceinline__ uint32_t emit_words(void *out, unsigned long long off
 // the per-record bookkeeping is paid once per 32 words instead of once per
 // record, and only the ids of set bits are loaded.
 constexpr uint32_t kUnitMaxWords = 8;
-constexpr int kUnitUnroll = 2;            // units whose id loads are issued together
+
+// An 8-byte shared-memory load kept where it is written (not merged with
+// another load of the same slot), so that a unit's descriptor is read again
+// where it is used instead of being held in registers.
+__device__ __forceinline__ uint2 ld_shared_v2(const uint32_t *p) {
+    uint2 v;
+    const unsigned a = (unsigned)__cvta_generic_to_shared(p);
+    asm volatile("ld.shared.v2.u32 {%0, %1}, [%2];" : "=r"(v.x), "=r"(v.y) : "r"(a) : "memory");
+    return v;
+}
+constexpr int kUnitUnroll = 4;            // units whose id loads are issued together
 
 // One warp per batch of 32 consecutive subquery records (query-major order,
 // so the output is written front to back): lane j loads the metadata of
@@ -429,7 +439,8 @@ emit_kernel(const uint32_t *__restrict__ sub_q, const uint32_t *__restrict__ sub
     __shared__ unsigned long long s_off[kEmitWarps][32];
     // per unit of the batch: record (low 5 bits) and word of the record (high 3 bits)
     __shared__ uint8_t s_map[kEmitWarps][32 * kUnitMaxWords];
-    // per unit of a round: {word, first object of the word, q} and the address of its first output element
+    // per unit of a round: {first object of the word, word, word, q} (the id loads read the first
+    // pair, the stores the second) and the address of its first output element
     __shared__ uint4 s_unit[kEmitWarps][32];
     __shared__ unsigned long long s_uptr[kEmitWarps][32];
     if (!tick_buffers_ok(info, caps)) return;
@@ -484,7 +495,7 @@ emit_kernel(const uint32_t *__restrict__ sub_q, const uint32_t *__restrict__ sub
                 const uint4 rec = s_rec[wib][r];
                 const uint32_t wi = m >> 5;
                 w = __ldg(bitmap + rec.y + wi);
-                unit = make_uint4(w, rec.z + 32u * wi, rec.x, 0u);
+                unit = make_uint4(rec.z + 32u * wi, w, w, rec.x);
             }
             // segmented inclusive scan of the popcounts over units of one record
             // (a record's units are consecutive): key r in the high half
@@ -504,16 +515,17 @@ emit_kernel(const uint32_t *__restrict__ sub_q, const uint32_t *__restrict__ sub
             const uint32_t nun = min(32u, nunits - u0);
             for (uint32_t t0 = 0; t0 < nun; t0 += kUnitUnroll) {
                 uint32_t id[kUnitUnroll];
-                uint4 ut[kUnitUnroll];
 #pragma unroll
                 for (int t = 0; t < kUnitUnroll; ++t) {      // slots past nun hold empty words
-                    ut[t] = s_unit[wib][(t0 + t) & 31u];
-                    if (ut[t].x & (1u << lane)) id[t] = __ldg(sid + ut[t].y + lane);
+                    const uint2 yw = ld_shared_v2(&s_unit[wib][(t0 + t) & 31u].x);
+                    if (yw.y & (1u << lane)) id[t] = __ldg(sid + yw.x + lane);
                 }
 #pragma unroll
-                for (int t = 0; t < kUnitUnroll; ++t)
-                    if (ut[t].x & (1u << lane))
-                        emit_at<KIND>(s_uptr[wib][(t0 + t) & 31u], __popc(ut[t].x & lt), ut[t].z, id[t], out, wpr);
+                for (int t = 0; t < kUnitUnroll; ++t) {
+                    const uint2 wq = ld_shared_v2(&s_unit[wib][(t0 + t) & 31u].z);
+                    if (wq.x & (1u << lane))
+                        emit_at<KIND>(s_uptr[wib][(t0 + t) & 31u], __popc(wq.x & lt), wq.y, id[t], out, wpr);
+                }
             }
             __syncwarp();
         }
