@@ -187,7 +187,6 @@ onesweep_kernel(const unsigned long long *__restrict__ in, unsigned long long *_
     constexpr int W = kSortThreads / 32;
     __shared__ unsigned long long s_keys[kSortTile];
     __shared__ uint16_t s_whist[W][256];   // per-warp digit counts (<= 32 * kSortItems)
-    __shared__ uint32_t s_dstart[256];
     __shared__ uint32_t s_gbase[256];
     __shared__ uint32_t s_scan[W + 1];
     __shared__ uint32_t s_tile;
@@ -241,7 +240,12 @@ onesweep_kernel(const unsigned long long *__restrict__ in, unsigned long long *_
     }
     uint32_t tot;
     uint32_t dstart = block_excl_scan<kSortThreads>(c, &tot, s_scan);
-    if (tid < 256) s_dstart[tid] = dstart;
+    // each warp's slot for its first key of digit tid: the digit's start in
+    // the tile plus the warp's exclusive count (one table read per key below)
+    if (tid < 256) {
+#pragma unroll 1
+        for (int w = 0; w < W; ++w) s_whist[w][tid] = (uint16_t)(s_whist[w][tid] + dstart);
+    }
     if (PRE) {
         // output start of this tile's keys of digit tid, from the tile-histogram scan
         if (tid < 256) s_gbase[tid] = tile_offs[(size_t)tid * num_tiles + tile] - dstart;
@@ -259,7 +263,7 @@ onesweep_kernel(const unsigned long long *__restrict__ in, unsigned long long *_
         uint32_t idx = wbase + it * 32 + lane;
         if (idx < n) {
             uint32_t dg = (uint32_t)(k[it] >> shift) & 255u;
-            s_keys[s_dstart[dg] + s_whist[warp][dg] + r[it]] = k[it];
+            s_keys[s_whist[warp][dg] + r[it]] = k[it];
         }
     }
     __syncthreads();
