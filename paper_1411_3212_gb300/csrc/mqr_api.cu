@@ -225,7 +225,7 @@ namespace {
 
 // Arena layout for one tick.
 struct Arena {
-    size_t info, hist, counters, st_leaf, st_lscan, st_qb_p, st_qb_c, st_cand, st_res, total;
+    size_t info, hist, counters, st_sort, st_leaf, st_lscan, st_qb_p, st_qb_c, st_cand, st_res, total;
     uint32_t sort_tiles, leaf_tiles, lscan_tiles, qb_tiles, res_tiles;
     unsigned long long cand_tiles;
 };
@@ -247,6 +247,9 @@ Arena arena_layout(uint32_t nmax, uint32_t Q, unsigned long long sub_cap, unsign
     a.info = take(sizeof(Info));
     a.hist = take(8 * 256 * sizeof(uint32_t));
     a.counters = take(16 * sizeof(uint32_t));
+    // look-back status of the object sort's four passes, when it runs them
+    // with look-back (a few tiles: see enqueue_index)
+    a.st_sort = take(a.sort_tiles <= kSortLookbackTiles ? (size_t)4 * 256 * a.sort_tiles * sizeof(uint32_t) : 0);
     a.st_leaf = take((size_t)a.leaf_tiles * sizeof(uint32_t));
     a.st_lscan = take((size_t)3 * a.lscan_tiles * sizeof(uint32_t));
     a.st_qb_p = take((size_t)a.qb_tiles * sizeof(uint32_t));
@@ -402,13 +405,24 @@ mqr_status enqueue_index(mqr_ctx *c, const Arena &a) {
     phase_end(c, MQR_PHASE_KEYS, nmax ? 1 : 0);
     unsigned long long *src = c->keysA.p, *dst = c->keysB.p;
     phase_begin(c, MQR_PHASE_SORT);
+    // A few tiles: each pass's tiles look back over one another (one launch
+    // per pass; the walk is short); more: the look-back-free passes (tile
+    // counts, digit scan, rank and scatter), whose tiles need not wait.
+    const bool sort_lookback = a.sort_tiles <= kSortLookbackTiles;
+    uint32_t *st_sort = at<uint32_t>(c, a.st_sort);
     for (int p = 0; p < 4; ++p) {
         const bool fin = p == 3;
-        launch_sort_pass_pre(st, src, dst, nmax, 32 + 8 * p, hist + 256 * p, c->sort_counts.p, c->sort_offs.p,
-                             err, fin, c->pos.p, c->skey.p, c->sid.p, c->sxy.p, p == 0);
+        if (sort_lookback)
+            launch_onesweep_pass(st, src, dst, nmax, 32 + 8 * p, hist + 256 * p,
+                                 st_sort + (size_t)256 * a.sort_tiles * p, ctr + p, err, fin, c->pos.p, c->skey.p,
+                                 c->sid.p, c->sxy.p);
+        else
+            launch_sort_pass_pre(st, src, dst, nmax, 32 + 8 * p, hist + 256 * p, c->sort_counts.p,
+                                 c->sort_offs.p, err, fin, c->pos.p, c->skey.p, c->sid.p, c->sxy.p, p == 0);
         std::swap(src, dst);
     }
-    phase_end(c, MQR_PHASE_SORT, nmax ? 11 : 0);     // the first pass's tile counts come from the key kernel
+    // the look-back-free passes: the first pass's tile counts come from the key kernel
+    phase_end(c, MQR_PHASE_SORT, nmax ? (sort_lookback ? 4 : 11) : 0);
     // a4
     phase_begin(c, MQR_PHASE_LEAVES);
     const uint32_t cap = c->cfg.leaf_cap;
