@@ -223,6 +223,9 @@ struct mqr_ctx {
 
 namespace {
 
+// The object sort runs its passes with look-back up to this many tiles.
+constexpr uint32_t kSortLookbackTiles = 16;
+
 // Arena layout for one tick.
 struct Arena {
     size_t info, hist, counters, st_sort, st_leaf, st_lscan, st_qb_p, st_qb_c, st_cand, st_res, total;

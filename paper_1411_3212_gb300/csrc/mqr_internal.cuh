@@ -340,7 +340,6 @@ void launch_morton_keys(cudaStream_t st, const float2 *pos, const unsigned long 
 // a3: one onesweep pass over n u64 keys, 8-bit digit at `shift`.  The final
 // pass of the object sort (`final_obj`) writes skey/sid/sxy instead of `out`.
 constexpr int kSortThreads = 512, kSortItems = 8, kSortTile = kSortThreads * kSortItems;
-constexpr uint32_t kSortLookbackTiles = 16;   // the object sort runs its passes with look-back up to this many tiles
 void launch_onesweep_pass(cudaStream_t st, const unsigned long long *in, unsigned long long *out,
                           uint32_t n, int shift, const uint32_t *hist256, uint32_t *status,
                           uint32_t *tile_counter, unsigned long long *err, bool final_obj,
