@@ -59,8 +59,11 @@ def test_uniform_16k_bitmap_and_sorted_lists(mqr):
 # Morton keys + radix sort (Alg. 1 GPUcalculateMortonHash / GPUradixSort) and
 # the leaf table (Alg. 1), exact against the oracle.
 # ---------------------------------------------------------------------------
+# (65_499 and 65_500 objects + 37 absent slots: 16 and 17 sort tiles of 4,096,
+# the largest sort run with look-back passes and the smallest without)
 @pytest.mark.parametrize("n,cap,seed", [(16384, 64, 0), (50_001, 128, 1), (5000, 1, 2), (70_000, 2, 3),
-                                        (3000, 5000, 4), (120_000, 20_000, 5)])
+                                        (3000, 5000, 4), (120_000, 20_000, 5), (65_499, 128, 6),
+                                        (65_500, 128, 7)])
 def test_sorted_keys_and_leaves(mqr, n, cap, seed):
     torch, dev = torch_dev()
     w = workloads.HotspotWalk(n=n, q=10, hotspots=8, seed=seed)
